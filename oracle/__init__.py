@@ -1,0 +1,284 @@
+"""TEST INFRASTRUCTURE ONLY: ctypes wrapper around the plain CPU oracle (msc_oracle.cpp).
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline legs may import
+this package. It shares no code with the CUDA library and never loads it.
+
+Arrays follow the library's conventions: a field is float32 [nz, ny, nx]; dims are
+(nx, ny, nz); cells are ids on the refined grid (2nx-1)x(2ny-1)x(2nz-1).
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "msc_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libmsc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NONE = 0xFFFFFFFF
+STATUS = {0: "ok", 1: "bad argument", 2: "NaN in field", 4: "grid too large for 32-bit cell ids",
+          6: "path count overflows uint64", 9: "internal error"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"oracle {what}: status {status} ({STATUS.get(status, '?')})")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C++ compiler (plain -O2, no target-specific flags)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_SIGNATURES = {
+    "ora_version": ([], ctypes.c_int),
+    "ora_gradient": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "ora_packed_at": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ora_pack": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "ora_critical_counts": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "ora_critical_list": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "ora_extremum_labels": ([ctypes.c_void_p] * 4, ctypes.c_int),
+    "ora_min_arcs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ora_max_arcs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ora_reachable": ([ctypes.c_void_p] * 3, ctypes.c_int64),
+    "ora_junctions": ([ctypes.c_void_p] * 4, ctypes.c_int64),
+    "ora_minor": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                   ctypes.c_int64, ctypes.c_void_p], ctypes.c_void_p),
+    "ora_minor_status": ([ctypes.c_void_p], ctypes.c_int),
+    "ora_minor_size": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int64),
+    "ora_minor_copy": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], None),
+    "ora_minor_free": ([ctypes.c_void_p], None),
+    "ora_path_counts": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_void_p),
+    "ora_result_status": ([ctypes.c_void_p], ctypes.c_int),
+    "ora_result_size": ([ctypes.c_void_p], ctypes.c_int64),
+    "ora_result_copy": ([ctypes.c_void_p] * 4, None),
+    "ora_result_free": ([ctypes.c_void_p], None),
+    "ora_n_iter": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
+                   ctypes.c_int64),
+}
+
+
+def _bind(path: str):
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(build())
+        return _lib
+
+
+@contextlib.contextmanager
+def swap_library(path: str):
+    """Run the wrappers against another build of the oracle (used to test that pins fail on
+    deliberately broken copies of the source)."""
+    global _lib
+    old = _load()
+    _lib = _bind(path)
+    try:
+        yield
+    finally:
+        _lib = old
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dims(f_or_dims):
+    if isinstance(f_or_dims, np.ndarray) and f_or_dims.ndim == 3:
+        nz, ny, nx = f_or_dims.shape
+        return np.array([nx, ny, nz], dtype=np.int64)
+    return np.asarray(f_or_dims, dtype=np.int64).reshape(3)
+
+
+def refined_shape(dims):
+    nx, ny, nz = (int(v) for v in dims)
+    return (2 * nz - 1, 2 * ny - 1, 2 * nx - 1)
+
+
+def gradient(f: np.ndarray) -> np.ndarray:
+    """Partner cell id per cell (0xFFFFFFFF = critical), flat over the refined grid."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    d = _dims(f)
+    n = int(np.prod(refined_shape(d)))
+    pair = np.empty(n, dtype=np.uint32)
+    st = _load().ora_gradient(_p(d), _p(f), _p(pair))
+    if st:
+        raise OracleError(st, "gradient")
+    return pair
+
+
+def packed_at(f: np.ndarray, verts) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    d = _dims(f)
+    verts = np.ascontiguousarray(verts, dtype=np.int64)
+    out = np.empty(len(verts), dtype=np.uint32)
+    st = _load().ora_packed_at(_p(d), _p(f), len(verts), _p(verts), _p(out))
+    if st:
+        raise OracleError(st, "packed_at")
+    return out
+
+
+def pack(dims, pair) -> np.ndarray:
+    d = _dims(dims)
+    nx, ny, nz = (int(v) for v in d)
+    out = np.empty((nz, ny, nx), dtype=np.uint32)
+    st = _load().ora_pack(_p(d), _p(pair), _p(out))
+    if st:
+        raise OracleError(st, "pack")
+    return out
+
+
+def critical(dims, pair):
+    d = _dims(dims)
+    lib = _load()
+    counts = np.zeros(4, dtype=np.int64)
+    lib.ora_critical_counts(_p(d), _p(pair), _p(counts))
+    lists = []
+    for k in range(4):
+        out = np.empty(int(counts[k]), dtype=np.uint32)
+        if counts[k]:
+            lib.ora_critical_list(_p(d), _p(pair), k, _p(out))
+        lists.append(out)
+    return counts, lists
+
+
+def extremum(dims, pair, s1, s2):
+    d = _dims(dims)
+    nx, ny, nz = (int(v) for v in d)
+    lib = _load()
+    vmin = np.empty((nz, ny, nx), dtype=np.uint32)
+    cmax = np.empty((nz, ny, nx), dtype=np.uint32)
+    st = lib.ora_extremum_labels(_p(d), _p(pair), _p(vmin), _p(cmax))
+    if st:
+        raise OracleError(st, "extremum_labels")
+    s1 = np.ascontiguousarray(s1, dtype=np.uint32)
+    s2 = np.ascontiguousarray(s2, dtype=np.uint32)
+    amin = np.empty(2 * len(s1), dtype=np.uint32)
+    amax = np.empty(2 * len(s2), dtype=np.uint32)
+    lib.ora_min_arcs(_p(d), _p(vmin), len(s1), _p(s1), _p(amin))
+    lib.ora_max_arcs(_p(d), _p(cmax), len(s2), _p(s2), _p(amax))
+    return vmin, cmax, amin, amax
+
+
+def reachable(dims, pair):
+    d = _dims(dims)
+    nx, ny, nz = (int(v) for v in d)
+    vis = np.empty((nz, ny, nx), dtype=np.uint8)
+    levels = _load().ora_reachable(_p(d), _p(pair), _p(vis))
+    if levels < 0:
+        raise OracleError(int(-levels), "reachable")
+    return vis, int(levels)
+
+
+def junctions(dims, pair, visited):
+    d = _dims(dims)
+    lib = _load()
+    n = lib.ora_junctions(_p(d), _p(pair), _p(visited), None)
+    out = np.empty(n, dtype=np.uint32)
+    if n:
+        lib.ora_junctions(_p(d), _p(pair), _p(visited), _p(out))
+    return out
+
+
+MINOR_NAMES = ("A", "B", "Bstar", "D")
+
+
+def minor(dims, pair, s1, junc, s2):
+    """COO (rows, cols, multiplicity) of A (1s x j), B (j x j), B* (j x 2s), D (1s x 2s)."""
+    d = _dims(dims)
+    lib = _load()
+    s1 = np.ascontiguousarray(s1, dtype=np.uint32)
+    junc = np.ascontiguousarray(junc, dtype=np.uint32)
+    s2 = np.ascontiguousarray(s2, dtype=np.uint32)
+    h = lib.ora_minor(_p(d), _p(pair), len(s1), _p(s1), len(junc), _p(junc), len(s2), _p(s2))
+    out = {}
+    try:
+        st = lib.ora_minor_status(h)
+        if st:
+            raise OracleError(st, "minor")
+        for which, name in enumerate(MINOR_NAMES):
+            n = lib.ora_minor_size(h, which)
+            rows = np.empty(n, dtype=np.uint32)
+            cols = np.empty(n, dtype=np.uint32)
+            mult = np.empty(n, dtype=np.uint64)
+            if n:
+                lib.ora_minor_copy(h, which, _p(rows), _p(cols), _p(mult))
+            out[name] = (rows, cols, mult)
+    finally:
+        lib.ora_minor_free(h)
+    return out
+
+
+def path_counts(dims, pair, s1, s2, src_ranks=None):
+    """D* entries (row = 1-saddle rank, col = 2-saddle rank, uint64 count), sorted by (row, col)."""
+    d = _dims(dims)
+    lib = _load()
+    s1 = np.ascontiguousarray(s1, dtype=np.uint32)
+    s2 = np.ascontiguousarray(s2, dtype=np.uint32)
+    src = None if src_ranks is None else np.ascontiguousarray(src_ranks, dtype=np.int64)
+    h = lib.ora_path_counts(_p(d), _p(pair), len(s1), _p(s1), len(s2), _p(s2),
+                            0 if src is None else len(src), _p(src))
+    try:
+        st = lib.ora_result_status(h)
+        if st:
+            raise OracleError(st, "path_counts")
+        n = lib.ora_result_size(h)
+        rows = np.empty(n, dtype=np.uint32)
+        cols = np.empty(n, dtype=np.uint32)
+        cnt = np.empty(n, dtype=np.uint64)
+        if n:
+            lib.ora_result_copy(h, _p(rows), _p(cols), _p(cnt))
+        return rows, cols, cnt
+    finally:
+        lib.ora_result_free(h)
+
+
+def n_iter(nj, A, B):
+    acols = np.ascontiguousarray(A[1], dtype=np.uint32)
+    brows = np.ascontiguousarray(B[0], dtype=np.uint32)
+    bcols = np.ascontiguousarray(B[1], dtype=np.uint32)
+    return int(_load().ora_n_iter(int(nj), len(acols), _p(acols), len(brows), _p(brows), _p(bcols)))
+
+
+def compute_all(f: np.ndarray, with_minor: bool = True, with_dstar: bool = True) -> dict:
+    """Every output of the pipeline for one field (small and medium grids)."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    d = _dims(f)
+    pair = gradient(f)
+    counts, lists = critical(d, pair)
+    vmin, cmax, amin, amax = extremum(d, pair, lists[1], lists[2])
+    vis, levels = reachable(d, pair)
+    junc = junctions(d, pair, vis)
+    res = dict(dims=d, pair=pair, packed=pack(d, pair), counts=counts, lists=lists, vertex_min=vmin,
+               cube_max=cmax, min_arcs=amin, max_arcs=amax, visited=vis, levels=levels, junctions=junc)
+    if with_minor:
+        mn = minor(d, pair, lists[1], junc, lists[2])
+        res["minor"] = mn
+        res["n_iter"] = n_iter(len(junc), mn["A"], mn["B"])
+    if with_dstar:
+        res["dstar"] = path_counts(d, pair, lists[1], lists[2])
+    return res

@@ -1,0 +1,813 @@
+// TEST INFRASTRUCTURE ONLY -- the CPU oracle for the Morse-Smale complex 1-skeleton.
+//
+// A plain, slow, single-threaded restatement of what the method computes, used only to
+// check the CUDA path. Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline
+// (and --impl reference) legs may load it. It shares no code, header, table or helper
+// with the CUDA library, and neither side includes the other.
+//
+// What it follows (sections of arXiv:2009.03707, Subhash/Pandey/Natarajan):
+//   * Sec. 2.2 (Discrete Morse theory): gradient pairs, discrete vector field, V-paths,
+//     critical cells.  The gradient rule itself is deferred by the paper (Sec. 3 and
+//     Sec. 3.5, "Gradient pairs and critical points") to the locally independent
+//     lower-star rules it cites in Sec. 1.1 (Robins, Wood, Sheppard 2011); this file
+//     restates that rule, ProcessLowerStars, in the order of their algorithm.
+//   * Sec. 3.4 / Sec. 3.5 "Saddle-Extrema arcs": saddle-extremum arcs and the
+//     destination extremum of every cell, here as plain memoised walks.
+//   * Sec. 3.2 / Sec. 3.5 "Saddle-Saddle reachability": the DAG of 1-2 gradient pairs
+//     (Fig. "msc-max-min-dag" (d)) and the set of its nodes reachable from 1-saddles.
+//   * Sec. 3.3 / Sec. 3.5 "Gradient path counting": junction nodes and the DAG minor
+//     (matrices A, B, B*, D), and the saddle-saddle path counts D*, here computed by the
+//     plain definition -- per 1-saddle, a topological-order count of paths in the DAG --
+//     rather than by the paper's iterated sparse products.
+//
+// Readings where the paper is silent (each one is also listed in the design notes):
+//   R1 vertex order: v < w iff (f(v), index(v)) < (f(w), index(w)); IEEE compare, so
+//      -0 == +0 and +-Inf order normally; NaN input is rejected (status 2).
+//   R2 key of a cell in the lower star of x: its vertices sorted in decreasing vertex
+//      order, compared lexicographically; a proper prefix is smaller.
+//   R3 the two priority queues are sets; a popped cell that is already classified is
+//      skipped.  "Unclassified" = neither paired nor critical.
+//   R4 a walk from a 2-saddle towards a maximum that leaves through a boundary quad
+//      (a quad with a single cofacet cube) ends at NONE.
+//   R5 junction = a reachable 1-cell that is not a 1-saddle and has DAG out-degree > 1.
+//   R6 path counts are exact uint64; an overflowing add is an error (status 6).
+//
+// Cells live on the refined grid R = (2nx-1) x (2ny-1) x (2nz-1): cell (cx,cy,cz) has
+// dimension = number of odd coordinates and id cx + (2nx-1)*(cy + (2ny-1)*cz).  Vertex
+// (x,y,z) is cell (2x,2y,2z) and has index x + nx*(y + ny*z).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <set>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;   // critical / no partner / no label
+constexpr uint32_t UNSET = 0xFFFFFFFEu;  // not yet classified (must not survive)
+
+enum Status { OK = 0, ERR_ARG = 1, ERR_NAN = 2, ERR_TOO_LARGE = 4, ERR_OVERFLOW = 6, ERR_INTERNAL = 9 };
+
+struct Grid {
+    int64_t nx, ny, nz;  // vertex counts
+    int64_t rx, ry, rz;  // refined grid extents
+    const float* f;      // may be null when only the combinatorics is needed
+
+    Grid(const int64_t* d, const float* field)
+        : nx(d[0]), ny(d[1]), nz(d[2]), rx(2 * d[0] - 1), ry(2 * d[1] - 1), rz(2 * d[2] - 1), f(field) {}
+
+    int64_t nverts() const { return nx * ny * nz; }
+    int64_t ncells() const { return rx * ry * rz; }
+    bool inside(int64_t cx, int64_t cy, int64_t cz) const {
+        return cx >= 0 && cy >= 0 && cz >= 0 && cx < rx && cy < ry && cz < rz;
+    }
+    int64_t cell(int64_t cx, int64_t cy, int64_t cz) const { return cx + rx * (cy + ry * cz); }
+    void coords(int64_t c, int64_t& cx, int64_t& cy, int64_t& cz) const {
+        cx = c % rx;
+        cy = (c / rx) % ry;
+        cz = c / (rx * ry);
+    }
+    int dim(int64_t c) const {
+        int64_t cx, cy, cz;
+        coords(c, cx, cy, cz);
+        return int(cx & 1) + int(cy & 1) + int(cz & 1);
+    }
+    int64_t vertex(int64_t x, int64_t y, int64_t z) const { return x + nx * (y + ny * z); }
+    int64_t vertex_cell(int64_t v) const {
+        int64_t x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+        return cell(2 * x, 2 * y, 2 * z);
+    }
+    int64_t cell_to_vertex(int64_t c) const {
+        int64_t cx, cy, cz;
+        coords(c, cx, cy, cz);
+        return vertex(cx / 2, cy / 2, cz / 2);
+    }
+    // R1: the total order on vertices.
+    bool vless(int64_t a, int64_t b) const {
+        if (f[a] < f[b]) return true;
+        if (f[b] < f[a]) return false;
+        return a < b;
+    }
+    // Vertices of a cell: along every odd coordinate both neighbours, along even ones itself.
+    // Writes up to 8 vertex ids into out[] and returns how many.
+    int vertices(int64_t c, int64_t* out) const {
+        int64_t cc[3];
+        coords(c, cc[0], cc[1], cc[2]);
+        int64_t lo[3], hi[3];
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = cc[i] / 2;
+            hi[i] = (cc[i] & 1) ? lo[i] + 1 : lo[i];
+        }
+        int n = 0;
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+            for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x) out[n++] = vertex(x, y, z);
+        return n;
+    }
+    std::vector<int64_t> vertices(int64_t c) const {
+        int64_t buf[8];
+        int n = vertices(c, buf);
+        return std::vector<int64_t>(buf, buf + n);
+    }
+    // Facets: move one odd coordinate by +-1.  Cofacets: move one even coordinate by +-1 inside R.
+    std::vector<int64_t> facets(int64_t c) const {
+        int64_t cc[3];
+        coords(c, cc[0], cc[1], cc[2]);
+        std::vector<int64_t> out;
+        for (int i = 0; i < 3; ++i) {
+            if (!(cc[i] & 1)) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                int64_t d[3] = {cc[0], cc[1], cc[2]};
+                d[i] += s;
+                out.push_back(cell(d[0], d[1], d[2]));
+            }
+        }
+        return out;
+    }
+    std::vector<int64_t> cofacets(int64_t c) const {
+        int64_t cc[3];
+        coords(c, cc[0], cc[1], cc[2]);
+        std::vector<int64_t> out;
+        for (int i = 0; i < 3; ++i) {
+            if (cc[i] & 1) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                int64_t d[3] = {cc[0], cc[1], cc[2]};
+                d[i] += s;
+                if (inside(d[0], d[1], d[2])) out.push_back(cell(d[0], d[1], d[2]));
+            }
+        }
+        return out;
+    }
+    int64_t max_vertex(int64_t c) const {
+        std::vector<int64_t> vs = vertices(c);
+        int64_t m = vs[0];
+        for (int64_t v : vs)
+            if (vless(m, v)) m = v;
+        return m;
+    }
+};
+
+bool check_dims(const int64_t* d) {
+    if (!d) return false;
+    for (int i = 0; i < 3; ++i)
+        if (d[i] < 2) return false;
+    return true;
+}
+
+bool ids_fit_u32(const Grid& g) { return g.ncells() < int64_t(UNSET); }
+
+bool has_nan(const Grid& g) {
+    for (int64_t v = 0; v < g.nverts(); ++v)
+        if (std::isnan(g.f[v])) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------------
+// ProcessLowerStars (Robins, Wood, Sheppard 2011) for one vertex x.
+// The lower star L(x) is the set of cells whose maximal vertex (under R1) is x.
+// Cells of L(x) are paired among themselves or declared critical; the result is
+// written into `pair_of` (partner id, or NONE for critical) for those cells only.
+// ---------------------------------------------------------------------------------
+struct LowerStar {
+    const Grid& g;
+    struct Cell {
+        int64_t id;
+        int dim;
+        std::vector<int64_t> key;   // R2: vertices in decreasing vertex order
+        std::vector<int> facets;    // local indices of the facets that lie in L(x)
+        std::vector<int> cofacets;  // local indices of the cofacets that lie in L(x)
+        int state;                  // 0 unclassified, 1 paired, 2 critical
+    };
+    std::vector<Cell> cells;
+
+    LowerStar(const Grid& grid, int64_t x) : g(grid) {
+        int64_t cx, cy, cz;
+        g.coords(g.vertex_cell(x), cx, cy, cz);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!g.inside(cx + dx, cy + dy, cz + dz)) continue;
+                    int64_t c = g.cell(cx + dx, cy + dy, cz + dz);
+                    int64_t vs[8];
+                    int nv = g.vertices(c, vs);
+                    bool x_is_max = true;
+                    for (int i = 0; i < nv; ++i)
+                        if (g.vless(x, vs[i])) x_is_max = false;
+                    if (!x_is_max) continue;  // c belongs to the lower star of another vertex
+                    Cell cell;
+                    cell.key.assign(vs, vs + nv);
+                    std::sort(cell.key.begin(), cell.key.end(),
+                              [&](int64_t a, int64_t b) { return g.vless(b, a); });
+                    cell.id = c;
+                    cell.dim = g.dim(c);
+                    cell.state = 0;
+                    cells.push_back(cell);
+                }
+        for (Cell& cell : cells) {
+            for (int64_t fc : g.facets(cell.id)) {
+                int i = index_of(fc);
+                if (i >= 0) cell.facets.push_back(i);
+            }
+            for (int64_t cf : g.cofacets(cell.id)) {
+                int i = index_of(cf);
+                if (i >= 0) cell.cofacets.push_back(i);
+            }
+        }
+    }
+
+    int index_of(int64_t id) const {
+        for (size_t i = 0; i < cells.size(); ++i)
+            if (cells[i].id == id) return int(i);
+        return -1;
+    }
+    // R2: lexicographic comparison of keys; a proper prefix is smaller.
+    bool key_less(int a, int b) const {
+        const std::vector<int64_t>& ka = cells[a].key;
+        const std::vector<int64_t>& kb = cells[b].key;
+        size_t n = std::min(ka.size(), kb.size());
+        for (size_t i = 0; i < n; ++i)
+            if (ka[i] != kb[i]) return g.vless(ka[i], kb[i]);
+        return ka.size() < kb.size();
+    }
+    const std::vector<int>& facets_in_L(int a) const { return cells[a].facets; }
+    const std::vector<int>& cofacets_in_L(int a) const { return cells[a].cofacets; }
+    int num_unclassified_facets(int a) const {
+        int n = 0;
+        for (int i : facets_in_L(a))
+            if (cells[i].state == 0) ++n;
+        return n;
+    }
+    int unclassified_facet(int a) const {
+        for (int i : facets_in_L(a))
+            if (cells[i].state == 0) return i;
+        return -1;
+    }
+};
+
+struct KeyOrder {
+    const LowerStar* ls;
+    bool operator()(int a, int b) const { return ls->key_less(a, b); }
+};
+
+// Returns false if the procedure left a cell of L(x) unclassified (cannot happen for a
+// correct restatement; reported as an internal error).
+bool process_lower_star(const Grid& g, int64_t x, std::map<int64_t, uint32_t>& out) {
+    LowerStar ls(g, x);
+    auto pair_cells = [&](int lo, int hi) {
+        ls.cells[lo].state = 1;
+        ls.cells[hi].state = 1;
+        out[ls.cells[lo].id] = uint32_t(ls.cells[hi].id);
+        out[ls.cells[hi].id] = uint32_t(ls.cells[lo].id);
+    };
+    auto make_critical = [&](int a) {
+        ls.cells[a].state = 2;
+        out[ls.cells[a].id] = NONE;
+    };
+    const int vx = ls.index_of(g.vertex_cell(x));
+
+    if (ls.cells.size() == 1) {  // L(x) = {x}: x is a minimum
+        make_critical(vx);
+        return true;
+    }
+    // x is paired with the edge of least key (the steepest descending edge).
+    int delta = -1;
+    for (int i = 0; i < int(ls.cells.size()); ++i)
+        if (ls.cells[i].dim == 1 && (delta < 0 || ls.key_less(i, delta))) delta = i;
+    pair_cells(vx, delta);
+
+    std::set<int, KeyOrder> pq_zero(KeyOrder{&ls}), pq_one(KeyOrder{&ls});
+    for (int i = 0; i < int(ls.cells.size()); ++i)
+        if (ls.cells[i].dim == 1 && i != delta) pq_zero.insert(i);
+    for (int b : ls.cofacets_in_L(delta))
+        if (ls.cells[b].state == 0 && ls.num_unclassified_facets(b) == 1) pq_one.insert(b);
+
+    while (!pq_one.empty() || !pq_zero.empty()) {
+        while (!pq_one.empty()) {
+            int a = *pq_one.begin();
+            pq_one.erase(pq_one.begin());
+            if (ls.cells[a].state != 0) continue;  // R3
+            if (ls.num_unclassified_facets(a) == 0) {
+                pq_zero.insert(a);
+                continue;
+            }
+            int p = ls.unclassified_facet(a);
+            pair_cells(p, a);
+            pq_zero.erase(p);
+            std::vector<int> nb = ls.cofacets_in_L(a);
+            const std::vector<int>& nb2 = ls.cofacets_in_L(p);
+            nb.insert(nb.end(), nb2.begin(), nb2.end());
+            for (int b : nb)
+                if (ls.cells[b].state == 0 && ls.num_unclassified_facets(b) == 1) pq_one.insert(b);
+        }
+        if (!pq_zero.empty()) {
+            int c = *pq_zero.begin();
+            pq_zero.erase(pq_zero.begin());
+            if (ls.cells[c].state != 0) continue;  // R3
+            make_critical(c);
+            for (int b : ls.cofacets_in_L(c))
+                if (ls.cells[b].state == 0 && ls.num_unclassified_facets(b) == 1) pq_one.insert(b);
+        }
+    }
+    for (const auto& c : ls.cells)
+        if (c.state == 0) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------------
+// Packed per-vertex gradient word (the library's exchange format).
+// Vertex (x,y,z) owns the 8 cells (2x+a, 2y+b, 2z+c), a,b,c in {0,1}; slot s = a + 2b + 4c
+// holds a 3-bit code in bits [3s, 3s+3): 0 = critical, 1..6 = partner at -x,+x,-y,+y,-z,+z,
+// 7 = the cell lies outside the refined grid.
+// ---------------------------------------------------------------------------------
+uint32_t direction_code(const Grid& g, int64_t c, uint32_t partner) {
+    if (partner == NONE) return 0;
+    int64_t ax, ay, az, bx, by, bz;
+    g.coords(c, ax, ay, az);
+    g.coords(int64_t(partner), bx, by, bz);
+    if (bx == ax - 1) return 1;
+    if (bx == ax + 1) return 2;
+    if (by == ay - 1) return 3;
+    if (by == ay + 1) return 4;
+    if (bz == az - 1) return 5;
+    return 6;
+}
+
+uint32_t packed_word(const Grid& g, int64_t v, const std::map<int64_t, uint32_t>& pairs) {
+    int64_t x = v % g.nx, y = (v / g.nx) % g.ny, z = v / (g.nx * g.ny);
+    uint32_t w = 0;
+    for (int s = 0; s < 8; ++s) {
+        int a = s & 1, b = (s >> 1) & 1, c = (s >> 2) & 1;
+        uint32_t code = 7;
+        if (g.inside(2 * x + a, 2 * y + b, 2 * z + c)) {
+            int64_t id = g.cell(2 * x + a, 2 * y + b, 2 * z + c);
+            code = direction_code(g, id, pairs.at(id));
+        }
+        w |= code << (3 * s);
+    }
+    return w;
+}
+
+// ---------------------------------------------------------------------------------
+// DAG of 1-2 gradient pairs (Sec. 3.2, Fig. "msc-max-min-dag" (d)).
+// Nodes: 1-saddles, 1-cells paired with a 2-cell, and 2-saddles.  For a 1-cell node e,
+// each cofacet quad q of e other than e's own partner gives an out-edge: to q if q is
+// critical (a 2-saddle), to the 1-cell paired with q if q is paired downwards, and none
+// if q is paired with a cube.  Following an out-edge walks a V-path backwards, i.e. the
+// traversal runs against the discrete gradient (Sec. 3.5).
+// ---------------------------------------------------------------------------------
+std::vector<int64_t> dag_out(const Grid& g, const uint32_t* pair_of, int64_t e) {
+    std::vector<int64_t> out;
+    for (int64_t q : g.cofacets(e)) {
+        if (uint32_t(q) == pair_of[e]) continue;
+        uint32_t p = pair_of[q];
+        if (p == NONE) {
+            out.push_back(q);
+        } else if (g.dim(int64_t(p)) == 1) {
+            out.push_back(int64_t(p));
+        }
+    }
+    return out;
+}
+
+bool is_dag_node_1cell(const Grid& g, const uint32_t* pair_of, int64_t e) {
+    if (g.dim(e) != 1) return false;
+    uint32_t p = pair_of[e];
+    return p == NONE || g.dim(int64_t(p)) == 2;
+}
+
+std::vector<int64_t> critical_list(const Grid& g, const uint32_t* pair_of, int dim) {
+    std::vector<int64_t> out;
+    for (int64_t c = 0; c < g.ncells(); ++c)
+        if (pair_of[c] == NONE && g.dim(c) == dim) out.push_back(c);
+    return out;
+}
+
+// Bit `axis` of visited[v] marks the 1-cell owned by vertex v along that axis.
+int64_t one_cell_slot(const Grid& g, int64_t e, int& axis) {
+    int64_t cx, cy, cz;
+    g.coords(e, cx, cy, cz);
+    axis = (cx & 1) ? 0 : ((cy & 1) ? 1 : 2);
+    return g.vertex(cx / 2, cy / 2, cz / 2);
+}
+
+bool visited_get(const Grid& g, const uint8_t* visited, int64_t e) {
+    int axis;
+    int64_t v = one_cell_slot(g, e, axis);
+    return (visited[v] >> axis) & 1;
+}
+
+struct Minor {
+    // (row rank, col rank) -> multiplicity, for A (1s x j), B (j x j), B* (j x 2s), D (1s x 2s)
+    std::map<std::pair<int64_t, int64_t>, uint64_t> m[4];
+    int status = OK;
+};
+
+int64_t rank_in(const std::vector<int64_t>& sorted, int64_t id) {
+    auto it = std::lower_bound(sorted.begin(), sorted.end(), id);
+    if (it == sorted.end() || *it != id) return -1;
+    return int64_t(it - sorted.begin());
+}
+
+}  // namespace
+
+// =====================================================================================
+// C entry points (ctypes).  dims = {nx, ny, nz}; field layout f[x + nx*(y + ny*z)].
+// =====================================================================================
+extern "C" {
+
+int ora_version() { return 1; }
+
+// Full discrete gradient: pair_of[c] = partner id or 0xFFFFFFFF (critical), for every cell.
+int ora_gradient(const int64_t* dims, const float* f, uint32_t* pair_of) {
+    if (!check_dims(dims) || !f || !pair_of) return ERR_ARG;
+    Grid g(dims, f);
+    if (!ids_fit_u32(g)) return ERR_TOO_LARGE;
+    if (has_nan(g)) return ERR_NAN;
+    for (int64_t c = 0; c < g.ncells(); ++c) pair_of[c] = UNSET;
+    std::map<int64_t, uint32_t> local;
+    for (int64_t x = 0; x < g.nverts(); ++x) {
+        local.clear();
+        if (!process_lower_star(g, x, local)) return ERR_INTERNAL;
+        for (const auto& kv : local) {
+            if (pair_of[kv.first] != UNSET) return ERR_INTERNAL;  // classified twice
+            pair_of[kv.first] = kv.second;
+        }
+    }
+    for (int64_t c = 0; c < g.ncells(); ++c)
+        if (pair_of[c] == UNSET) return ERR_INTERNAL;
+    return OK;
+}
+
+// Pairing restricted to the lower star of each listed vertex: writes the packed words of
+// the listed vertices (computing every lower star those 8 cells fall into).
+int ora_packed_at(const int64_t* dims, const float* f, int64_t n, const int64_t* verts, uint32_t* words) {
+    if (!check_dims(dims) || !f || (n > 0 && (!verts || !words))) return ERR_ARG;
+    Grid g(dims, f);
+    if (!ids_fit_u32(g)) return ERR_TOO_LARGE;
+    std::map<int64_t, uint32_t> pairs;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = verts[i];
+        if (v < 0 || v >= g.nverts()) return ERR_ARG;
+        int64_t x = v % g.nx, y = (v / g.nx) % g.ny, z = v / (g.nx * g.ny);
+        pairs.clear();
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    if (!g.inside(2 * x + a, 2 * y + b, 2 * z + c)) continue;
+                    int64_t id = g.cell(2 * x + a, 2 * y + b, 2 * z + c);
+                    if (pairs.count(id)) continue;
+                    for (int64_t w : g.vertices(id))
+                        if (std::isnan(g.f[w])) return ERR_NAN;
+                    if (!process_lower_star(g, g.max_vertex(id), pairs)) return ERR_INTERNAL;
+                }
+        words[i] = packed_word(g, v, pairs);
+    }
+    return OK;
+}
+
+// Packed words of all vertices from a full pairing.
+int ora_pack(const int64_t* dims, const uint32_t* pair_of, uint32_t* words) {
+    if (!check_dims(dims) || !pair_of || !words) return ERR_ARG;
+    Grid g(dims, nullptr);
+    for (int64_t v = 0; v < g.nverts(); ++v) {
+        int64_t x = v % g.nx, y = (v / g.nx) % g.ny, z = v / (g.nx * g.ny);
+        uint32_t w = 0;
+        for (int s = 0; s < 8; ++s) {
+            int a = s & 1, b = (s >> 1) & 1, c = (s >> 2) & 1;
+            uint32_t code = 7;
+            if (g.inside(2 * x + a, 2 * y + b, 2 * z + c)) {
+                int64_t id = g.cell(2 * x + a, 2 * y + b, 2 * z + c);
+                code = direction_code(g, id, pair_of[id]);
+            }
+            w |= code << (3 * s);
+        }
+        words[v] = w;
+    }
+    return OK;
+}
+
+// Critical cells: counts per dimension, and the list of one dimension in cell-id order.
+int ora_critical_counts(const int64_t* dims, const uint32_t* pair_of, int64_t* counts) {
+    if (!check_dims(dims) || !pair_of || !counts) return ERR_ARG;
+    Grid g(dims, nullptr);
+    for (int k = 0; k < 4; ++k) counts[k] = 0;
+    for (int64_t c = 0; c < g.ncells(); ++c)
+        if (pair_of[c] == NONE) counts[g.dim(c)]++;
+    return OK;
+}
+
+int ora_critical_list(const int64_t* dims, const uint32_t* pair_of, int dim, uint32_t* out) {
+    if (!check_dims(dims) || !pair_of || !out || dim < 0 || dim > 3) return ERR_ARG;
+    Grid g(dims, nullptr);
+    int64_t n = 0;
+    for (int64_t c = 0; c < g.ncells(); ++c)
+        if (pair_of[c] == NONE && g.dim(c) == dim) out[n++] = uint32_t(c);
+    return OK;
+}
+
+// Destination extrema (Sec. 3.4): vertex_min[v] = cell id of the minimum that the
+// descending walk from v reaches; cube_max[v] = cell id of the maximum that the ascending
+// walk from cube (2x+1,2y+1,2z+1) reaches, NONE if it leaves the domain (R4) or if v has
+// no such cube (x = nx-1, y = ny-1 or z = nz-1).
+int ora_extremum_labels(const int64_t* dims, const uint32_t* pair_of, uint32_t* vertex_min, uint32_t* cube_max) {
+    if (!check_dims(dims) || !pair_of || !vertex_min || !cube_max) return ERR_ARG;
+    Grid g(dims, nullptr);
+    const int64_t nv = g.nverts();
+    // Vertices: v paired with edge (v,w) steps to w; an unpaired vertex is a minimum.
+    for (int64_t v = 0; v < nv; ++v) vertex_min[v] = UNSET;
+    std::vector<int64_t> stack;
+    for (int64_t v0 = 0; v0 < nv; ++v0) {
+        int64_t v = v0;
+        stack.clear();
+        uint32_t label = UNSET;
+        while (true) {
+            if (vertex_min[v] != UNSET) { label = vertex_min[v]; break; }
+            stack.push_back(v);
+            int64_t vc = g.vertex_cell(v);
+            uint32_t e = pair_of[vc];
+            if (e == NONE) { label = uint32_t(vc); break; }
+            int64_t other = -1;
+            for (int64_t w : g.vertices(int64_t(e)))
+                if (w != v) other = w;
+            v = other;
+            if (int64_t(stack.size()) > nv) return ERR_INTERNAL;  // a cycle
+        }
+        for (int64_t s : stack) vertex_min[s] = label;
+    }
+    // Cubes: a cube paired with quad p steps to the other cofacet cube of p (NONE if p is on
+    // the boundary); an unpaired cube is a maximum.
+    for (int64_t v = 0; v < nv; ++v) cube_max[v] = UNSET;
+    auto cube_slot = [&](int64_t c) { return g.cell_to_vertex(c); };
+    for (int64_t v0 = 0; v0 < nv; ++v0) {
+        int64_t x = v0 % g.nx, y = (v0 / g.nx) % g.ny, z = v0 / (g.nx * g.ny);
+        if (x == g.nx - 1 || y == g.ny - 1 || z == g.nz - 1) { cube_max[v0] = NONE; continue; }
+        int64_t c = g.cell(2 * x + 1, 2 * y + 1, 2 * z + 1);
+        stack.clear();
+        uint32_t label = UNSET;
+        while (true) {
+            int64_t slot = cube_slot(c);
+            if (cube_max[slot] != UNSET) { label = cube_max[slot]; break; }
+            stack.push_back(slot);
+            uint32_t p = pair_of[c];
+            if (p == NONE) { label = uint32_t(c); break; }
+            int64_t cx, cy, cz, px, py, pz;
+            g.coords(c, cx, cy, cz);
+            g.coords(int64_t(p), px, py, pz);
+            int64_t nxc = 2 * px - cx, nyc = 2 * py - cy, nzc = 2 * pz - cz;  // across the quad
+            if (!g.inside(nxc, nyc, nzc)) { label = NONE; break; }
+            c = g.cell(nxc, nyc, nzc);
+            if (int64_t(stack.size()) > nv) return ERR_INTERNAL;
+        }
+        for (int64_t s : stack) cube_max[s] = label;
+    }
+    return OK;
+}
+
+// Saddle-extremum arcs.  1-saddle edge: labels of its lower-coordinate then upper-coordinate
+// vertex.  2-saddle quad: labels of its cofacet cube on the - side then the + side of the
+// quad's even axis (NONE where the cube does not exist).
+int ora_min_arcs(const int64_t* dims, const uint32_t* vertex_min, int64_t n1, const uint32_t* s1, uint32_t* out) {
+    if (!check_dims(dims) || !vertex_min || (n1 > 0 && (!s1 || !out))) return ERR_ARG;
+    Grid g(dims, nullptr);
+    for (int64_t i = 0; i < n1; ++i) {
+        std::vector<int64_t> vs = g.vertices(int64_t(s1[i]));
+        if (vs.size() != 2) return ERR_ARG;
+        out[2 * i] = vertex_min[std::min(vs[0], vs[1])];
+        out[2 * i + 1] = vertex_min[std::max(vs[0], vs[1])];
+    }
+    return OK;
+}
+
+int ora_max_arcs(const int64_t* dims, const uint32_t* cube_max, int64_t n2, const uint32_t* s2, uint32_t* out) {
+    if (!check_dims(dims) || !cube_max || (n2 > 0 && (!s2 || !out))) return ERR_ARG;
+    Grid g(dims, nullptr);
+    for (int64_t i = 0; i < n2; ++i) {
+        int64_t cc[3];
+        g.coords(int64_t(s2[i]), cc[0], cc[1], cc[2]);
+        int axis = !(cc[0] & 1) ? 0 : (!(cc[1] & 1) ? 1 : 2);
+        for (int side = 0; side < 2; ++side) {
+            int64_t d[3] = {cc[0], cc[1], cc[2]};
+            d[axis] += side ? 1 : -1;
+            out[2 * i + side] = g.inside(d[0], d[1], d[2]) ? cube_max[g.cell_to_vertex(g.cell(d[0], d[1], d[2]))] : NONE;
+        }
+    }
+    return OK;
+}
+
+// Saddle-saddle reachability (Sec. 3.2): multi-source BFS over the DAG from all 1-saddles.
+// visited[v] bit a (a = 0,1,2) marks the 1-cell of vertex v along axis a as reachable
+// (the 1-saddles themselves included).  Returns the number of non-empty BFS levels
+// (level 0 = the 1-saddles), or -status on error.
+int64_t ora_reachable(const int64_t* dims, const uint32_t* pair_of, uint8_t* visited) {
+    if (!check_dims(dims) || !pair_of || !visited) return -ERR_ARG;
+    Grid g(dims, nullptr);
+    std::memset(visited, 0, size_t(g.nverts()));
+    std::vector<int64_t> frontier = critical_list(g, pair_of, 1), next;
+    for (int64_t e : frontier) {
+        int axis;
+        int64_t v = one_cell_slot(g, e, axis);
+        visited[v] |= uint8_t(1u << axis);
+    }
+    int64_t levels = 0;
+    while (!frontier.empty()) {
+        ++levels;
+        next.clear();
+        for (int64_t e : frontier)
+            for (int64_t t : dag_out(g, pair_of, e)) {
+                if (g.dim(t) != 1) continue;
+                int axis;
+                int64_t v = one_cell_slot(g, t, axis);
+                if ((visited[v] >> axis) & 1) continue;
+                visited[v] |= uint8_t(1u << axis);
+                next.push_back(t);
+            }
+        frontier.swap(next);
+    }
+    return levels;
+}
+
+// Junction nodes (R5), in cell-id order.  Returns the count; out may be null.
+int64_t ora_junctions(const int64_t* dims, const uint32_t* pair_of, const uint8_t* visited, uint32_t* out) {
+    if (!check_dims(dims) || !pair_of || !visited) return -ERR_ARG;
+    Grid g(dims, nullptr);
+    int64_t n = 0;
+    for (int64_t c = 0; c < g.ncells(); ++c) {
+        if (g.dim(c) != 1 || pair_of[c] == NONE) continue;
+        if (!visited_get(g, visited, c)) continue;
+        if (dag_out(g, pair_of, c).size() > 1) {
+            if (out) out[n] = uint32_t(c);
+            ++n;
+        }
+    }
+    return n;
+}
+
+// DAG minor (Sec. 3.3 "DAG minor construction"): from every out-edge of every 1-saddle and
+// junction, follow the unique successor while the node is neither a junction nor a
+// 2-saddle; a node without successors ends a dead path, which is dropped.  Each traced
+// path adds 1 to the multiplicity of its (source, destination) entry in A (1s->j),
+// B (j->j), B* (j->2s) or D (1s->2s).  The four matrices are kept behind a handle; each
+// is read back sorted by (row, col).
+void* ora_minor(const int64_t* dims, const uint32_t* pair_of, int64_t n1, const uint32_t* s1, int64_t nj,
+                const uint32_t* junc, int64_t n2, const uint32_t* s2) {
+    Minor* mn = new Minor();
+    if (!check_dims(dims) || !pair_of) {
+        mn->status = ERR_ARG;
+        return mn;
+    }
+    Grid g(dims, nullptr);
+    std::vector<int64_t> L1(s1, s1 + n1), LJ(junc, junc + nj), L2(s2, s2 + n2);
+    std::unordered_set<int64_t> jset(LJ.begin(), LJ.end());
+    auto trace_from = [&](int64_t u, bool u_is_saddle) {
+        int64_t urank = u_is_saddle ? rank_in(L1, u) : rank_in(LJ, u);
+        for (int64_t w : dag_out(g, pair_of, u)) {
+            for (int64_t steps = 0;; ++steps) {
+                if (steps > g.ncells()) {  // longer than any simple path: the DAG has a cycle
+                    mn->status = ERR_INTERNAL;
+                    return;
+                }
+                if (g.dim(w) == 2) {  // a 2-saddle
+                    mn->m[u_is_saddle ? 3 : 2][{urank, rank_in(L2, w)}] += 1;
+                    break;
+                }
+                if (jset.count(w)) {
+                    mn->m[u_is_saddle ? 0 : 1][{urank, rank_in(LJ, w)}] += 1;
+                    break;
+                }
+                std::vector<int64_t> nxt = dag_out(g, pair_of, w);
+                if (nxt.empty()) break;  // dead path
+                w = nxt[0];
+            }
+        }
+    };
+    for (int64_t u : L1) trace_from(u, true);
+    for (int64_t u : LJ) trace_from(u, false);
+    return mn;
+}
+
+int ora_minor_status(void* h) { return static_cast<Minor*>(h)->status; }
+
+int64_t ora_minor_size(void* h, int which) { return int64_t(static_cast<Minor*>(h)->m[which].size()); }
+
+void ora_minor_copy(void* h, int which, uint32_t* rows, uint32_t* cols, uint64_t* mult) {
+    int64_t i = 0;
+    for (const auto& kv : static_cast<Minor*>(h)->m[which]) {
+        rows[i] = uint32_t(kv.first.first);
+        cols[i] = uint32_t(kv.first.second);
+        mult[i] = kv.second;
+        ++i;
+    }
+}
+
+void ora_minor_free(void* h) { delete static_cast<Minor*>(h); }
+
+// Saddle-saddle path counts D* (O5): for each requested 1-saddle s (by rank in s1), collect
+// the DAG nodes reachable from s, visit them in topological order (Kahn) with cnt[s] = 1
+// and cnt[w] += cnt[v] along every edge, and emit (rank(s), rank(t), cnt[t]) for every
+// 2-saddle t with cnt > 0.  Results are kept behind a handle, sorted by (row, col).
+struct PathCounts {
+    std::vector<uint32_t> rows, cols;
+    std::vector<uint64_t> counts;
+    int status = OK;
+};
+
+void* ora_path_counts(const int64_t* dims, const uint32_t* pair_of, int64_t n1, const uint32_t* s1, int64_t n2,
+                      const uint32_t* s2, int64_t nsrc, const int64_t* src_ranks) {
+    PathCounts* res = new PathCounts();
+    if (!check_dims(dims) || !pair_of) { res->status = ERR_ARG; return res; }
+    Grid g(dims, nullptr);
+    std::vector<int64_t> L2(s2, s2 + n2);
+    std::vector<int64_t> order;
+    if (src_ranks) order.assign(src_ranks, src_ranks + nsrc);
+    else for (int64_t i = 0; i < n1; ++i) order.push_back(i);
+    std::sort(order.begin(), order.end());
+    std::vector<int64_t> stack;
+    for (int64_t r : order) {
+        if (r < 0 || r >= n1) { res->status = ERR_ARG; return res; }
+        int64_t s = int64_t(s1[r]);
+        // reachable set R(s) and in-degrees within it
+        std::unordered_map<int64_t, int64_t> indeg;
+        std::unordered_set<int64_t> seen{s};
+        stack.assign(1, s);
+        while (!stack.empty()) {
+            int64_t v = stack.back();
+            stack.pop_back();
+            if (g.dim(v) != 1) continue;  // 2-saddles are sinks
+            for (int64_t w : dag_out(g, pair_of, v)) {
+                indeg[w] += 1;
+                if (seen.insert(w).second) stack.push_back(w);
+            }
+        }
+        // Kahn's order from s
+        std::unordered_map<int64_t, uint64_t> cnt;
+        cnt[s] = 1;
+        std::vector<int64_t> queue{s};
+        std::map<int64_t, uint64_t> row;  // 2-saddle rank -> count
+        for (size_t qi = 0; qi < queue.size(); ++qi) {
+            int64_t v = queue[qi];
+            uint64_t cv = cnt[v];
+            if (g.dim(v) == 2) {
+                if (cv > 0) row[rank_in(L2, v)] = cv;
+                continue;
+            }
+            for (int64_t w : dag_out(g, pair_of, v)) {
+                uint64_t before = cnt[w];
+                uint64_t after = before + cv;
+                if (after < before) { res->status = ERR_OVERFLOW; return res; }  // R6
+                cnt[w] = after;
+                if (--indeg[w] == 0) queue.push_back(w);
+            }
+        }
+        for (const auto& kv : row) {
+            res->rows.push_back(uint32_t(r));
+            res->cols.push_back(uint32_t(kv.first));
+            res->counts.push_back(kv.second);
+        }
+    }
+    return res;
+}
+
+int ora_result_status(void* h) { return static_cast<PathCounts*>(h)->status; }
+int64_t ora_result_size(void* h) { return int64_t(static_cast<PathCounts*>(h)->rows.size()); }
+void ora_result_copy(void* h, uint32_t* rows, uint32_t* cols, uint64_t* counts) {
+    PathCounts* r = static_cast<PathCounts*>(h);
+    std::copy(r->rows.begin(), r->rows.end(), rows);
+    std::copy(r->cols.begin(), r->cols.end(), cols);
+    std::copy(r->counts.begin(), r->counts.end(), counts);
+}
+void ora_result_free(void* h) { delete static_cast<PathCounts*>(h); }
+
+// Number of non-zero iterates A_k = A B^k (k >= 0) of the paper's product loop: the length,
+// in minor edges, of the longest minor path that starts with an A edge and stays among
+// junctions.  Computed by longest-path DP over the B edges, given A and B as COO lists.
+int64_t ora_n_iter(int64_t nj, int64_t nnzA, const uint32_t* Acols, int64_t nnzB, const uint32_t* Brows,
+                   const uint32_t* Bcols) {
+    std::vector<std::vector<int64_t>> succ(static_cast<size_t>(nj));
+    std::vector<int64_t> indeg(static_cast<size_t>(nj), 0), depth(static_cast<size_t>(nj), 0);
+    for (int64_t i = 0; i < nnzB; ++i) {
+        succ[Brows[i]].push_back(Bcols[i]);
+        indeg[Bcols[i]]++;
+    }
+    for (int64_t i = 0; i < nnzA; ++i) depth[Acols[i]] = 1;
+    std::vector<int64_t> queue;
+    for (int64_t j = 0; j < nj; ++j)
+        if (indeg[j] == 0) queue.push_back(j);
+    int64_t best = 0;
+    for (size_t qi = 0; qi < queue.size(); ++qi) {
+        int64_t j = queue[qi];
+        best = std::max(best, depth[j]);
+        for (int64_t k : succ[j]) {
+            if (depth[j] > 0) depth[k] = std::max(depth[k], depth[j] + 1);
+            if (--indeg[k] == 0) queue.push_back(k);
+        }
+    }
+    return best;
+}
+
+}  // extern "C"

@@ -1,0 +1,409 @@
+"""Pins for the CPU oracle: checks against what the mathematics fixes, not against itself.
+
+* Euler characteristic of a box: #min - #1s + #2s - #max = 1 (every field).
+* Structural invariants of a discrete gradient (Sec. 2.2): each cell in at most one pair,
+  pairs are facet/cofacet, no non-trivial closed V-path (acyclic modified Hasse diagram),
+  both cells of a pair share their maximal vertex (lower-star locality).
+* Closed form for the 0-1 pairs: a non-minimal vertex is paired with the edge to its
+  lowest lower neighbour; a vertex is critical iff no axis neighbour is lower.
+* Lower-star persistent homology by textbook Z2 column reduction: the number of critical
+  k-cells equals the number of k-cells that open or close a homology class of non-zero
+  persistence, plus essential classes (Robins, Wood, Sheppard 2011).
+* Analytic fields with known critical counts (bowl, linear, inverted bowl, cosine lattice).
+* Saddle-saddle path counts against exhaustive enumeration of V-paths downward from every
+  2-saddle (independent of the oracle's upward DAG walk), and against the paper's own
+  iterated-product formulation (Sec. 3.3) in exact Python integers.
+* Destination minima against steepest descent on the raw field.
+"""
+from __future__ import annotations
+
+from collections import defaultdict
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+from tests.cubical import Complex, pairs_dict, random_field, vertex_rank
+
+NONE = 0xFFFFFFFF
+
+SMALL_SHAPES = [(2, 2, 2), (2, 3, 4), (3, 3, 3), (4, 3, 2), (4, 4, 4), (5, 4, 3), (3, 5, 5)]
+
+
+def _dims(f):
+    nz, ny, nx = f.shape
+    return (nx, ny, nz)
+
+
+def _fields_small():
+    out = []
+    for i, shp in enumerate(SMALL_SHAPES):
+        out.append(random_field(shp, 10 + i, "normal"))
+        out.append(random_field(shp, 50 + i, "ties"))
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# helpers written from the definitions
+# ----------------------------------------------------------------------------------
+def persistence_critical_counts(f):
+    """Critical-cell counts implied by lower-star persistent homology (Z2 column reduction)."""
+    C = Complex(_dims(f))
+    rank = vertex_rank(f)
+    val = {c: max(rank[v] for v in C.vertices(c)) for c in C.cells()}
+    order = sorted(C.cells(), key=lambda c: (val[c], C.dim(c), c))
+    pos = {c: i for i, c in enumerate(order)}
+    low_owner = {}
+    cols = []
+    paired = set()
+    counts = [0, 0, 0, 0]
+    for j, c in enumerate(order):
+        col = {pos[x] for x in C.facets(c)}
+        while col:
+            low = max(col)
+            if low not in low_owner:
+                break
+            col ^= cols[low_owner[low]]
+        cols.append(col)
+        if col:
+            low = max(col)
+            low_owner[low] = j
+            paired.update((low, j))
+            if val[order[low]] != val[c]:
+                counts[C.dim(order[low])] += 1
+                counts[C.dim(c)] += 1
+    for j, c in enumerate(order):
+        if j not in paired:
+            counts[C.dim(c)] += 1
+    return counts
+
+
+def vpath_counts(C, pair, crit1, crit2):
+    """{(1-saddle cell, 2-saddle cell): number of V-paths}, by enumeration downward from 2-saddles.
+
+    A path leaves a quad through any facet other than the one the quad is paired with; at a
+    1-cell it ends if the cell is critical, continues into the quad the cell is paired with,
+    and is abandoned if the cell is paired with a vertex.
+    """
+    pd = pairs_dict(pair)
+    crit1 = set(int(c) for c in crit1)
+    counts = defaultdict(int)
+    for t in crit2:
+        t = int(t)
+        stack = [(t, None)]
+        while stack:
+            q, excluded = stack.pop()
+            for e in C.facets(q):
+                if e == excluded:
+                    continue
+                if e in crit1:
+                    counts[(e, t)] += 1
+                    continue
+                p = pd[e]
+                if C.dim(p) == 2:
+                    stack.append((p, e))
+    return dict(counts)
+
+
+def sparse_mul(X, Y):
+    out = defaultdict(int)
+    rows_y = defaultdict(list)
+    for (r, c), v in Y.items():
+        rows_y[r].append((c, v))
+    for (r, k), v in X.items():
+        for c, w in rows_y.get(k, ()):
+            out[(r, c)] += v * w
+    return {k: v for k, v in out.items() if v}
+
+
+def paper_iterated_product(mn):
+    """Sec. 3.3: A* = sum_k A B^k (iterate while the product is non-zero), D* = A* B* + D."""
+    to_d = lambda t: {(int(r), int(c)): int(m) for r, c, m in zip(*t)}
+    A, B, Bs, D = (to_d(mn[k]) for k in oracle.MINOR_NAMES)
+    Astar = defaultdict(int)
+    Ak = dict(A)
+    iters = 0
+    while Ak:
+        iters += 1
+        for k, v in Ak.items():
+            Astar[k] += v
+        Ak = sparse_mul(Ak, B)
+    Dstar = defaultdict(int, sparse_mul(dict(Astar), Bs))
+    for k, v in D.items():
+        Dstar[k] += v
+    return {k: v for k, v in Dstar.items() if v}, iters
+
+
+# ----------------------------------------------------------------------------------
+# tests
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("f", _fields_small(), ids=lambda f: "x".join(map(str, f.shape)))
+def test_invariants_and_persistence(f):
+    C = Complex(_dims(f))
+    pair = oracle.gradient(f)
+    rank = vertex_rank(f)
+    pd = pairs_dict(pair)
+    maxv = lambda c: max(C.vertices(c), key=lambda v: rank[v])
+    for a, b in pd.items():
+        assert pd[b] == a, "pairing not symmetric"
+        lo, hi = (a, b) if C.dim(a) < C.dim(b) else (b, a)
+        assert C.dim(hi) == C.dim(lo) + 1
+        assert lo in C.facets(hi), "pair is not facet/cofacet"
+        assert maxv(lo) == maxv(hi), "pair leaves a lower star"
+    # acyclicity of the modified Hasse diagram: pair edges up, other facet edges down
+    succ = defaultdict(list)
+    indeg = defaultdict(int)
+    for c in C.cells():
+        for x in C.facets(c):
+            if pd.get(x) == c:
+                succ[x].append(c)
+                indeg[c] += 1
+            else:
+                succ[c].append(x)
+                indeg[x] += 1
+    queue = [c for c in C.cells() if indeg[c] == 0]
+    seen = 0
+    while queue:
+        c = queue.pop()
+        seen += 1
+        for d in succ[c]:
+            indeg[d] -= 1
+            if indeg[d] == 0:
+                queue.append(d)
+    assert seen == C.ncells(), "closed V-path found"
+    counts, _ = oracle.critical(_dims(f), pair)
+    assert counts[0] - counts[1] + counts[2] - counts[3] == 1
+    assert list(counts) == persistence_critical_counts(f)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_vertex_pairs_are_steepest_descent(seed):
+    f = random_field((5, 6, 7), seed, "ties" if seed % 2 else "normal")
+    nz, ny, nx = f.shape
+    C = Complex(_dims(f))
+    rank = vertex_rank(f)
+    pair = oracle.gradient(f)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                v = C.vid(x, y, z)
+                lower = []
+                for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    X, Y, Z = x + dx, y + dy, z + dz
+                    if 0 <= X < nx and 0 <= Y < ny and 0 <= Z < nz and rank[C.vid(X, Y, Z)] < rank[v]:
+                        lower.append((rank[C.vid(X, Y, Z)], (X, Y, Z)))
+                vc = C.cid((2 * x, 2 * y, 2 * z))
+                if not lower:
+                    assert pair[vc] == NONE
+                else:
+                    X, Y, Z = min(lower)[1]
+                    assert pair[vc] == C.cid((x + X, y + Y, z + Z))  # the edge between them
+
+
+def test_euler_on_medium_fields():
+    for f in (fields.grf((20, 24, 28), 3.0, seed=5), fields.batch_volume(7, lo=16, hi=24),
+              fields.gaussian_blobs(n=24, n_blobs=6, sigma_range=(2, 5), seed=3)):
+        counts, _ = oracle.critical(_dims(f), oracle.gradient(f))
+        assert counts[0] - counts[1] + counts[2] - counts[3] == 1
+
+
+def _grid(n):
+    i = np.arange(n, dtype=np.float64)
+    return np.meshgrid(i, i, i, indexing="ij")  # z, y, x
+
+
+@pytest.mark.parametrize("n", [5, 8, 9])
+def test_analytic_fields(n):
+    z, y, x = _grid(n)
+    c = (n - 1) / 2.0
+    r2 = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2
+    for f, want in ((r2, [1, 0, 0, 0]),
+                    (0.3 * x + 0.5 * y + 0.7 * z, [1, 0, 0, 0]),
+                    (-r2, [8, 12, 6, 1])):
+        f = np.ascontiguousarray(f.astype(np.float32))
+        counts, _ = oracle.critical(_dims(f), oracle.gradient(f))
+        assert list(counts) == want
+
+
+def test_cosine_lattice_counts():
+    """32^3 lattice: per axis minima at 8 and 24 and an interior maximum at 16 -> (8, 12, 6, 1)."""
+    f = fields.cosine_lattice()
+    counts, _ = oracle.critical(_dims(f), oracle.gradient(f))
+    assert list(counts) == [8, 12, 6, 1]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_dstar_matches_vpath_enumeration_and_paper_products(seed):
+    shp = [(4, 4, 4), (5, 5, 4), (3, 6, 5), (6, 5, 5)][seed % 4]
+    f = random_field(shp, 100 + seed, "normal" if seed < 6 else "ties")
+    d = _dims(f)
+    C = Complex(d)
+    r = oracle.compute_all(f)
+    s1, s2 = r["lists"][1], r["lists"][2]
+    rows, cols, cnt = r["dstar"]
+    got = {(int(s1[a]), int(s2[b])): int(c) for a, b, c in zip(rows, cols, cnt)}
+    assert got == vpath_counts(C, r["pair"], s1, s2)
+    prod, iters = paper_iterated_product(r["minor"])
+    assert {(int(s1[a]), int(s2[b])): v for (a, b), v in prod.items()} == got
+    assert iters == r["n_iter"]
+
+
+def test_adjacent_saddles_two_node_component():
+    """Fig. "msc-max-min-dag" (c): a 2-saddle adjacent to a 1-saddle gives a direct DAG edge."""
+    found = 0
+    for seed in range(40):
+        f = random_field((4, 4, 4), 500 + seed)
+        r = oracle.compute_all(f)
+        C = Complex(_dims(f))
+        s1 = [int(c) for c in r["lists"][1]]
+        s2 = [int(c) for c in r["lists"][2]]
+        rows, cols, cnt = r["dstar"]
+        got = {(s1[a], s2[b]): int(c) for a, b, c in zip(rows, cols, cnt)}
+        D = {(s1[a], s2[b]): int(m) for a, b, m in zip(*r["minor"]["D"])}
+        for t in s2:
+            for e in C.facets(t):
+                if e in set(s1):
+                    found += 1
+                    assert D.get((e, t), 0) >= 1 and got[(e, t)] >= 1
+    assert found > 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_min_labels_are_steepest_descent(seed):
+    f = random_field((6, 5, 7), 200 + seed, "ties" if seed % 2 else "normal")
+    nz, ny, nx = f.shape
+    C = Complex(_dims(f))
+    rank = vertex_rank(f)
+    r = oracle.compute_all(f, with_minor=False, with_dstar=False)
+    vmin = r["vertex_min"].reshape(-1)
+    for v0 in range(nx * ny * nz):
+        v = v0
+        while True:
+            x, y, z = v % nx, (v // nx) % ny, v // (nx * ny)
+            best = None
+            for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                X, Y, Z = x + dx, y + dy, z + dz
+                if 0 <= X < nx and 0 <= Y < ny and 0 <= Z < nz:
+                    w = C.vid(X, Y, Z)
+                    if rank[w] < rank[v] and (best is None or rank[w] < rank[best]):
+                        best = w
+            if best is None:
+                break
+            v = best
+        x, y, z = v % nx, (v // nx) % ny, v // (nx * ny)
+        assert vmin[v0] == C.cid((2 * x, 2 * y, 2 * z))
+    # 1-saddle arcs are the destinations of the edge's two vertices, lower coordinate first
+    for i, e in enumerate(r["lists"][1]):
+        a, b = sorted(C.vertices(int(e)))
+        assert (r["min_arcs"][2 * i], r["min_arcs"][2 * i + 1]) == (vmin[a], vmin[b])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_max_labels_properties(seed):
+    f = random_field((6, 7, 5), 300 + seed)
+    nz, ny, nx = f.shape
+    C = Complex(_dims(f))
+    rank = vertex_rank(f)
+    r = oracle.compute_all(f, with_minor=False, with_dstar=False)
+    pd = pairs_dict(r["pair"])
+    cmax = r["cube_max"]
+    maxes = set(int(c) for c in r["lists"][3])
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                lab = int(cmax[z, y, x])
+                if x == nx - 1 or y == ny - 1 or z == nz - 1:
+                    assert lab == NONE
+                    continue
+                c = C.cid((2 * x + 1, 2 * y + 1, 2 * z + 1))
+                if c in maxes:
+                    assert lab == c
+                    continue
+                assert lab == NONE or lab in maxes
+                if lab != NONE:
+                    top = lambda cell: max(rank[v] for v in C.vertices(cell))
+                    assert top(lab) >= top(c)
+                q = pd[c]
+                other = [k for k in C.cofacets(q) if k != c]
+                if not other:
+                    assert lab == NONE
+                else:
+                    ox, oy, oz = (v // 2 for v in C.coords(other[0]))
+                    assert lab == int(cmax[oz, oy, ox])
+    for i, q in enumerate(r["lists"][2]):
+        cc = C.coords(int(q))
+        k = [a for a in range(3) if cc[a] % 2 == 0][0]
+        for side, s in enumerate((-1, 1)):
+            d = list(cc)
+            d[k] += s
+            want = int(cmax[d[2] // 2, d[1] // 2, d[0] // 2]) if C.inside(d) else NONE
+            assert r["max_arcs"][2 * i + side] == want
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_reachable_and_junctions(seed):
+    f = random_field((5, 6, 5), 400 + seed)
+    nz, ny, nx = f.shape
+    C = Complex(_dims(f))
+    r = oracle.compute_all(f)
+    pd = pairs_dict(r["pair"])
+    s1 = set(int(c) for c in r["lists"][1])
+    s2 = set(int(c) for c in r["lists"][2])
+
+    def out(e):
+        res = []
+        for q in C.cofacets(e):
+            if pd.get(e) == q:
+                continue
+            if q in s2:
+                res.append(q)
+            elif C.dim(pd[q]) == 1:
+                res.append(pd[q])
+        return res
+
+    vis = r["visited"]
+
+    def visited(e):
+        cx, cy, cz = C.coords(e)
+        axis = 0 if cx & 1 else (1 if cy & 1 else 2)
+        return bool((vis[cz // 2, cy // 2, cx // 2] >> axis) & 1)
+
+    # every 1-cell on a V-path between saddles is reachable; the set is closed under out-edges
+    nodes = [e for e in C.cells() if C.dim(e) == 1 and (e in s1 or C.dim(pd[e]) == 2)]
+    for e in nodes:
+        if visited(e):
+            for w in out(e):
+                assert w in s2 or visited(w)
+    for e in s1:
+        assert visited(e)
+    marked = sum(int(np.unpackbits(np.array([b], dtype=np.uint8)).sum()) for b in vis.reshape(-1))
+    assert marked == sum(visited(e) for e in nodes)
+    want_j = sorted(e for e in nodes if visited(e) and e not in s1 and len(out(e)) > 1)
+    assert [int(j) for j in r["junctions"]] == want_j
+
+
+def test_nan_rejected_and_infinities_ordered():
+    f = random_field((3, 3, 3), 1)
+    g = f.copy()
+    g[1, 1, 1] = np.nan
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.gradient(g)
+    assert e.value.status == 2
+    h = f.copy()
+    h[0, 0, 0] = -np.inf
+    h[2, 2, 2] = np.inf
+    counts, _ = oracle.critical(_dims(h), oracle.gradient(h))
+    assert counts[0] - counts[1] + counts[2] - counts[3] == 1
+    # -0 and +0 compare equal: ties are broken by vertex index only
+    z = np.zeros((2, 2, 2), dtype=np.float32)
+    z[0, 0, 0] = -0.0
+    assert list(oracle.critical((2, 2, 2), oracle.gradient(z))[0]) == [1, 0, 0, 0]
+
+
+def test_packed_at_matches_full_pack():
+    f = fields.grf((9, 10, 11), 3.0, seed=9)
+    pair = oracle.gradient(f)
+    full = oracle.pack(_dims(f), pair).reshape(-1)
+    verts = np.arange(full.size)
+    assert np.array_equal(oracle.packed_at(f, verts), full)
