@@ -1,0 +1,167 @@
+/*
+ * msc.h -- C ABI of libmsc: the Morse-Smale complex 1-skeleton of a float32 scalar field
+ * on a 3D structured grid, computed on one GPU (arXiv:2009.03707, Subhash, Pandey,
+ * Natarajan, "A GPU Parallel Algorithm for Computing Morse-Smale Complexes").
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * Grid:   dims = {nx, ny, nz} vertex counts (each >= 2).  The field is float32, vertex
+ *         (x,y,z) at index x + nx*(y + ny*z) (a C-contiguous [nz][ny][nx] array).
+ * Cells:  the cubical complex of the grid lives on the refined grid
+ *         R = (2nx-1) x (2ny-1) x (2nz-1) (Sec. 2.2): cell (cx,cy,cz) has dimension =
+ *         number of odd coordinates, and cell id = cx + (2nx-1)*(cy + (2ny-1)*cz), a
+ *         uint32 (grids whose cell count does not fit return MSC_ERR_TOO_LARGE).
+ * Order:  vertices are ordered by (value, index); IEEE comparison (-0 == +0, +-Inf are
+ *         ordered); a NaN anywhere in the field is MSC_ERR_NAN.
+ * NONE:   0xFFFFFFFF marks "no cell" in arcs and labels.
+ * Memory: pointers named d_* are device pointers.  Buffers returned through `const T**`
+ *         are owned by the plan and stay valid until the next msc_gradient on the same
+ *         plan or msc_plan_destroy.  Host buffers are caller-owned.
+ * Streams: every call enqueues its work on `stream` (a cudaStream_t).  Calls that return
+ *         counts on the host synchronise that stream before returning.  One plan must not
+ *         be used from two host threads at once.
+ * Errors: every call returns an msc_status; msc_last_error_string(plan) describes the
+ *         last failure of that plan.  After MSC_ERR_CUDA the plan should be destroyed.
+ */
+#ifndef MSC_H_
+#define MSC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* msc_stream_t; /* identical to cudaStream_t */
+
+typedef enum msc_status {
+    MSC_OK = 0,
+    MSC_ERR_ARG = 1,        /* a null pointer, a dimension < 2, an out-of-range selector */
+    MSC_ERR_NAN = 2,        /* the field holds a NaN */
+    MSC_ERR_OOM = 3,        /* a device allocation failed */
+    MSC_ERR_TOO_LARGE = 4,  /* cell ids would not fit in 32 bits */
+    MSC_ERR_OVERFLOW = 6,   /* a saddle-saddle path count exceeds 2^64 - 1 */
+    MSC_ERR_ITER_LIMIT = 7, /* an iterative stage exceeded its iteration cap */
+    MSC_ERR_TIMEOUT = 8,    /* a bounded device wait gave up */
+    MSC_ERR_CUDA = 9,       /* a CUDA runtime error (message in msc_last_error_string) */
+    MSC_NOT_READY = 10,     /* msc_poll: the ticket has not finished yet */
+    MSC_ERR_STATE = 11      /* a stage was requested before msc_gradient */
+} msc_status;
+
+typedef struct msc_plan_s* msc_plan_t;
+
+/* Plan options (all fields may be zero for defaults). */
+typedef struct msc_opts {
+    int64_t max_iterations; /* cap on every iterative stage; 0 = 1<<20 */
+    int32_t flags;          /* reserved, must be 0 */
+    int32_t reserved;
+} msc_opts;
+
+/* Per-stage diagnostics (Sec. 4.2 "performance analysis" quantities). Times are the
+ * device time of the last run of each stage, from CUDA events on the plan's stream. */
+typedef struct msc_stats {
+    int64_t counts[4];        /* critical cells by index: min, 1-saddle, 2-saddle, max */
+    int64_t n_reachable;      /* 1-cells reachable from 1-saddles (1-saddles included) */
+    int64_t n_bfs_levels;     /* non-empty BFS levels, level 0 = the 1-saddles */
+    int64_t n_junctions;      /* junction nodes of the DAG minor */
+    int64_t nnz_A, nnz_B, nnz_Bstar, nnz_D, nnz_Dstar;
+    int64_t n_iter;           /* non-zero iterates A B^k of the product loop */
+    int64_t n_pointer_jumps;  /* pointer-jumping rounds of the extremum forests */
+    uint64_t max_path_count;  /* largest entry of D* */
+    int64_t peak_device_bytes;
+    float ms_gradient, ms_critical, ms_extremum, ms_reachability, ms_minor, ms_path_count;
+} msc_stats;
+
+/* ---- plan ----------------------------------------------------------------------------
+ * Creates a plan for one grid shape on the current CUDA device.  The plan owns every
+ * device buffer of the pipeline; they are grown on demand and reused across runs.
+ * dims: host array {nx, ny, nz}, each >= 2.  opts: nullable.  *out receives the plan. */
+msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out);
+msc_status msc_plan_destroy(msc_plan_t plan);
+const char* msc_last_error_string(msc_plan_t plan);
+
+/* ---- (a1) discrete gradient ----------------------------------------------------------
+ * Sec. 3 / Sec. 3.5 "Gradient pairs and critical points": every cell of the grid is paired
+ * with a facet or cofacet, or left critical, by the lower-star rule (Robins, Wood, Sheppard
+ * 2011, cited in Sec. 1.1): the cells whose maximal vertex is x are processed together.
+ * d_field: caller-owned device float32 field, valid until `stream` reaches this call.
+ * Result (plan-owned, read with msc_gradient_words): one uint32 word per vertex; vertex
+ * (x,y,z) owns the 8 cells (2x+a, 2y+b, 2z+c), a,b,c in {0,1}; slot s = a + 2b + 4c holds
+ * a 3-bit code in bits [3s, 3s+3): 0 = critical, 1..6 = paired with the neighbouring cell
+ * at -x,+x,-y,+y,-z,+z on the refined grid, 7 = no such cell (beyond the far boundary).
+ * Returns MSC_ERR_NAN (checked when the next call synchronises) if the field has a NaN. */
+msc_status msc_gradient(msc_plan_t plan, const float* d_field, msc_stream_t stream);
+msc_status msc_gradient_words(msc_plan_t plan, const uint32_t** d_words);
+
+/* ---- (a2) critical cells -------------------------------------------------------------
+ * Sec. 3.5 "Gradient pairs and critical points": critical cells are counted and
+ * stream-compacted.  counts: host int64[4], filled after a stream synchronisation.
+ * d_cells[k]: plan-owned device list of the critical k-cells' ids in increasing cell-id
+ * order (counts[k] entries).  d_cells may be null when only the counts are wanted. */
+msc_status msc_critical(msc_plan_t plan, msc_stream_t stream, int64_t counts[4], const uint32_t* d_cells[4]);
+
+/* ---- (a3) saddle-extremum arcs and manifold labels -----------------------------------
+ * Sec. 3.4 and Sec. 3.5 "Saddle-Extrema arcs": gradient paths from every cell are followed
+ * to their extremum by pointer jumping.
+ * d_vertex_min_label: [nz][ny][nx] uint32, the cell id of the minimum that the descending
+ *   path from each vertex reaches.
+ * d_cube_max_label:   [nz][ny][nx] uint32, entry (x,y,z) for the cube (2x+1,2y+1,2z+1): the
+ *   cell id of the maximum its ascending path reaches, NONE if the path leaves the domain
+ *   through a boundary quad, NONE where x = nx-1, y = ny-1 or z = nz-1.
+ * d_min_arcs: 2 per 1-saddle (in d_cells[1] order): the minima of its lower-coordinate and
+ *   upper-coordinate vertex.
+ * d_max_arcs: 2 per 2-saddle (in d_cells[2] order): the maxima of its cofacet cube on the
+ *   - side and + side of the quad's even axis (NONE if the cube does not exist or the
+ *   path leaves the domain).
+ * Any output pointer may be null. */
+msc_status msc_extremum_arcs(msc_plan_t plan, msc_stream_t stream, const uint32_t** d_min_arcs,
+                             const uint32_t** d_max_arcs, const uint32_t** d_vertex_min_label,
+                             const uint32_t** d_cube_max_label);
+
+/* ---- (a4) saddle-saddle reachability ---------------------------------------------------
+ * Sec. 3.2 and Sec. 3.5 "Saddle-Saddle reachability": a frontier BFS from all 1-saddles
+ * over the DAG of 1-2 gradient pairs (Fig. "msc-max-min-dag" (d)), moving against the
+ * gradient: a 1-cell e leads to the 1-cell paired with each cofacet quad q != pair(e)
+ * (when q is paired with a facet) or to q itself (when q is a 2-saddle).
+ * d_visited: plan-owned bitmap in the 1-cell row layout: word index
+ *   (((z*2 + c)*ny + y)*2 + b)*W + w, W = ceil(nx/32), bit (x & 31) with w = x >> 5, for
+ *   the 1-cell (2x+a, 2y+b, 2z+c), a = 1-b-c (rows with b = c = 1 are unused).
+ * n_words: number of words in d_visited.  n_levels: host, non-empty BFS levels. */
+msc_status msc_reachability(msc_plan_t plan, msc_stream_t stream, const uint32_t** d_visited, int64_t* n_words,
+                            int64_t* n_levels);
+
+/* ---- (a5) junction nodes and the DAG minor ---------------------------------------------
+ * Sec. 3.3 "DAG minor construction" and Sec. 3.5 "Gradient path counting": a junction is a
+ * reachable 1-cell, not a 1-saddle, with DAG out-degree > 1; simple paths from every
+ * 1-saddle and junction are traced to the first junction or 2-saddle (dead ends dropped).
+ * msc_junctions: d_cells = junction ids in increasing cell-id order, n = count (host).
+ * msc_minor: which = 0 A (1-saddle x junction), 1 B (junction x junction), 2 B* (junction x
+ *   2-saddle), 3 D (1-saddle x 2-saddle); CSR with rows/cols by rank in the d_cells[1],
+ *   junction and d_cells[2] lists, columns increasing within a row, uint32 multiplicities.
+ *   rowptr has rows+1 entries; nnz and rows are returned on the host. */
+msc_status msc_junctions(msc_plan_t plan, msc_stream_t stream, const uint32_t** d_cells, int64_t* n);
+msc_status msc_minor(msc_plan_t plan, msc_stream_t stream, int which, int64_t* rows, int64_t* nnz,
+                     const int64_t** d_rowptr, const uint32_t** d_col, const uint32_t** d_mult);
+
+/* ---- (a6) saddle-saddle arcs with multiplicity -----------------------------------------
+ * Sec. 3.3 "Path counting via matrix operations": D* = D + sum_{k>=0} A B^k B*, iterating
+ * A <- A B while the product is non-zero; every entry is the exact number of gradient paths
+ * between a 1-saddle and a 2-saddle, in uint64 (MSC_ERR_OVERFLOW if one exceeds 2^64-1).
+ * CSR over 1-saddle ranks (rows = counts[1], rowptr has rows+1 int64 entries), columns are
+ * 2-saddle ranks increasing within a row.  nnz: host. */
+msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, const int64_t** d_rowptr,
+                           const uint32_t** d_col, const uint64_t** d_count);
+
+/* Runs every stage (a1..a6) on `stream` for one field; equivalent to the calls above in
+ * order.  Results are read afterwards with the getters (they do no further work). */
+msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t stream);
+
+msc_status msc_get_stats(msc_plan_t plan, msc_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSC_H_ */

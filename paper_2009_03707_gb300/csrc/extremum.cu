@@ -1,0 +1,197 @@
+// (a3) Saddle-extremum arcs and the destination extremum of every vertex and cube.
+//
+// Sec. 3.4 and Sec. 3.5 "Saddle-Extrema arcs": gradient paths that end at extrema only merge
+// or only split, so following them is root finding in a forest, done by pointer jumping.
+//  * Vertex forest: a vertex paired with edge (v,w) points to w; a minimum points to itself.
+//  * Cube forest: a cube paired with quad q points to the other cube of q; a maximum points
+//    to itself; a cube whose quad lies on the domain boundary points to NONE (the path leaves
+//    the domain).
+// Labels are vertex indices while jumping (every cube is named by its owner vertex), and
+// become cell ids at the end.  Each jump round lets every thread follow up to JUMPS links,
+// updating its own entry in place; the paper's ping-pong buffers are not needed because any
+// value a thread reads is an ancestor of the one it replaces.  Rounds repeat until no entry
+// changes (a device flag, capped by the plan's iteration limit).
+#include "msc_internal.cuh"
+
+namespace msc {
+
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int JUMPS = 16;
+constexpr uint32_t NO_LINK = 0xFFFFFFFFu;
+
+// Initial links.  lab_v[v] = the vertex across v's paired edge, or v for a minimum.
+// lab_c[v] = owner of the cube across the quad paired with v's cube, v for a maximum,
+// NO_LINK if that quad is on the boundary or v owns no cube.
+__global__ void __launch_bounds__(THREADS) init_links(Geom g, const uint32_t* __restrict__ words,
+                                                      uint32_t* __restrict__ lab_v, uint32_t* __restrict__ lab_c,
+                                                      uint32_t* __restrict__ status) {
+    const int64_t v = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (v >= g.nverts) return;
+    const uint32_t w = words[v];
+    const int x = int(v % g.nx), y = int((v / g.nx) % g.ny), z = int(v / (int64_t(g.nx) * g.ny));
+    // vertex slot 0
+    const uint32_t cv = slot_code(w, 0);
+    int64_t pv = v;
+    if (cv >= 1 && cv <= 6) {
+        const int axis = (cv - 1) >> 1, sign = (cv & 1) ? -1 : 1;
+        int o[3] = {x, y, z};
+        const int n[3] = {g.nx, g.ny, g.nz};
+        o[axis] += sign;
+        if (o[axis] >= 0 && o[axis] < n[axis]) pv = g.vid(o[0], o[1], o[2]);
+        else atomicOr(status, ST_INTERNAL);  // a vertex paired with an edge that leaves the grid
+    }
+    lab_v[v] = uint32_t(pv);
+    // cube slot 7
+    const uint32_t cc = slot_code(w, 7);
+    uint32_t pc = NO_LINK;
+    if (cc == 0) {
+        pc = uint32_t(v);
+    } else if (cc <= 6) {
+        const int axis = (cc - 1) >> 1, sign = (cc & 1) ? -1 : 1;
+        int o[3] = {x, y, z};
+        const int n[3] = {g.nx, g.ny, g.nz};
+        o[axis] += sign;
+        if (o[axis] >= 0 && o[axis] <= n[axis] - 2) pc = uint32_t(g.vid(o[0], o[1], o[2]));
+    }
+    lab_c[v] = pc;
+}
+
+// One round of in-place pointer jumping over both forests.
+__global__ void __launch_bounds__(THREADS) jump_round(int64_t n, uint32_t* __restrict__ lab_v,
+                                                      uint32_t* __restrict__ lab_c, uint32_t* __restrict__ changed) {
+    const int64_t v = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (v >= n) return;
+    bool open = false;
+    {
+        uint32_t p = lab_v[v], start = p;
+        for (int j = 0; j < JUMPS; ++j) {
+            uint32_t q = lab_v[p];
+            if (q == p) break;
+            p = q;
+        }
+        if (p != start) lab_v[v] = p;
+        open |= lab_v[p] != p;
+    }
+    {
+        uint32_t p = lab_c[v], start = p;
+        if (p != NO_LINK) {
+            for (int j = 0; j < JUMPS; ++j) {
+                uint32_t q = lab_c[p];
+                if (q == p || q == NO_LINK) {
+                    p = q == NO_LINK ? NO_LINK : p;
+                    break;
+                }
+                p = q;
+            }
+            if (p != start) lab_c[v] = p;
+            open |= p != NO_LINK && lab_c[p] != p;
+        }
+    }
+    if (open) *changed = 1;
+}
+
+// Vertex indices -> cell ids of the extremum (in place).
+__global__ void __launch_bounds__(THREADS) finish_labels(Geom g, uint32_t* __restrict__ lab_v,
+                                                         uint32_t* __restrict__ lab_c) {
+    const int64_t v = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (v >= g.nverts) return;
+    auto cell_of = [&](uint32_t u, int off) {
+        const int x = int(u % uint32_t(g.nx)), y = int((u / uint32_t(g.nx)) % uint32_t(g.ny)),
+                  z = int(u / (uint32_t(g.nx) * uint32_t(g.ny)));
+        return g.cell_id(2 * x + off, 2 * y + off, 2 * z + off);
+    };
+    lab_v[v] = cell_of(lab_v[v], 0);
+    const uint32_t c = lab_c[v];
+    lab_c[v] = c == NO_LINK ? NONE : cell_of(c, 1);
+}
+
+struct CellCoord {
+    int x, y, z;
+};
+
+__device__ __forceinline__ CellCoord decode_cell(const Geom& g, uint32_t id) {
+    CellCoord c;
+    c.x = int(id % g.rx);
+    uint32_t q = id / g.rx;
+    c.y = int(q % g.ry);
+    c.z = int(q / g.ry);
+    return c;
+}
+
+// 1-saddle arcs: the minima of the edge's lower-coordinate and upper-coordinate vertices.
+__global__ void __launch_bounds__(THREADS) min_arcs_kernel(Geom g, const uint32_t* __restrict__ s1, int64_t n1,
+                                                           const uint32_t* __restrict__ vmin,
+                                                           uint32_t* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (i >= n1) return;
+    CellCoord c = decode_cell(g, s1[i]);
+    int lo[3] = {c.x >> 1, c.y >> 1, c.z >> 1};
+    int hi[3] = {(c.x + 1) >> 1, (c.y + 1) >> 1, (c.z + 1) >> 1};
+    out[2 * i] = vmin[g.vid(lo[0], lo[1], lo[2])];
+    out[2 * i + 1] = vmin[g.vid(hi[0], hi[1], hi[2])];
+}
+
+// 2-saddle arcs: the maxima of the quad's cofacet cubes on the - and + side of its even axis.
+__global__ void __launch_bounds__(THREADS) max_arcs_kernel(Geom g, const uint32_t* __restrict__ s2, int64_t n2,
+                                                           const uint32_t* __restrict__ cmax,
+                                                           uint32_t* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (i >= n2) return;
+    CellCoord c = decode_cell(g, s2[i]);
+    int cc[3] = {c.x, c.y, c.z};
+    const int axis = !(cc[0] & 1) ? 0 : !(cc[1] & 1) ? 1 : 2;
+    const int extent[3] = {2 * g.nx - 1, 2 * g.ny - 1, 2 * g.nz - 1};
+    for (int side = 0; side < 2; ++side) {
+        int d[3] = {cc[0], cc[1], cc[2]};
+        d[axis] += side ? 1 : -1;
+        uint32_t lab = NONE;
+        if (d[axis] >= 0 && d[axis] < extent[axis]) lab = cmax[g.vid(d[0] >> 1, d[1] >> 1, d[2] >> 1)];
+        out[2 * i + side] = lab;
+    }
+}
+
+int blocks(int64_t n) { return int((n + THREADS - 1) / THREADS); }
+
+}  // namespace
+
+msc_status run_extremum(Plan* p, cudaStream_t s) {
+    const Geom& g = p->g;
+    msc_status st;
+    if ((st = ensure(p, p->vmin, sizeof(uint32_t) * size_t(g.nverts)))) return st;
+    if ((st = ensure(p, p->cmax, sizeof(uint32_t) * size_t(g.nverts)))) return st;
+    if ((st = ensure(p, p->flag, sizeof(uint32_t) * 4))) return st;
+    if ((st = ensure(p, p->min_arcs, sizeof(uint32_t) * size_t(2 * p->counts[1] + 1)))) return st;
+    if ((st = ensure(p, p->max_arcs, sizeof(uint32_t) * size_t(2 * p->counts[2] + 1)))) return st;
+    auto* vmin = static_cast<uint32_t*>(p->vmin.ptr);
+    auto* cmax = static_cast<uint32_t*>(p->cmax.ptr);
+    auto* flag = static_cast<uint32_t*>(p->flag.ptr);
+    init_links<<<blocks(g.nverts), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), vmin, cmax,
+                                                     static_cast<uint32_t*>(p->status.ptr));
+    int64_t rounds = 0;
+    uint32_t more = 1;
+    while (more) {
+        if (rounds >= p->opts.max_iterations) return fail(p, MSC_ERR_ITER_LIMIT, "pointer jumping did not converge");
+        if ((st = check_cuda(p, cudaMemsetAsync(flag, 0, sizeof(uint32_t), s), "memset flag"))) return st;
+        jump_round<<<blocks(g.nverts), THREADS, 0, s>>>(g.nverts, vmin, cmax, flag);
+        if ((st = check_cuda(p, cudaMemcpyAsync(&more, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
+                             "flag copy")))
+            return st;
+        if ((st = check_cuda(p, cudaStreamSynchronize(s), "jump sync"))) return st;
+        ++rounds;
+    }
+    p->stats.n_pointer_jumps = rounds;
+    finish_labels<<<blocks(g.nverts), THREADS, 0, s>>>(g, vmin, cmax);
+    if (p->counts[1])
+        min_arcs_kernel<<<blocks(p->counts[1]), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[1].ptr),
+                                                                 p->counts[1], vmin,
+                                                                 static_cast<uint32_t*>(p->min_arcs.ptr));
+    if (p->counts[2])
+        max_arcs_kernel<<<blocks(p->counts[2]), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[2].ptr),
+                                                                 p->counts[2], cmax,
+                                                                 static_cast<uint32_t*>(p->max_arcs.ptr));
+    return check_cuda(p, cudaGetLastError(), "extremum launch");
+}
+
+}  // namespace msc

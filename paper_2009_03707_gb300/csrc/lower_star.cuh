@@ -1,0 +1,193 @@
+// Lower-star pairing of one vertex (a1) on 27-bit masks; host+device so the same code can
+// be exercised on the CPU.
+//
+// The star of vertex x is indexed by position p = 9*(dz+1) + 3*(dy+1) + (dx+1) of the offset
+// d in {-1,0,1}^3 of the cell 2x+d on the refined grid (p = 13 is x itself).  The vertex at
+// offset d has the same position index.  The rule is ProcessLowerStars (Robins, Wood and
+// Sheppard 2011, the locally independent gradient the paper cites in Sec. 1.1 and uses in
+// Sec. 3): x is paired with its lowest edge; cells of the lower star with exactly one
+// unclassified facet wait in queue "one", the others in queue "zero"; "one" is drained first
+// (pairing each popped cell with its free facet), then the least cell of "zero" becomes
+// critical; a popped cell that is already classified is skipped.
+//
+// Everything is a 27-bit mask: membership in L(x) (a cell is in L(x) iff all its vertices
+// other than x are lower, i.e. every sub-offset is lower), facets through x (clear one
+// non-zero component), cofacets (set one zero component), the classified set and both
+// queues.  The order of cells is a rank bitmask: rank the vertices of L(x), give each cell
+// the OR of its vertices' rank bits; comparing these integers compares the cells' vertex
+// lists sorted downwards lexicographically.
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDA_ARCH__
+#define MSC_FFS(x) __ffs(x)
+#define MSC_POPC(x) __popc(x)
+#else
+#define MSC_FFS(x) __builtin_ffs(int(x))
+#define MSC_POPC(x) __builtin_popcount(x)
+#endif
+
+namespace msc {
+namespace star {
+
+constexpr int CENTER = 13;
+constexpr uint32_t ALL = 0x7FFFFFFu;
+// positions with dx = -1 / 0 / +1, dy = -1 / 0 / +1, dz = -1 / 0 / +1
+constexpr uint32_t XN = 0x1249249u, XZ = XN << 1, XP = XN << 2;
+constexpr uint32_t YN = 0x1C0E07u, YZ = YN << 3, YP = YN << 6;
+constexpr uint32_t ZN = 0x1FFu, ZZ = ZN << 9, ZP = ZN << 18;
+constexpr uint32_t DIM1 = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
+constexpr uint32_t DIM3 =
+    (1u << 0) | (1u << 2) | (1u << 6) | (1u << 8) | (1u << 18) | (1u << 20) | (1u << 24) | (1u << 26);
+constexpr uint32_t DIM2 = ALL & ~DIM1 & ~DIM3 & ~(1u << CENTER);
+
+__host__ __device__ constexpr int pdx(int p) { return p % 3 - 1; }
+__host__ __device__ constexpr int pdy(int p) { return (p / 3) % 3 - 1; }
+__host__ __device__ constexpr int pdz(int p) { return p / 9 - 1; }
+
+__host__ __device__ constexpr uint32_t facet_mask(int p) {
+    return (pdx(p) ? 1u << (p - pdx(p)) : 0u) | (pdy(p) ? 1u << (p - 3 * pdy(p)) : 0u) |
+           (pdz(p) ? 1u << (p - 9 * pdz(p)) : 0u);
+}
+__host__ __device__ constexpr uint32_t cofacet_mask(int p) {
+    return (pdx(p) ? 0u : (1u << (p - 1)) | (1u << (p + 1))) | (pdy(p) ? 0u : (1u << (p - 3)) | (1u << (p + 3))) |
+           (pdz(p) ? 0u : (1u << (p - 9)) | (1u << (p + 9)));
+}
+
+// 3-bit direction code of the partner at position q seen from the cell at position p.
+__host__ __device__ inline uint32_t dir_code(int p, int q) {
+    int d = q - p;
+    return d == -1 ? 1u : d == 1 ? 2u : d == -3 ? 3u : d == 3 ? 4u : d == -9 ? 5u : 6u;
+}
+
+// Cells of the star in L(x): AND of the "lower" mask over every projection of the offset.
+__host__ __device__ inline uint32_t lower_star_mask(uint32_t lower_with_center) {
+    uint32_t m = lower_with_center;
+    m &= ((m >> 1) & XN) | ((m << 1) & XP) | XZ;
+    m &= ((m >> 3) & YN) | ((m << 3) & YP) | YZ;
+    m &= ((m >> 9) & ZN) | ((m << 9) & ZP) | ZZ;
+    return m & ALL;
+}
+
+// Per-thread scratch: vertex keys and cell keys of the 27 positions.  On the device they
+// live in shared memory with a [position][thread] layout (stride = threads per CTA).
+struct Scratch {
+    uint32_t* vkey;
+    uint32_t* ckey;
+    int stride;
+    __host__ __device__ uint32_t& v(int p) const { return vkey[p * stride]; }
+    __host__ __device__ uint32_t& c(int p) const { return ckey[p * stride]; }
+};
+
+__host__ __device__ inline int pop_min(uint32_t mask, const Scratch& sc) {
+    int best = MSC_FFS(mask) - 1;
+    uint32_t bk = sc.c(best);
+    mask &= mask - 1;
+    while (mask) {
+        int p = MSC_FFS(mask) - 1;
+        mask &= mask - 1;
+        uint32_t k = sc.c(p);
+        if (k < bk) {
+            bk = k;
+            best = p;
+        }
+    }
+    return best;
+}
+
+__host__ __device__ inline bool one_free_facet(int q, uint32_t inL, uint32_t cls) {
+    return MSC_POPC(facet_mask(q) & inL & ~cls) == 1;
+}
+
+// Pairs the cells of L(x) given the 27 vertex order keys k[] (k[13] = x; an off-grid vertex
+// has key 0xFFFFFFFF).  Vertices with equal keys are ordered by position, which is their
+// index order.  emit(p, code) is called for every non-critical cell with its direction code.
+// Returns false if the procedure did not classify every cell (an internal error).
+template <class Emit>
+__host__ __device__ bool process_lower_star(const uint32_t* k, const Scratch& sc, Emit&& emit) {
+    const uint32_t kc = k[CENTER];
+    uint32_t lower = 1u << CENTER;
+#pragma unroll
+    for (int p = 0; p < 27; ++p) {
+        if (p == CENTER) continue;
+        bool lo = (k[p] < kc) || (k[p] == kc && p < CENTER);
+        lower |= uint32_t(lo) << p;
+    }
+    const uint32_t inL = lower_star_mask(lower);
+    if (inL == (1u << CENTER)) return true;  // a minimum: every code stays 0
+
+    // rank the vertices of L(x) other than x
+    const uint32_t V = inL & ~(1u << CENTER);
+#pragma unroll
+    for (int p = 0; p < 27; ++p) sc.v(p) = k[p];
+    for (uint32_t a = V; a; a &= a - 1) {
+        int p = MSC_FFS(a) - 1;
+        uint32_t kp = sc.v(p);
+        int r = 0;
+        for (uint32_t b = V; b; b &= b - 1) {
+            int q = MSC_FFS(b) - 1;
+            uint32_t kq = sc.v(q);
+            r += (kq < kp) || (kq == kp && q < p);
+        }
+        sc.c(p) = 1u << r;
+    }
+    // cell keys in increasing dimension: own vertex bit | keys of the facets through x
+    for (uint32_t a = V & DIM2; a; a &= a - 1) {
+        int p = MSC_FFS(a) - 1;
+        uint32_t key = sc.c(p);
+        for (uint32_t f = facet_mask(p); f; f &= f - 1) key |= sc.c(MSC_FFS(f) - 1);
+        sc.c(p) = key;
+    }
+    for (uint32_t a = V & DIM3; a; a &= a - 1) {
+        int p = MSC_FFS(a) - 1;
+        uint32_t key = sc.c(p);
+        for (uint32_t f = facet_mask(p); f; f &= f - 1) key |= sc.c(MSC_FFS(f) - 1);
+        sc.c(p) = key;
+    }
+
+    const int delta = pop_min(inL & DIM1, sc);
+    uint32_t cls = (1u << CENTER) | (1u << delta);
+    emit(CENTER, dir_code(CENTER, delta));
+    emit(delta, dir_code(delta, CENTER));
+    uint32_t pq0 = inL & DIM1 & ~(1u << delta);
+    uint32_t pq1 = 0;
+    for (uint32_t c = cofacet_mask(delta) & inL & ~cls; c; c &= c - 1) {
+        int q = MSC_FFS(c) - 1;
+        if (one_free_facet(q, inL, cls)) pq1 |= 1u << q;
+    }
+    for (int guard = 0; guard < 64; ++guard) {
+        while (pq1) {
+            int a = pop_min(pq1, sc);
+            pq1 &= ~(1u << a);
+            if (cls & (1u << a)) continue;
+            uint32_t uf = facet_mask(a) & inL & ~cls;
+            if (uf == 0) {
+                pq0 |= 1u << a;
+                continue;
+            }
+            int pf = MSC_FFS(uf) - 1;  // the only unclassified facet
+            cls |= (1u << pf) | (1u << a);
+            pq0 &= ~(1u << pf);
+            emit(pf, dir_code(pf, a));
+            emit(a, dir_code(a, pf));
+            for (uint32_t c = (cofacet_mask(a) | cofacet_mask(pf)) & inL & ~cls; c; c &= c - 1) {
+                int q = MSC_FFS(c) - 1;
+                if (one_free_facet(q, inL, cls)) pq1 |= 1u << q;
+            }
+        }
+        if (!pq0) return cls == inL;
+        int c0 = pop_min(pq0, sc);
+        pq0 &= ~(1u << c0);
+        if (cls & (1u << c0)) continue;
+        cls |= 1u << c0;  // critical
+        for (uint32_t c = cofacet_mask(c0) & inL & ~cls; c; c &= c - 1) {
+            int q = MSC_FFS(c) - 1;
+            if (one_free_facet(q, inL, cls)) pq1 |= 1u << q;
+        }
+    }
+    return false;
+}
+
+}  // namespace star
+}  // namespace msc

@@ -1,0 +1,239 @@
+// (a5) DAG minor: simple-path tracing and the adjacency matrices A, B, B*, D.
+//
+// Sec. 3.3 "DAG minor construction" and Sec. 3.5 "Gradient path counting": every maximal
+// simple path of the reachable DAG is contracted to one edge.  From each out-edge of every
+// 1-saddle and junction the path follows the unique successor until it reaches a junction
+// or a 2-saddle; a path that runs into a node without successors is dropped.  Each traced
+// path is one unit of multiplicity of its (source, destination) entry in
+// A (1-saddle -> junction), B (junction -> junction), B* (junction -> 2-saddle) or
+// D (1-saddle -> 2-saddle).
+//
+// The paper traces all paths in lock step with a stream compaction per step and builds the
+// matrices through adjacency lists and cuSPARSE.  Here one thread traces its source's <= 4
+// paths to the end (no global step barrier), and the destinations -- ranked in O(1) from
+// the junction and critical-cell bitmaps -- are stored as a fixed 4-slot trace per source.
+// The path-count stage reads that trace directly as the minor's adjacency; CSR matrices are
+// built from it (count, scan, fill) for the ABI and the statistics.
+#include "dag.cuh"
+#include "rowscan.cuh"
+
+namespace msc {
+
+namespace {
+
+constexpr int THREADS = 256;
+int blocks(int64_t n) { return int((n + THREADS - 1) / THREADS); }
+
+__device__ __forceinline__ uint32_t bit_rank(const uint32_t* bits, const uint32_t* prefix, int64_t wi, int bit) {
+    return prefix[wi] + __popc(bits[wi] & ((1u << bit) - 1u));
+}
+
+struct TraceArgs {
+    Geom g;
+    const uint32_t* words;
+    const uint32_t* s1;
+    int64_t n1;
+    const uint32_t* junc_cells;
+    int64_t nj;
+    const uint32_t* junc_bits;
+    const uint32_t* junc_prefix;
+    const uint32_t* crit_bits;
+    const uint32_t* crit_prefix;
+    uint32_t* tgt;     // 4 per source: destination rank
+    uint8_t* kinds;    // per source: 2 bits per slot, 0 none / 1 junction / 2 2-saddle
+    int64_t max_steps;
+    uint32_t* status;
+};
+
+__global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
+    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (u >= a.n1 + a.nj) return;
+    const Geom& g = a.g;
+    const uint32_t id = u < a.n1 ? a.s1[u] : a.junc_cells[u - a.n1];
+    const int cx = int(id % g.rx), cy = int((id / g.rx) % g.ry), cz = int(id / g.rx / g.ry);
+    const int axis = (cx & 1) ? 0 : (cy & 1) ? 1 : 2;
+    DagTarget t[4];
+    const int n = dag_out(g, a.words, cx >> 1, cy >> 1, cz >> 1, axis, t);
+    uint32_t kinds = 0;
+    for (int k = 0; k < 4; ++k) {
+        uint32_t rank = 0, kind = 0;
+        if (k < n) {
+            DagTarget cur = t[k];
+            for (int64_t step = 0;; ++step) {
+                if (step > a.max_steps) {
+                    atomicOr(a.status, ST_ITER);
+                    break;
+                }
+                const Vtx q = vtx_of(g, cur.v);
+                if (cur.kind == 2) {  // a 2-saddle: rank among the critical 2-cells
+                    rank = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(cur.sub, q.z, q.y, q.x >> 5), q.x & 31);
+                    kind = 2;
+                    break;
+                }
+                const int64_t wi = edge_bitmap_word(g, q.x, q.y, q.z, cur.sub);
+                if ((a.junc_bits[wi] >> (q.x & 31)) & 1u) {
+                    rank = bit_rank(a.junc_bits, a.junc_prefix, wi, q.x & 31);
+                    kind = 1;
+                    break;
+                }
+                DagTarget nx[4];
+                const int m = dag_out(g, a.words, q.x, q.y, q.z, cur.sub, nx);
+                if (m == 0) break;  // dead path: dropped
+                if (m > 1) {        // cannot happen: every reachable non-junction has out-degree <= 1
+                    atomicOr(a.status, ST_INTERNAL);
+                    break;
+                }
+                cur = nx[0];
+            }
+        }
+        a.tgt[u * 4 + k] = rank;
+        kinds |= kind << (2 * k);
+    }
+    a.kinds[u] = uint8_t(kinds);
+}
+
+// Distinct destinations of one source among slots of kind `want`, sorted, with multiplicity.
+__device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t kinds, uint32_t want, uint32_t col[4],
+                                                uint32_t mult[4]) {
+    uint32_t v[4];
+    int n = 0;
+    for (int k = 0; k < 4; ++k)
+        if (((kinds >> (2 * k)) & 3u) == want) v[n++] = tgt[k];
+    for (int i = 1; i < n; ++i)  // insertion sort of <= 4 values
+        for (int j = i; j > 0 && v[j - 1] > v[j]; --j) {
+            uint32_t tmp = v[j];
+            v[j] = v[j - 1];
+            v[j - 1] = tmp;
+        }
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (m > 0 && col[m - 1] == v[i]) {
+            mult[m - 1] += 1;
+        } else {
+            col[m] = v[i];
+            mult[m] = 1;
+            ++m;
+        }
+    }
+    return m;
+}
+
+// which: 0 A, 1 B, 2 B*, 3 D.  Sources 0..n1-1 are 1-saddles (rows of A and D), n1.. are
+// junctions (rows of B and B*).
+struct CsrArgs {
+    int64_t n1, nj;
+    const uint32_t* tgt;
+    const uint8_t* kinds;
+    uint32_t* cnt[4];
+    const int64_t* rowptr[4];
+    uint32_t* col[4];
+    uint32_t* mult[4];
+};
+
+__global__ void __launch_bounds__(THREADS) csr_count(CsrArgs a) {
+    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (u >= a.n1 + a.nj) return;
+    uint32_t col[4], mult[4];
+    const bool saddle = u < a.n1;
+    const int64_t row = saddle ? u : u - a.n1;
+    const int mj = distinct_targets(a.tgt + 4 * u, a.kinds[u], 1, col, mult);
+    const int m2 = distinct_targets(a.tgt + 4 * u, a.kinds[u], 2, col, mult);
+    a.cnt[saddle ? 0 : 1][row] = uint32_t(mj);
+    a.cnt[saddle ? 3 : 2][row] = uint32_t(m2);
+}
+
+__global__ void __launch_bounds__(THREADS) csr_fill(CsrArgs a) {
+    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (u >= a.n1 + a.nj) return;
+    uint32_t col[4], mult[4];
+    const bool saddle = u < a.n1;
+    const int64_t row = saddle ? u : u - a.n1;
+    for (int want = 1; want <= 2; ++want) {
+        const int which = saddle ? (want == 1 ? 0 : 3) : (want == 1 ? 1 : 2);
+        const int m = distinct_targets(a.tgt + 4 * u, a.kinds[u], uint32_t(want), col, mult);
+        const int64_t base = a.rowptr[which][row];
+        for (int i = 0; i < m; ++i) {
+            a.col[which][base + i] = col[i];
+            a.mult[which][base + i] = mult[i];
+        }
+    }
+}
+
+}  // namespace
+
+msc_status run_minor(Plan* p, cudaStream_t s) {
+    const Geom& g = p->g;
+    msc_status st;
+    const int64_t n1 = p->counts[1], nj = p->n_junctions, nsrc = n1 + nj;
+    if ((st = ensure(p, p->trace, sizeof(uint32_t) * 4 * size_t(nsrc ? nsrc : 1)))) return st;
+    if ((st = ensure(p, p->trace_kinds, size_t(nsrc ? nsrc : 1)))) return st;
+    TraceArgs ta{};
+    ta.g = g;
+    ta.words = static_cast<const uint32_t*>(p->words.ptr);
+    ta.s1 = static_cast<const uint32_t*>(p->cells[1].ptr);
+    ta.n1 = n1;
+    ta.junc_cells = static_cast<const uint32_t*>(p->junc_cells.ptr);
+    ta.nj = nj;
+    ta.junc_bits = static_cast<const uint32_t*>(p->junc_bits.ptr);
+    ta.junc_prefix = static_cast<const uint32_t*>(p->junc_prefix.ptr);
+    ta.crit_bits = static_cast<const uint32_t*>(p->crit_bits.ptr);
+    ta.crit_prefix = static_cast<const uint32_t*>(p->crit_prefix.ptr);
+    ta.tgt = static_cast<uint32_t*>(p->trace.ptr);
+    ta.kinds = static_cast<uint8_t*>(p->trace_kinds.ptr);
+    ta.max_steps = p->opts.max_iterations;
+    ta.status = static_cast<uint32_t*>(p->status.ptr);
+    if (nsrc) trace_kernel<<<blocks(nsrc), THREADS, 0, s>>>(ta);
+    if ((st = check_cuda(p, cudaGetLastError(), "trace launch"))) return st;
+
+    // CSR of A, B, B*, D
+    const int64_t rows[4] = {n1, nj, nj, n1};
+    size_t cnt_elems = 0;
+    for (int w = 0; w < 4; ++w) cnt_elems += size_t(rows[w]);
+    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * (cnt_elems ? cnt_elems : 1)))) return st;
+    size_t scratch = 0;
+    for (int w = 0; w < 4; ++w) scratch = std::max(scratch, row_scan_scratch_bytes(rows[w]));
+    if ((st = ensure(p, p->minor_scan, scratch))) return st;
+    CsrArgs ca{};
+    ca.n1 = n1;
+    ca.nj = nj;
+    ca.tgt = ta.tgt;
+    ca.kinds = ta.kinds;
+    size_t off = 0;
+    for (int w = 0; w < 4; ++w) {
+        ca.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
+        off += size_t(rows[w]);
+        if ((st = ensure(p, p->minor_rowptr[w], sizeof(int64_t) * size_t(rows[w] + 1)))) return st;
+        ca.rowptr[w] = static_cast<const int64_t*>(p->minor_rowptr[w].ptr);
+        p->minor_rows[w] = rows[w];
+    }
+    if (nsrc) csr_count<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+    int64_t nnz[4];
+    for (int w = 0; w < 4; ++w) {
+        if ((st = check_cuda(p,
+                             row_scan(ca.cnt[w], rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr),
+                                      static_cast<unsigned long long*>(p->minor_scan.ptr), s),
+                             "minor row scan")))
+            return st;
+        if ((st = check_cuda(p, cudaMemcpyAsync(&nnz[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr) + rows[w],
+                                                sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                             "nnz copy")))
+            return st;
+        // the scratch is reused by the next matrix: finish this one first
+        if ((st = check_cuda(p, cudaStreamSynchronize(s), "minor sync"))) return st;
+    }
+    for (int w = 0; w < 4; ++w) {
+        p->minor_nnz[w] = nnz[w];
+        if ((st = ensure(p, p->minor_col[w], sizeof(uint32_t) * size_t(nnz[w] ? nnz[w] : 1)))) return st;
+        if ((st = ensure(p, p->minor_mult[w], sizeof(uint32_t) * size_t(nnz[w] ? nnz[w] : 1)))) return st;
+        ca.col[w] = static_cast<uint32_t*>(p->minor_col[w].ptr);
+        ca.mult[w] = static_cast<uint32_t*>(p->minor_mult[w].ptr);
+    }
+    if (nsrc) csr_fill<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+    p->stats.nnz_A = nnz[0];
+    p->stats.nnz_B = nnz[1];
+    p->stats.nnz_Bstar = nnz[2];
+    p->stats.nnz_D = nnz[3];
+    return check_cuda(p, cudaGetLastError(), "csr launch");
+}
+
+}  // namespace msc

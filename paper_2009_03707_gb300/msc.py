@@ -1,0 +1,224 @@
+"""Thin Python binding of libmsc (include/msc.h): argument marshalling only.
+
+Every function has the name of the C entry point it wraps and passes torch device
+pointers and the current CUDA stream straight through; all pipeline arithmetic runs in
+the library's CUDA kernels.  Plan-owned outputs are returned as zero-copy torch views
+(``__cuda_array_interface__``) that stay valid until the next ``msc_gradient`` on the
+same plan or its destruction -- clone them to keep them longer.  There is no CPU path:
+if the library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MSC_OK = 0
+STATUS_NAMES = {0: "MSC_OK", 1: "MSC_ERR_ARG", 2: "MSC_ERR_NAN", 3: "MSC_ERR_OOM", 4: "MSC_ERR_TOO_LARGE",
+                6: "MSC_ERR_OVERFLOW", 7: "MSC_ERR_ITER_LIMIT", 8: "MSC_ERR_TIMEOUT", 9: "MSC_ERR_CUDA",
+                10: "MSC_NOT_READY", 11: "MSC_ERR_STATE"}
+
+# Every symbol declared in include/msc.h with its ctypes signature.
+_P, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "msc_plan": ([_PI64, _P, _PP], _I32),
+    "msc_plan_destroy": ([_P], _I32),
+    "msc_last_error_string": ([_P], ctypes.c_char_p),
+    "msc_gradient": ([_P, _P, _P], _I32),
+    "msc_gradient_words": ([_P, _PP], _I32),
+    "msc_critical": ([_P, _P, _PI64, _PP], _I32),
+    "msc_extremum_arcs": ([_P, _P, _PP, _PP, _PP, _PP], _I32),
+    "msc_reachability": ([_P, _P, _PP, _PI64, _PI64], _I32),
+    "msc_junctions": ([_P, _P, _PP, _PI64], _I32),
+    "msc_minor": ([_P, _P, _I32, _PI64, _PI64, _PP, _PP, _PP], _I32),
+    "msc_saddle_arcs": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
+    "msc_compute": ([_P, _P, _P], _I32),
+    "msc_get_stats": ([_P, _P], _I32),
+}
+
+
+class MscStats(ctypes.Structure):
+    _fields_ = [("counts", ctypes.c_int64 * 4), ("n_reachable", ctypes.c_int64), ("n_bfs_levels", ctypes.c_int64),
+                ("n_junctions", ctypes.c_int64), ("nnz_A", ctypes.c_int64), ("nnz_B", ctypes.c_int64),
+                ("nnz_Bstar", ctypes.c_int64), ("nnz_D", ctypes.c_int64), ("nnz_Dstar", ctypes.c_int64),
+                ("n_iter", ctypes.c_int64), ("n_pointer_jumps", ctypes.c_int64),
+                ("max_path_count", ctypes.c_uint64), ("peak_device_bytes", ctypes.c_int64),
+                ("ms_gradient", ctypes.c_float), ("ms_critical", ctypes.c_float), ("ms_extremum", ctypes.c_float),
+                ("ms_reachability", ctypes.c_float), ("ms_minor", ctypes.c_float),
+                ("ms_path_count", ctypes.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["counts"] = list(self.counts)
+        return d
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libmsc.so is not built ({path}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+class MscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, plan=None, what=""):
+    if st != MSC_OK:
+        msg = lib.msc_last_error_string(plan).decode() if plan else what
+        raise MscError(st, msg or what)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class _DevArray:
+    """Zero-copy view of a plan-owned device buffer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def _view(ptr, shape, typestr):
+    n = 1
+    for s in shape:
+        n *= int(s)
+    if n == 0 or not ptr:
+        dt = {"<u4": torch.uint32, "<u8": torch.uint64, "<i8": torch.int64}[typestr]
+        return torch.empty(tuple(int(s) for s in shape), dtype=dt, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
+class Plan:
+    """Owns an msc_plan_t for one grid shape (nx, ny, nz)."""
+
+    def __init__(self, dims):
+        self.dims = tuple(int(d) for d in dims)
+        arr = (ctypes.c_int64 * 3)(*self.dims)
+        h = ctypes.c_void_p()
+        _check(lib.msc_plan(arr, None, ctypes.byref(h)), what=f"msc_plan{self.dims}")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib.msc_plan_destroy(h)
+            self.handle = None
+
+    @property
+    def shape_zyx(self):
+        nx, ny, nz = self.dims
+        return (nz, ny, nx)
+
+
+# ---- the C entry points, by name ---------------------------------------------------------
+def msc_plan(dims) -> Plan:
+    return Plan(dims)
+
+
+def msc_gradient(plan: Plan, field: torch.Tensor) -> None:
+    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    if tuple(field.shape) != plan.shape_zyx:
+        raise ValueError(f"field shape {tuple(field.shape)} does not match the plan {plan.shape_zyx}")
+    _check(lib.msc_gradient(plan.handle, ctypes.c_void_p(field.data_ptr()), _stream()), plan.handle)
+
+
+def msc_gradient_words(plan: Plan) -> torch.Tensor:
+    p = ctypes.c_void_p()
+    _check(lib.msc_gradient_words(plan.handle, ctypes.byref(p)), plan.handle)
+    return _view(p.value, plan.shape_zyx, "<u4")
+
+
+def msc_critical(plan: Plan):
+    counts = (ctypes.c_int64 * 4)()
+    cells = (ctypes.c_void_p * 4)()
+    _check(lib.msc_critical(plan.handle, _stream(), counts, cells), plan.handle)
+    return [int(c) for c in counts], [_view(cells[k], (counts[k],), "<u4") for k in range(4)]
+
+
+def msc_extremum_arcs(plan: Plan):
+    out = [ctypes.c_void_p() for _ in range(4)]
+    _check(lib.msc_extremum_arcs(plan.handle, _stream(), *[ctypes.byref(o) for o in out]), plan.handle)
+    counts, _ = msc_critical(plan)
+    return (_view(out[0].value, (2 * counts[1],), "<u4"), _view(out[1].value, (2 * counts[2],), "<u4"),
+            _view(out[2].value, plan.shape_zyx, "<u4"), _view(out[3].value, plan.shape_zyx, "<u4"))
+
+
+def msc_reachability(plan: Plan):
+    p = ctypes.c_void_p()
+    nw = ctypes.c_int64()
+    lv = ctypes.c_int64()
+    _check(lib.msc_reachability(plan.handle, _stream(), ctypes.byref(p), ctypes.byref(nw), ctypes.byref(lv)),
+           plan.handle)
+    return _view(p.value, (nw.value,), "<u4"), int(lv.value)
+
+
+def msc_junctions(plan: Plan):
+    p = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    _check(lib.msc_junctions(plan.handle, _stream(), ctypes.byref(p), ctypes.byref(n)), plan.handle)
+    return _view(p.value, (n.value,), "<u4")
+
+
+def msc_minor(plan: Plan, which: int):
+    rows, nnz = ctypes.c_int64(), ctypes.c_int64()
+    rp, col, mult = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.msc_minor(plan.handle, _stream(), which, ctypes.byref(rows), ctypes.byref(nnz), ctypes.byref(rp),
+                         ctypes.byref(col), ctypes.byref(mult)), plan.handle)
+    return (_view(rp.value, (rows.value + 1,), "<i8"), _view(col.value, (nnz.value,), "<u4"),
+            _view(mult.value, (nnz.value,), "<u4"))
+
+
+def msc_saddle_arcs(plan: Plan):
+    nnz = ctypes.c_int64()
+    rp, col, cnt = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.msc_saddle_arcs(plan.handle, _stream(), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(col),
+                               ctypes.byref(cnt)), plan.handle)
+    counts, _ = msc_critical(plan)
+    return (_view(rp.value, (counts[1] + 1,), "<i8"), _view(col.value, (nnz.value,), "<u4"),
+            _view(cnt.value, (nnz.value,), "<u8"))
+
+
+def msc_compute(plan: Plan, field: torch.Tensor) -> None:
+    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    if tuple(field.shape) != plan.shape_zyx:
+        raise ValueError(f"field shape {tuple(field.shape)} does not match the plan {plan.shape_zyx}")
+    _check(lib.msc_compute(plan.handle, ctypes.c_void_p(field.data_ptr()), _stream()), plan.handle)
+
+
+def msc_get_stats(plan: Plan) -> dict:
+    s = MscStats()
+    _check(lib.msc_get_stats(plan.handle, ctypes.byref(s)), plan.handle)
+    return s.as_dict()
+
+
+def compute(field: torch.Tensor, plan: Plan | None = None) -> dict:
+    """All outputs of the pipeline for one device field, as torch tensors on its device."""
+    nz, ny, nx = field.shape
+    plan = plan or Plan((nx, ny, nz))
+    msc_compute(plan, field)
+    counts, cells = msc_critical(plan)
+    min_arcs, max_arcs, vmin, cmax = msc_extremum_arcs(plan)
+    rowptr, col, cnt = msc_saddle_arcs(plan)
+    return dict(plan=plan, counts=counts, cells=cells, min_arcs=min_arcs, max_arcs=max_arcs, vertex_min=vmin,
+                cube_max=cmax, dstar=(rowptr, col, cnt), stats=msc_get_stats(plan))

@@ -1,0 +1,108 @@
+"""Parity of stages (a1) lower-star gradient and (a2) critical cells: CUDA path (through the
+C ABI) vs the CPU oracle, bit-exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+from tests.cubical import random_field
+from tests.gpu_util import dims_of, msc, run_gradient
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_fields():
+    out = [("cos32", fields.cosine_lattice())]
+    shapes = [(2, 2, 2), (3, 5, 7), (9, 8, 33), (10, 9, 34), (17, 16, 65), (20, 40, 70), (5, 3, 100), (64, 1 + 1, 3)]
+    for i, shp in enumerate(shapes):
+        out.append((f"normal{shp}", random_field(shp, 700 + i, "normal")))
+        out.append((f"ties{shp}", random_field(shp, 800 + i, "ties")))
+    out.append(("grf48", fields.grf((48, 48, 48), 3.0, seed=11)))
+    out.append(("blobs40", fields.gaussian_blobs(n=40, n_blobs=12, sigma_range=(2, 6), seed=4)))
+    inf = random_field((6, 7, 8), 3)
+    inf[0, 0, 0], inf[5, 6, 7], inf[2, 3, 4] = -np.inf, np.inf, np.inf
+    inf[1, 1, 1] = -0.0
+    inf[1, 1, 2] = 0.0
+    out.append(("inf_zero", inf))
+    return out
+
+
+@pytest.mark.parametrize("name,f", _small_fields(), ids=[n for n, _ in _small_fields()])
+def test_gradient_and_critical_match_oracle(name, f):
+    d = dims_of(f)
+    pair = oracle.gradient(f)
+    want_words = oracle.pack(d, pair)
+    want_counts, want_lists = oracle.critical(d, pair)
+    _, words, counts, lists, _ = run_gradient(f)
+    assert np.array_equal(words, want_words), f"{int((words != want_words).sum())} packed words differ"
+    assert counts == [int(c) for c in want_counts]
+    for k in range(4):
+        assert np.array_equal(lists[k], want_lists[k]), f"critical {k}-cells differ"
+
+
+def test_plan_reuse_and_repeat():
+    f1 = random_field((12, 13, 40), 1)
+    f2 = random_field((12, 13, 40), 2)
+    m = msc()
+    plan = m.Plan(dims_of(f1))
+    for f in (f1, f2, f1):
+        _, words, counts, lists, _ = run_gradient(f, plan)
+        pair = oracle.gradient(f)
+        assert np.array_equal(words, oracle.pack(dims_of(f), pair))
+        assert counts == [int(c) for c in oracle.critical(dims_of(f), pair)[0]]
+
+
+def test_nan_is_rejected():
+    f = random_field((8, 8, 8), 5)
+    f[3, 4, 5] = np.nan
+    m = msc()
+    with pytest.raises(m.MscError) as e:
+        run_gradient(f)
+    assert e.value.status == 2
+
+
+def test_bad_arguments():
+    m = msc()
+    with pytest.raises(m.MscError):
+        m.Plan((1, 4, 4))
+    plan = m.Plan((4, 4, 4))
+    with pytest.raises(m.MscError) as e:
+        m.msc_critical(plan)  # before msc_gradient
+    assert e.value.status == 11
+
+
+@pytest.mark.slow
+def test_grf256_sampled_parity():
+    """256^3 k^-3 GRF (the bench workload): packed words at sampled vertices vs the oracle's
+    per-vertex lower stars, and properties of the full critical lists."""
+    f = fields.config_field("grf256")
+    _, words, counts, lists, _ = run_gradient(f)
+    nz, ny, nx = f.shape
+    rng = np.random.default_rng(0)
+    sample = rng.integers(0, nx * ny * nz, size=4000)
+    # plus a full 40x12x12 box that straddles CTA tiles
+    z, y, x = np.meshgrid(np.arange(100, 112), np.arange(60, 72), np.arange(20, 60), indexing="ij")
+    box = (x + nx * (y + ny * z)).reshape(-1)
+    verts = np.concatenate([sample, box, [0, nx * ny * nz - 1]])
+    want = oracle.packed_at(f, verts)
+    assert np.array_equal(words.reshape(-1)[verts], want)
+    assert counts[0] - counts[1] + counts[2] - counts[3] == 1
+    for k in range(4):
+        assert np.all(np.diff(lists[k].astype(np.int64)) > 0), "lists must be strictly increasing"
+        assert len(lists[k]) == counts[k]
+    # every listed cell is critical in the packed words, and every critical slot is listed
+    rx, ry = 2 * nx - 1, 2 * ny - 1
+    flat = words.reshape(-1)
+    total = 0
+    for k in range(4):
+        c = lists[k].astype(np.int64)
+        cx, cy, cz = c % rx, (c // rx) % ry, c // (rx * ry)
+        assert np.all((cx & 1) + (cy & 1) + (cz & 1) == k)
+        slot = (cx & 1) + 2 * (cy & 1) + 4 * (cz & 1)
+        code = (flat[(cx // 2) + nx * ((cy // 2) + ny * (cz // 2))] >> (3 * slot)) & 7
+        assert np.all(code == 0)
+        total += len(c)
+    codes = (flat[:, None] >> (3 * np.arange(8))[None, :]) & 7
+    assert int((codes == 0).sum()) == total

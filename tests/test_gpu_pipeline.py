@@ -1,0 +1,96 @@
+"""Parity of stages (a3)-(a6) through the C ABI against the CPU oracle, bit-exact:
+extremum labels and arcs, reachability (visited bitmap and level count), junctions, the
+minor matrices A, B, B*, D, and the saddle-saddle path counts D*."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+from tests.cubical import random_field
+from tests.gpu_util import csr_to_coo, dims_of, edge_layout, gpu_field, msc, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    out = [("cos32", fields.cosine_lattice()), ("grf40", fields.grf((40, 40, 40), 3.0, seed=12)),
+           ("grf25x30x70", fields.grf((25, 30, 70), 2.5, seed=13)),
+           ("blobs36", fields.gaussian_blobs(n=36, n_blobs=10, sigma_range=(2, 6), seed=5))]
+    for i, shp in enumerate([(2, 2, 2), (3, 4, 5), (6, 6, 6), (9, 8, 33), (5, 3, 65)]):
+        out.append((f"normal{shp}", random_field(shp, 900 + i, "normal")))
+        out.append((f"ties{shp}", random_field(shp, 950 + i, "ties")))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.fixture(scope="module")
+def results():
+    m = msc()
+    res = {}
+    for name, f in CASES:
+        plan = m.Plan(dims_of(f))
+        d = gpu_field(f)
+        m.msc_compute(plan, d)
+        counts, cells = m.msc_critical(plan)
+        amin, amax, vmin, cmax = m.msc_extremum_arcs(plan)
+        vis, levels = m.msc_reachability(plan)
+        junc = m.msc_junctions(plan)
+        minor = [tuple(to_np(x) for x in m.msc_minor(plan, w)) for w in range(4)]
+        dstar = tuple(to_np(x) for x in m.msc_saddle_arcs(plan))
+        res[name] = dict(counts=counts, cells=[to_np(c) for c in cells], min_arcs=to_np(amin),
+                         max_arcs=to_np(amax), vmin=to_np(vmin), cmax=to_np(cmax), visited=to_np(vis),
+                         levels=levels, junctions=to_np(junc), minor=minor, dstar=dstar,
+                         stats=m.msc_get_stats(plan))
+    return res
+
+
+@pytest.fixture(scope="module")
+def expected():
+    return {name: oracle.compute_all(f) for name, f in CASES}
+
+
+IDS = [n for n, _ in CASES]
+
+
+@pytest.mark.parametrize("name", IDS)
+def test_extremum(name, results, expected):
+    r, e = results[name], expected[name]
+    assert np.array_equal(r["vmin"], e["vertex_min"])
+    assert np.array_equal(r["cmax"], e["cube_max"])
+    assert np.array_equal(r["min_arcs"], e["min_arcs"])
+    assert np.array_equal(r["max_arcs"], e["max_arcs"])
+
+
+@pytest.mark.parametrize("name", IDS)
+def test_reachability(name, results, expected):
+    r, e = results[name], expected[name]
+    assert np.array_equal(r["visited"], edge_layout(e["visited"]))
+    assert r["levels"] == e["levels"]
+    assert r["stats"]["n_reachable"] == int(sum(bin(int(v)).count("1") for v in e["visited"].reshape(-1)))
+
+
+@pytest.mark.parametrize("name", IDS)
+def test_junctions_and_minor(name, results, expected):
+    r, e = results[name], expected[name]
+    assert np.array_equal(r["junctions"], e["junctions"])
+    for w, key in enumerate(oracle.MINOR_NAMES):
+        rows, cols, mult = csr_to_coo(*r["minor"][w])
+        er, ec, em = e["minor"][key]
+        assert np.array_equal(rows, er) and np.array_equal(cols, ec), key
+        assert np.array_equal(mult.astype(np.uint64), em), key
+
+
+@pytest.mark.parametrize("name", IDS)
+def test_dstar(name, results, expected):
+    r, e = results[name], expected[name]
+    rows, cols, cnt = csr_to_coo(*r["dstar"])
+    er, ec, en = e["dstar"]
+    assert np.array_equal(rows, er)
+    assert np.array_equal(cols, ec)
+    assert np.array_equal(cnt, en)
+    assert r["stats"]["n_iter"] == e["n_iter"]
+    assert r["stats"]["nnz_Dstar"] == len(er)
