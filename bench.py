@@ -1,0 +1,358 @@
+"""End-to-end Morse-Smale complex 1-skeleton throughput on GB300 (Mvoxel/s).
+
+One step = the whole hot path (lower-star gradient, critical cells, saddle-extremum arcs,
+saddle-saddle reachability, DAG minor, D* path counts) over one synthetic volume, through
+the library's C ABI.  The default workload is the 256^3 float32 Gaussian random field with
+P(k) ~ k^-3 (seed 1).  The timed region starts with the field resident in HBM; the L2 is
+flushed (a 256 MB write) before every timed step.  A second pass times the same steps
+end to end from pinned host memory (H2D of the field, D2H of the 1-skeleton).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the plain CPU oracle (the only other implementation of this path)
+on bounded crops of the same workload on the host cores.  With N > 1 (torchrun) every rank
+runs an independent replica on its own GPU (the path does not shard; no collective is on
+the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "grf256": "256^3 float32 Gaussian random field, P(k) ~ k^-3, zero mean, unit variance, seed 1",
+    "blobs512": "512^3 float32 sum of 2000 Gaussian blobs (sigma 2-20, amplitude U[-1,1]) + N(0,1e-3), seed 2",
+    "cos32": "32^3 float32 cos(2 pi x/16)+cos(2 pi y/16)+cos(2 pi z/16) + U[0,1e-3], seed 0",
+}
+METRIC = "end-to-end MS-complex Mvoxel/s on 1 GB300 (batched vs plain) + per-stage HBM GB/s"
+L2_FLUSH_BYTES = 256 << 20
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+           0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+           0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _field(name):
+    from synth import fields
+
+    return fields.config_field(name)
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        time.sleep(0.15)
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                active = int(parts[3], 16)
+            except Exception:
+                continue
+            for bit, name in REASONS.items():
+                if active & bit and name != "gpu_idle":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+def _traffic_record(kernel):
+    """DRAM bytes per unit of one ncu capture, if the kernel's sources are unchanged since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for rel in rec["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec
+
+
+def cpu_baseline(field, seconds_hint=""):
+    """The oracle as it stands, single-threaded, on a bounded crop of the workload."""
+    import numpy as np
+
+    import oracle
+
+    crop = np.ascontiguousarray(field[:64, :96, :96])
+    t = time.perf_counter()
+    oracle.compute_all(crop)
+    dt = time.perf_counter() - t
+    nvox = crop.size
+    return {"value": nvox / dt / 1e6, "unit": "Mvoxel/s", "cores": 1, "kind": "oracle",
+            "sample": f"full pipeline on the 96x96x64 corner crop ({nvox} voxels) of the workload field, "
+                      f"one oracle run of {dt:.1f} s on {os.cpu_count()} host cores (oracle uses 1)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    f = _field(args.workload)
+    crop = np.ascontiguousarray(f[:48, :48, :48])
+    for _ in range(args.warmup):
+        oracle.compute_all(crop)
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.compute_all(crop)
+        times.append(time.perf_counter() - t)
+    total = time.perf_counter() - t0
+    ms = 1e3 * total / args.steps
+    value = crop.size / (total / args.steps) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32-compare/u64-count", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                       "sample": "48^3 corner crop per step (the oracle cannot run the full volume in a bench step)"},
+            "cpu_baseline": {"value": value, "unit": "Mvoxel/s", "cores": 1, "kind": "oracle",
+                             "sample": f"48^3 corner crop ({crop.size} voxels) per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2009_03707_gb300 import msc
+
+    f = _field(args.workload)
+    nz, ny, nx = f.shape
+    nvox = f.size
+    plan = msc.Plan((nx, ny, nz))
+    d_field = torch.from_numpy(f).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        msc.msc_compute(plan, d_field)
+    torch.cuda.synchronize()
+    stats = msc.msc_get_stats(plan)
+
+    # ---- device-resident timing -------------------------------------------------------
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    step_ms, stage_ms, kernel_ms = [], [], {"gradient_kernel": [], "rows_warp": []}
+    launches = 0
+    barrier()
+    with ClockSampler(uuid) as clk:
+        t_region = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(2.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            msc.msc_compute(plan, d_field)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            st = msc.msc_get_stats(plan)
+            launches += int(st["n_launches"])
+            stage_ms.append(st)
+            kernel_ms["gradient_kernel"].append(st["ms_gradient"])
+            kernel_ms["rows_warp"].append(st["ms_rows_kernel"])
+        barrier()
+        wall = time.perf_counter() - t_region
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nvox / (ms / 1e3) / 1e6
+
+    # ---- end to end from pinned host memory -------------------------------------------
+    h_field = torch.from_numpy(f).pin_memory()
+    counts = stats["counts"]
+    out_bufs = {}
+
+    def d2h(name, t):
+        n = t.numel() * t.element_size()
+        buf = out_bufs.get(name)
+        if buf is None or buf.numel() < n:
+            buf = out_bufs[name] = torch.empty(max(n, 1), dtype=torch.uint8, pin_memory=True)
+        if n:
+            buf[:n].copy_(t.view(torch.uint8).reshape(-1), non_blocking=True)
+        return n
+
+    e2e_ms = []
+    bo = 0
+    for i in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(3.0)
+        e0.record(stream)
+        d_field.copy_(h_field, non_blocking=True)
+        msc.msc_compute(plan, d_field)
+        _, cells = msc.msc_critical(plan)
+        amin, amax, _, _ = msc.msc_extremum_arcs(plan)
+        rowptr, col, cnt = msc.msc_saddle_arcs(plan)
+        nbytes = 0
+        for k in range(4):
+            nbytes += d2h(f"cells{k}", cells[k])
+        nbytes += d2h("amin", amin) + d2h("amax", amax)
+        nbytes += d2h("rowptr", rowptr) + d2h("col", col) + d2h("cnt", cnt)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+            bo = nbytes
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----------------------------------------------
+    peak, peak_kind = _peaks()
+    last = stage_ms[-1]
+    km = {k: statistics.median(v) for k, v in kernel_ms.items()}
+    algo = {"gradient_kernel": 8.0 * nvox,
+            "rows_warp": 17.0 * (counts[1] + last["n_frontier_entries"]) + 12.0 * last["nnz_Dstar"]}
+    units = {"gradient_kernel": nvox, "rows_warp": counts[1] + last["n_frontier_entries"]}
+    dom = max(km, key=km.get)
+    achieved = algo[dom] / (km[dom] / 1e3) / 1e9
+    rec = _traffic_record(dom)
+    traffic = None
+    if rec and rec.get("workload") == args.workload:
+        traffic = rec["bytes_per_unit"] * units[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel_ms": km[dom], "algorithmic_bytes": algo[dom]}
+
+    def med(key):
+        return statistics.median(s[key] for s in stage_ms)
+
+    stage_bytes = {"gradient": 8.0 * nvox, "critical": 1.0 * nvox + 4.0 * sum(counts),
+                   "extremum": 4.0 * nvox + 8.0 * nvox, "reachability": 4.0 * last["n_reachable"],
+                   "minor": 17.0 * (counts[1] + last["n_junctions"]),
+                   "path_count": algo["rows_warp"]}
+    stages = {}
+    for name in stage_bytes:
+        t = med("ms_" + name)
+        stages[name] = {"ms": t, "GB/s": stage_bytes[name] / (t / 1e3) / 1e9 if t > 0 else None}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-compare/u64-count", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "dims": [nx, ny, nz],
+                   "voxels_per_step": nvox, "parallelism": f"replicas x{world}",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "critical_counts": counts, "nnz_Dstar": last["nnz_Dstar"], "n_iter": last["n_iter"]},
+        "e2e": {"value": world * nvox / (e2e / 1e3) / 1e6, "unit": "Mvoxel/s",
+                "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(bo)},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "stages": stages,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(f)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["msc", "reference"], default="msc")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="grf256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

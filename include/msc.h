@@ -71,7 +71,11 @@ typedef struct msc_stats {
     int64_t n_pointer_jumps;  /* pointer-jumping rounds of the extremum forests */
     uint64_t max_path_count;  /* largest entry of D* */
     int64_t peak_device_bytes;
+    int64_t n_launches;       /* kernels this plan launched since the last msc_gradient */
     float ms_gradient, ms_critical, ms_extremum, ms_reachability, ms_minor, ms_path_count;
+    float ms_rows_kernel;      /* the row-wise product kernel alone (tier 1), CUDA events */
+    float ms_trace_kernel;     /* the simple-path tracing kernel alone, CUDA events */
+    int64_t n_frontier_entries; /* sum over 1-saddles and iterations of the frontier sizes */
 } msc_stats;
 
 /* ---- plan ----------------------------------------------------------------------------

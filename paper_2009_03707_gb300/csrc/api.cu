@@ -144,6 +144,8 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
                                   "cudaDeviceGetAttribute");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->ev0), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->ev1), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->kev0), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->kev1), "cudaEventCreate");
     if (!st) st = msc::ensure(p, p->status, sizeof(uint32_t) * 4);
     if (!st) st = msc::check_cuda(p, cudaMemset(p->status.ptr, 0, sizeof(uint32_t) * 4), "cudaMemset(status)");
     if (st) {
@@ -164,6 +166,8 @@ msc_status msc_plan_destroy(msc_plan_t plan) {
     });
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->kev0) cudaEventDestroy(p->kev0);
+    if (p->kev1) cudaEventDestroy(p->kev1);
     delete p;
     return MSC_OK;
 }
@@ -180,6 +184,7 @@ msc_status msc_gradient(msc_plan_t plan, const float* d_field, msc_stream_t stre
     msc_status st;
     if ((st = msc::bind_device(p))) return st;
     msc::invalidate(p);
+    p->stats.n_launches = 0;
     msc::StageTimer tm(p, s, &p->stats.ms_gradient);
     if ((st = msc::run_gradient(p, d_field, s))) return st;
     cudaEventRecord(p->ev1, s);  // stage time is read when the next stage synchronises

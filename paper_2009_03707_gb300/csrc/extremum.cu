@@ -169,12 +169,14 @@ msc_status run_extremum(Plan* p, cudaStream_t s) {
     auto* flag = static_cast<uint32_t*>(p->flag.ptr);
     init_links<<<blocks(g.nverts), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), vmin, cmax,
                                                      static_cast<uint32_t*>(p->status.ptr));
+    launched(p);
     int64_t rounds = 0;
     uint32_t more = 1;
     while (more) {
         if (rounds >= p->opts.max_iterations) return fail(p, MSC_ERR_ITER_LIMIT, "pointer jumping did not converge");
         if ((st = check_cuda(p, cudaMemsetAsync(flag, 0, sizeof(uint32_t), s), "memset flag"))) return st;
         jump_round<<<blocks(g.nverts), THREADS, 0, s>>>(g.nverts, vmin, cmax, flag);
+        launched(p);
         if ((st = check_cuda(p, cudaMemcpyAsync(&more, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
                              "flag copy")))
             return st;
@@ -183,14 +185,19 @@ msc_status run_extremum(Plan* p, cudaStream_t s) {
     }
     p->stats.n_pointer_jumps = rounds;
     finish_labels<<<blocks(g.nverts), THREADS, 0, s>>>(g, vmin, cmax);
-    if (p->counts[1])
+    launched(p);
+    if (p->counts[1]) {
         min_arcs_kernel<<<blocks(p->counts[1]), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[1].ptr),
                                                                  p->counts[1], vmin,
                                                                  static_cast<uint32_t*>(p->min_arcs.ptr));
-    if (p->counts[2])
+        launched(p);
+    }
+    if (p->counts[2]) {
         max_arcs_kernel<<<blocks(p->counts[2]), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[2].ptr),
                                                                  p->counts[2], cmax,
                                                                  static_cast<uint32_t*>(p->max_arcs.ptr));
+        launched(p);
+    }
     return check_cuda(p, cudaGetLastError(), "extremum launch");
 }
 

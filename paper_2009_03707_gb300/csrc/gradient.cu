@@ -141,6 +141,7 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, static_cast<uint32_t*>(p->words.ptr),
                                                 static_cast<uint32_t*>(p->crit_bits.ptr),
                                                 static_cast<uint32_t*>(p->status.ptr));
+    launched(p);
     return check_cuda(p, cudaGetLastError(), "gradient_kernel launch");
 }
 

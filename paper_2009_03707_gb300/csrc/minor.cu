@@ -182,7 +182,12 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     ta.kinds = static_cast<uint8_t*>(p->trace_kinds.ptr);
     ta.max_steps = p->opts.max_iterations;
     ta.status = static_cast<uint32_t*>(p->status.ptr);
-    if (nsrc) trace_kernel<<<blocks(nsrc), THREADS, 0, s>>>(ta);
+    cudaEventRecord(p->kev0, s);
+    if (nsrc) {
+        trace_kernel<<<blocks(nsrc), THREADS, 0, s>>>(ta);
+        launched(p);
+    }
+    cudaEventRecord(p->kev1, s);
     if ((st = check_cuda(p, cudaGetLastError(), "trace launch"))) return st;
 
     // CSR of A, B, B*, D
@@ -206,11 +211,14 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
         ca.rowptr[w] = static_cast<const int64_t*>(p->minor_rowptr[w].ptr);
         p->minor_rows[w] = rows[w];
     }
-    if (nsrc) csr_count<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+    if (nsrc) {
+        csr_count<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+        launched(p);
+    }
     int64_t nnz[4];
     for (int w = 0; w < 4; ++w) {
         if ((st = check_cuda(p,
-                             row_scan(ca.cnt[w], rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr),
+                             row_scan(p, ca.cnt[w], rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr),
                                       static_cast<unsigned long long*>(p->minor_scan.ptr), s),
                              "minor row scan")))
             return st;
@@ -228,7 +236,11 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
         ca.col[w] = static_cast<uint32_t*>(p->minor_col[w].ptr);
         ca.mult[w] = static_cast<uint32_t*>(p->minor_mult[w].ptr);
     }
-    if (nsrc) csr_fill<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+    if (nsrc) {
+        csr_fill<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+        launched(p);
+    }
+    if (cudaEventSynchronize(p->kev1) == cudaSuccess) cudaEventElapsedTime(&p->stats.ms_trace_kernel, p->kev0, p->kev1);
     p->stats.nnz_A = nnz[0];
     p->stats.nnz_B = nnz[1];
     p->stats.nnz_Bstar = nnz[2];

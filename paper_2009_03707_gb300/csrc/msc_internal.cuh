@@ -71,8 +71,11 @@ struct Plan {
     // which stages are valid for the current field
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
          have_junctions = false, have_minor = false, have_dstar = false;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;  // stage / kernel timing
 };
+
+// Counts one kernel launch of this plan (reported in msc_stats.n_launches).
+inline void launched(Plan* p, int n = 1) { p->stats.n_launches += n; }
 
 // Buffer helpers (api.cu): grow-only device allocations owned by the plan.
 msc_status ensure(Plan* p, DeviceBuffer& b, size_t bytes);

@@ -62,6 +62,7 @@ struct PcArgs {
     unsigned long long* next_source;
     unsigned long long* max_count;
     unsigned long long* n_iter;
+    unsigned long long* n_entries;  // sum of frontier sizes (for the roofline's byte count)
     int64_t max_iter;
     uint32_t* status;
 };
@@ -149,6 +150,7 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
         }
         group_sync<G>();
         if (n == 0 || bad) break;
+        if (r == 0) atomicAdd(a.n_entries, (unsigned long long)n);
         if (++iter > a.max_iter) {
             if (r == 0) atomicOr(a.status, ST_ITER);
             break;
@@ -327,6 +329,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         a.big_count = ctr + 2;
         a.max_count = ctr + 3;
         a.n_iter = ctr + 4;
+        a.n_entries = ctr + 6;
         a.row_start = static_cast<int64_t*>(p->pc_rowstart.ptr);
         a.row_len = static_cast<uint32_t*>(p->pc_rowlen.ptr);
         a.big = static_cast<uint32_t*>(p->pc_big.ptr);
@@ -335,13 +338,17 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         a.status = static_cast<uint32_t*>(p->status.ptr);
         if (n1) {
             const int grid = std::max(1, p->num_sms) * 4;
+            cudaEventRecord(p->kev0, s);
             rows_warp<<<grid, T1_WARPS * 32, 0, s>>>(a);
+            cudaEventRecord(p->kev1, s);
+            launched(p);
             if ((st = check_cuda(p, cudaGetLastError(), "rows_warp launch"))) return st;
         }
         unsigned long long h[8];
         if ((st = check_cuda(p, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s), "counter copy")))
             return st;
         if ((st = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return st;
+        if (n1) cudaEventElapsedTime(&p->stats.ms_rows_kernel, p->kev0, p->kev1);
         // deferred rows: CTAs with global tables, growing until every row fits
         int64_t nbig = int64_t(h[2]);
         uint32_t* list = static_cast<uint32_t*>(p->pc_big.ptr);
@@ -357,10 +364,12 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             if ((st = ensure(p, p->pc_gv, sizeof(unsigned long long) * slots))) return st;
             init_tables<<<1024, 256, 0, s>>>(static_cast<uint32_t*>(p->pc_gk.ptr),
                                              static_cast<unsigned long long*>(p->pc_gv.ptr), slots);
+            launched(p);
             if ((st = check_cuda(p, cudaMemsetAsync(ctr + 5, 0, sizeof(unsigned long long), s), "memset"))) return st;
             rows_block<<<ctas, T2_THREADS, 0, s>>>(a, list, nbig, static_cast<uint32_t*>(p->pc_gk.ptr),
                                                   static_cast<unsigned long long*>(p->pc_gv.ptr), cap_t, lg, next_list,
                                                   ctr + 5);
+            launched(p);
             if ((st = check_cuda(p, cudaGetLastError(), "rows_block launch"))) return st;
             unsigned long long still = 0;
             if ((st = check_cuda(p, cudaMemcpyAsync(&still, ctr + 5, sizeof(still), cudaMemcpyDeviceToHost, s),
@@ -388,17 +397,20 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         p->stats.nnz_Dstar = nnz;
         p->stats.max_path_count = h[3];
         p->stats.n_iter = int64_t(h[4]);
+        p->stats.n_frontier_entries = int64_t(h[6]);
         if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
         if ((st = ensure(p, p->dstar_count, sizeof(unsigned long long) * size_t(nnz ? nnz : 1)))) return st;
         if ((st = check_cuda(p,
-                             row_scan(a.row_len, n1, static_cast<int64_t*>(p->dstar_rowptr.ptr),
+                             row_scan(p, a.row_len, n1, static_cast<int64_t*>(p->dstar_rowptr.ptr),
                                       static_cast<unsigned long long*>(p->minor_scan.ptr), s),
                              "D* row scan")))
             return st;
-        if (n1)
+        if (n1) {
             gather_rows<<<int((n1 + 255) / 256), 256, 0, s>>>(
                 n1, a.row_start, static_cast<const int64_t*>(p->dstar_rowptr.ptr), a.out_col, a.out_cnt,
                 static_cast<uint32_t*>(p->dstar_col.ptr), static_cast<unsigned long long*>(p->dstar_count.ptr));
+            launched(p);
+        }
         return check_cuda(p, cudaGetLastError(), "gather launch");
     }
     return fail(p, MSC_ERR_CUDA, "internal: D* staging did not converge");

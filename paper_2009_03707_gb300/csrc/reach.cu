@@ -128,9 +128,11 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
                          "memset visited")))
         return st;
     int cur = 0;
-    if (n1)
+    if (n1) {
         bfs_seed<<<blocks(n1), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[1].ptr), n1, visited,
                                                 static_cast<uint32_t*>(p->frontier[0].ptr));
+        launched(p);
+    }
     int64_t ncur = n1, levels = 0, reached = n1;
     while (ncur > 0) {
         if (levels >= p->opts.max_iterations) return fail(p, MSC_ERR_ITER_LIMIT, "BFS exceeded the iteration cap");
@@ -143,6 +145,7 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
                                                     static_cast<const uint32_t*>(p->frontier[cur].ptr), ncur, visited,
                                                     static_cast<uint32_t*>(p->frontier[cur ^ 1].ptr), qcount,
                                                     uint64_t(cap), static_cast<uint32_t*>(p->status.ptr));
+        launched(p);
         unsigned long long nn = 0;
         if ((st = check_cuda(p, cudaMemcpyAsync(&nn, qcount, sizeof(nn), cudaMemcpyDeviceToHost, s), "qcount copy")))
             return st;
@@ -166,6 +169,7 @@ msc_status run_junctions(Plan* p, cudaStream_t s) {
     mark_junctions<<<blocks(nw), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr),
                                                   static_cast<const uint32_t*>(p->visited.ptr),
                                                   static_cast<uint32_t*>(p->junc_bits.ptr));
+    launched(p);
     if ((st = check_cuda(p, cudaGetLastError(), "mark_junctions launch"))) return st;
     EdgeSource src{};
     src.g = g;

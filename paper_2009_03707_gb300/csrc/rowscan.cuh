@@ -105,18 +105,20 @@ static __global__ void __launch_bounds__(RS_THREADS) rowscan_emit(const uint32_t
 static __global__ void rowscan_finish(int64_t* rowptr, int64_t n, const long long* total) { rowptr[n] = *total; }
 
 // rowptr (n+1 int64) from cnt (n uint32); scratch holds >= ceil(n/RS_CHUNK) + 1 uint64.
-inline cudaError_t row_scan(const uint32_t* cnt, int64_t n, int64_t* rowptr, unsigned long long* scratch,
-                            cudaStream_t s) {
+inline cudaError_t row_scan(Plan* p, const uint32_t* cnt, int64_t n, int64_t* rowptr,
+                            unsigned long long* scratch, cudaStream_t s) {
     const int nb = int((n + RS_CHUNK - 1) / RS_CHUNK);
     long long* total = reinterpret_cast<long long*>(scratch + (nb > 0 ? nb : 1));
     if (nb > 0) {
         rowscan_reduce<<<nb, RS_THREADS, 0, s>>>(cnt, n, scratch);
         rowscan_top<<<1, 1024, 0, s>>>(scratch, nb, total);
         rowscan_emit<<<nb, RS_THREADS, 0, s>>>(cnt, n, scratch, rowptr);
+        launched(p, 3);
     } else {
         cudaMemsetAsync(total, 0, sizeof(long long), s);
     }
     rowscan_finish<<<1, 1, 0, s>>>(rowptr, n, total);
+    launched(p);
     return cudaGetLastError();
 }
 

@@ -217,6 +217,7 @@ msc_status compaction_count(Plan* p, cudaStream_t s, const Src& src, int nseq, u
     auto* totals = static_cast<unsigned long long*>(p->totals.ptr);
     scan_reduce_kernel<Src><<<bps * nseq, SCAN_THREADS, 0, s>>>(src, len, bps, sums);
     scan_top_kernel<<<nseq, 1024, 0, s>>>(sums, bps, totals);
+    launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "scan launch"))) return st;
     if ((st = check_cuda(p, cudaMemcpyAsync(host_totals, totals, sizeof(unsigned long long) * size_t(nseq),
                                             cudaMemcpyDeviceToHost, s),
@@ -232,6 +233,7 @@ msc_status compaction_emit(Plan* p, cudaStream_t s, const Src& src, int nseq) {
     const int bps = int((len + SCAN_CHUNK - 1) / SCAN_CHUNK);
     auto* sums = static_cast<unsigned long long*>(p->scan_sums.ptr);
     scan_emit_kernel<Src><<<bps * nseq, SCAN_THREADS, 0, s>>>(src, len, bps, sums);
+    launched(p);
     return check_cuda(p, cudaGetLastError(), "scan emit launch");
 }
 

@@ -48,9 +48,11 @@ class MscStats(ctypes.Structure):
                 ("nnz_Bstar", ctypes.c_int64), ("nnz_D", ctypes.c_int64), ("nnz_Dstar", ctypes.c_int64),
                 ("n_iter", ctypes.c_int64), ("n_pointer_jumps", ctypes.c_int64),
                 ("max_path_count", ctypes.c_uint64), ("peak_device_bytes", ctypes.c_int64),
+                ("n_launches", ctypes.c_int64),
                 ("ms_gradient", ctypes.c_float), ("ms_critical", ctypes.c_float), ("ms_extremum", ctypes.c_float),
                 ("ms_reachability", ctypes.c_float), ("ms_minor", ctypes.c_float),
-                ("ms_path_count", ctypes.c_float)]
+                ("ms_path_count", ctypes.c_float), ("ms_rows_kernel", ctypes.c_float),
+                ("ms_trace_kernel", ctypes.c_float), ("n_frontier_entries", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
