@@ -47,7 +47,8 @@ typedef enum msc_status {
     MSC_ERR_TIMEOUT = 8,    /* a bounded device wait gave up */
     MSC_ERR_CUDA = 9,       /* a CUDA runtime error (message in msc_last_error_string) */
     MSC_NOT_READY = 10,     /* msc_poll: the ticket has not finished yet */
-    MSC_ERR_STATE = 11      /* a stage was requested before msc_gradient */
+    MSC_ERR_STATE = 11,     /* a stage was requested before msc_gradient */
+    MSC_ERR_CAPACITY = 12   /* a caller-provided output buffer is too small (counts are still reported) */
 } msc_status;
 
 typedef struct msc_plan_s* msc_plan_t;
@@ -163,6 +164,35 @@ msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, c
 msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t stream);
 
 msc_status msc_get_stats(msc_plan_t plan, msc_stats* out);
+
+/* ---- (a1)+(a2) without any device allocation ---------------------------------------------
+ * The paper has no counterpart: this is a convenience for callers that cannot allocate device
+ * memory -- a host program that has already reserved the whole GPU for its own memory pool, or
+ * code running in a callback or a deadline-bound loop where a cudaMalloc (which may synchronise
+ * the device, and may fail) is not allowed.  It computes the same packed gradient and critical
+ * lists as msc_gradient + msc_critical, but needs no plan: all of its scratch (critical-cell
+ * bitmaps, their word prefixes, scan block sums and a status word) lives in one static device
+ * array of MSC_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until exit.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * dims: host {nx, ny, nz}.  d_field: caller-owned float32 field (as msc_gradient).
+ * d_words: caller-owned output, nx*ny*nz uint32 in the msc_gradient word layout.
+ * d_cells[k], capacity[k]: caller-owned output lists of the critical k-cells (increasing cell
+ *   id) and their capacities in entries.  counts: host int64[4], filled before returning.
+ * Size limit: 8 * (8 * nz * ny * ceil(nx/32)) bytes of bitmaps and prefixes plus the scan sums
+ *   must fit in MSC_STATIC_SCRATCH_BYTES (about 200^3 vertices); larger grids return
+ *   MSC_ERR_TOO_LARGE before any GPU work.  If a count exceeds its capacity the lists are not
+ *   written, counts are still filled, and MSC_ERR_CAPACITY is returned.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents: calls that overlap on the GPU (two
+ * streams, or two host threads) race on it and must be serialised by the caller.  The call
+ * synchronises `stream` once (to read the counts); the lists are complete when `stream`
+ * reaches the end of the call. */
+#define MSC_STATIC_SCRATCH_BYTES (16u << 20)
+msc_status msc_gradient_critical_static(const int64_t dims[3], const float* d_field, uint32_t* d_words,
+                                        uint32_t* const d_cells[4], const int64_t capacity[4], int64_t counts[4],
+                                        msc_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -145,4 +145,16 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     return check_cuda(p, cudaGetLastError(), "gradient_kernel launch");
 }
 
+// Launch of the same kernel on caller-supplied buffers, with no plan and no allocation (used by
+// the no-allocation entry point, static_entry.cu).
+cudaError_t launch_gradient_raw(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
+                                uint32_t* status, cudaStream_t s) {
+    const size_t smem = sizeof(Shared);
+    cudaError_t e = cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+    gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, words, crit_bits, status);
+    return cudaGetLastError();
+}
+
 }  // namespace msc

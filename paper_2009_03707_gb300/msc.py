@@ -19,7 +19,9 @@ from . import build as _build
 MSC_OK = 0
 STATUS_NAMES = {0: "MSC_OK", 1: "MSC_ERR_ARG", 2: "MSC_ERR_NAN", 3: "MSC_ERR_OOM", 4: "MSC_ERR_TOO_LARGE",
                 6: "MSC_ERR_OVERFLOW", 7: "MSC_ERR_ITER_LIMIT", 8: "MSC_ERR_TIMEOUT", 9: "MSC_ERR_CUDA",
-                10: "MSC_NOT_READY", 11: "MSC_ERR_STATE"}
+                10: "MSC_NOT_READY", 11: "MSC_ERR_STATE", 12: "MSC_ERR_CAPACITY"}
+MSC_ERR_CAPACITY = 12
+MSC_STATIC_SCRATCH_BYTES = 16 << 20
 
 # Every symbol declared in include/msc.h with its ctypes signature.
 _P, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
@@ -39,6 +41,7 @@ SIGNATURES = {
     "msc_saddle_arcs": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
+    "msc_gradient_critical_static": ([_PI64, _P, _P, _PP, _PI64, _PI64, _P], _I32),
 }
 
 
@@ -212,6 +215,31 @@ def msc_get_stats(plan: Plan) -> dict:
     s = MscStats()
     _check(lib.msc_get_stats(plan.handle, ctypes.byref(s)), plan.handle)
     return s.as_dict()
+
+
+def msc_gradient_critical_static(field: torch.Tensor, words: torch.Tensor, cells, capacity) -> list:
+    """Stages (a1)+(a2) into caller-owned tensors with no device allocation by the library.
+
+    For callers that cannot allocate device memory (the GPU's memory already belongs to their
+    own pool, or they run inside a callback or deadline-bound loop where cudaMalloc is not
+    allowed).  field: [nz,ny,nx] float32; words: [nz,ny,nx] uint32 output; cells: 4 uint32
+    output tensors; capacity: their entry capacities.  Returns the 4 critical counts.  Scratch
+    lives in one static device array shared by every call, so overlapping calls race.
+    """
+    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    nz, ny, nx = field.shape
+    if tuple(words.shape) != (nz, ny, nx) or words.dtype != torch.uint32 or not words.is_contiguous():
+        raise ValueError("words must be a contiguous uint32 tensor shaped like the field")
+    dims = (ctypes.c_int64 * 3)(nx, ny, nz)
+    ptrs = (ctypes.c_void_p * 4)(*[c.data_ptr() if c.numel() else None for c in cells])
+    cap = (ctypes.c_int64 * 4)(*[int(c) for c in capacity])
+    counts = (ctypes.c_int64 * 4)()
+    st = lib.msc_gradient_critical_static(dims, ctypes.c_void_p(field.data_ptr()), ctypes.c_void_p(words.data_ptr()),
+                                          ptrs, cap, counts, _stream())
+    if st != MSC_OK:
+        raise MscError(st, f"msc_gradient_critical_static{(nx, ny, nz)} counts={list(counts)}")
+    return [int(c) for c in counts]
 
 
 def compute(field: torch.Tensor, plan: Plan | None = None) -> dict:
