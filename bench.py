@@ -212,7 +212,7 @@ def run_gpu(args):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
-    step_ms, stage_ms, kernel_ms = [], [], {"gradient_kernel": [], "rows_warp": []}
+    step_ms, stage_ms, kernel_ms = [], [], {"gradient_kernel": [], "rows_thread": []}
     launches = 0
     barrier()
     with ClockSampler(uuid) as clk:
@@ -229,7 +229,7 @@ def run_gpu(args):
             launches += int(st["n_launches"])
             stage_ms.append(st)
             kernel_ms["gradient_kernel"].append(st["ms_gradient"])
-            kernel_ms["rows_warp"].append(st["ms_rows_kernel"])
+            kernel_ms["rows_thread"].append(st["ms_rows_kernel"])
         barrier()
         wall = time.perf_counter() - t_region
     ms = sum(step_ms) / len(step_ms)
@@ -289,8 +289,8 @@ def run_gpu(args):
     last = stage_ms[-1]
     km = {k: statistics.median(v) for k, v in kernel_ms.items()}
     algo = {"gradient_kernel": 8.0 * nvox,
-            "rows_warp": 17.0 * (counts[1] + last["n_frontier_entries"]) + 12.0 * last["nnz_Dstar"]}
-    units = {"gradient_kernel": nvox, "rows_warp": counts[1] + last["n_frontier_entries"]}
+            "rows_thread": 17.0 * (counts[1] + last["n_frontier_entries"]) + 12.0 * last["nnz_Dstar"]}
+    units = {"gradient_kernel": nvox, "rows_thread": counts[1] + last["n_frontier_entries"]}
     dom = max(km, key=km.get)
     achieved = algo[dom] / (km[dom] / 1e3) / 1e9
     rec = _traffic_record(dom)
@@ -307,7 +307,7 @@ def run_gpu(args):
     stage_bytes = {"gradient": 8.0 * nvox, "critical": 1.0 * nvox + 4.0 * sum(counts),
                    "extremum": 4.0 * nvox + 8.0 * nvox, "reachability": 4.0 * last["n_reachable"],
                    "minor": 17.0 * (counts[1] + last["n_junctions"]),
-                   "path_count": algo["rows_warp"]}
+                   "path_count": algo["rows_thread"]}
     stages = {}
     for name in stage_bytes:
         t = med("ms_" + name)

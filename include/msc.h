@@ -55,9 +55,11 @@ typedef struct msc_plan_s* msc_plan_t;
 
 /* Plan options (all fields may be zero for defaults). */
 typedef struct msc_opts {
-    int64_t max_iterations; /* cap on every iterative stage; 0 = 1<<20 */
-    int32_t flags;          /* reserved, must be 0 */
-    int32_t reserved;
+    int64_t max_iterations;  /* cap on every iterative stage; 0 = 1<<20 */
+    int32_t flags;           /* reserved, must be 0 */
+    int32_t path_count_tier; /* first tier of the row-wise path count: 0 = per-thread registers
+                                (default), 1 = per-warp shared-memory tables, 2 = per-CTA global
+                                tables.  Results are identical; tests use it to cover every tier. */
 } msc_opts;
 
 /* Per-stage diagnostics (Sec. 4.2 "performance analysis" quantities). Times are the

@@ -42,12 +42,23 @@ __device__ __forceinline__ uint32_t order_key(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+constexpr int NEXT = EX * EY * EZ;  // vertices whose lower stars a CTA computes
+
 struct Shared {
     uint32_t fkey[FZ][FY][FX];   // order keys of the field tile (OUTSIDE_KEY off-grid)
     uint32_t words[TZ][TY][TX];  // packed codes of the owned tile
     uint32_t vkey[27][THREADS];  // per-thread scratch: keys of the star's vertices
     uint32_t ckey[27][THREADS];  // per-thread scratch: rank-bitmask keys of the star's cells
+    uint16_t order[NEXT];        // non-minimal vertices, grouped by lower-star size
+    uint8_t size[NEXT];          // |L(x)| - 1 of every vertex (0 for minima and off-grid)
+    int bin[28];                 // counting-sort bins by size
 };
+
+// The 27 order keys of the star of the vertex at tile-local (lx,ly,lz).
+__device__ __forceinline__ void star_keys(const Shared& sh, int lx, int ly, int lz, uint32_t (&k)[27]) {
+#pragma unroll
+    for (int p = 0; p < 27; ++p) k[p] = sh.fkey[lz + 1 + pdz(p)][ly + 1 + pdy(p)][lx + 1 + pdx(p)];
+}
 
 __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* __restrict__ field,
                                                            uint32_t* __restrict__ words_out,
@@ -74,14 +85,47 @@ __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* 
     if (saw_nan) atomicOr(status, ST_NAN);
     __syncthreads();
 
+    // Lower stars differ widely in size (1..27 cells), and a warp runs as long as its largest
+    // one.  So first size every star (cheap mask arithmetic), counting-sort the non-minimal
+    // vertices by size, and let consecutive threads take consecutive entries.
+    if (t < 28) sh.bin[t] = 0;
+    __syncthreads();
+    for (int i = t; i < NEXT; i += THREADS) {
+        const int lx = i % EX, ly = (i / EX) % EY, lz = i / (EX * EY);
+        int m = 0;
+        if (x0 + lx < g.nx && y0 + ly < g.ny && z0 + lz < g.nz) {
+            uint32_t k[27];
+            star_keys(sh, lx, ly, lz, k);
+            m = __popc(star::lower_star_mask(star::lower_mask(k))) - 1;
+        }
+        sh.size[i] = uint8_t(m);
+        if (m > 0) atomicAdd(&sh.bin[m], 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+        int acc = 0;
+        for (int m = 27; m >= 1; --m) {  // largest stars first
+            const int c = sh.bin[m];
+            sh.bin[m] = acc;
+            acc += c;
+        }
+        sh.bin[0] = acc;  // number of non-minimal vertices
+    }
+    __syncthreads();
+    for (int i = t; i < NEXT; i += THREADS) {
+        const int m = sh.size[i];
+        if (m > 0) sh.order[atomicAdd(&sh.bin[m], 1)] = uint16_t(i);
+    }
+    __syncthreads();
+    const int n_items = sh.bin[0];
+
     bool ok = true;
     const star::Scratch sc{&sh.vkey[0][t], &sh.ckey[0][t], THREADS};
-    for (int i = t; i < EX * EY * EZ; i += THREADS) {
+    for (int it = t; it < n_items; it += THREADS) {
+        const int i = sh.order[it];
         const int lx = i % EX, ly = (i / EX) % EY, lz = i / (EX * EY);
-        if (x0 + lx >= g.nx || y0 + ly >= g.ny || z0 + lz >= g.nz) continue;
         uint32_t k[27];
-#pragma unroll
-        for (int p = 0; p < 27; ++p) k[p] = sh.fkey[lz + 1 + pdz(p)][ly + 1 + pdy(p)][lx + 1 + pdx(p)];
+        star_keys(sh, lx, ly, lz, k);
         // a cell is owned by its lowest corner vertex: record its code there if that vertex
         // belongs to this CTA's tile
         auto emit = [&](int p, uint32_t code) {

@@ -100,21 +100,27 @@ __host__ __device__ inline bool one_free_facet(int q, uint32_t inL, uint32_t cls
     return MSC_POPC(facet_mask(q) & inL & ~cls) == 1;
 }
 
+// Bit p set iff the vertex at position p is lower than x (value, then index; the index order
+// of the star's vertices is the order of their positions).  Bit 13 (x itself) is set too.
+__host__ __device__ inline uint32_t lower_mask(const uint32_t* k) {
+    const uint32_t kc = k[CENTER];
+    uint32_t lower = 1u << CENTER;
+#pragma unroll
+    for (int p = 0; p < 27; ++p) {
+        if (p == CENTER) continue;
+        const bool lo = (k[p] < kc) || (k[p] == kc && p < CENTER);
+        lower |= uint32_t(lo) << p;
+    }
+    return lower;
+}
+
 // Pairs the cells of L(x) given the 27 vertex order keys k[] (k[13] = x; an off-grid vertex
 // has key 0xFFFFFFFF).  Vertices with equal keys are ordered by position, which is their
 // index order.  emit(p, code) is called for every non-critical cell with its direction code.
 // Returns false if the procedure did not classify every cell (an internal error).
 template <class Emit>
 __host__ __device__ bool process_lower_star(const uint32_t* k, const Scratch& sc, Emit&& emit) {
-    const uint32_t kc = k[CENTER];
-    uint32_t lower = 1u << CENTER;
-#pragma unroll
-    for (int p = 0; p < 27; ++p) {
-        if (p == CENTER) continue;
-        bool lo = (k[p] < kc) || (k[p] == kc && p < CENTER);
-        lower |= uint32_t(lo) << p;
-    }
-    const uint32_t inL = lower_star_mask(lower);
+    const uint32_t inL = lower_star_mask(lower_mask(k));
     if (inL == (1u << CENTER)) return true;  // a minimum: every code stays 0
 
     // rank the vertices of L(x) other than x

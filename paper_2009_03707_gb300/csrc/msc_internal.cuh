@@ -47,7 +47,7 @@ struct Plan {
     DeviceBuffer visited, frontier[2], qcount;
     DeviceBuffer junc_bits, junc_prefix, junc_cells;
     DeviceBuffer trace, trace_kinds, minor_rowcnt, minor_scan, minor_rowptr[4], minor_col[4], minor_mult[4];
-    DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_counters, pc_col, pc_cnt, pc_gk, pc_gv;
+    DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_counters, pc_col, pc_cnt, pc_gk, pc_gv, pc_gocc;
     DeviceBuffer dstar_rowptr, dstar_col, dstar_count;
 
     template <class F>
@@ -58,7 +58,7 @@ struct Plan {
                                &trace_kinds, &minor_rowcnt, &minor_scan, &minor_rowptr[0], &minor_rowptr[1],
                                &minor_rowptr[2], &minor_rowptr[3], &minor_col[0], &minor_col[1], &minor_col[2],
                                &minor_col[3], &minor_mult[0], &minor_mult[1], &minor_mult[2], &minor_mult[3],
-                               &pc_rowstart, &pc_rowlen, &pc_big, &pc_counters, &pc_col, &pc_cnt, &pc_gk, &pc_gv,
+                               &pc_rowstart, &pc_rowlen, &pc_big, &pc_counters, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc,
                                &dstar_rowptr, &dstar_col, &dstar_count};
         for (DeviceBuffer* b : all) f(*b);
     }

@@ -2,22 +2,23 @@
 // via matrix operations").
 //
 // The paper iterates A <- A B over the whole matrix (cuSPARSE SpGEMM), accumulating A* until
-// the product is zero, then forms A* B* + D.  Row s of every product depends only on row s
-// of A, so here the same iteration runs row by row (Gustavson's row-wise product): a group of
-// threads owns one 1-saddle s and keeps
-//   * the frontier A_k[s,:] as a hash table keyed by junction rank,
-//   * the accumulator D*[s,:] as a hash table keyed by 2-saddle rank,
-// and repeats "for each (j, c) in A_k[s,:]: every traced path j -> j' adds c to A_{k+1}[s,j'],
-// every traced path j -> t adds c to D*[s,t]" until the frontier is empty.  The minor's
-// adjacency is the 4-slot trace of each junction (minor.cu); a repeated destination is a
-// repeated path, i.e. the multiplicity.  Counts are exact uint64; an add that wraps sets the
-// overflow flag (the paper reports multiplicities near 1e10, beyond 32 bits).
+// the product is zero, then forms A* B* + D.  Row s of every product depends only on row s of
+// A, so here the same iteration runs row by row (Gustavson's row-wise product): the worker that
+// owns 1-saddle s keeps the frontier A_k[s,:] keyed by junction rank and the accumulator
+// D*[s,:] keyed by 2-saddle rank, and repeats "for each (j, c) in A_k[s,:]: every traced path
+// j -> j' adds c to A_{k+1}[s,j'], every traced path j -> t adds c to D*[s,t]" until the
+// frontier is empty.  The minor's adjacency is the 4-slot trace of each junction (minor.cu); a
+// repeated destination is a repeated path, i.e. the multiplicity.  Counts are exact uint64 and
+// an add that wraps sets the overflow flag (the paper reports multiplicities near 1e10).
 //
-// Tier 1: one warp per 1-saddle with 256-slot tables in shared memory; 1-saddles whose rows
-// outgrow them are queued for tier 2: one CTA per 1-saddle with tables in global memory,
-// sized up again (tier 3) for whatever still does not fit.  Each finished row is sorted by
-// column and appended to a staging buffer; a scan of the row lengths and one gather give the
-// CSR of D*.
+// Rows are latency-bound chains of dependent gathers, so the work goes to the smallest worker
+// that can hold it, to keep as many rows in flight as possible:
+//   tier 0  one thread per row, frontier (<= 4) and D* row (<= 8) in registers;
+//   tier 1  one warp per row, 256-slot hash tables in shared memory;
+//   tier 2+ one CTA per row, hash tables in global memory, grown until the row fits.
+// A row that overflows its worker is deferred, intact, to the next tier.  Finished rows are
+// sorted by column and appended to a staging buffer; a scan of the row lengths and one gather
+// give the CSR of D*.
 #include "rowscan.cuh"
 
 namespace msc {
@@ -25,65 +26,235 @@ namespace msc {
 namespace {
 
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr int T0_THREADS = 256;
+constexpr int T0_F = 4;  // frontier slots per thread
+constexpr int T0_D = 8;  // D* row slots per thread
 constexpr int T1_WARPS = 4;
 constexpr int T1_HASH = 256;  // slots per table (power of two)
 constexpr int T1_LIST = T1_HASH / 2;
 constexpr int T2_THREADS = 256;
 
-struct Tables {
-    uint32_t* fk;            // frontier hash keys (junction rank)
-    unsigned long long* fv;  // frontier hash counts
-    uint32_t* dk;            // D* row hash keys (2-saddle rank)
-    unsigned long long* dv;  // D* row hash counts
-    uint32_t* lk;            // current frontier list / sort buffer keys
-    unsigned long long* lv;  // current frontier list / sort buffer counts
-    int cap;                 // hash slots (power of two); the list holds cap/2
-    int lg;                  // log2(cap)
-    int* fsize;              // occupied frontier slots
-    int* dsize;              // occupied D* slots
-    int* lsize;              // list length
-    int* bad;                // table overflow in this row
-    unsigned long long* base;  // staging offset of the finished row
-};
+typedef unsigned long long u64;
 
 struct PcArgs {
     int64_t n1;
+    const uint32_t* rows;   // the 1-saddle ranks this launch owns (null: 0..nrows-1)
+    int64_t nrows;
     const uint32_t* tgt;    // 4 destination ranks per source (1-saddles, then junctions)
     const uint8_t* kinds;   // 2 bits per slot: 1 junction, 2 2-saddle
     uint32_t* out_col;      // staging: columns of finished rows
-    unsigned long long* out_cnt;
+    u64* out_cnt;
     uint64_t out_cap;
-    unsigned long long* out_cursor;
+    u64* out_cursor;
     int64_t* row_start;
     uint32_t* row_len;
-    uint32_t* big;          // 1-saddles deferred to the next tier
-    unsigned long long* big_count;
-    uint64_t big_cap;
-    unsigned long long* next_source;
-    unsigned long long* max_count;
-    unsigned long long* n_iter;
-    unsigned long long* n_entries;  // sum of frontier sizes (for the roofline's byte count)
+    uint32_t* deferred;     // rows handed to the next tier
+    u64* deferred_count;
+    u64* max_count;
+    u64* n_iter;
+    u64* n_entries;         // sum of frontier sizes of finished rows
     int64_t max_iter;
     uint32_t* status;
 };
 
+__device__ __forceinline__ int64_t row_of(const PcArgs& a, int64_t i) { return a.rows ? int64_t(a.rows[i]) : i; }
+
+__device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
+    return *reinterpret_cast<const uint4*>(a.tgt + 4 * src);
+}
+
+// ---------------------------------------------------------------------------------------
+// tier 0: registers
+// ---------------------------------------------------------------------------------------
+// Adds (key, val) to a small register map; false if it is full.  Indices are compile-time
+// constants throughout so the arrays stay in registers.
+template <int N>
+__device__ __forceinline__ bool reg_add(uint32_t (&k)[N], u64 (&v)[N], int& n, uint32_t key, u64 val, bool& ovf) {
+    bool found = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i < n && k[i] == key) {
+            const u64 o = v[i];
+            v[i] = o + val;
+            ovf |= v[i] < o;
+            found = true;
+        }
+    if (found) return true;
+    if (n >= N) return false;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i == n) {
+            k[i] = key;
+            v[i] = val;
+        }
+    ++n;
+    return true;
+}
+
+__device__ __forceinline__ u64 warp_sum(u64 v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+__device__ __forceinline__ u64 warp_max(u64 v) {
+    for (int o = 16; o; o >>= 1) v = max(v, (u64)__shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+// Warp-wide exclusive offsets of n, with one atomicAdd on `counter` for the whole warp.
+__device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
+    const int lane = threadIdx.x & 31;
+    unsigned incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    u64 base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (u64)total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    return base + (incl - n);
+}
+
+__global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
+    const int64_t i = int64_t(blockIdx.x) * T0_THREADS + threadIdx.x;
+    const bool valid = i < a.nrows;  // every lane stays to the warp-wide appends at the end
+    const int64_t s = valid ? row_of(a, i) : 0;
+    uint32_t fk[T0_F], dk[T0_D];
+    u64 fv[T0_F], dv[T0_D];
+#pragma unroll
+    for (int e = 0; e < T0_D; ++e) {
+        dk[e] = EMPTY;
+        dv[e] = 0;
+    }
+    int nf = 0, nd = 0;
+    bool fit = true, ovf = false;
+    u64 iter = 0, entries = 0;
+    if (valid) {
+        const uint32_t kinds = a.kinds[s];
+        const uint4 t4 = trace_of(a, s);
+        const uint32_t tg[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t kind = (kinds >> (2 * k)) & 3u;
+            if (kind == 1) fit = fit && reg_add(fk, fv, nf, tg[k], 1, ovf);
+            if (kind == 2) fit = fit && reg_add(dk, dv, nd, tg[k], 1, ovf);
+        }
+        while (fit && nf > 0) {
+            if (int64_t(++iter) > a.max_iter) {
+                atomicOr(a.status, ST_ITER);
+                break;
+            }
+            entries += nf;
+            uint32_t gk[T0_F];
+            u64 gv[T0_F];
+            int ng = 0;
+#pragma unroll
+            for (int e = 0; e < T0_F; ++e) {
+                if (e < nf) {
+                    const int64_t j = a.n1 + int64_t(fk[e]);
+                    const u64 c = fv[e];
+                    const uint32_t kj = a.kinds[j];
+                    const uint4 q = trace_of(a, j);
+                    const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t kind = (kj >> (2 * k)) & 3u;
+                        if (kind == 1) fit = fit && reg_add(gk, gv, ng, tq[k], c, ovf);
+                        if (kind == 2) fit = fit && reg_add(dk, dv, nd, tq[k], c, ovf);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < T0_F; ++e) {
+                fk[e] = gk[e];
+                fv[e] = gv[e];
+            }
+            nf = ng;
+        }
+    }
+    if (ovf) atomicOr(a.status, ST_OVERFLOW);
+    const bool done = valid && fit;
+    // sort the row by column (odd-even transposition; empty slots hold EMPTY and sink)
+#pragma unroll
+    for (int round = 0; round < T0_D; ++round)
+#pragma unroll
+        for (int e = round & 1; e + 1 < T0_D; e += 2)
+            if (dk[e] > dk[e + 1]) {
+                const uint32_t tk = dk[e];
+                dk[e] = dk[e + 1];
+                dk[e + 1] = tk;
+                const u64 tv = dv[e];
+                dv[e] = dv[e + 1];
+                dv[e + 1] = tv;
+            }
+    const unsigned n_out = done ? unsigned(nd) : 0u;
+    const u64 base = warp_append(a.out_cursor, n_out);
+    u64 mx = 0;
+#pragma unroll
+    for (int e = 0; e < T0_D; ++e)
+        if (e < int(n_out)) {
+            if (base + e < a.out_cap) {
+                a.out_col[base + e] = dk[e];
+                a.out_cnt[base + e] = dv[e];
+            } else {
+                atomicOr(a.status, ST_CAPACITY);
+            }
+            mx = max(mx, dv[e]);
+        }
+    if (done) {
+        a.row_start[s] = int64_t(base);
+        a.row_len[s] = n_out;
+    }
+    const u64 dpos = warp_append(a.deferred_count, (valid && !fit) ? 1u : 0u);
+    if (valid && !fit) a.deferred[dpos] = uint32_t(s);
+    mx = warp_max(mx);
+    const u64 it = warp_max(done ? iter : 0);
+    const u64 en = warp_sum(done ? entries : 0);
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(a.max_count, mx);
+        if (it) atomicMax(a.n_iter, it);
+        if (en) atomicAdd(a.n_entries, en);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// tiers 1 and 2+: hash tables shared by a group of G threads
+// ---------------------------------------------------------------------------------------
+struct Tables {
+    uint32_t* fk;     // frontier hash keys (junction rank)
+    u64* fv;          // frontier hash counts
+    uint32_t* focc;   // occupied frontier slots, in claim order
+    uint32_t* dk;     // D* row hash keys (2-saddle rank)
+    u64* dv;          // D* row hash counts
+    uint32_t* docc;   // occupied D* slots
+    uint32_t* lk;     // current frontier list / sort buffer keys
+    u64* lv;          // current frontier list / sort buffer counts
+    int cap;          // hash slots (power of two); lists hold cap/2
+    int lg;           // log2(cap)
+    int* fsize;       // claimed frontier slots
+    int* dsize;       // claimed D* slots
+    int* bad;         // a table overflowed in this row
+    u64* base;        // staging offset of the finished row
+};
+
 __device__ __forceinline__ uint32_t slot_of(uint32_t key, int lg) { return (key * 2654435761u) >> (32 - lg); }
 
-// Adds val to key's entry; returns false if the table is over its load limit.
-__device__ bool table_add(uint32_t* K, unsigned long long* V, int cap, int lg, int* size, uint32_t key,
-                          unsigned long long val, uint32_t* status) {
+// Adds val to key's entry; false if the table is over its load limit.
+__device__ bool table_add(uint32_t* K, u64* V, uint32_t* occ, int cap, int lg, int* size, uint32_t key, u64 val,
+                          uint32_t* status) {
     uint32_t h = slot_of(key, lg);
     for (int probe = 0; probe < cap; ++probe) {
         uint32_t k = K[h];
         if (k == EMPTY) {
             k = atomicCAS(&K[h], EMPTY, key);
             if (k == EMPTY) {
-                if (atomicAdd(size, 1) >= cap / 2) return false;
+                const int idx = atomicAdd(size, 1);
+                if (idx >= cap / 2) return false;  // the row is abandoned and the tables scrubbed
+                occ[idx] = h;
                 k = key;
             }
         }
         if (k == key) {
-            unsigned long long old = atomicAdd(&V[h], val);
+            const u64 old = atomicAdd(&V[h], val);
             if (old + val < old) atomicOr(status, ST_OVERFLOW);
             return true;
         }
@@ -98,95 +269,99 @@ __device__ __forceinline__ void group_sync() {
     else __syncthreads();
 }
 
-// Moves every occupied slot of a hash table into the list (lk, lv) and clears the table.
+// Moves the n occupied entries of a table into the list (in claim order) and clears them.
 template <int G>
-__device__ void drain(uint32_t* K, unsigned long long* V, const Tables& t, int r) {
-    for (int i = r; i < t.cap; i += G) {
-        const uint32_t k = K[i];
-        if (k == EMPTY) continue;
-        const int pos = atomicAdd(t.lsize, 1);
-        if (pos < t.cap / 2) {
-            t.lk[pos] = k;
-            t.lv[pos] = V[i];
-        } else {
-            *t.bad = 1;
-        }
-        K[i] = EMPTY;
-        V[i] = 0;
+__device__ void drain(uint32_t* K, u64* V, const uint32_t* occ, int n, const Tables& t, int r) {
+    for (int i = r; i < n; i += G) {
+        const uint32_t h = occ[i];
+        t.lk[i] = K[h];
+        t.lv[i] = V[h];
+        K[h] = EMPTY;
+        V[h] = 0;
     }
 }
 
-// Row s of D*, computed by a group of G threads (rank r in the group).  Returns false if
-// a table overflowed; the tables are left cleared either way.
+template <int G>
+__device__ void scrub(const Tables& t, int r) {
+    for (int i = r; i < t.cap; i += G) {
+        t.fk[i] = EMPTY;
+        t.fv[i] = 0;
+        t.dk[i] = EMPTY;
+        t.dv[i] = 0;
+    }
+}
+
+// Row s of D*, computed by a group of G threads (rank r in the group).  Returns false if a
+// table overflowed; the tables are left clean either way.
 template <int G>
 __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
     if (r == 0) {
         *t.fsize = 0;
         *t.dsize = 0;
-        *t.lsize = 0;
         *t.bad = 0;
     }
     group_sync<G>();
-    // row s of A (the frontier A_0) and of D
-    if (r < 4) {
+    if (r < 4) {  // row s of A (the frontier A_0) and of D
         const uint32_t kind = (a.kinds[s] >> (2 * r)) & 3u;
         const uint32_t dst = a.tgt[s * 4 + r];
         bool ok = true;
-        if (kind == 1) ok = table_add(t.fk, t.fv, t.cap, t.lg, t.fsize, dst, 1, a.status);
-        if (kind == 2) ok = table_add(t.dk, t.dv, t.cap, t.lg, t.dsize, dst, 1, a.status);
+        if (kind == 1) ok = table_add(t.fk, t.fv, t.focc, t.cap, t.lg, t.fsize, dst, 1, a.status);
+        if (kind == 2) ok = table_add(t.dk, t.dv, t.docc, t.cap, t.lg, t.dsize, dst, 1, a.status);
         if (!ok) *t.bad = 1;
     }
     group_sync<G>();
-    int64_t iter = 0;
+    u64 iter = 0, entries = 0;
+    bool ok = true;
     while (true) {
-        drain<G>(t.fk, t.fv, t, r);  // A_k[s,:] -> list; frontier table cleared
+        const int claimed = *t.fsize;
+        const bool bad = *t.bad || claimed > t.cap / 2;
         group_sync<G>();
-        const int n = min(*t.lsize, t.cap / 2);
-        const int bad = *t.bad;
-        group_sync<G>();
-        if (r == 0) {
-            *t.lsize = 0;
-            *t.fsize = 0;
+        if (bad) {
+            ok = false;
+            break;
         }
+        const int n = claimed;
+        drain<G>(t.fk, t.fv, t.focc, n, t, r);  // A_k[s,:] -> list; frontier table cleared
         group_sync<G>();
-        if (n == 0 || bad) break;
-        if (r == 0) atomicAdd(a.n_entries, (unsigned long long)n);
-        if (++iter > a.max_iter) {
+        if (r == 0) *t.fsize = 0;
+        group_sync<G>();
+        if (n == 0) break;
+        if (int64_t(++iter) > a.max_iter) {
             if (r == 0) atomicOr(a.status, ST_ITER);
             break;
         }
+        entries += u64(n);
         // A_{k+1}[s,:] += c B[j,:]  and  D*[s,:] += c B*[j,:]: one unit per traced path
         for (int i = r; i < n; i += G) {
             const int64_t j = a.n1 + int64_t(t.lk[i]);
-            const unsigned long long c = t.lv[i];
+            const u64 c = t.lv[i];
             const uint32_t kinds = a.kinds[j];
+            const uint4 q = trace_of(a, j);
+            const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
             for (int k = 0; k < 4; ++k) {
                 const uint32_t kind = (kinds >> (2 * k)) & 3u;
                 if (!kind) continue;
-                const uint32_t dst = a.tgt[j * 4 + k];
-                const bool ok = kind == 1 ? table_add(t.fk, t.fv, t.cap, t.lg, t.fsize, dst, c, a.status)
-                                          : table_add(t.dk, t.dv, t.cap, t.lg, t.dsize, dst, c, a.status);
-                if (!ok) *t.bad = 1;
+                const bool added = kind == 1 ? table_add(t.fk, t.fv, t.focc, t.cap, t.lg, t.fsize, tq[k], c, a.status)
+                                             : table_add(t.dk, t.dv, t.docc, t.cap, t.lg, t.dsize, tq[k], c, a.status);
+                if (!added) *t.bad = 1;
             }
         }
         group_sync<G>();
     }
-    if (r == 0 && iter > 0) atomicMax(a.n_iter, (unsigned long long)iter);
-    // D*[s,:] -> list (and drop frontier leftovers after an overflow)
-    drain<G>(t.dk, t.dv, t, r);
-    for (int i = r; i < t.cap; i += G)
-        if (t.fk[i] != EMPTY) {
-            t.fk[i] = EMPTY;
-            t.fv[i] = 0;
-        }
+    const int nd = *t.dsize;
+    ok = ok && !*t.bad && nd <= t.cap / 2;
     group_sync<G>();
-    const bool ok = *t.bad == 0;
-    const int n = min(*t.lsize, t.cap / 2);
-    group_sync<G>();
-    if (!ok) return false;
+    if (!ok) {
+        scrub<G>(t, r);
+        group_sync<G>();
+        return false;
+    }
+    if (r == 0 && iter > 0) atomicMax(a.n_iter, iter);
+    if (r == 0 && entries > 0) atomicAdd(a.n_entries, entries);
+    drain<G>(t.dk, t.dv, t.docc, nd, t, r);  // D*[s,:] -> list
     int P = 1;
-    while (P < n) P <<= 1;
-    for (int i = n + r; i < P; i += G) {
+    while (P < nd) P <<= 1;
+    for (int i = nd + r; i < P; i += G) {
         t.lk[i] = EMPTY;
         t.lv[i] = 0;
     }
@@ -201,7 +376,7 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
                     if ((ki > kl) == up) {
                         t.lk[i] = kl;
                         t.lk[l] = ki;
-                        const unsigned long long v = t.lv[i];
+                        const u64 v = t.lv[i];
                         t.lv[i] = t.lv[l];
                         t.lv[l] = v;
                     }
@@ -210,15 +385,15 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
             group_sync<G>();
         }
     if (r == 0) {
-        const unsigned long long b = n ? atomicAdd(a.out_cursor, (unsigned long long)n) : 0ull;
+        const u64 b = nd ? atomicAdd(a.out_cursor, (u64)nd) : 0ull;
         a.row_start[s] = int64_t(b);
-        a.row_len[s] = uint32_t(n);
+        a.row_len[s] = uint32_t(nd);
         *t.base = b;
     }
     group_sync<G>();
-    const unsigned long long base = *t.base;
-    unsigned long long mx = 0;
-    for (int i = r; i < n; i += G) {
+    const u64 base = *t.base;
+    u64 mx = 0;
+    for (int i = r; i < nd; i += G) {
         if (base + i < a.out_cap) {
             a.out_col[base + i] = t.lk[i];
             a.out_cnt[base + i] = t.lv[i];
@@ -232,54 +407,56 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
     return true;
 }
 
-// Tier 1: warps pull 1-saddles from a shared counter.
-__global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs a) {
-    __shared__ uint32_t fk[T1_WARPS][T1_HASH], dk[T1_WARPS][T1_HASH], lk[T1_WARPS][T1_LIST];
-    __shared__ unsigned long long fv[T1_WARPS][T1_HASH], dv[T1_WARPS][T1_HASH], lv[T1_WARPS][T1_LIST];
-    __shared__ int counters[T1_WARPS][4];
-    __shared__ unsigned long long bases[T1_WARPS];
+// Tier 1: warps pull rows from a shared counter.
+__global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs a, u64* next_row) {
+    __shared__ uint32_t fk[T1_WARPS][T1_HASH], dk[T1_WARPS][T1_HASH];
+    __shared__ u64 fv[T1_WARPS][T1_HASH], dv[T1_WARPS][T1_HASH];
+    __shared__ uint32_t focc[T1_WARPS][T1_LIST], docc[T1_WARPS][T1_LIST], lk[T1_WARPS][T1_LIST];
+    __shared__ u64 lv[T1_WARPS][T1_LIST];
+    __shared__ int counters[T1_WARPS][3];
+    __shared__ u64 bases[T1_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = lane; i < T1_HASH; i += 32) {
         fk[w][i] = dk[w][i] = EMPTY;
         fv[w][i] = dv[w][i] = 0;
     }
     __syncwarp();
-    Tables t{fk[w], fv[w], dk[w], dv[w], lk[w], lv[w], T1_HASH, 8, &counters[w][0], &counters[w][1], &counters[w][2],
-             &counters[w][3], &bases[w]};
+    const Tables t{fk[w], fv[w], focc[w], dk[w], dv[w], docc[w], lk[w], lv[w], T1_HASH, 8,
+                   &counters[w][0], &counters[w][1], &counters[w][2], &bases[w]};
     while (true) {
-        unsigned long long s = 0;
-        if (lane == 0) s = atomicAdd(a.next_source, 1ull);
-        s = __shfl_sync(0xFFFFFFFFu, s, 0);
-        if (s >= (unsigned long long)a.n1) break;
-        if (!count_row<32>(a, t, int64_t(s), lane) && lane == 0) {
-            const unsigned long long pos = atomicAdd(a.big_count, 1ull);
-            if (pos < a.big_cap) a.big[pos] = uint32_t(s);
-            else atomicOr(a.status, ST_CAPACITY);
+        u64 i = 0;
+        if (lane == 0) i = atomicAdd(next_row, 1ull);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        if (i >= (u64)a.nrows) break;
+        const int64_t s = row_of(a, int64_t(i));
+        if (!count_row<32>(a, t, s, lane) && lane == 0) {
+            const u64 pos = atomicAdd(a.deferred_count, 1ull);
+            a.deferred[pos] = uint32_t(s);
         }
     }
 }
 
-// Tiers 2 and 3: one CTA per deferred 1-saddle, tables in global memory (one set per CTA).
-__global__ void __launch_bounds__(T2_THREADS) rows_block(PcArgs a, const uint32_t* __restrict__ list, int64_t n,
-                                                         uint32_t* gk, unsigned long long* gv, int cap, int lg,
-                                                         uint32_t* still_big, unsigned long long* still_count) {
-    __shared__ int counters[4];
-    __shared__ unsigned long long base;
+// Tiers 2+: one CTA per row, tables in global memory (one set per CTA).
+__global__ void __launch_bounds__(T2_THREADS) rows_block(PcArgs a, uint32_t* gk, u64* gv, uint32_t* gocc, int cap,
+                                                         int lg) {
+    __shared__ int counters[3];
+    __shared__ u64 base;
     const size_t per = size_t(cap);
-    uint32_t* fk = gk + size_t(blockIdx.x) * 3 * per;
-    unsigned long long* fv = gv + size_t(blockIdx.x) * 3 * per;
-    Tables t{fk, fv, fk + per, fv + per, fk + 2 * per, fv + 2 * per, cap, lg, &counters[0], &counters[1],
-             &counters[2], &counters[3], &base};
-    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-        const int64_t s = list[i];
+    uint32_t* k = gk + size_t(blockIdx.x) * 3 * per;
+    u64* v = gv + size_t(blockIdx.x) * 3 * per;
+    uint32_t* occ = gocc + size_t(blockIdx.x) * per;
+    const Tables t{k, v, occ, k + per, v + per, occ + per / 2, k + 2 * per, v + 2 * per, cap, lg,
+                   &counters[0], &counters[1], &counters[2], &base};
+    for (int64_t i = blockIdx.x; i < a.nrows; i += gridDim.x) {
+        const int64_t s = row_of(a, i);
         if (!count_row<T2_THREADS>(a, t, s, threadIdx.x) && threadIdx.x == 0) {
-            const unsigned long long pos = atomicAdd(still_count, 1ull);
-            still_big[pos] = uint32_t(s);
+            const u64 pos = atomicAdd(a.deferred_count, 1ull);
+            a.deferred[pos] = uint32_t(s);
         }
     }
 }
 
-__global__ void init_tables(uint32_t* k, unsigned long long* v, size_t n) {
+__global__ void init_tables(uint32_t* k, u64* v, size_t n) {
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
         k[i] = EMPTY;
         v[i] = 0;
@@ -287,8 +464,8 @@ __global__ void init_tables(uint32_t* k, unsigned long long* v, size_t n) {
 }
 
 __global__ void gather_rows(int64_t n1, const int64_t* __restrict__ row_start, const int64_t* __restrict__ rowptr,
-                            const uint32_t* __restrict__ in_col, const unsigned long long* __restrict__ in_cnt,
-                            uint32_t* __restrict__ col, unsigned long long* __restrict__ cnt) {
+                            const uint32_t* __restrict__ in_col, const u64* __restrict__ in_cnt,
+                            uint32_t* __restrict__ col, u64* __restrict__ cnt) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= n1) return;
     const int64_t b = row_start[s], o = rowptr[s], len = rowptr[s + 1] - rowptr[s];
@@ -298,117 +475,131 @@ __global__ void gather_rows(int64_t n1, const int64_t* __restrict__ row_start, c
     }
 }
 
+// Counter slots in pc_counters.
+enum { C_CURSOR = 0, C_MAX = 1, C_ITER = 2, C_ENTRIES = 3, C_DEFER0 = 4, C_DEFER1 = 5, C_NEXT = 6 };
+
 }  // namespace
 
 msc_status run_path_count(Plan* p, cudaStream_t s) {
     msc_status st;
     const int64_t n1 = p->counts[1], nj = p->n_junctions, n2 = p->counts[2];
+    const size_t n1c = size_t(n1 ? n1 : 1);
     if ((st = ensure(p, p->dstar_rowptr, sizeof(int64_t) * size_t(n1 + 1)))) return st;
-    if ((st = ensure(p, p->pc_rowstart, sizeof(int64_t) * size_t(n1 ? n1 : 1)))) return st;
-    if ((st = ensure(p, p->pc_rowlen, sizeof(uint32_t) * size_t(n1 ? n1 : 1)))) return st;
-    if ((st = ensure(p, p->pc_big, sizeof(uint32_t) * size_t(n1 ? n1 : 1) * 2))) return st;
-    if ((st = ensure(p, p->pc_counters, sizeof(unsigned long long) * 8))) return st;
+    if ((st = ensure(p, p->pc_rowstart, sizeof(int64_t) * n1c))) return st;
+    if ((st = ensure(p, p->pc_rowlen, sizeof(uint32_t) * n1c))) return st;
+    if ((st = ensure(p, p->pc_big, sizeof(uint32_t) * n1c * 2))) return st;
+    if ((st = ensure(p, p->pc_counters, sizeof(u64) * 8))) return st;
     if ((st = ensure(p, p->minor_scan, row_scan_scratch_bytes(n1)))) return st;
-    auto* ctr = static_cast<unsigned long long*>(p->pc_counters.ptr);
+    auto* ctr = static_cast<u64*>(p->pc_counters.ptr);
+    const int first_tier = std::max(0, std::min(2, int(p->opts.path_count_tier)));
     // staging capacity: grown and the stage re-run if a run overflows it
     uint64_t cap = uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1 + 1024));
     for (int attempt = 0; attempt < 8; ++attempt) {
         if ((st = ensure(p, p->pc_col, sizeof(uint32_t) * cap))) return st;
-        if ((st = ensure(p, p->pc_cnt, sizeof(unsigned long long) * cap))) return st;
-        if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 8, s), "memset counters")))
-            return st;
+        if ((st = ensure(p, p->pc_cnt, sizeof(u64) * cap))) return st;
+        if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * 8, s), "memset counters"))) return st;
+        uint32_t* lists[2] = {static_cast<uint32_t*>(p->pc_big.ptr), static_cast<uint32_t*>(p->pc_big.ptr) + n1c};
         PcArgs a{};
         a.n1 = n1;
         a.tgt = static_cast<const uint32_t*>(p->trace.ptr);
         a.kinds = static_cast<const uint8_t*>(p->trace_kinds.ptr);
         a.out_col = static_cast<uint32_t*>(p->pc_col.ptr);
-        a.out_cnt = static_cast<unsigned long long*>(p->pc_cnt.ptr);
+        a.out_cnt = static_cast<u64*>(p->pc_cnt.ptr);
         a.out_cap = cap;
-        a.out_cursor = ctr + 0;
-        a.next_source = ctr + 1;
-        a.big_count = ctr + 2;
-        a.max_count = ctr + 3;
-        a.n_iter = ctr + 4;
-        a.n_entries = ctr + 6;
+        a.out_cursor = ctr + C_CURSOR;
+        a.max_count = ctr + C_MAX;
+        a.n_iter = ctr + C_ITER;
+        a.n_entries = ctr + C_ENTRIES;
         a.row_start = static_cast<int64_t*>(p->pc_rowstart.ptr);
         a.row_len = static_cast<uint32_t*>(p->pc_rowlen.ptr);
-        a.big = static_cast<uint32_t*>(p->pc_big.ptr);
-        a.big_cap = uint64_t(n1 ? n1 : 1);
         a.max_iter = p->opts.max_iterations;
         a.status = static_cast<uint32_t*>(p->status.ptr);
-        if (n1) {
-            const int grid = std::max(1, p->num_sms) * 4;
-            cudaEventRecord(p->kev0, s);
-            rows_warp<<<grid, T1_WARPS * 32, 0, s>>>(a);
-            cudaEventRecord(p->kev1, s);
-            launched(p);
-            if ((st = check_cuda(p, cudaGetLastError(), "rows_warp launch"))) return st;
-        }
-        unsigned long long h[8];
-        if ((st = check_cuda(p, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s), "counter copy")))
-            return st;
-        if ((st = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return st;
-        if (n1) cudaEventElapsedTime(&p->stats.ms_rows_kernel, p->kev0, p->kev1);
-        // deferred rows: CTAs with global tables, growing until every row fits
-        int64_t nbig = int64_t(h[2]);
-        uint32_t* list = static_cast<uint32_t*>(p->pc_big.ptr);
-        uint32_t* next_list = list + (n1 ? n1 : 1);
+        // rows of the current tier: all of them, or those the previous tier deferred
+        const uint32_t* rows = nullptr;
+        int64_t nrows = n1;
+        int which = 0;
+        auto run_tier = [&](int tier, int lg) -> msc_status {
+            a.rows = rows;
+            a.nrows = nrows;
+            a.deferred = lists[which];
+            a.deferred_count = ctr + C_DEFER0 + which;
+            msc_status e;
+            if ((e = check_cuda(p, cudaMemsetAsync(a.deferred_count, 0, sizeof(u64), s), "memset"))) return e;
+            if (tier == 0) {
+                cudaEventRecord(p->kev0, s);
+                rows_thread<<<int((nrows + T0_THREADS - 1) / T0_THREADS), T0_THREADS, 0, s>>>(a);
+                cudaEventRecord(p->kev1, s);
+                launched(p);
+            } else if (tier == 1) {
+                if ((e = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return e;
+                rows_warp<<<std::max(1, p->num_sms) * 8, T1_WARPS * 32, 0, s>>>(a, ctr + C_NEXT);
+                launched(p);
+            } else {
+                const int cap_t = 1 << lg;
+                const int ctas = int(std::min<int64_t>(nrows, lg <= 14 ? 1024 : lg <= 18 ? 64 : 2));
+                const size_t slots = size_t(ctas) * 3 * size_t(cap_t);
+                if ((e = ensure(p, p->pc_gk, sizeof(uint32_t) * slots))) return e;
+                if ((e = ensure(p, p->pc_gv, sizeof(u64) * slots))) return e;
+                if ((e = ensure(p, p->pc_gocc, sizeof(uint32_t) * size_t(ctas) * size_t(cap_t)))) return e;
+                init_tables<<<1024, 256, 0, s>>>(static_cast<uint32_t*>(p->pc_gk.ptr), static_cast<u64*>(p->pc_gv.ptr),
+                                                 slots);
+                rows_block<<<ctas, T2_THREADS, 0, s>>>(a, static_cast<uint32_t*>(p->pc_gk.ptr),
+                                                      static_cast<u64*>(p->pc_gv.ptr),
+                                                      static_cast<uint32_t*>(p->pc_gocc.ptr), cap_t, lg);
+                launched(p, 2);
+            }
+            if ((e = check_cuda(p, cudaGetLastError(), "path count launch"))) return e;
+            u64 deferred = 0;
+            if ((e = check_cuda(p, cudaMemcpyAsync(&deferred, a.deferred_count, sizeof(deferred),
+                                                   cudaMemcpyDeviceToHost, s),
+                                "counter copy")))
+                return e;
+            if ((e = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return e;
+            if (tier == 0 && nrows) cudaEventElapsedTime(&p->stats.ms_rows_kernel, p->kev0, p->kev1);
+            rows = lists[which];
+            nrows = int64_t(deferred);
+            which ^= 1;
+            return MSC_OK;
+        };
+        if (first_tier <= 0 && nrows > 0 && (st = run_tier(0, 0))) return st;
+        if (first_tier <= 1 && nrows > 0 && (st = run_tier(1, 0))) return st;
         // a row never needs more slots than 2 x max(junctions, 2-saddles)
         const int lg_max = 1 + int(std::ceil(std::log2(double(std::max<int64_t>({nj, n2, 64}) + 1))));
         int lg = std::min(14, lg_max);
-        while (nbig > 0) {
-            const int cap_t = 1 << lg;
-            const int ctas = int(std::min<int64_t>(nbig, lg <= 14 ? 1024 : lg <= 18 ? 64 : 2));
-            const size_t slots = size_t(ctas) * 3 * size_t(cap_t);
-            if ((st = ensure(p, p->pc_gk, sizeof(uint32_t) * slots))) return st;
-            if ((st = ensure(p, p->pc_gv, sizeof(unsigned long long) * slots))) return st;
-            init_tables<<<1024, 256, 0, s>>>(static_cast<uint32_t*>(p->pc_gk.ptr),
-                                             static_cast<unsigned long long*>(p->pc_gv.ptr), slots);
-            launched(p);
-            if ((st = check_cuda(p, cudaMemsetAsync(ctr + 5, 0, sizeof(unsigned long long), s), "memset"))) return st;
-            rows_block<<<ctas, T2_THREADS, 0, s>>>(a, list, nbig, static_cast<uint32_t*>(p->pc_gk.ptr),
-                                                  static_cast<unsigned long long*>(p->pc_gv.ptr), cap_t, lg, next_list,
-                                                  ctr + 5);
-            launched(p);
-            if ((st = check_cuda(p, cudaGetLastError(), "rows_block launch"))) return st;
-            unsigned long long still = 0;
-            if ((st = check_cuda(p, cudaMemcpyAsync(&still, ctr + 5, sizeof(still), cudaMemcpyDeviceToHost, s),
-                                 "counter copy")))
-                return st;
-            if ((st = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return st;
-            if (still > 0 && lg >= lg_max) return fail(p, MSC_ERR_CUDA, "internal: a path-count row does not fit");
-            std::swap(list, next_list);
-            nbig = int64_t(still);
+        while (nrows > 0) {
+            if ((st = run_tier(2, lg))) return st;
+            if (nrows > 0 && lg >= lg_max) return fail(p, MSC_ERR_CUDA, "internal: a path-count row does not fit");
             lg = std::min(lg + 4, lg_max);
         }
+        u64 h[8];
         if ((st = check_cuda(p, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s), "counter copy")))
             return st;
         if ((st = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return st;
-        if (h[0] > cap) {  // staging overflow: grow and redo the stage
+        if (h[C_CURSOR] > cap) {  // staging overflow: grow and redo the stage
             uint32_t zero = 0;
             if ((st = check_cuda(p, cudaMemcpyAsync(p->status.ptr, &zero, sizeof(zero), cudaMemcpyHostToDevice, s),
                                  "status reset")))
                 return st;
-            cap = h[0] + h[0] / 4 + 1024;
+            cap = h[C_CURSOR] + h[C_CURSOR] / 4 + 1024;
             continue;
         }
-        const int64_t nnz = int64_t(h[0]);
+        const int64_t nnz = int64_t(h[C_CURSOR]);
         p->dstar_nnz = nnz;
         p->stats.nnz_Dstar = nnz;
-        p->stats.max_path_count = h[3];
-        p->stats.n_iter = int64_t(h[4]);
-        p->stats.n_frontier_entries = int64_t(h[6]);
+        p->stats.max_path_count = h[C_MAX];
+        p->stats.n_iter = int64_t(h[C_ITER]);
+        p->stats.n_frontier_entries = int64_t(h[C_ENTRIES]);
         if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
-        if ((st = ensure(p, p->dstar_count, sizeof(unsigned long long) * size_t(nnz ? nnz : 1)))) return st;
+        if ((st = ensure(p, p->dstar_count, sizeof(u64) * size_t(nnz ? nnz : 1)))) return st;
         if ((st = check_cuda(p,
                              row_scan(p, a.row_len, n1, static_cast<int64_t*>(p->dstar_rowptr.ptr),
-                                      static_cast<unsigned long long*>(p->minor_scan.ptr), s),
+                                      static_cast<u64*>(p->minor_scan.ptr), s),
                              "D* row scan")))
             return st;
         if (n1) {
             gather_rows<<<int((n1 + 255) / 256), 256, 0, s>>>(
                 n1, a.row_start, static_cast<const int64_t*>(p->dstar_rowptr.ptr), a.out_col, a.out_cnt,
-                static_cast<uint32_t*>(p->dstar_col.ptr), static_cast<unsigned long long*>(p->dstar_count.ptr));
+                static_cast<uint32_t*>(p->dstar_col.ptr), static_cast<u64*>(p->dstar_count.ptr));
             launched(p);
         }
         return check_cuda(p, cudaGetLastError(), "gather launch");

@@ -45,6 +45,10 @@ SIGNATURES = {
 }
 
 
+class MscOpts(ctypes.Structure):
+    _fields_ = [("max_iterations", ctypes.c_int64), ("flags", ctypes.c_int32), ("path_count_tier", ctypes.c_int32)]
+
+
 class MscStats(ctypes.Structure):
     _fields_ = [("counts", ctypes.c_int64 * 4), ("n_reachable", ctypes.c_int64), ("n_bfs_levels", ctypes.c_int64),
                 ("n_junctions", ctypes.c_int64), ("nnz_A", ctypes.c_int64), ("nnz_B", ctypes.c_int64),
@@ -115,11 +119,12 @@ def _view(ptr, shape, typestr):
 class Plan:
     """Owns an msc_plan_t for one grid shape (nx, ny, nz)."""
 
-    def __init__(self, dims):
+    def __init__(self, dims, max_iterations: int = 0, path_count_tier: int = 0):
         self.dims = tuple(int(d) for d in dims)
         arr = (ctypes.c_int64 * 3)(*self.dims)
+        opts = MscOpts(int(max_iterations), 0, int(path_count_tier))
         h = ctypes.c_void_p()
-        _check(lib.msc_plan(arr, None, ctypes.byref(h)), what=f"msc_plan{self.dims}")
+        _check(lib.msc_plan(arr, ctypes.byref(opts), ctypes.byref(h)), what=f"msc_plan{self.dims}")
         self.handle = h
 
     def __del__(self):

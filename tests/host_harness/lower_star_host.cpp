@@ -1,0 +1,51 @@
+// Host harness for tests only: runs the kernel's lower-star core (lower_star.cuh) on the CPU,
+// one vertex at a time, and assembles the packed gradient words of a whole grid.
+#include <cstdint>
+#include <cstring>
+
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#include "../../paper_2009_03707_gb300/csrc/lower_star.cuh"
+
+using namespace msc::star;
+
+static uint32_t order_key(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) == 0) u = 0;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+extern "C" int host_words(const int64_t* d, const float* f, uint32_t* words) {
+    const int nx = int(d[0]), ny = int(d[1]), nz = int(d[2]);
+    std::memset(words, 0, sizeof(uint32_t) * size_t(nx) * ny * nz);
+    uint32_t vk[27], ck[27];
+    Scratch sc{vk, ck, 1};
+    int bad = 0;
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                uint32_t k[27];
+                for (int p = 0; p < 27; p++) {
+                    const int X = x + pdx(p), Y = y + pdy(p), Z = z + pdz(p);
+                    const bool out = X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz;
+                    k[p] = out ? 0xFFFFFFFFu : order_key(f[X + nx * (Y + ny * Z)]);
+                }
+                auto emit = [&](int p, uint32_t code) {
+                    const int dx = pdx(p), dy = pdy(p), dz = pdz(p);
+                    const int ox = x + (dx < 0 ? -1 : 0), oy = y + (dy < 0 ? -1 : 0), oz = z + (dz < 0 ? -1 : 0);
+                    const int slot = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+                    words[ox + nx * (oy + ny * oz)] |= code << (3 * slot);
+                };
+                if (!process_lower_star(k, sc, emit)) bad++;
+            }
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++)
+                for (int s = 0; s < 8; s++) {
+                    const bool out = ((s & 1) && x == nx - 1) || ((s & 2) && y == ny - 1) || ((s & 4) && z == nz - 1);
+                    if (out) words[x + nx * (y + ny * z)] |= 7u << (3 * s);
+                }
+    return bad;
+}

@@ -94,3 +94,17 @@ def test_dstar(name, results, expected):
     assert np.array_equal(cnt, en)
     assert r["stats"]["n_iter"] == e["n_iter"]
     assert r["stats"]["nnz_Dstar"] == len(er)
+
+
+@pytest.mark.parametrize("tier", [1, 2])
+@pytest.mark.parametrize("name", ["grf40", "grf25x30x70", "cos32", "ties(9, 8, 33)"])
+def test_dstar_every_path_count_tier(name, tier, expected):
+    """The warp-table and CTA-table tiers give the same D* as the register tier and the oracle."""
+    m = msc()
+    f = dict(CASES)[name]
+    plan = m.Plan(dims_of(f), path_count_tier=tier)
+    m.msc_compute(plan, gpu_field(f))
+    rows, cols, cnt = csr_to_coo(*(to_np(x) for x in m.msc_saddle_arcs(plan)))
+    er, ec, en = expected[name]["dstar"]
+    assert np.array_equal(rows, er) and np.array_equal(cols, ec) and np.array_equal(cnt, en)
+    assert m.msc_get_stats(plan)["n_iter"] == expected[name]["n_iter"]
