@@ -191,6 +191,41 @@ msc_status msc_get_stats(msc_plan_t plan, msc_stats* out);
  * streams, or two host threads) race on it and must be serialised by the caller.  The call
  * synchronises `stream` once (to read the counts); the lists are complete when `stream`
  * reaches the end of the call. */
+/* ---- batching and serving ------------------------------------------------------------------
+ * Many volumes of uneven size, processed concurrently (the paper's time-varying use, Sec. 1:
+ * "each time step may have to be analyzed within a short time budget").  A batch owns a pool of
+ * host worker threads, each driving its own CUDA stream on the batch's device; submitted
+ * volumes are queued and started as workers and device memory free up (continuous batching):
+ * a volume is admitted while the summed working-set estimates of the volumes in flight stay
+ * within hbm_budget_bytes (one volume is always admitted when nothing else runs).  The
+ * estimate is the plan's measured peak from earlier runs, else 128 bytes per voxel.
+ *
+ * msc_batch_create: n_workers >= 1 host threads (0 = 4); hbm_budget_bytes <= 0 = no limit.
+ * msc_batch_submit: vols[i].d_field is a caller-owned device field (valid until the volume
+ *   completes); vols[i].plan is an existing plan of the same dims to reuse (a time series keeps
+ *   its state on the device) or NULL, in which case a plan is created and returned in
+ *   vols[i].plan; the caller owns it and destroys it with msc_plan_destroy after the ticket is
+ *   done.  Work on one plan is never run concurrently: later submissions on a plan wait for the
+ *   earlier ones.  Every volume's work is ordered after the work already queued on `stream` at
+ *   submission.  Returns immediately; *ticket names the submission.
+ * msc_poll: never blocks; *done = 1 once every volume of the ticket has finished, *status =
+ *   the first non-OK status among them (MSC_OK otherwise).  Results are read from each
+ *   volume's plan with the getters above (they do no further work).
+ * msc_batch_wait: blocks until the ticket is done, then reports like msc_poll.
+ * msc_batch_destroy: waits for all queued work, then stops the workers. */
+typedef struct msc_batch_s* msc_batch_t;
+typedef struct msc_volume {
+    int64_t dims[3];
+    const float* d_field;
+    msc_plan_t plan; /* in: plan to reuse, or NULL; out: the plan holding this volume's results */
+} msc_volume;
+
+msc_status msc_batch_create(int n_workers, int64_t hbm_budget_bytes, msc_batch_t* out);
+msc_status msc_batch_destroy(msc_batch_t batch);
+msc_status msc_batch_submit(msc_batch_t batch, msc_volume* vols, int n, msc_stream_t stream, uint64_t* ticket);
+msc_status msc_poll(msc_batch_t batch, uint64_t ticket, int* done, int* status);
+msc_status msc_batch_wait(msc_batch_t batch, uint64_t ticket, int* status);
+
 #define MSC_STATIC_SCRATCH_BYTES (16u << 20)
 msc_status msc_gradient_critical_static(const int64_t dims[3], const float* d_field, uint32_t* d_words,
                                         uint32_t* const d_cells[4], const int64_t capacity[4], int64_t counts[4],

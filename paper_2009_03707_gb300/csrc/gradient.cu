@@ -173,14 +173,11 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     if ((st = ensure(p, p->words, sizeof(uint32_t) * size_t(g.nverts)))) return st;
     if ((st = ensure(p, p->crit_bits, sizeof(uint32_t) * size_t(g.slot_words())))) return st;
     const size_t smem = sizeof(Shared);
-    static bool attr_set = false;
-    if (!attr_set) {
-        if ((st = check_cuda(p, cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     int(smem)),
-                             "cudaFuncSetAttribute(gradient)")))
-            return st;
-        attr_set = true;
-    }
+    // set on every call: the attribute is per device, and plans may live on several devices
+    if ((st = check_cuda(p, cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(smem)),
+                         "cudaFuncSetAttribute(gradient)")))
+        return st;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
     gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, static_cast<uint32_t*>(p->words.ptr),
                                                 static_cast<uint32_t*>(p->crit_bits.ptr),

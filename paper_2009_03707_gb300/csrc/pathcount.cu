@@ -13,7 +13,8 @@
 //
 // Rows are latency-bound chains of dependent gathers, so the work goes to the smallest worker
 // that can hold it, to keep as many rows in flight as possible:
-//   tier 0  one thread per row, frontier (<= 4) and D* row (<= 8) in registers;
+//   tier 0  one thread per row, frontier (<= 8) and D* row (<= 16) in shared memory, 32-bit
+//           counts;
 //   tier 1  one warp per row, 256-slot hash tables in shared memory;
 //   tier 2+ one CTA per row, hash tables in global memory, grown until the row fits.
 // A row that overflows its worker is deferred, intact, to the next tier.  Finished rows are
@@ -27,8 +28,8 @@ namespace {
 
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr int T0_THREADS = 256;
-constexpr int T0_F = 4;  // frontier slots per thread
-constexpr int T0_D = 8;  // D* row slots per thread
+constexpr int T0_F = 8;   // frontier slots per thread
+constexpr int T0_D = 16;  // D* row slots per thread
 constexpr int T1_WARPS = 4;
 constexpr int T1_HASH = 256;  // slots per table (power of two)
 constexpr int T1_LIST = T1_HASH / 2;
@@ -64,29 +65,33 @@ __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
 }
 
 // ---------------------------------------------------------------------------------------
-// tier 0: registers
+// tier 0: one thread per row, small maps in shared memory
 // ---------------------------------------------------------------------------------------
-// Adds (key, val) to a small register map; false if it is full.  Indices are compile-time
-// constants throughout so the arrays stay in registers.
+// Each thread owns columns of [slot][thread] arrays (conflict-free across a warp): two
+// frontier buffers of T0_F entries and a D* row of T0_D entries, keys and 32-bit counts.  Loops
+// run over the entries actually present.  A row that needs more slots, or whose counts outgrow
+// 32 bits, is deferred intact to the uint64 warp tier.
+struct T0Shared {
+    uint32_t fk[2][T0_F][T0_THREADS];
+    uint32_t fv[2][T0_F][T0_THREADS];
+    uint32_t dk[T0_D][T0_THREADS];
+    uint32_t dv[T0_D][T0_THREADS];
+};
+
+// Adds (key, val) to the column map K/V of n entries; false if full or a count would wrap.
 template <int N>
-__device__ __forceinline__ bool reg_add(uint32_t (&k)[N], u64 (&v)[N], int& n, uint32_t key, u64 val, bool& ovf) {
-    bool found = false;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < n && k[i] == key) {
-            const u64 o = v[i];
-            v[i] = o + val;
-            ovf |= v[i] < o;
-            found = true;
+__device__ __forceinline__ bool col_add(uint32_t (*K)[T0_THREADS], uint32_t (*V)[T0_THREADS], int& n, int t,
+                                        uint32_t key, uint32_t val) {
+    for (int i = 0; i < n; ++i)
+        if (K[i][t] == key) {
+            const uint32_t v = V[i][t] + val;
+            if (v < val) return false;
+            V[i][t] = v;
+            return true;
         }
-    if (found) return true;
     if (n >= N) return false;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i == n) {
-            k[i] = key;
-            v[i] = val;
-        }
+    K[n][t] = key;
+    V[n][t] = val;
     ++n;
     return true;
 }
@@ -115,18 +120,14 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
 }
 
 __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
-    const int64_t i = int64_t(blockIdx.x) * T0_THREADS + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char t0_raw[];
+    T0Shared& sh = *reinterpret_cast<T0Shared*>(t0_raw);
+    const int t = threadIdx.x;
+    const int64_t i = int64_t(blockIdx.x) * T0_THREADS + t;
     const bool valid = i < a.nrows;  // every lane stays to the warp-wide appends at the end
     const int64_t s = valid ? row_of(a, i) : 0;
-    uint32_t fk[T0_F], dk[T0_D];
-    u64 fv[T0_F], dv[T0_D];
-#pragma unroll
-    for (int e = 0; e < T0_D; ++e) {
-        dk[e] = EMPTY;
-        dv[e] = 0;
-    }
-    int nf = 0, nd = 0;
-    bool fit = true, ovf = false;
+    int cur = 0, nf = 0, nd = 0;
+    bool fit = true;
     u64 iter = 0, entries = 0;
     if (valid) {
         const uint32_t kinds = a.kinds[s];
@@ -135,8 +136,8 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t kind = (kinds >> (2 * k)) & 3u;
-            if (kind == 1) fit = fit && reg_add(fk, fv, nf, tg[k], 1, ovf);
-            if (kind == 2) fit = fit && reg_add(dk, dv, nd, tg[k], 1, ovf);
+            if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[0], sh.fv[0], nf, t, tg[k], 1);
+            if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tg[k], 1);
         }
         while (fit && nf > 0) {
             if (int64_t(++iter) > a.max_iter) {
@@ -144,62 +145,50 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
                 break;
             }
             entries += nf;
-            uint32_t gk[T0_F];
-            u64 gv[T0_F];
             int ng = 0;
+            for (int e = 0; e < nf && fit; ++e) {
+                const int64_t j = a.n1 + int64_t(sh.fk[cur][e][t]);
+                const uint32_t c = sh.fv[cur][e][t];
+                const uint32_t kj = a.kinds[j];
+                const uint4 q = trace_of(a, j);
+                const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int e = 0; e < T0_F; ++e) {
-                if (e < nf) {
-                    const int64_t j = a.n1 + int64_t(fk[e]);
-                    const u64 c = fv[e];
-                    const uint32_t kj = a.kinds[j];
-                    const uint4 q = trace_of(a, j);
-                    const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t kind = (kj >> (2 * k)) & 3u;
-                        if (kind == 1) fit = fit && reg_add(gk, gv, ng, tq[k], c, ovf);
-                        if (kind == 2) fit = fit && reg_add(dk, dv, nd, tq[k], c, ovf);
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t kind = (kj >> (2 * k)) & 3u;
+                    if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[cur ^ 1], sh.fv[cur ^ 1], ng, t, tq[k], c);
+                    if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tq[k], c);
                 }
             }
-#pragma unroll
-            for (int e = 0; e < T0_F; ++e) {
-                fk[e] = gk[e];
-                fv[e] = gv[e];
-            }
+            cur ^= 1;
             nf = ng;
         }
     }
-    if (ovf) atomicOr(a.status, ST_OVERFLOW);
     const bool done = valid && fit;
-    // sort the row by column (odd-even transposition; empty slots hold EMPTY and sink)
-#pragma unroll
-    for (int round = 0; round < T0_D; ++round)
-#pragma unroll
-        for (int e = round & 1; e + 1 < T0_D; e += 2)
-            if (dk[e] > dk[e + 1]) {
-                const uint32_t tk = dk[e];
-                dk[e] = dk[e + 1];
-                dk[e + 1] = tk;
-                const u64 tv = dv[e];
-                dv[e] = dv[e + 1];
-                dv[e + 1] = tv;
+    // sort the row by column (insertion sort over the thread's column)
+    if (done)
+        for (int e = 1; e < nd; ++e) {
+            const uint32_t k = sh.dk[e][t], v = sh.dv[e][t];
+            int f = e;
+            while (f > 0 && sh.dk[f - 1][t] > k) {
+                sh.dk[f][t] = sh.dk[f - 1][t];
+                sh.dv[f][t] = sh.dv[f - 1][t];
+                --f;
             }
+            sh.dk[f][t] = k;
+            sh.dv[f][t] = v;
+        }
     const unsigned n_out = done ? unsigned(nd) : 0u;
     const u64 base = warp_append(a.out_cursor, n_out);
     u64 mx = 0;
-#pragma unroll
-    for (int e = 0; e < T0_D; ++e)
-        if (e < int(n_out)) {
-            if (base + e < a.out_cap) {
-                a.out_col[base + e] = dk[e];
-                a.out_cnt[base + e] = dv[e];
-            } else {
-                atomicOr(a.status, ST_CAPACITY);
-            }
-            mx = max(mx, dv[e]);
+    for (unsigned e = 0; e < n_out; ++e) {
+        if (base + e < a.out_cap) {
+            a.out_col[base + e] = sh.dk[e][t];
+            a.out_cnt[base + e] = sh.dv[e][t];
+        } else {
+            atomicOr(a.status, ST_CAPACITY);
         }
+        mx = max(mx, (u64)sh.dv[e][t]);
+    }
     if (done) {
         a.row_start[s] = int64_t(base);
         a.row_len[s] = n_out;
@@ -526,8 +515,12 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             msc_status e;
             if ((e = check_cuda(p, cudaMemsetAsync(a.deferred_count, 0, sizeof(u64), s), "memset"))) return e;
             if (tier == 0) {
+                if ((e = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                            int(sizeof(T0Shared))),
+                                    "cudaFuncSetAttribute(rows_thread)")))
+                    return e;
                 cudaEventRecord(p->kev0, s);
-                rows_thread<<<int((nrows + T0_THREADS - 1) / T0_THREADS), T0_THREADS, 0, s>>>(a);
+                rows_thread<<<int((nrows + T0_THREADS - 1) / T0_THREADS), T0_THREADS, sizeof(T0Shared), s>>>(a);
                 cudaEventRecord(p->kev1, s);
                 launched(p);
             } else if (tier == 1) {

@@ -42,6 +42,11 @@ SIGNATURES = {
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
     "msc_gradient_critical_static": ([_PI64, _P, _P, _PP, _PI64, _PI64, _P], _I32),
+    "msc_batch_create": ([_I32, _I64, _PP], _I32),
+    "msc_batch_destroy": ([_P], _I32),
+    "msc_batch_submit": ([_P, _P, _I32, _P, ctypes.POINTER(ctypes.c_uint64)], _I32),
+    "msc_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], _I32),
+    "msc_batch_wait": ([_P, ctypes.c_uint64, ctypes.POINTER(_I32)], _I32),
 }
 
 
@@ -126,6 +131,14 @@ class Plan:
         h = ctypes.c_void_p()
         _check(lib.msc_plan(arr, ctypes.byref(opts), ctypes.byref(h)), what=f"msc_plan{self.dims}")
         self.handle = h
+
+    @classmethod
+    def adopt(cls, handle: int, dims):
+        """Wrap (and take ownership of) a plan the library created, e.g. by msc_batch_submit."""
+        obj = cls.__new__(cls)
+        obj.dims = tuple(int(d) for d in dims)
+        obj.handle = ctypes.c_void_p(handle)
+        return obj
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -245,6 +258,67 @@ def msc_gradient_critical_static(field: torch.Tensor, words: torch.Tensor, cells
     if st != MSC_OK:
         raise MscError(st, f"msc_gradient_critical_static{(nx, ny, nz)} counts={list(counts)}")
     return [int(c) for c in counts]
+
+
+class MscVolume(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int64 * 3), ("d_field", ctypes.c_void_p), ("plan", ctypes.c_void_p)]
+
+
+class Batch:
+    """msc_batch_*: a pool of worker threads/streams that runs submitted volumes concurrently,
+    admitting them against an HBM budget (continuous batching)."""
+
+    def __init__(self, n_workers: int = 4, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib.msc_batch_create(int(n_workers), int(hbm_budget_bytes), ctypes.byref(h)), what="msc_batch_create")
+        self.handle = h
+        self._inflight = {}
+
+    def msc_batch_submit(self, fields, plans=None):
+        """Queue volumes; returns (ticket, plans).  A None plan is created by the library."""
+        n = len(fields)
+        plans = list(plans) if plans is not None else [None] * n
+        vols = (MscVolume * n)()
+        for i, f in enumerate(fields):
+            if f.dtype != torch.float32 or not f.is_cuda or not f.is_contiguous():
+                raise ValueError("fields must be contiguous float32 CUDA tensors")
+            nz, ny, nx = f.shape
+            vols[i].dims[:] = (nx, ny, nz)
+            vols[i].d_field = f.data_ptr()
+            vols[i].plan = plans[i].handle.value if plans[i] is not None else None
+        t = ctypes.c_uint64()
+        _check(lib.msc_batch_submit(self.handle, vols, n, _stream(), ctypes.byref(t)), what="msc_batch_submit")
+        out = []
+        for i, f in enumerate(fields):
+            if plans[i] is None:
+                nz, ny, nx = f.shape
+                plans[i] = Plan.adopt(vols[i].plan, (nx, ny, nz))
+            out.append(plans[i])
+        self._inflight[t.value] = (list(fields), out)  # keep inputs and plans alive
+        return t.value, out
+
+    def msc_poll(self, ticket: int):
+        done, status = ctypes.c_int(), ctypes.c_int()
+        _check(lib.msc_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(status)),
+               what="msc_poll")
+        if done.value:
+            self._inflight.pop(ticket, None)
+        return bool(done.value), int(status.value)
+
+    def msc_batch_wait(self, ticket: int) -> int:
+        status = ctypes.c_int()
+        _check(lib.msc_batch_wait(self.handle, ctypes.c_uint64(ticket), ctypes.byref(status)), what="msc_batch_wait")
+        self._inflight.pop(ticket, None)
+        return int(status.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.msc_batch_destroy(self.handle)
+            self.handle = None
+            self._inflight.clear()
+
+    def __del__(self):
+        self.close()
 
 
 def compute(field: torch.Tensor, plan: Plan | None = None) -> dict:

@@ -123,6 +123,23 @@ class ServingStream:
     mean: float
     std: float
 
+    def step_device(self, t: int, device="cuda"):
+        """The same step synthesised with torch.fft on `device` (for feeding a server at
+        request rate); float32 [n, n, n] tensor.  Matches step() to float32 rounding."""
+        import torch
+
+        n = self.size
+        spec = getattr(self, "_spec_dev", None)
+        if spec is None or spec.device != torch.device(device):
+            spec = self._spec_dev = torch.from_numpy(self.spectrum).to(device)
+        kz = torch.fft.fftfreq(n, device=device, dtype=torch.float64)[:, None, None]
+        ky = torch.fft.fftfreq(n, device=device, dtype=torch.float64)[None, :, None]
+        kx = torch.fft.rfftfreq(n, device=device, dtype=torch.float64)[None, None, :]
+        vx, vy, vz = (float(v) * float(t) for v in self.velocity)
+        phase = torch.exp(-2j * np.pi * (kx * vx + ky * vy + kz * vz))
+        f = torch.fft.irfftn(spec * phase, s=(n, n, n), dim=(0, 1, 2))
+        return ((f - self.mean) / self.std).to(torch.float32).contiguous()
+
     def step(self, t: int) -> np.ndarray:
         n = self.size
         kz = np.fft.fftfreq(n)[:, None, None]
