@@ -6,18 +6,19 @@
 // (the lower star L(x)) are paired among themselves, so every vertex is independent work.
 //
 // GB300 design (not the paper's texture-object kernel):
-//  * One CTA owns a 32 x 8 x 8 tile of vertices.  The field tile plus a (-1,+2) halo is
-//    staged in shared memory as order-preserving uint32 keys.  The CTA computes the lower
-//    stars of the tile plus one layer on the + side (a cell is owned by its lowest corner
-//    vertex but decided by its highest one) and ORs 3-bit codes into shared words.
-//  * A lower star is handled as 27-bit masks over the offsets d in {-1,0,1}^3: membership
-//    (all sub-offsets lower), facets / cofacets (one component cleared / set), classified,
-//    and the two priority queues.  Cell keys are rank bitmasks: with the vertices of L(x)
-//    ranked, the key of a cell is the OR of its vertices' rank bits, and comparing these
-//    integers is exactly the lexicographic comparison of the vertices sorted downwards.
-//  * The epilogue writes the packed words with coalesced 128-byte rows, and one warp ballot
-//    per slot turns 32 vertices into one 32-bit word of the critical-cell bitmap of that
-//    slot -- the input of the ordered compaction (critical.cu).
+//  * One CTA owns a 32 x 8 x 8 tile of vertices and computes exactly their lower stars.  The
+//    field tile plus a one-vertex halo is staged in shared memory as order-preserving uint32 keys.
+//  * A cell's 3-bit code lives in the word of its lowest corner vertex (its owner) but is decided
+//    by its highest vertex.  Codes whose owner is in the tile are OR-ed into shared words; codes
+//    whose owner is in the neighbouring tile on the - side go straight to global memory with
+//    atomicOr.  So the tile's words on its + faces are finished with atomicOr too, into words
+//    zeroed beforehand, and every other word is a plain coalesced store.
+//  * A lower star is handled as 27-bit masks over the offsets d in {-1,0,1}^3 (lower_star.cuh).
+//    Stars differ widely in size (1..27 cells) and a warp runs as long as its largest, so the
+//    CTA first sizes every star and counting-sorts its vertices by size; consecutive threads
+//    then take stars of equal size.
+//  * A second, bandwidth-bound kernel turns the finished words into per-slot critical bitmaps:
+//    one warp ballot per slot gives 32 vertices' bits -- the input of the ordered compaction.
 #include "lower_star.cuh"
 #include "msc_internal.cuh"
 
@@ -26,9 +27,9 @@ namespace msc {
 namespace {
 
 constexpr int TX = 32, TY = 8, TZ = 8;               // owned tile
-constexpr int EX = TX + 1, EY = TY + 1, EZ = TZ + 1;  // lower stars computed (tile + 1 on + side)
-constexpr int FX = TX + 3, FY = TY + 3, FZ = TZ + 3;  // field keys staged (x0-1 .. x0+TX+1)
-constexpr int THREADS = 256;
+constexpr int FX = TX + 2, FY = TY + 2, FZ = TZ + 2;  // field keys staged (x0-1 .. x0+TX)
+constexpr int NOWN = TX * TY * TZ;
+constexpr int THREADS = 512;
 constexpr uint32_t OUTSIDE_KEY = 0xFFFFFFFFu;
 
 using star::pdx;
@@ -42,41 +43,32 @@ __device__ __forceinline__ uint32_t order_key(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-constexpr int NEXT = EX * EY * EZ;  // vertices whose lower stars a CTA computes
-
 struct Shared {
     uint32_t fkey[FZ][FY][FX];   // order keys of the field tile (OUTSIDE_KEY off-grid)
     uint32_t words[TZ][TY][TX];  // packed codes of the owned tile
     uint32_t vkey[27][THREADS];  // per-thread scratch: keys of the star's vertices
-    uint32_t ckey[27][THREADS];  // per-thread scratch: rank-bitmask keys of the star's cells
-    uint16_t order[NEXT];        // non-minimal vertices, grouped by lower-star size
-    uint8_t size[NEXT];          // |L(x)| - 1 of every vertex (0 for minima and off-grid)
-    int bin[28];                 // counting-sort bins by size
+    uint32_t inl[NOWN];          // lower-star mask of every owned vertex (0: off-grid)
+    uint16_t order[NOWN];        // non-minimal vertices, largest stars first
+    int bin[28];                 // counting-sort bins by star size
 };
-
-// The 27 order keys of the star of the vertex at tile-local (lx,ly,lz).
-__device__ __forceinline__ void star_keys(const Shared& sh, int lx, int ly, int lz, uint32_t (&k)[27]) {
-#pragma unroll
-    for (int p = 0; p < 27; ++p) k[p] = sh.fkey[lz + 1 + pdz(p)][ly + 1 + pdy(p)][lx + 1 + pdx(p)];
-}
 
 __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* __restrict__ field,
                                                            uint32_t* __restrict__ words_out,
-                                                           uint32_t* __restrict__ crit_bits,
                                                            uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
 
-    for (int i = t; i < TX * TY * TZ; i += THREADS) (&sh.words[0][0][0])[i] = 0;
+    for (int i = t; i < NOWN; i += THREADS) (&sh.words[0][0][0])[i] = 0;
+    if (t < 28) sh.bin[t] = 0;
     bool saw_nan = false;
     for (int i = t; i < FX * FY * FZ; i += THREADS) {
-        int fx = i % FX, fy = (i / FX) % FY, fz = i / (FX * FY);
-        int gx = x0 - 1 + fx, gy = y0 - 1 + fy, gz = z0 - 1 + fz;
+        const int fx = i % FX, fy = (i / FX) % FY, fz = i / (FX * FY);
+        const int gx = x0 - 1 + fx, gy = y0 - 1 + fy, gz = z0 - 1 + fz;
         uint32_t key = OUTSIDE_KEY;
         if (gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz) {
-            float v = __ldg(field + g.vid(gx, gy, gz));
+            const float v = __ldg(field + g.vid(gx, gy, gz));
             saw_nan |= isnan(v);
             key = order_key(v);
         }
@@ -85,26 +77,24 @@ __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* 
     if (saw_nan) atomicOr(status, ST_NAN);
     __syncthreads();
 
-    // Lower stars differ widely in size (1..27 cells), and a warp runs as long as its largest
-    // one.  So first size every star (cheap mask arithmetic), counting-sort the non-minimal
-    // vertices by size, and let consecutive threads take consecutive entries.
-    if (t < 28) sh.bin[t] = 0;
-    __syncthreads();
-    for (int i = t; i < NEXT; i += THREADS) {
-        const int lx = i % EX, ly = (i / EX) % EY, lz = i / (EX * EY);
-        int m = 0;
+    // size every star (cheap mask arithmetic) and counting-sort the non-minimal ones
+    for (int i = t; i < NOWN; i += THREADS) {
+        const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+        uint32_t inL = 0;
         if (x0 + lx < g.nx && y0 + ly < g.ny && z0 + lz < g.nz) {
             uint32_t k[27];
-            star_keys(sh, lx, ly, lz, k);
-            m = __popc(star::lower_star_mask(star::lower_mask(k))) - 1;
+#pragma unroll
+            for (int p = 0; p < 27; ++p) k[p] = sh.fkey[lz + 1 + pdz(p)][ly + 1 + pdy(p)][lx + 1 + pdx(p)];
+            inL = star::lower_star_mask(star::lower_mask(k));
+            const int m = __popc(inL) - 1;
+            if (m > 0) atomicAdd(&sh.bin[m], 1);
         }
-        sh.size[i] = uint8_t(m);
-        if (m > 0) atomicAdd(&sh.bin[m], 1);
+        sh.inl[i] = inL;
     }
     __syncthreads();
     if (t == 0) {
         int acc = 0;
-        for (int m = 27; m >= 1; --m) {  // largest stars first
+        for (int m = 26; m >= 1; --m) {
             const int c = sh.bin[m];
             sh.bin[m] = acc;
             acc += c;
@@ -112,57 +102,87 @@ __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* 
         sh.bin[0] = acc;  // number of non-minimal vertices
     }
     __syncthreads();
-    for (int i = t; i < NEXT; i += THREADS) {
-        const int m = sh.size[i];
+    for (int i = t; i < NOWN; i += THREADS) {
+        const int m = __popc(sh.inl[i]) - 1;
         if (m > 0) sh.order[atomicAdd(&sh.bin[m], 1)] = uint16_t(i);
     }
     __syncthreads();
     const int n_items = sh.bin[0];
 
     bool ok = true;
-    const star::Scratch sc{&sh.vkey[0][t], &sh.ckey[0][t], THREADS};
+    const star::Scratch sc{&sh.vkey[0][t], THREADS};
     for (int it = t; it < n_items; it += THREADS) {
         const int i = sh.order[it];
-        const int lx = i % EX, ly = (i / EX) % EY, lz = i / (EX * EY);
-        uint32_t k[27];
-        star_keys(sh, lx, ly, lz, k);
-        // a cell is owned by its lowest corner vertex: record its code there if that vertex
-        // belongs to this CTA's tile
+        const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+        const uint32_t inL = sh.inl[i];
+        const uint32_t* center = &sh.fkey[lz + 1][ly + 1][lx + 1];
+#pragma unroll
+        for (int p = 0; p < 27; ++p)  // the keys of the star's vertices (constant offsets)
+            if ((inL >> p) & 1u) sc.v(p) = center[pdz(p) * FY * FX + pdy(p) * FX + pdx(p)];
+        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+        // a cell is owned by its lowest corner vertex: OR its code into that vertex's word
         auto emit = [&](int p, uint32_t code) {
-            const int dx = pdx(p), dy = pdy(p), dz = pdz(p);
-            const int ox = lx + (dx < 0 ? -1 : 0), oy = ly + (dy < 0 ? -1 : 0), oz = lz + (dz < 0 ? -1 : 0);
-            if (ox < 0 || oy < 0 || oz < 0 || ox >= TX || oy >= TY || oz >= TZ) return;
-            const int slot = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
-            atomicOr(&sh.words[oz][oy][ox], code << (3 * slot));
+            const int xn = (star::XN >> p) & 1, yn = (star::YN >> p) & 1, zn = (star::ZN >> p) & 1;
+            const int slot = (((star::XZ >> p) & 1) ^ 1) | ((((star::YZ >> p) & 1) ^ 1) << 1) |
+                             ((((star::ZZ >> p) & 1) ^ 1) << 2);
+            const int ox = lx - xn, oy = ly - yn, oz = lz - zn;
+            if ((ox | oy | oz) >= 0) atomicOr(&sh.words[oz][oy][ox], code << (3 * slot));
+            else atomicOr(words_out + g.vid(gx - xn, gy - yn, gz - zn), code << (3 * slot));
         };
-        ok &= star::process_lower_star(k, sc, emit);
+        ok &= star::pair_lower_star(inL, sc, emit);
     }
     if (!ok) atomicOr(status, ST_INTERNAL);
     __syncthreads();
 
-    // epilogue: packed words + per-slot critical bitmaps (one ballot per slot and row)
+    // epilogue: far-boundary codes, then plain stores -- or atomicOr on the tile's + faces,
+    // whose words also receive codes from the neighbouring tiles
     const int lane = t & 31, warp = t >> 5;
     const int gx = x0 + lane;
     for (int r = warp; r < TY * TZ; r += THREADS / 32) {
         const int ly = r % TY, lz = r / TY;
         const int gy = y0 + ly, gz = z0 + lz;
-        if (gy >= g.ny || gz >= g.nz) continue;  // warp-uniform
-        const bool valid = gx < g.nx;
+        if (gy >= g.ny || gz >= g.nz || gx >= g.nx) continue;
         uint32_t w = sh.words[lz][ly][lane];
-        // slots beyond the far boundary hold code 7
         for (int s = 0; s < 8; ++s) {
-            bool out = ((s & 1) && gx == g.nx - 1) || ((s & 2) && gy == g.ny - 1) || ((s & 4) && gz == g.nz - 1);
+            const bool out = ((s & 1) && gx == g.nx - 1) || ((s & 2) && gy == g.ny - 1) || ((s & 4) && gz == g.nz - 1);
             if (out) w |= 7u << (3 * s);
         }
-        if (valid) words_out[g.vid(gx, gy, gz)] = w;
-        uint32_t mine = 0;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            uint32_t bits = __ballot_sync(0xFFFFFFFFu, valid && slot_code(w, s) == 0);
-            if (lane == s) mine = bits;
-        }
-        if (lane < 8) crit_bits[g.slot_word(lane, gz, gy, x0 >> 5)] = mine;
+        if (lane == TX - 1 || ly == TY - 1 || lz == TZ - 1) atomicOr(words_out + g.vid(gx, gy, gz), w);
+        else words_out[g.vid(gx, gy, gz)] = w;
     }
+}
+
+// Per-slot critical bitmaps from finished words: one warp per 32 vertices of a row.
+__global__ void __launch_bounds__(256) critical_bitmaps(Geom g, const uint32_t* __restrict__ words,
+                                                        uint32_t* __restrict__ crit_bits) {
+    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= int64_t(g.nz) * g.ny * g.W) return;  // warp-uniform
+    const int w = int(wid % g.W), y = int((wid / g.W) % g.ny), z = int(wid / (int64_t(g.W) * g.ny));
+    const int x = w * 32 + lane;
+    const bool valid = x < g.nx;
+    const uint32_t word = valid ? words[g.vid(x, y, z)] : 0x00FFFFFFu;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, valid && slot_code(word, s) == 0);
+        if (lane == s) mine = bits;
+    }
+    if (lane < 8) crit_bits[g.slot_word(lane, z, y, w)] = mine;
+}
+
+cudaError_t launch_gradient(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
+                            uint32_t* status, cudaStream_t s) {
+    const size_t smem = sizeof(Shared);
+    // set on every call: the attribute is per device, and plans may live on several devices
+    cudaError_t e = cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * size_t(g.nverts), s)) != cudaSuccess) return e;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
+    gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, words, status);
+    const int64_t warps = int64_t(g.nz) * g.ny * g.W;
+    critical_bitmaps<<<int((warps * 32 + 255) / 256), 256, 0, s>>>(g, words, crit_bits);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -172,30 +192,18 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     msc_status st;
     if ((st = ensure(p, p->words, sizeof(uint32_t) * size_t(g.nverts)))) return st;
     if ((st = ensure(p, p->crit_bits, sizeof(uint32_t) * size_t(g.slot_words())))) return st;
-    const size_t smem = sizeof(Shared);
-    // set on every call: the attribute is per device, and plans may live on several devices
-    if ((st = check_cuda(p, cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int(smem)),
-                         "cudaFuncSetAttribute(gradient)")))
-        return st;
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-    gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, static_cast<uint32_t*>(p->words.ptr),
-                                                static_cast<uint32_t*>(p->crit_bits.ptr),
-                                                static_cast<uint32_t*>(p->status.ptr));
-    launched(p);
-    return check_cuda(p, cudaGetLastError(), "gradient_kernel launch");
+    launched(p, 2);
+    return check_cuda(p,
+                      launch_gradient(g, d_field, static_cast<uint32_t*>(p->words.ptr),
+                                      static_cast<uint32_t*>(p->crit_bits.ptr), static_cast<uint32_t*>(p->status.ptr), s),
+                      "gradient launch");
 }
 
-// Launch of the same kernel on caller-supplied buffers, with no plan and no allocation (used by
-// the no-allocation entry point, static_entry.cu).
+// The same launches on caller-supplied buffers, with no plan and no allocation (used by the
+// no-allocation entry point, static_entry.cu).
 cudaError_t launch_gradient_raw(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
                                 uint32_t* status, cudaStream_t s) {
-    const size_t smem = sizeof(Shared);
-    cudaError_t e = cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-    gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, words, crit_bits, status);
-    return cudaGetLastError();
+    return launch_gradient(g, d_field, words, crit_bits, status, s);
 }
 
 }  // namespace msc

@@ -12,10 +12,11 @@
 //
 // Everything is a 27-bit mask: membership in L(x) (a cell is in L(x) iff all its vertices
 // other than x are lower, i.e. every sub-offset is lower), facets through x (clear one
-// non-zero component), cofacets (set one zero component), the classified set and both
-// queues.  The order of cells is a rank bitmask: rank the vertices of L(x), give each cell
-// the OR of its vertices' rank bits; comparing these integers compares the cells' vertex
-// lists sorted downwards lexicographically.
+// non-zero component), cofacets (set one zero component), a cell's vertex set (its
+// sub-offsets), the classified set and both queues.  Two cells are compared by their vertex
+// lists sorted downwards, lexicographically: the cell whose vertex set holds the largest vertex
+// of the symmetric difference is the larger one (a proper prefix is therefore smaller), so a
+// comparison costs one key lookup per vertex in the symmetric difference and no ranking.
 #pragma once
 
 #include <stdint.h>
@@ -70,28 +71,50 @@ __host__ __device__ inline uint32_t lower_star_mask(uint32_t lower_with_center) 
     return m & ALL;
 }
 
-// Per-thread scratch: vertex keys and cell keys of the 27 positions.  On the device they
-// live in shared memory with a [position][thread] layout (stride = threads per CTA).
+// The vertices of the cell at position p (other than x): the positions q whose every
+// component is 0 or equal to p's.
+__host__ __device__ inline uint32_t cell_vertices(int p) {
+    const uint32_t xs = XZ | (XN & (0u - ((XN >> p) & 1u))) | (XP & (0u - ((XP >> p) & 1u)));
+    const uint32_t ys = YZ | (YN & (0u - ((YN >> p) & 1u))) | (YP & (0u - ((YP >> p) & 1u)));
+    const uint32_t zs = ZZ | (ZN & (0u - ((ZN >> p) & 1u))) | (ZP & (0u - ((ZP >> p) & 1u)));
+    return xs & ys & zs & ~(1u << CENTER);
+}
+
+// Per-thread scratch: the order keys of the star's vertices.  On the device it lives in shared
+// memory with a [position][thread] layout (stride = threads per CTA).
 struct Scratch {
     uint32_t* vkey;
-    uint32_t* ckey;
     int stride;
     __host__ __device__ uint32_t& v(int p) const { return vkey[p * stride]; }
-    __host__ __device__ uint32_t& c(int p) const { return ckey[p * stride]; }
 };
+
+// True if the cell at position a is smaller than the one at b (a != b): the larger one owns
+// the largest vertex (key, then position) of the symmetric difference of their vertex sets.
+__host__ __device__ inline bool cell_less(int a, int b, const Scratch& sc) {
+    const uint32_t vb = cell_vertices(b);
+    uint32_t d = cell_vertices(a) ^ vb;
+    int w = MSC_FFS(d) - 1;
+    uint32_t kw = sc.v(w);
+    d &= d - 1;
+    while (d) {  // ascending positions: on equal keys the later position wins
+        const int q = MSC_FFS(d) - 1;
+        d &= d - 1;
+        const uint32_t kq = sc.v(q);
+        if (kq >= kw) {
+            kw = kq;
+            w = q;
+        }
+    }
+    return (vb >> w) & 1u;
+}
 
 __host__ __device__ inline int pop_min(uint32_t mask, const Scratch& sc) {
     int best = MSC_FFS(mask) - 1;
-    uint32_t bk = sc.c(best);
     mask &= mask - 1;
     while (mask) {
-        int p = MSC_FFS(mask) - 1;
+        const int p = MSC_FFS(mask) - 1;
         mask &= mask - 1;
-        uint32_t k = sc.c(p);
-        if (k < bk) {
-            bk = k;
-            best = p;
-        }
+        if (cell_less(p, best, sc)) best = p;
     }
     return best;
 }
@@ -114,44 +137,13 @@ __host__ __device__ inline uint32_t lower_mask(const uint32_t* k) {
     return lower;
 }
 
-// Pairs the cells of L(x) given the 27 vertex order keys k[] (k[13] = x; an off-grid vertex
-// has key 0xFFFFFFFF).  Vertices with equal keys are ordered by position, which is their
-// index order.  emit(p, code) is called for every non-critical cell with its direction code.
-// Returns false if the procedure did not classify every cell (an internal error).
+// Pairs the cells of L(x) given inL (the lower-star mask, with more than x in it) and the order
+// keys of the vertices of L(x) in sc.v(p) for every p in inL other than 13.  Vertices with equal
+// keys are ordered by position, which is their index order.  emit(p, code) is called for every
+// non-critical cell with its direction code.  Returns false if the procedure did not classify
+// every cell (an internal error).
 template <class Emit>
-__host__ __device__ bool process_lower_star(const uint32_t* k, const Scratch& sc, Emit&& emit) {
-    const uint32_t inL = lower_star_mask(lower_mask(k));
-    if (inL == (1u << CENTER)) return true;  // a minimum: every code stays 0
-
-    // rank the vertices of L(x) other than x
-    const uint32_t V = inL & ~(1u << CENTER);
-#pragma unroll
-    for (int p = 0; p < 27; ++p) sc.v(p) = k[p];
-    for (uint32_t a = V; a; a &= a - 1) {
-        int p = MSC_FFS(a) - 1;
-        uint32_t kp = sc.v(p);
-        int r = 0;
-        for (uint32_t b = V; b; b &= b - 1) {
-            int q = MSC_FFS(b) - 1;
-            uint32_t kq = sc.v(q);
-            r += (kq < kp) || (kq == kp && q < p);
-        }
-        sc.c(p) = 1u << r;
-    }
-    // cell keys in increasing dimension: own vertex bit | keys of the facets through x
-    for (uint32_t a = V & DIM2; a; a &= a - 1) {
-        int p = MSC_FFS(a) - 1;
-        uint32_t key = sc.c(p);
-        for (uint32_t f = facet_mask(p); f; f &= f - 1) key |= sc.c(MSC_FFS(f) - 1);
-        sc.c(p) = key;
-    }
-    for (uint32_t a = V & DIM3; a; a &= a - 1) {
-        int p = MSC_FFS(a) - 1;
-        uint32_t key = sc.c(p);
-        for (uint32_t f = facet_mask(p); f; f &= f - 1) key |= sc.c(MSC_FFS(f) - 1);
-        sc.c(p) = key;
-    }
-
+__host__ __device__ bool pair_lower_star(const uint32_t inL, const Scratch& sc, Emit&& emit) {
     const int delta = pop_min(inL & DIM1, sc);
     uint32_t cls = (1u << CENTER) | (1u << delta);
     emit(CENTER, dir_code(CENTER, delta));
@@ -193,6 +185,17 @@ __host__ __device__ bool process_lower_star(const uint32_t* k, const Scratch& sc
         }
     }
     return false;
+}
+
+// Pairs the cells of L(x) given the 27 vertex order keys k[] (k[13] = x; an off-grid vertex
+// has key 0xFFFFFFFF).  See pair_lower_star.
+template <class Emit>
+__host__ __device__ bool process_lower_star(const uint32_t* k, const Scratch& sc, Emit&& emit) {
+    const uint32_t inL = lower_star_mask(lower_mask(k));
+    if (inL == (1u << CENTER)) return true;  // a minimum: every code stays 0
+    for (int p = 0; p < 27; ++p)
+        if ((inL >> p) & 1u) sc.v(p) = k[p];
+    return pair_lower_star(inL, sc, emit);
 }
 
 }  // namespace star
