@@ -133,10 +133,7 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
     p->g.nx = int(dims[0]);
     p->g.ny = int(dims[1]);
     p->g.nz = int(dims[2]);
-    p->g.W = int((dims[0] + 31) / 32);
-    p->g.nverts = dims[0] * dims[1] * dims[2];
-    p->g.rx = uint32_t(rx);
-    p->g.ry = uint32_t(ry);
+    p->g.finish();
     if (opts) p->opts = *opts;
     if (p->opts.max_iterations <= 0) p->opts.max_iterations = int64_t(1) << 20;
     msc_status st = msc::check_cuda(p, cudaGetDevice(&p->device), "cudaGetDevice");

@@ -9,7 +9,8 @@
 //
 // A 1-cell is named by its owner vertex and axis: handle = (vertex index << 2) | axis, where
 // the cell is (2x+1,2y,2z), (2x,2y+1,2z) or (2x,2y,2z+1) for axis 0, 1, 2.  A 2-saddle target
-// is named by its owner vertex and slot.
+// is named by its owner vertex and slot.  All index arithmetic is 32-bit: a plan's cell ids
+// fit in 32 bits, so its vertex count is below 2^29.
 #pragma once
 
 #include "geom.cuh"
@@ -17,8 +18,9 @@
 namespace msc {
 
 struct DagTarget {
-    uint32_t v;     // owner vertex index
-    uint8_t kind;   // 1 = 1-cell (then `sub` is its axis), 2 = 2-saddle (then `sub` is its slot)
+    uint32_t v;    // owner vertex index
+    int x, y, z;   // owner vertex coordinates
+    uint8_t kind;  // 1 = 1-cell (then `sub` is its axis), 2 = 2-saddle (then `sub` is its slot)
     uint8_t sub;
 };
 
@@ -30,56 +32,92 @@ struct Vtx {
 
 __host__ __device__ __forceinline__ Vtx vtx_of(const Geom& g, uint32_t v) {
     Vtx r;
-    r.x = int(v % uint32_t(g.nx));
-    uint32_t q = v / uint32_t(g.nx);
-    r.y = int(q % uint32_t(g.ny));
-    r.z = int(q / uint32_t(g.ny));
+    const uint32_t q = g.div_nx.div(v);
+    r.x = int(v - q * uint32_t(g.nx));
+    r.z = int(g.div_ny.div(q));
+    r.y = int(q - uint32_t(r.z) * uint32_t(g.ny));
     return r;
+}
+
+__host__ __device__ __forceinline__ uint32_t vid32(const Geom& g, int x, int y, int z) {
+    return uint32_t(x) + uint32_t(g.nx) * (uint32_t(y) + uint32_t(g.ny) * uint32_t(z));
 }
 
 // Slot of the 1-cell along `axis` in its owner's word: a=1 (slot 1), b=1 (slot 2), c=1 (slot 4).
 __host__ __device__ __forceinline__ int edge_slot(int axis) { return 1 << axis; }
 
-// Word index and bit of a 1-cell in the 1-cell row bitmap layout (see Geom::edge_word).
+// Word index of a 1-cell in the 1-cell row bitmap layout (see Geom::edge_word); bit x & 31.
 __host__ __device__ __forceinline__ int64_t edge_bitmap_word(const Geom& g, int x, int y, int z, int axis) {
     return g.edge_word(z, axis == 2, y, axis == 1, x >> 5);
 }
 
-// Out-edges of the 1-cell (x,y,z,axis); returns how many were written to out[0..3].
+// Out-edges of the 1-cell of vertex (x,y,z) along `axis`, one slot per cofacet quad: the quads
+// are e +- u_b for the two axes b != axis (slots 0,1 for the first such b, 2,3 for the second);
+// the quad on the + side of b shares e's owner, the one on the - side is owned by the vertex
+// one step back along b.  A slot without an edge has kind 0.  Returns the number of edges.
+// (Fixed slots keep the targets in registers.)
+__host__ __device__ __forceinline__ int pick3(int i, int a0, int a1, int a2) { return i == 0 ? a0 : i == 1 ? a1 : a2; }
+
 __host__ __device__ __forceinline__ int dag_out(const Geom& g, const uint32_t* __restrict__ words, int x, int y, int z,
-                                       int axis, DagTarget out[4]) {
-    int c[3] = {2 * x, 2 * y, 2 * z};
-    c[axis] += 1;
-    const int ext[3] = {2 * g.nx - 1, 2 * g.ny - 1, 2 * g.nz - 1};
-    const uint32_t own = slot_code(words[g.vid(x, y, z)], edge_slot(axis));
-    int n = 0;
+                                                int axis, DagTarget out[4]) {
+    const uint32_t v = vid32(g, x, y, z);
+    const uint32_t sy = uint32_t(g.nx), sz = uint32_t(g.nx) * uint32_t(g.ny);
+    const uint32_t own = slot_code(words[v], edge_slot(axis));
+    int cnt = 0;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        if (b == axis) continue;
-#pragma unroll
-        for (int sgn = -1; sgn <= 1; sgn += 2) {
-            int q[3] = {c[0], c[1], c[2]};
-            q[b] += sgn;
-            if (q[b] < 0 || q[b] >= ext[b]) continue;
-            if (own == uint32_t(1 + 2 * b + (sgn > 0))) continue;  // q is e's own partner
-            const int ox = q[0] >> 1, oy = q[1] >> 1, oz = q[2] >> 1;
-            const int slot = (q[0] & 1) | ((q[1] & 1) << 1) | ((q[2] & 1) << 2);
-            const uint32_t ov = uint32_t(g.vid(ox, oy, oz));
-            const uint32_t qc = slot_code(words[ov], slot);
-            if (qc == 0) {
-                out[n++] = DagTarget{ov, 2, uint8_t(slot)};
-                continue;
-            }
-            const int k = int(qc - 1) >> 1;
-            if (k != axis && k != b) continue;  // paired with a cube: no edge
-            const int s2 = (qc & 1) ? -1 : 1;
-            int e[3] = {q[0], q[1], q[2]};
-            e[k] += s2;
-            const int eaxis = (k == axis) ? b : axis;  // the odd coordinate that remains
-            out[n++] = DagTarget{uint32_t(g.vid(e[0] >> 1, e[1] >> 1, e[2] >> 1)), 1, uint8_t(eaxis)};
+    for (int i = 0; i < 4; ++i) {
+        const int b = axis + 1 + (i >> 1) - (axis + 1 + (i >> 1) >= 3 ? 3 : 0);  // the two axes other than `axis`
+        const bool plus = i & 1;
+        const int other = 3 - axis - b;  // the quad's even axis
+        out[i].kind = 0;
+        const int cb = pick3(b, x, y, z), nb = pick3(b, g.nx, g.ny, g.nz);
+        if (plus ? cb >= nb - 1 : cb == 0) continue;               // no quad on that side
+        if (own == uint32_t(1 + 2 * b + (plus ? 1 : 0))) continue;  // q is e's own partner
+        // owner of q: e's owner, or one step back along b
+        const int back = plus ? 0 : 1;
+        int ox = x - (b == 0 ? back : 0), oy = y - (b == 1 ? back : 0), oz = z - (b == 2 ? back : 0);
+        uint32_t ov = v - (plus ? 0u : (b == 0 ? 1u : b == 1 ? sy : sz));
+        const int slot = (1 << axis) | (1 << b);
+        const uint32_t qc = slot_code(words[ov], slot);
+        if (qc == 0) {
+            out[i] = DagTarget{ov, ox, oy, oz, 2, uint8_t(slot)};
+            ++cnt;
+            continue;
         }
+        const int k = int(qc - 1) >> 1;
+        if (k == other) continue;  // paired with a cube: no edge
+        if (!(qc & 1u)) {          // partner on the + side along k: owner one step forward
+            ox += k == 0;
+            oy += k == 1;
+            oz += k == 2;
+            ov += k == 0 ? 1u : k == 1 ? sy : sz;
+        }
+        out[i] = DagTarget{ov, ox, oy, oz, 1, uint8_t(k == axis ? b : axis)};
+        ++cnt;
     }
-    return n;
+    return cnt;
+}
+
+// Per-node record written by the BFS when it expands a 1-cell (indexed by its handle): whether
+// the node is a dead end, a branch point (out-degree > 1), or else its one successor.  A 1-cell
+// successor is its handle; a 2-saddle successor has bit 31 set and (owner << 2 | even axis).
+constexpr uint32_t INFO_DEAD = 0xFFFFFFFFu;
+constexpr uint32_t INFO_BRANCH = 0xFFFFFFFEu;
+
+__host__ __device__ __forceinline__ uint32_t encode_successor(const DagTarget& t) {
+    if (t.kind == 1) return edge_handle(t.v, t.sub);
+    const uint32_t even = (t.sub & 1u) == 0 ? 0u : (t.sub & 2u) == 0 ? 1u : 2u;  // the quad's even axis
+    return 0x80000000u | (t.v << 2) | even;
+}
+
+__host__ __device__ __forceinline__ uint32_t node_info(int n, const DagTarget out[4]) {
+    if (n == 0) return INFO_DEAD;
+    if (n > 1) return INFO_BRANCH;
+    uint32_t w = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (out[i].kind) w = encode_successor(out[i]);
+    return w;
 }
 
 }  // namespace msc

@@ -30,7 +30,10 @@ __global__ void __launch_bounds__(THREADS) init_links(Geom g, const uint32_t* __
     const int64_t v = int64_t(blockIdx.x) * THREADS + threadIdx.x;
     if (v >= g.nverts) return;
     const uint32_t w = words[v];
-    const int x = int(v % g.nx), y = int((v / g.nx) % g.ny), z = int(v / (int64_t(g.nx) * g.ny));
+    const uint32_t qv = g.div_nx.div(uint32_t(v));
+    const int x = int(uint32_t(v) - qv * uint32_t(g.nx));
+    const int z = int(g.div_ny.div(qv));
+    const int y = int(qv - uint32_t(z) * uint32_t(g.ny));
     // vertex slot 0
     const uint32_t cv = slot_code(w, 0);
     int64_t pv = v;
@@ -98,8 +101,10 @@ __global__ void __launch_bounds__(THREADS) finish_labels(Geom g, uint32_t* __res
     const int64_t v = int64_t(blockIdx.x) * THREADS + threadIdx.x;
     if (v >= g.nverts) return;
     auto cell_of = [&](uint32_t u, int off) {
-        const int x = int(u % uint32_t(g.nx)), y = int((u / uint32_t(g.nx)) % uint32_t(g.ny)),
-                  z = int(u / (uint32_t(g.nx) * uint32_t(g.ny)));
+        const uint32_t q = g.div_nx.div(u);
+        const int x = int(u - q * uint32_t(g.nx));
+        const int z = int(g.div_ny.div(q));
+        const int y = int(q - uint32_t(z) * uint32_t(g.ny));
         return g.cell_id(2 * x + off, 2 * y + off, 2 * z + off);
     };
     lab_v[v] = cell_of(lab_v[v], 0);
@@ -113,10 +118,10 @@ struct CellCoord {
 
 __device__ __forceinline__ CellCoord decode_cell(const Geom& g, uint32_t id) {
     CellCoord c;
-    c.x = int(id % g.rx);
-    uint32_t q = id / g.rx;
-    c.y = int(q % g.ry);
-    c.z = int(q / g.ry);
+    const uint32_t q = g.div_rx.div(id);
+    c.x = int(id - q * g.rx);
+    c.z = int(g.div_ry.div(q));
+    c.y = int(q - uint32_t(c.z) * g.ry);
     return c;
 }
 

@@ -39,57 +39,66 @@ struct TraceArgs {
     const uint32_t* junc_prefix;
     const uint32_t* crit_bits;
     const uint32_t* crit_prefix;
-    uint32_t* tgt;     // 4 per source: destination rank
-    uint8_t* kinds;    // per source: 2 bits per slot, 0 none / 1 junction / 2 2-saddle
+    const uint32_t* info;  // per 1-cell handle: dead end, branch point, or its one successor
+    uint32_t* tgt;    // 4 per source: destination rank
+    uint8_t* kinds;   // 4 per source: 0 none / 1 junction / 2 2-saddle (read as one word per source)
     int64_t max_steps;
     uint32_t* status;
 };
 
+// One thread per (source, out-edge slot): follows that simple path to its end.
 __global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
-    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (u >= a.n1 + a.nj) return;
+    const int64_t tid = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (tid >= 4 * (a.n1 + a.nj)) return;
+    const int64_t u = tid >> 2;
+    const int slot = int(tid & 3);
     const Geom& g = a.g;
     const uint32_t id = u < a.n1 ? a.s1[u] : a.junc_cells[u - a.n1];
-    const int cx = int(id % g.rx), cy = int((id / g.rx) % g.ry), cz = int(id / g.rx / g.ry);
+    const uint32_t q1 = g.div_rx.div(id);
+    const int cx = int(id - q1 * g.rx);
+    const int cz = int(g.div_ry.div(q1));
+    const int cy = int(q1 - uint32_t(cz) * g.ry);
     const int axis = (cx & 1) ? 0 : (cy & 1) ? 1 : 2;
-    DagTarget t[4];
-    const int n = dag_out(g, a.words, cx >> 1, cy >> 1, cz >> 1, axis, t);
-    uint32_t kinds = 0;
-    for (int k = 0; k < 4; ++k) {
-        uint32_t rank = 0, kind = 0;
-        if (k < n) {
-            DagTarget cur = t[k];
-            for (int64_t step = 0;; ++step) {
-                if (step > a.max_steps) {
-                    atomicOr(a.status, ST_ITER);
-                    break;
-                }
-                const Vtx q = vtx_of(g, cur.v);
-                if (cur.kind == 2) {  // a 2-saddle: rank among the critical 2-cells
-                    rank = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(cur.sub, q.z, q.y, q.x >> 5), q.x & 31);
-                    kind = 2;
-                    break;
-                }
-                const int64_t wi = edge_bitmap_word(g, q.x, q.y, q.z, cur.sub);
-                if ((a.junc_bits[wi] >> (q.x & 31)) & 1u) {
-                    rank = bit_rank(a.junc_bits, a.junc_prefix, wi, q.x & 31);
-                    kind = 1;
-                    break;
-                }
-                DagTarget nx[4];
-                const int m = dag_out(g, a.words, q.x, q.y, q.z, cur.sub, nx);
-                if (m == 0) break;  // dead path: dropped
-                if (m > 1) {        // cannot happen: every reachable non-junction has out-degree <= 1
-                    atomicOr(a.status, ST_INTERNAL);
-                    break;
-                }
-                cur = nx[0];
+    DagTarget out[4];
+    dag_out(g, a.words, cx >> 1, cy >> 1, cz >> 1, axis, out);
+    DagTarget cur = out[0];
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+        if (i == slot) cur = out[i];
+    uint32_t rank = 0, kind = 0;
+    // follow the path with one load per node: the BFS recorded every reachable node's successor
+    if (cur.kind == 2) {
+        rank = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(cur.sub, cur.z, cur.y, cur.x >> 5), cur.x & 31);
+        kind = 2;
+    } else if (cur.kind == 1) {
+        uint32_t h = edge_handle(cur.v, cur.sub);
+        for (int64_t step = 0;; ++step) {
+            if (step > a.max_steps) {
+                atomicOr(a.status, ST_ITER);
+                break;
             }
+            const uint32_t w = a.info[h];
+            if (w == INFO_DEAD) break;  // a dead path: dropped
+            if (w == INFO_BRANCH) {     // a junction
+                const Vtx q = vtx_of(g, h >> 2);
+                const int64_t wi = edge_bitmap_word(g, q.x, q.y, q.z, int(h & 3));
+                if (!((a.junc_bits[wi] >> (q.x & 31)) & 1u)) atomicOr(a.status, ST_INTERNAL);
+                rank = bit_rank(a.junc_bits, a.junc_prefix, wi, q.x & 31);
+                kind = 1;
+                break;
+            }
+            if (w & 0x80000000u) {  // the path ends at a 2-saddle
+                const Vtx q = vtx_of(g, (w & 0x7FFFFFFFu) >> 2);
+                const int slot = 7 ^ (1 << (w & 3u));
+                rank = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(slot, q.z, q.y, q.x >> 5), q.x & 31);
+                kind = 2;
+                break;
+            }
+            h = w;
         }
-        a.tgt[u * 4 + k] = rank;
-        kinds |= kind << (2 * k);
     }
-    a.kinds[u] = uint8_t(kinds);
+    a.tgt[tid] = rank;
+    a.kinds[tid] = uint8_t(kind);
 }
 
 // Distinct destinations of one source among slots of kind `want`, sorted, with multiplicity.
@@ -98,7 +107,7 @@ __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t ki
     uint32_t v[4];
     int n = 0;
     for (int k = 0; k < 4; ++k)
-        if (((kinds >> (2 * k)) & 3u) == want) v[n++] = tgt[k];
+        if (trace_kind(kinds, k) == want) v[n++] = tgt[k];
     for (int i = 1; i < n; ++i)  // insertion sort of <= 4 values
         for (int j = i; j > 0 && v[j - 1] > v[j]; --j) {
             uint32_t tmp = v[j];
@@ -123,7 +132,7 @@ __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t ki
 struct CsrArgs {
     int64_t n1, nj;
     const uint32_t* tgt;
-    const uint8_t* kinds;
+    const uint32_t* kinds;
     uint32_t* cnt[4];
     const int64_t* rowptr[4];
     uint32_t* col[4];
@@ -166,7 +175,7 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     msc_status st;
     const int64_t n1 = p->counts[1], nj = p->n_junctions, nsrc = n1 + nj;
     if ((st = ensure(p, p->trace, sizeof(uint32_t) * 4 * size_t(nsrc ? nsrc : 1)))) return st;
-    if ((st = ensure(p, p->trace_kinds, size_t(nsrc ? nsrc : 1)))) return st;
+    if ((st = ensure(p, p->trace_kinds, sizeof(uint32_t) * size_t(nsrc ? nsrc : 1)))) return st;
     TraceArgs ta{};
     ta.g = g;
     ta.words = static_cast<const uint32_t*>(p->words.ptr);
@@ -178,13 +187,14 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     ta.junc_prefix = static_cast<const uint32_t*>(p->junc_prefix.ptr);
     ta.crit_bits = static_cast<const uint32_t*>(p->crit_bits.ptr);
     ta.crit_prefix = static_cast<const uint32_t*>(p->crit_prefix.ptr);
+    ta.info = static_cast<const uint32_t*>(p->node_info.ptr);
     ta.tgt = static_cast<uint32_t*>(p->trace.ptr);
     ta.kinds = static_cast<uint8_t*>(p->trace_kinds.ptr);
     ta.max_steps = p->opts.max_iterations;
     ta.status = static_cast<uint32_t*>(p->status.ptr);
     cudaEventRecord(p->kev0, s);
     if (nsrc) {
-        trace_kernel<<<blocks(nsrc), THREADS, 0, s>>>(ta);
+        trace_kernel<<<blocks(4 * nsrc), THREADS, 0, s>>>(ta);
         launched(p);
     }
     cudaEventRecord(p->kev1, s);
@@ -202,7 +212,7 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     ca.n1 = n1;
     ca.nj = nj;
     ca.tgt = ta.tgt;
-    ca.kinds = ta.kinds;
+    ca.kinds = reinterpret_cast<const uint32_t*>(ta.kinds);
     size_t off = 0;
     for (int w = 0; w < 4; ++w) {
         ca.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;

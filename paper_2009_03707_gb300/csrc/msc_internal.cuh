@@ -44,7 +44,7 @@ struct Plan {
     DeviceBuffer words, status, crit_bits, crit_prefix, scan_sums, totals;
     DeviceBuffer cells[4];
     DeviceBuffer vmin, cmax, min_arcs, max_arcs, flag;
-    DeviceBuffer visited, frontier[2], qcount;
+    DeviceBuffer visited, frontier[2], qcount, node_info;
     DeviceBuffer junc_bits, junc_prefix, junc_cells;
     DeviceBuffer trace, trace_kinds, minor_rowcnt, minor_scan, minor_rowptr[4], minor_col[4], minor_mult[4];
     DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_counters, pc_col, pc_cnt, pc_gk, pc_gv, pc_gocc;
@@ -53,7 +53,7 @@ struct Plan {
     template <class F>
     void for_each_buffer(F&& f) {
         DeviceBuffer* all[] = {&words, &status, &crit_bits, &crit_prefix, &scan_sums, &totals, &cells[0], &cells[1],
-                               &cells[2], &cells[3], &vmin, &cmax, &min_arcs, &max_arcs, &flag, &visited,
+                               &cells[2], &cells[3], &vmin, &cmax, &min_arcs, &max_arcs, &flag, &visited, &node_info,
                                &frontier[0], &frontier[1], &qcount, &junc_bits, &junc_prefix, &junc_cells, &trace,
                                &trace_kinds, &minor_rowcnt, &minor_scan, &minor_rowptr[0], &minor_rowptr[1],
                                &minor_rowptr[2], &minor_rowptr[3], &minor_col[0], &minor_col[1], &minor_col[2],
@@ -73,6 +73,11 @@ struct Plan {
          have_junctions = false, have_minor = false, have_dstar = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;  // stage / kernel timing
 };
+
+// The trace of the DAG minor (minor.cu): for every 1-saddle (ranks 0..n1-1) then every junction
+// (n1 + rank), 4 destination ranks, and a 32-bit word whose byte k is the kind of slot k:
+// 0 none, 1 a junction, 2 a 2-saddle.
+__host__ __device__ __forceinline__ uint32_t trace_kind(uint32_t kinds, int k) { return (kinds >> (8 * k)) & 0xFFu; }
 
 // Counts one kernel launch of this plan (reported in msc_stats.n_launches).
 inline void launched(Plan* p, int n = 1) { p->stats.n_launches += n; }

@@ -42,7 +42,7 @@ struct PcArgs {
     const uint32_t* rows;   // the 1-saddle ranks this launch owns (null: 0..nrows-1)
     int64_t nrows;
     const uint32_t* tgt;    // 4 destination ranks per source (1-saddles, then junctions)
-    const uint8_t* kinds;   // 2 bits per slot: 1 junction, 2 2-saddle
+    const uint32_t* kinds;  // per source, byte k = kind of slot k: 1 junction, 2 2-saddle
     uint32_t* out_col;      // staging: columns of finished rows
     u64* out_cnt;
     uint64_t out_cap;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
         const uint32_t tg[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint32_t kind = (kinds >> (2 * k)) & 3u;
+            const uint32_t kind = trace_kind(kinds, k);
             if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[0], sh.fv[0], nf, t, tg[k], 1);
             if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tg[k], 1);
         }
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
                 const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const uint32_t kind = (kj >> (2 * k)) & 3u;
+                    const uint32_t kind = trace_kind(kj, k);
                     if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[cur ^ 1], sh.fv[cur ^ 1], ng, t, tq[k], c);
                     if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tq[k], c);
                 }
@@ -291,7 +291,7 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
     }
     group_sync<G>();
     if (r < 4) {  // row s of A (the frontier A_0) and of D
-        const uint32_t kind = (a.kinds[s] >> (2 * r)) & 3u;
+        const uint32_t kind = trace_kind(a.kinds[s], r);
         const uint32_t dst = a.tgt[s * 4 + r];
         bool ok = true;
         if (kind == 1) ok = table_add(t.fk, t.fv, t.focc, t.cap, t.lg, t.fsize, dst, 1, a.status);
@@ -328,7 +328,7 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
             const uint4 q = trace_of(a, j);
             const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
             for (int k = 0; k < 4; ++k) {
-                const uint32_t kind = (kinds >> (2 * k)) & 3u;
+                const uint32_t kind = trace_kind(kinds, k);
                 if (!kind) continue;
                 const bool added = kind == 1 ? table_add(t.fk, t.fv, t.focc, t.cap, t.lg, t.fsize, tq[k], c, a.status)
                                              : table_add(t.dk, t.dv, t.docc, t.cap, t.lg, t.dsize, tq[k], c, a.status);
@@ -491,7 +491,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         PcArgs a{};
         a.n1 = n1;
         a.tgt = static_cast<const uint32_t*>(p->trace.ptr);
-        a.kinds = static_cast<const uint8_t*>(p->trace_kinds.ptr);
+        a.kinds = static_cast<const uint32_t*>(p->trace_kinds.ptr);
         a.out_col = static_cast<uint32_t*>(p->pc_col.ptr);
         a.out_cnt = static_cast<u64*>(p->pc_cnt.ptr);
         a.out_cap = cap;

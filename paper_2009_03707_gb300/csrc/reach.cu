@@ -28,10 +28,10 @@ struct CellXYZ {
 };
 __device__ __forceinline__ CellXYZ decode(const Geom& g, uint32_t id) {
     CellXYZ c;
-    c.x = int(id % g.rx);
-    uint32_t q = id / g.rx;
-    c.y = int(q % g.ry);
-    c.z = int(q / g.ry);
+    const uint32_t q = g.div_rx.div(id);
+    c.x = int(id - q * g.rx);
+    c.z = int(g.div_ry.div(q));
+    c.y = int(q - uint32_t(c.z) * g.ry);
     return c;
 }
 
@@ -44,13 +44,14 @@ __global__ void __launch_bounds__(THREADS) bfs_seed(Geom g, const uint32_t* __re
     const int axis = (c.x & 1) ? 0 : (c.y & 1) ? 1 : 2;
     const int x = c.x >> 1, y = c.y >> 1, z = c.z >> 1;
     atomicOr(&visited[edge_bitmap_word(g, x, y, z, axis)], 1u << (x & 31));
-    front[i] = edge_handle(uint32_t(g.vid(x, y, z)), axis);
+    front[i] = edge_handle(vid32(g, x, y, z), axis);
 }
 
 // One BFS level.  All lanes of a warp reach the aggregated append.
 __global__ void __launch_bounds__(THREADS) bfs_expand(Geom g, const uint32_t* __restrict__ words,
                                                       const uint32_t* __restrict__ cur, int64_t ncur,
-                                                      uint32_t* __restrict__ visited, uint32_t* __restrict__ next,
+                                                      uint32_t* __restrict__ visited, uint32_t* __restrict__ info,
+                                                      uint32_t* __restrict__ next,
                                                       unsigned long long* __restrict__ next_count, uint64_t cap,
                                                       uint32_t* __restrict__ status) {
     const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
@@ -61,11 +62,12 @@ __global__ void __launch_bounds__(THREADS) bfs_expand(Geom g, const uint32_t* __
         const Vtx v = vtx_of(g, h >> 2);
         DagTarget t[4];
         const int n = dag_out(g, words, v.x, v.y, v.z, int(h & 3), t);
-        for (int k = 0; k < n; ++k) {
+        info[h] = node_info(n, t);  // read later by the junction marking and the path tracer
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
             if (t[k].kind != 1) continue;
-            const Vtx u = vtx_of(g, t[k].v);
-            const uint32_t bit = 1u << (u.x & 31);
-            const uint32_t old = atomicOr(&visited[edge_bitmap_word(g, u.x, u.y, u.z, t[k].sub)], bit);
+            const uint32_t bit = 1u << (t[k].x & 31);
+            const uint32_t old = atomicOr(&visited[edge_bitmap_word(g, t[k].x, t[k].y, t[k].z, t[k].sub)], bit);
             if (!(old & bit)) found[nf++] = edge_handle(t[k].v, t[k].sub);
         }
     }
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(THREADS) bfs_expand(Geom g, const uint32_t* __
 // has more than one out-edge is a junction.
 __global__ void __launch_bounds__(THREADS) mark_junctions(Geom g, const uint32_t* __restrict__ words,
                                                           const uint32_t* __restrict__ visited,
+                                                          const uint32_t* __restrict__ info,
                                                           uint32_t* __restrict__ junc) {
     const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
     if (i >= g.edge_words()) return;
@@ -103,9 +106,9 @@ __global__ void __launch_bounds__(THREADS) mark_junctions(Geom g, const uint32_t
             const int bit = __ffs(vis) - 1;
             vis &= vis - 1;
             const int x = r.w * 32 + bit;
-            if (slot_code(words[g.vid(x, r.y, r.z)], edge_slot(axis)) == 0) continue;  // a 1-saddle
-            DagTarget t[4];
-            if (dag_out(g, words, x, r.y, r.z, axis, t) > 1) out |= 1u << bit;
+            const uint32_t v = vid32(g, x, r.y, r.z);
+            if (slot_code(words[v], edge_slot(axis)) == 0) continue;  // a 1-saddle
+            if (info[edge_handle(v, axis)] == INFO_BRANCH) out |= 1u << bit;
         }
     }
     junc[i] = out;
@@ -121,6 +124,7 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
                             int64_t(g.nx) * g.ny * (g.nz - 1);
     if ((st = ensure(p, p->visited, sizeof(uint32_t) * size_t(g.edge_words())))) return st;
     if ((st = ensure(p, p->qcount, sizeof(unsigned long long) * 2))) return st;
+    if ((st = ensure(p, p->node_info, sizeof(uint32_t) * 4 * size_t(g.nverts)))) return st;
     if ((st = ensure(p, p->frontier[0], sizeof(uint32_t) * size_t(n1 ? n1 : 1)))) return st;
     auto* visited = static_cast<uint32_t*>(p->visited.ptr);
     auto* qcount = static_cast<unsigned long long*>(p->qcount.ptr);
@@ -143,6 +147,7 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
             return st;
         bfs_expand<<<blocks(ncur), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr),
                                                     static_cast<const uint32_t*>(p->frontier[cur].ptr), ncur, visited,
+                                                    static_cast<uint32_t*>(p->node_info.ptr),
                                                     static_cast<uint32_t*>(p->frontier[cur ^ 1].ptr), qcount,
                                                     uint64_t(cap), static_cast<uint32_t*>(p->status.ptr));
         launched(p);
@@ -168,6 +173,7 @@ msc_status run_junctions(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->junc_prefix, sizeof(uint32_t) * size_t(nw)))) return st;
     mark_junctions<<<blocks(nw), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr),
                                                   static_cast<const uint32_t*>(p->visited.ptr),
+                                                  static_cast<const uint32_t*>(p->node_info.ptr),
                                                   static_cast<uint32_t*>(p->junc_bits.ptr));
     launched(p);
     if ((st = check_cuda(p, cudaGetLastError(), "mark_junctions launch"))) return st;

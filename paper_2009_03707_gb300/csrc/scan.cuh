@@ -26,16 +26,17 @@ struct RowCoord {
     int z, c, y, b, w;
 };
 
-__host__ __device__ __forceinline__ RowCoord decode_row(const Geom& g, int64_t i) {
+__host__ __device__ __forceinline__ RowCoord decode_row(const Geom& g, int64_t i64) {
     RowCoord r;
-    r.w = int(i % g.W);
-    int64_t q = i / g.W;
-    r.b = int(q & 1);
+    const uint32_t i = uint32_t(i64);  // 4*nz*ny*W < 2^32 for every plan
+    uint32_t q = g.div_W.div(i);
+    r.w = int(i - q * uint32_t(g.W));
+    r.b = int(q & 1u);
     q >>= 1;
-    r.y = int(q % g.ny);
-    q /= g.ny;
-    r.c = int(q & 1);
-    r.z = int(q >> 1);
+    const uint32_t q2 = g.div_ny.div(q);
+    r.y = int(q - q2 * uint32_t(g.ny));
+    r.c = int(q2 & 1u);
+    r.z = int(q2 >> 1);
     return r;
 }
 

@@ -62,10 +62,7 @@ extern "C" msc_status msc_gradient_critical_static(const int64_t dims[3], const 
     g.nx = int(dims[0]);
     g.ny = int(dims[1]);
     g.nz = int(dims[2]);
-    g.W = int((dims[0] + 31) / 32);
-    g.nverts = dims[0] * dims[1] * dims[2];
-    g.rx = uint32_t(rx);
-    g.ry = uint32_t(ry);
+    g.finish();
 
     // scratch layout: status | bitmaps | prefixes | scan block sums | totals
     const int64_t len = seq_length(g);
