@@ -70,6 +70,13 @@ _SIGNATURES = {
     "ora_result_free": ([ctypes.c_void_p], None),
     "ora_n_iter": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
                    ctypes.c_int64),
+    "ora_lazy_pairs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ora_lazy_vertex_min": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
+                            ctypes.c_int),
+    "ora_lazy_cube_max": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
+                          ctypes.c_int),
+    "ora_lazy_nodes": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ora_lazy_dstar_rows": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_void_p),
 }
 
 
@@ -282,3 +289,69 @@ def compute_all(f: np.ndarray, with_minor: bool = True, with_dstar: bool = True)
     if with_dstar:
         res["dstar"] = path_counts(d, pair, lists[1], lists[2])
     return res
+
+
+# ---- sampled queries on large volumes (pairs computed lazily, one lower star at a time) ----
+def lazy_pairs(f, cells):
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    out = np.empty(len(cells), dtype=np.uint32)
+    st = _load().ora_lazy_pairs(_p(_dims(f)), _p(f), len(cells), _p(cells), _p(out))
+    if st:
+        raise OracleError(st, "lazy_pairs")
+    return out
+
+
+def lazy_vertex_min(f, verts):
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    verts = np.ascontiguousarray(verts, dtype=np.int64)
+    out = np.empty(len(verts), dtype=np.uint32)
+    st = _load().ora_lazy_vertex_min(_p(_dims(f)), _p(f), len(verts), _p(verts), _p(out))
+    if st:
+        raise OracleError(st, "lazy_vertex_min")
+    return out
+
+
+def lazy_cube_max(f, verts):
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    verts = np.ascontiguousarray(verts, dtype=np.int64)
+    out = np.empty(len(verts), dtype=np.uint32)
+    st = _load().ora_lazy_cube_max(_p(_dims(f)), _p(f), len(verts), _p(verts), _p(out))
+    if st:
+        raise OracleError(st, "lazy_cube_max")
+    return out
+
+
+def lazy_nodes(f, cells):
+    """(is DAG node, is critical, out-degree) of each listed 1-cell."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    out = np.empty((len(cells), 3), dtype=np.int32)
+    st = _load().ora_lazy_nodes(_p(_dims(f)), _p(f), len(cells), _p(cells), _p(out))
+    if st:
+        raise OracleError(st, "lazy_nodes")
+    return out
+
+
+def lazy_dstar_rows(f, s1_cells):
+    """{1-saddle cell: {2-saddle cell: count}} for the listed 1-saddles."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    cells = np.ascontiguousarray(s1_cells, dtype=np.uint32)
+    lib = _load()
+    h = lib.ora_lazy_dstar_rows(_p(_dims(f)), _p(f), len(cells), _p(cells))
+    try:
+        st = lib.ora_result_status(h)
+        if st:
+            raise OracleError(st, "lazy_dstar_rows")
+        n = lib.ora_result_size(h)
+        rows = np.empty(n, dtype=np.uint32)
+        cols = np.empty(n, dtype=np.uint32)
+        cnt = np.empty(n, dtype=np.uint64)
+        if n:
+            lib.ora_result_copy(h, _p(rows), _p(cols), _p(cnt))
+    finally:
+        lib.ora_result_free(h)
+    out = {int(c): {} for c in cells}
+    for r, c, k in zip(rows, cols, cnt):
+        out[int(cells[r])][int(c)] = int(k)
+    return out

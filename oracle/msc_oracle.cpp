@@ -361,11 +361,15 @@ uint32_t packed_word(const Grid& g, int64_t v, const std::map<int64_t, uint32_t>
 // if q is paired with a cube.  Following an out-edge walks a V-path backwards, i.e. the
 // traversal runs against the discrete gradient (Sec. 3.5).
 // ---------------------------------------------------------------------------------
-std::vector<int64_t> dag_out(const Grid& g, const uint32_t* pair_of, int64_t e) {
+// The pairing is read through an accessor P with `uint32_t operator()(int64_t cell)`: a full
+// array for whole-volume runs, or LazyPairs (below) for sampled queries on large volumes.
+template <class P>
+std::vector<int64_t> dag_out_p(const Grid& g, P& pair, int64_t e) {
     std::vector<int64_t> out;
+    const uint32_t own = pair(e);
     for (int64_t q : g.cofacets(e)) {
-        if (uint32_t(q) == pair_of[e]) continue;
-        uint32_t p = pair_of[q];
+        if (uint32_t(q) == own) continue;
+        uint32_t p = pair(q);
         if (p == NONE) {
             out.push_back(q);
         } else if (g.dim(int64_t(p)) == 1) {
@@ -373,6 +377,16 @@ std::vector<int64_t> dag_out(const Grid& g, const uint32_t* pair_of, int64_t e) 
         }
     }
     return out;
+}
+
+struct ArrayPairs {
+    const uint32_t* a;
+    uint32_t operator()(int64_t c) const { return a[c]; }
+};
+
+std::vector<int64_t> dag_out(const Grid& g, const uint32_t* pair_of, int64_t e) {
+    ArrayPairs ap{pair_of};
+    return dag_out_p(g, ap, e);
 }
 
 bool is_dag_node_1cell(const Grid& g, const uint32_t* pair_of, int64_t e) {
@@ -414,6 +428,30 @@ int64_t rank_in(const std::vector<int64_t>& sorted, int64_t id) {
     return int64_t(it - sorted.begin());
 }
 
+
+// ---------------------------------------------------------------------------------
+// Sampled queries on large volumes.  The lower-star rule is local: the pair of a cell is
+// decided inside the lower star of its maximal vertex alone.  LazyPairs runs
+// ProcessLowerStars for a vertex the first time one of its cells is asked for, and keeps the
+// result; the walks and counts below are the same definitions as the whole-volume ones.
+// ---------------------------------------------------------------------------------
+struct LazyPairs {
+    const Grid& g;
+    std::unordered_map<int64_t, uint32_t> pair;
+    int status = OK;
+    explicit LazyPairs(const Grid& grid) : g(grid) {}
+    uint32_t operator()(int64_t c) {
+        auto it = pair.find(c);
+        if (it != pair.end()) return it->second;
+        std::map<int64_t, uint32_t> local;
+        for (int64_t w : g.vertices(c))
+            if (std::isnan(g.f[w])) status = ERR_NAN;
+        if (!process_lower_star(g, g.max_vertex(c), local)) status = ERR_INTERNAL;
+        for (const auto& kv : local) pair[kv.first] = kv.second;
+        it = pair.find(c);
+        return it == pair.end() ? NONE : it->second;
+    }
+};
 }  // namespace
 
 // =====================================================================================
@@ -808,6 +846,157 @@ int64_t ora_n_iter(int64_t nj, int64_t nnzA, const uint32_t* Acols, int64_t nnzB
         }
     }
     return best;
+}
+
+
+// ---- sampled queries (LazyPairs) ------------------------------------------------------
+// For each listed cell: the partner id (0xFFFFFFFF = critical).
+int ora_lazy_pairs(const int64_t* dims, const float* f, int64_t n, const uint32_t* cells, uint32_t* out) {
+    if (!check_dims(dims) || !f || (n > 0 && (!cells || !out))) return ERR_ARG;
+    Grid g(dims, f);
+    if (!ids_fit_u32(g)) return ERR_TOO_LARGE;
+    LazyPairs lp(g);
+    for (int64_t i = 0; i < n; ++i) {
+        if (int64_t(cells[i]) >= g.ncells()) return ERR_ARG;
+        out[i] = lp(int64_t(cells[i]));
+    }
+    return lp.status;
+}
+
+// Destination minimum (cell id) of each listed vertex: the descending walk of Sec. 3.4.
+int ora_lazy_vertex_min(const int64_t* dims, const float* f, int64_t n, const int64_t* verts, uint32_t* out) {
+    if (!check_dims(dims) || !f || (n > 0 && (!verts || !out))) return ERR_ARG;
+    Grid g(dims, f);
+    LazyPairs lp(g);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = verts[i];
+        for (int64_t steps = 0;; ++steps) {
+            if (steps > g.nverts()) return ERR_INTERNAL;
+            const int64_t vc = g.vertex_cell(v);
+            const uint32_t e = lp(vc);
+            if (e == NONE) {
+                out[i] = uint32_t(vc);
+                break;
+            }
+            int64_t other = -1;
+            for (int64_t w : g.vertices(int64_t(e)))
+                if (w != v) other = w;
+            v = other;
+        }
+    }
+    return lp.status;
+}
+
+// Destination maximum (cell id, NONE if the walk leaves the domain) of the cube owned by each
+// listed vertex (NONE where the vertex owns no cube): the ascending walk of Sec. 3.4.
+int ora_lazy_cube_max(const int64_t* dims, const float* f, int64_t n, const int64_t* verts, uint32_t* out) {
+    if (!check_dims(dims) || !f || (n > 0 && (!verts || !out))) return ERR_ARG;
+    Grid g(dims, f);
+    LazyPairs lp(g);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t v = verts[i];
+        const int64_t x = v % g.nx, y = (v / g.nx) % g.ny, z = v / (g.nx * g.ny);
+        if (x == g.nx - 1 || y == g.ny - 1 || z == g.nz - 1) {
+            out[i] = NONE;
+            continue;
+        }
+        int64_t c = g.cell(2 * x + 1, 2 * y + 1, 2 * z + 1);
+        for (int64_t steps = 0;; ++steps) {
+            if (steps > g.nverts()) return ERR_INTERNAL;
+            const uint32_t p = lp(c);
+            if (p == NONE) {
+                out[i] = uint32_t(c);
+                break;
+            }
+            int64_t cx, cy, cz, px, py, pz;
+            g.coords(c, cx, cy, cz);
+            g.coords(int64_t(p), px, py, pz);
+            const int64_t nxc = 2 * px - cx, nyc = 2 * py - cy, nzc = 2 * pz - cz;
+            if (!g.inside(nxc, nyc, nzc)) {
+                out[i] = NONE;
+                break;
+            }
+            c = g.cell(nxc, nyc, nzc);
+        }
+    }
+    return lp.status;
+}
+
+// DAG facts of each listed 1-cell: out[3i] = 1 if it is a DAG node (critical or paired with a
+// quad), out[3i+1] = 1 if it is critical, out[3i+2] = its out-degree (0 if not a node).
+int ora_lazy_nodes(const int64_t* dims, const float* f, int64_t n, const uint32_t* cells, int32_t* out) {
+    if (!check_dims(dims) || !f || (n > 0 && (!cells || !out))) return ERR_ARG;
+    Grid g(dims, f);
+    LazyPairs lp(g);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t e = cells[i];
+        if (g.dim(e) != 1) return ERR_ARG;
+        const uint32_t p = lp(e);
+        const bool node = p == NONE || g.dim(int64_t(p)) == 2;
+        out[3 * i] = node;
+        out[3 * i + 1] = p == NONE;
+        out[3 * i + 2] = node ? int32_t(dag_out_p(g, lp, e).size()) : 0;
+    }
+    return lp.status;
+}
+
+// D* rows of listed 1-saddles (O5 on the lazily paired DAG): entries (sample index, 2-saddle
+// cell id, count), sorted by (sample, cell id).  Kept behind a handle like ora_path_counts.
+void* ora_lazy_dstar_rows(const int64_t* dims, const float* f, int64_t n, const uint32_t* s1_cells) {
+    PathCounts* res = new PathCounts();
+    if (!check_dims(dims) || !f || (n > 0 && !s1_cells)) {
+        res->status = ERR_ARG;
+        return res;
+    }
+    Grid g(dims, f);
+    LazyPairs lp(g);
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t s = s1_cells[r];
+        if (g.dim(s) != 1 || lp(s) != NONE) {
+            res->status = ERR_ARG;  // not a 1-saddle
+            return res;
+        }
+        std::unordered_map<int64_t, int64_t> indeg;
+        std::unordered_set<int64_t> seen{s};
+        std::vector<int64_t> stack{s};
+        while (!stack.empty()) {
+            const int64_t v = stack.back();
+            stack.pop_back();
+            if (g.dim(v) != 1) continue;
+            for (int64_t w : dag_out_p(g, lp, v)) {
+                indeg[w] += 1;
+                if (seen.insert(w).second) stack.push_back(w);
+            }
+        }
+        std::unordered_map<int64_t, uint64_t> cnt;
+        cnt[s] = 1;
+        std::vector<int64_t> queue{s};
+        std::map<int64_t, uint64_t> row;
+        for (size_t qi = 0; qi < queue.size(); ++qi) {
+            const int64_t v = queue[qi];
+            const uint64_t cv = cnt[v];
+            if (g.dim(v) == 2) {
+                if (cv > 0) row[v] = cv;
+                continue;
+            }
+            for (int64_t w : dag_out_p(g, lp, v)) {
+                const uint64_t before = cnt[w], after = before + cv;
+                if (after < before) {
+                    res->status = ERR_OVERFLOW;
+                    return res;
+                }
+                cnt[w] = after;
+                if (--indeg[w] == 0) queue.push_back(w);
+            }
+        }
+        for (const auto& kv : row) {
+            res->rows.push_back(uint32_t(r));
+            res->cols.push_back(uint32_t(kv.first));
+            res->counts.push_back(kv.second);
+        }
+    }
+    if (lp.status) res->status = lp.status;
+    return res;
 }
 
 }  // extern "C"

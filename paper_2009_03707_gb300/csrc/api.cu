@@ -2,6 +2,7 @@
 // the stage entry points.  Every stage's arithmetic runs in the kernels of the other
 // translation units; this file only orders the launches and manages memory.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -27,6 +28,8 @@ msc_status check_cuda(Plan* p, cudaError_t e, const char* what) {
 msc_status ensure(Plan* p, DeviceBuffer& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.ptr && b.bytes >= bytes) return MSC_OK;
+    if (p->fault_kind == 1 && ++p->alloc_calls == p->fault_at)
+        return fail(p, MSC_ERR_OOM, "injected allocation failure (MSC_FAULT)");
     if (b.ptr) {
         cudaFree(b.ptr);
         p->live_bytes -= int64_t(b.bytes);
@@ -65,6 +68,27 @@ msc_status check_status_word(Plan* p, cudaStream_t s) {
 }
 
 namespace {
+
+// MSC_FAULT = alloc@k | timeout | overflow: host-side fault injection for tests.
+void read_fault(Plan* p) {
+    const char* f = std::getenv("MSC_FAULT");
+    if (!f) return;
+    if (!std::strncmp(f, "alloc@", 6)) {
+        p->fault_kind = 1;
+        p->fault_at = std::atoll(f + 6);
+    } else if (!std::strcmp(f, "timeout")) {
+        p->fault_kind = 2;
+    } else if (!std::strcmp(f, "overflow")) {
+        p->fault_kind = 3;
+    }
+}
+
+// Raises a status bit on the device exactly as a kernel would (for injected faults).
+void raise_status(Plan* p, uint32_t bit, cudaStream_t s) {
+    uint32_t word = bit;
+    cudaMemcpyAsync(p->status.ptr, &word, sizeof(word), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+}
 
 struct StageTimer {
     Plan* p;
@@ -136,6 +160,7 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
     p->g.finish();
     if (opts) p->opts = *opts;
     if (p->opts.max_iterations <= 0) p->opts.max_iterations = int64_t(1) << 20;
+    msc::read_fault(p);
     msc_status st = msc::check_cuda(p, cudaGetDevice(&p->device), "cudaGetDevice");
     if (!st) st = msc::check_cuda(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
                                   "cudaDeviceGetAttribute");
@@ -261,6 +286,7 @@ static msc_status ensure_reach(Plan* p, cudaStream_t s) {
     msc::StageTimer tm(p, s, &p->stats.ms_reachability);
     if ((st = msc::run_reachability(p, s))) return st;
     tm.stop();
+    if (p->fault_kind == 2) msc::raise_status(p, msc::ST_TIMEOUT, s);
     if ((st = msc::check_status_word(p, s))) return st;
     p->have_reach = true;
     return MSC_OK;
@@ -343,6 +369,7 @@ static msc_status ensure_dstar(Plan* p, cudaStream_t s) {
     msc::StageTimer tm(p, s, &p->stats.ms_path_count);
     if ((st = msc::run_path_count(p, s))) return st;
     tm.stop();
+    if (p->fault_kind == 3) msc::raise_status(p, msc::ST_OVERFLOW, s);
     if ((st = msc::check_status_word(p, s))) return st;
     p->have_dstar = true;
     return MSC_OK;

@@ -72,6 +72,10 @@ struct Plan {
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
          have_junctions = false, have_minor = false, have_dstar = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;  // stage / kernel timing
+    // host-side fault injection (MSC_FAULT, read at plan creation; tests only): the failure is
+    // made on the host -- a faked allocation failure, or a status bit raised as a kernel would
+    int fault_kind = 0;  // 0 none, 1 alloc, 2 timeout (reachability), 3 overflow (path count)
+    int64_t fault_at = 0, alloc_calls = 0;
 };
 
 // The trace of the DAG minor (minor.cu): for every 1-saddle (ranks 0..n1-1) then every junction

@@ -71,38 +71,3 @@ def test_bad_arguments():
     with pytest.raises(m.MscError) as e:
         m.msc_critical(plan)  # before msc_gradient
     assert e.value.status == 11
-
-
-@pytest.mark.slow
-def test_grf256_sampled_parity():
-    """256^3 k^-3 GRF (the bench workload): packed words at sampled vertices vs the oracle's
-    per-vertex lower stars, and properties of the full critical lists."""
-    f = fields.config_field("grf256")
-    _, words, counts, lists, _ = run_gradient(f)
-    nz, ny, nx = f.shape
-    rng = np.random.default_rng(0)
-    sample = rng.integers(0, nx * ny * nz, size=4000)
-    # plus a full 40x12x12 box that straddles CTA tiles
-    z, y, x = np.meshgrid(np.arange(100, 112), np.arange(60, 72), np.arange(20, 60), indexing="ij")
-    box = (x + nx * (y + ny * z)).reshape(-1)
-    verts = np.concatenate([sample, box, [0, nx * ny * nz - 1]])
-    want = oracle.packed_at(f, verts)
-    assert np.array_equal(words.reshape(-1)[verts], want)
-    assert counts[0] - counts[1] + counts[2] - counts[3] == 1
-    for k in range(4):
-        assert np.all(np.diff(lists[k].astype(np.int64)) > 0), "lists must be strictly increasing"
-        assert len(lists[k]) == counts[k]
-    # every listed cell is critical in the packed words, and every critical slot is listed
-    rx, ry = 2 * nx - 1, 2 * ny - 1
-    flat = words.reshape(-1)
-    total = 0
-    for k in range(4):
-        c = lists[k].astype(np.int64)
-        cx, cy, cz = c % rx, (c // rx) % ry, c // (rx * ry)
-        assert np.all((cx & 1) + (cy & 1) + (cz & 1) == k)
-        slot = (cx & 1) + 2 * (cy & 1) + 4 * (cz & 1)
-        code = (flat[(cx // 2) + nx * ((cy // 2) + ny * (cz // 2))] >> (3 * slot)) & 7
-        assert np.all(code == 0)
-        total += len(c)
-    codes = (flat[:, None] >> (3 * np.arange(8))[None, :]) & 7
-    assert int((codes == 0).sum()) == total

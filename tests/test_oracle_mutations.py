@@ -23,7 +23,7 @@ MUTANTS = [
     ("critical_without_pushing_cofacets",
      "            make_critical(c);\n            for (int b : ls.cofacets_in_L(c))",
      "            make_critical(c);\n            for (int b : std::vector<int>())"),
-    ("dag_keeps_own_partner", "        if (uint32_t(q) == pair_of[e]) continue;\n", ""),
+    ("dag_keeps_own_partner", "        if (uint32_t(q) == own) continue;\n", ""),
     ("count_assign_not_add", "                cnt[w] = after;", "                cnt[w] = cv;"),
     ("min_arcs_swapped", "out[2 * i] = vertex_min[std::min(vs[0], vs[1])];",
      "out[2 * i] = vertex_min[std::max(vs[0], vs[1])];"),
@@ -59,7 +59,7 @@ def _run_pins():
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_reject_mutant(name, old, new, tmp_path):
     src = open(oracle._SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"  # every copy of the line is mutated
     path = tmp_path / "mutant.cpp"
     path.write_text(src.replace(old, new))
     lib = str(tmp_path / "libmutant.so")

@@ -407,3 +407,35 @@ def test_packed_at_matches_full_pack():
     full = oracle.pack(_dims(f), pair).reshape(-1)
     verts = np.arange(full.size)
     assert np.array_equal(oracle.packed_at(f, verts), full)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_lazy_sampled_queries_equal_whole_volume(seed):
+    """The sampled (lazily paired) oracle queries used on full-size volumes reproduce the
+    whole-volume oracle: pairs, labels, DAG-node facts and D* rows."""
+    f = [fields.grf((30, 31, 32), 3.0, seed=40 + seed), random_field((9, 10, 11), 41 + seed, "ties"),
+         fields.gaussian_blobs(n=28, n_blobs=6, sigma_range=(2, 6), seed=42 + seed)][seed]
+    r = oracle.compute_all(f)
+    s1, s2 = r["lists"][1], r["lists"][2]
+    cells = np.arange(0, len(r["pair"]), 5, dtype=np.uint32)
+    assert np.array_equal(oracle.lazy_pairs(f, cells), r["pair"][cells])
+    v = np.arange(0, f.size, 3)
+    assert np.array_equal(oracle.lazy_vertex_min(f, v), r["vertex_min"].reshape(-1)[v])
+    assert np.array_equal(oracle.lazy_cube_max(f, v), r["cube_max"].reshape(-1)[v])
+    rows = oracle.lazy_dstar_rows(f, s1)
+    R, C, K = r["dstar"]
+    full = {}
+    for a, b, k in zip(R, C, K):
+        full.setdefault(int(s1[a]), {})[int(s2[b])] = int(k)
+    assert all(rows[int(c)] == full.get(int(c), {}) for c in s1)
+    C3 = Complex(_dims(f))
+    ones = np.array([c for c in range(C3.ncells()) if C3.dim(c) == 1], dtype=np.uint32)
+    facts = oracle.lazy_nodes(f, ones)
+    jset = set(int(j) for j in r["junctions"])
+    vis = r["visited"]
+    for c, (node, crit, deg) in zip(ones, facts):
+        cx, cy, cz = C3.coords(int(c))
+        axis = 0 if cx & 1 else (1 if cy & 1 else 2)
+        visited = bool((vis[cz // 2, cy // 2, cx // 2] >> axis) & 1)
+        assert (int(c) in jset) == (visited and node and not crit and deg > 1)
+        assert crit == (r["pair"][c] == 0xFFFFFFFF)
