@@ -126,6 +126,22 @@ def _traffic_record(kernel):
     return rec
 
 
+def aggregate_replicas(ms_local, e2e_local, voxels_per_rank, dist=None, device="cpu"):
+    """Replicas only: every rank times the same per-GPU work; the job's step time is the
+    slowest rank's, and throughput counts the voxels of all ranks (weak scaling)."""
+    import torch
+
+    world = 1
+    ms, e2e = float(ms_local), float(e2e_local)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms, e2e], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e = float(t[0]), float(t[1])
+    return {"world": world, "ms": ms, "e2e_ms": e2e, "value": world * voxels_per_rank / (ms / 1e3) / 1e6,
+            "e2e_value": world * voxels_per_rank / (e2e / 1e3) / 1e6}
+
+
 def cpu_baseline(field, seconds_hint=""):
     """The oracle as it stands, single-threaded, on a bounded crop of the workload."""
     import numpy as np
@@ -234,12 +250,7 @@ def run_gpu(args):
             kernel_ms["rows_thread"].append(st["ms_rows_kernel"])
         barrier()
         wall = time.perf_counter() - t_region
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nvox / (ms / 1e3) / 1e6
+    ms_local = sum(step_ms) / len(step_ms)
 
     # ---- end to end from pinned host memory -------------------------------------------
     h_field = torch.from_numpy(f).pin_memory()
@@ -276,11 +287,8 @@ def run_gpu(args):
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
             bo = nbytes
-    e2e = sum(e2e_ms) / len(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    agg = aggregate_replicas(ms_local, sum(e2e_ms) / len(e2e_ms), nvox, dist, device="cuda")
+    ms, value = agg["ms"], agg["value"]
 
     if rank != 0:
         dist.destroy_process_group()
@@ -324,7 +332,7 @@ def run_gpu(args):
                    "voxels_per_step": nvox, "parallelism": f"replicas x{world}",
                    "l2": "flushed before every timed step (256 MB write)",
                    "critical_counts": counts, "nnz_Dstar": last["nnz_Dstar"], "n_iter": last["n_iter"]},
-        "e2e": {"value": world * nvox / (e2e / 1e3) / 1e6, "unit": "Mvoxel/s",
+        "e2e": {"value": agg["e2e_value"], "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(bo)},
         "gpu_launches": launches,
         "roofline": roofline,

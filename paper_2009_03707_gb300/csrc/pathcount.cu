@@ -119,89 +119,118 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
     return base + (incl - n);
 }
 
-__global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a) {
+// Persistent: each round, every lane advances its own row by one frontier step; lanes whose
+// row is finished (or deferred) take new rows with one warp-wide atomic, so lanes do not idle
+// while the longest row of their warp runs to the end.  Finished rows are appended with one
+// warp-aggregated atomic per round.
+__global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a, u64* next_row) {
     extern __shared__ __align__(16) unsigned char t0_raw[];
     T0Shared& sh = *reinterpret_cast<T0Shared*>(t0_raw);
-    const int t = threadIdx.x;
-    const int64_t i = int64_t(blockIdx.x) * T0_THREADS + t;
-    const bool valid = i < a.nrows;  // every lane stays to the warp-wide appends at the end
-    const int64_t s = valid ? row_of(a, i) : 0;
+    const int t = threadIdx.x, lane = t & 31;
+    int64_t s = -1;  // the lane's current row (-1: none)
     int cur = 0, nf = 0, nd = 0;
-    bool fit = true;
-    u64 iter = 0, entries = 0;
-    if (valid) {
-        const uint32_t kinds = a.kinds[s];
-        const uint4 t4 = trace_of(a, s);
-        const uint32_t tg[4] = {t4.x, t4.y, t4.z, t4.w};
+    u64 iter = 0, entries = 0, it_max = 0, en_sum = 0, mx_all = 0;
+    bool exhausted = false;
+    while (true) {
+        // lanes without a row take the next ones (one atomic for the warp)
+        const unsigned want = __ballot_sync(0xFFFFFFFFu, s < 0 && !exhausted);
+        if (want) {
+            u64 base = 0;
+            if (lane == __ffs(want) - 1) base = atomicAdd(next_row, (u64)__popc(want));
+            base = __shfl_sync(0xFFFFFFFFu, base, __ffs(want) - 1);
+            if (s < 0 && !exhausted) {
+                const u64 mine = base + __popc(want & ((1u << lane) - 1u));
+                if (mine < (u64)a.nrows) {
+                    s = row_of(a, int64_t(mine));
+                    cur = 0;
+                    nf = nd = 0;
+                    iter = entries = 0;
+                    bool fit = true;
+                    const uint32_t kinds = a.kinds[s];
+                    const uint4 t4 = trace_of(a, s);
+                    const uint32_t tg[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t kind = trace_kind(kinds, k);
-            if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[0], sh.fv[0], nf, t, tg[k], 1);
-            if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tg[k], 1);
-        }
-        while (fit && nf > 0) {
-            if (int64_t(++iter) > a.max_iter) {
-                atomicOr(a.status, ST_ITER);
-                break;
-            }
-            entries += nf;
-            int ng = 0;
-            for (int e = 0; e < nf && fit; ++e) {
-                const int64_t j = a.n1 + int64_t(sh.fk[cur][e][t]);
-                const uint32_t c = sh.fv[cur][e][t];
-                const uint32_t kj = a.kinds[j];
-                const uint4 q = trace_of(a, j);
-                const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t kind = trace_kind(kj, k);
-                    if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[cur ^ 1], sh.fv[cur ^ 1], ng, t, tq[k], c);
-                    if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tq[k], c);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t kind = trace_kind(kinds, k);
+                        if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[0], sh.fv[0], nf, t, tg[k], 1);
+                        if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tg[k], 1);
+                    }
+                    if (!fit) nf = -1;  // defer
+                } else {
+                    exhausted = true;
                 }
             }
-            cur ^= 1;
-            nf = ng;
         }
-    }
-    const bool done = valid && fit;
-    // sort the row by column (insertion sort over the thread's column)
-    if (done)
-        for (int e = 1; e < nd; ++e) {
-            const uint32_t k = sh.dk[e][t], v = sh.dv[e][t];
-            int f = e;
-            while (f > 0 && sh.dk[f - 1][t] > k) {
-                sh.dk[f][t] = sh.dk[f - 1][t];
-                sh.dv[f][t] = sh.dv[f - 1][t];
-                --f;
+        if (!__any_sync(0xFFFFFFFFu, s >= 0)) break;
+        // one frontier step of the lane's row
+        if (s >= 0 && nf > 0) {
+            if (int64_t(++iter) > a.max_iter) {
+                atomicOr(a.status, ST_ITER);
+                nf = 0;
+            } else {
+                entries += nf;
+                int ng = 0;
+                bool fit = true;
+                for (int e = 0; e < nf && fit; ++e) {
+                    const int64_t j = a.n1 + int64_t(sh.fk[cur][e][t]);
+                    const uint32_t c = sh.fv[cur][e][t];
+                    const uint32_t kj = a.kinds[j];
+                    const uint4 q = trace_of(a, j);
+                    const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t kind = trace_kind(kj, k);
+                        if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[cur ^ 1], sh.fv[cur ^ 1], ng, t, tq[k], c);
+                        if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tq[k], c);
+                    }
+                }
+                cur ^= 1;
+                nf = fit ? ng : -1;
             }
-            sh.dk[f][t] = k;
-            sh.dv[f][t] = v;
         }
-    const unsigned n_out = done ? unsigned(nd) : 0u;
-    const u64 base = warp_append(a.out_cursor, n_out);
-    u64 mx = 0;
-    for (unsigned e = 0; e < n_out; ++e) {
-        if (base + e < a.out_cap) {
-            a.out_col[base + e] = sh.dk[e][t];
-            a.out_cnt[base + e] = sh.dv[e][t];
-        } else {
-            atomicOr(a.status, ST_CAPACITY);
+        // rows that finished this round (frontier empty) or must be deferred (a map overflowed)
+        const bool done = s >= 0 && nf == 0;
+        const bool defer = s >= 0 && nf < 0;
+        if (done)
+            for (int e = 1; e < nd; ++e) {  // insertion sort of the row by column
+                const uint32_t k = sh.dk[e][t], v = sh.dv[e][t];
+                int f = e;
+                while (f > 0 && sh.dk[f - 1][t] > k) {
+                    sh.dk[f][t] = sh.dk[f - 1][t];
+                    sh.dv[f][t] = sh.dv[f - 1][t];
+                    --f;
+                }
+                sh.dk[f][t] = k;
+                sh.dv[f][t] = v;
+            }
+        const unsigned n_out = done ? unsigned(nd) : 0u;
+        const u64 base = warp_append(a.out_cursor, n_out);
+        for (unsigned e = 0; e < n_out; ++e) {
+            if (base + e < a.out_cap) {
+                a.out_col[base + e] = sh.dk[e][t];
+                a.out_cnt[base + e] = sh.dv[e][t];
+            } else {
+                atomicOr(a.status, ST_CAPACITY);
+            }
+            mx_all = max(mx_all, (u64)sh.dv[e][t]);
         }
-        mx = max(mx, (u64)sh.dv[e][t]);
+        if (done) {
+            a.row_start[s] = int64_t(base);
+            a.row_len[s] = n_out;
+            it_max = max(it_max, iter);
+            en_sum += entries;
+        }
+        const u64 dpos = warp_append(a.deferred_count, defer ? 1u : 0u);
+        if (defer) a.deferred[dpos] = uint32_t(s);
+        if (done || defer) s = -1;
     }
-    if (done) {
-        a.row_start[s] = int64_t(base);
-        a.row_len[s] = n_out;
-    }
-    const u64 dpos = warp_append(a.deferred_count, (valid && !fit) ? 1u : 0u);
-    if (valid && !fit) a.deferred[dpos] = uint32_t(s);
-    mx = warp_max(mx);
-    const u64 it = warp_max(done ? iter : 0);
-    const u64 en = warp_sum(done ? entries : 0);
-    if ((threadIdx.x & 31) == 0) {
-        if (mx) atomicMax(a.max_count, mx);
-        if (it) atomicMax(a.n_iter, it);
-        if (en) atomicAdd(a.n_entries, en);
+    mx_all = warp_max(mx_all);
+    it_max = warp_max(it_max);
+    en_sum = warp_sum(en_sum);
+    if (lane == 0) {
+        if (mx_all) atomicMax(a.max_count, mx_all);
+        if (it_max) atomicMax(a.n_iter, it_max);
+        if (en_sum) atomicAdd(a.n_entries, en_sum);
     }
 }
 
@@ -519,8 +548,13 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
                                                             int(sizeof(T0Shared))),
                                     "cudaFuncSetAttribute(rows_thread)")))
                     return e;
+                if ((e = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return e;
+                int per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_thread, T0_THREADS, sizeof(T0Shared));
+                const int64_t want = (nrows + T0_THREADS - 1) / T0_THREADS;
+                const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(1, per_sm)) * p->num_sms)));
                 cudaEventRecord(p->kev0, s);
-                rows_thread<<<int((nrows + T0_THREADS - 1) / T0_THREADS), T0_THREADS, sizeof(T0Shared), s>>>(a);
+                rows_thread<<<grid, T0_THREADS, sizeof(T0Shared), s>>>(a, ctr + C_NEXT);
                 cudaEventRecord(p->kev1, s);
                 launched(p);
             } else if (tier == 1) {
