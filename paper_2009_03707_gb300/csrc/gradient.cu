@@ -13,10 +13,11 @@
 //    whose owner is in the neighbouring tile on the - side go straight to global memory with
 //    atomicOr.  So the tile's words on its + faces are finished with atomicOr too, into words
 //    zeroed beforehand, and every other word is a plain coalesced store.
-//  * A lower star is handled as 27-bit masks over the offsets d in {-1,0,1}^3 (lower_star.cuh).
-//    Stars differ widely in size (1..27 cells) and a warp runs as long as its largest, so the
-//    CTA first sizes every star and counting-sorts its vertices by size; consecutive threads
-//    then take stars of equal size.
+//  * A lower star is handled as 27-bit masks over the offsets d in {-1,0,1}^3 (lower_star.cuh),
+//    with the per-position masks tabulated in shared memory and the vertex keys read straight
+//    from the staged tile.  Stars differ widely in size (1..27 cells) and a warp runs as long as
+//    its largest, so the CTA first sizes every star and counting-sorts its vertices by size;
+//    warps then claim 32 consecutive stars at a time, largest first.
 //  * A second, bandwidth-bound kernel turns the finished words into per-slot critical bitmaps:
 //    one warp ballot per slot gives 32 vertices' bits -- the input of the ordered compaction.
 #include "lower_star.cuh"
@@ -46,10 +47,14 @@ __device__ __forceinline__ uint32_t order_key(float f) {
 struct Shared {
     uint32_t fkey[FZ][FY][FX];   // order keys of the field tile (OUTSIDE_KEY off-grid)
     uint32_t words[TZ][TY][TX];  // packed codes of the owned tile
-    uint32_t vkey[27][THREADS];  // per-thread scratch: keys of the star's vertices
     uint32_t inl[NOWN];          // lower-star mask of every owned vertex (0: off-grid)
     uint16_t order[NOWN];        // non-minimal vertices, largest stars first
     int bin[28];                 // counting-sort bins by star size
+    int next;                    // next unclaimed entry of `order`
+    star::Tables tab;            // per-position masks; key offsets within fkey
+    // per position p: slot of the cell (bits 0-2), whether its owner is one step back along
+    // x, y, z (bits 3-5), and the owner's distance back in `words` (bits 8+)
+    uint32_t emit_info[27];
 };
 
 __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* __restrict__ field,
@@ -62,6 +67,13 @@ __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* 
 
     for (int i = t; i < NOWN; i += THREADS) (&sh.words[0][0][0])[i] = 0;
     if (t < 28) sh.bin[t] = 0;
+    if (t == 0) sh.next = 0;
+    if (t < 27) {
+        star::fill_tables(sh.tab, t, FX, FX * FY);
+        const uint32_t xn = (star::XN >> t) & 1, yn = (star::YN >> t) & 1, zn = (star::ZN >> t) & 1;
+        const uint32_t slot = (pdx(t) != 0) | ((pdy(t) != 0) << 1) | ((pdz(t) != 0) << 2);
+        sh.emit_info[t] = slot | (xn << 3) | (yn << 4) | (zn << 5) | ((xn + yn * TX + zn * TX * TY) << 8);
+    }
     bool saw_nan = false;
     for (int i = t; i < FX * FY * FZ; i += THREADS) {
         const int fx = i % FX, fy = (i / FX) % FY, fz = i / (FX * FY);
@@ -109,34 +121,43 @@ __global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* 
     __syncthreads();
     const int n_items = sh.bin[0];
 
+    // warps claim 32 consecutive stars at a time, largest first, so the CTA's stars are
+    // spread over its warps by longest-processing-time order
     bool ok = true;
-    const star::Scratch sc{&sh.vkey[0][t], THREADS};
-    for (int it = t; it < n_items; it += THREADS) {
-        const int i = sh.order[it];
+    const int lane = t & 31;
+    uint32_t* const wtile = &sh.words[0][0][0];
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&sh.next, 32);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n_items) break;
+        if (base + lane < n_items) {
+        const int i = sh.order[base + lane];
         const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
         const uint32_t inL = sh.inl[i];
-        const uint32_t* center = &sh.fkey[lz + 1][ly + 1][lx + 1];
-#pragma unroll
-        for (int p = 0; p < 27; ++p)  // the keys of the star's vertices (constant offsets)
-            if ((inL >> p) & 1u) sc.v(p) = center[pdz(p) * FY * FX + pdy(p) * FX + pdx(p)];
+        const star::Star st{&sh.fkey[lz + 1][ly + 1][lx + 1], &sh.tab};
+        const uint32_t low_face = (lx == 0) | ((ly == 0) << 1) | ((lz == 0) << 2);
         const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
         // a cell is owned by its lowest corner vertex: OR its code into that vertex's word
         auto emit = [&](int p, uint32_t code) {
-            const int xn = (star::XN >> p) & 1, yn = (star::YN >> p) & 1, zn = (star::ZN >> p) & 1;
-            const int slot = (((star::XZ >> p) & 1) ^ 1) | ((((star::YZ >> p) & 1) ^ 1) << 1) |
-                             ((((star::ZZ >> p) & 1) ^ 1) << 2);
-            const int ox = lx - xn, oy = ly - yn, oz = lz - zn;
-            if ((ox | oy | oz) >= 0) atomicOr(&sh.words[oz][oy][ox], code << (3 * slot));
-            else atomicOr(words_out + g.vid(gx - xn, gy - yn, gz - zn), code << (3 * slot));
+            const uint32_t e = sh.emit_info[p];
+            const uint32_t bits = code << (3 * (e & 7u));
+            if (((e >> 3) & low_face) == 0) {
+                atomicOr(wtile + (i - int(e >> 8)), bits);
+            } else {
+                const int xn = (e >> 3) & 1, yn = (e >> 4) & 1, zn = (e >> 5) & 1;
+                atomicOr(words_out + g.vid(gx - xn, gy - yn, gz - zn), bits);
+            }
         };
-        ok &= star::pair_lower_star(inL, sc, emit);
+        ok &= star::pair_lower_star(inL, st, emit);
+        }
     }
     if (!ok) atomicOr(status, ST_INTERNAL);
     __syncthreads();
 
     // epilogue: far-boundary codes, then plain stores -- or atomicOr on the tile's + faces,
     // whose words also receive codes from the neighbouring tiles
-    const int lane = t & 31, warp = t >> 5;
+    const int warp = t >> 5;
     const int gx = x0 + lane;
     for (int r = warp; r < TY * TZ; r += THREADS / 32) {
         const int ly = r % TY, lz = r / TY;

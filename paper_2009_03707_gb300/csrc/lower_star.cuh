@@ -56,10 +56,12 @@ __host__ __device__ constexpr uint32_t cofacet_mask(int p) {
            (pdz(p) ? 0u : (1u << (p - 9)) | (1u << (p + 9)));
 }
 
-// 3-bit direction code of the partner at position q seen from the cell at position p.
+// 3-bit direction code of the partner at position q seen from the cell at position p:
+// q - p = -1, +1, -3, +3, -9, +9 gives 1..6 (axis x, y, z; - side first).
 __host__ __device__ inline uint32_t dir_code(int p, int q) {
-    int d = q - p;
-    return d == -1 ? 1u : d == 1 ? 2u : d == -3 ? 3u : d == 3 ? 4u : d == -9 ? 5u : 6u;
+    const int d = q - p;
+    const int ad = d < 0 ? -d : d;
+    return 1u + 2u * (uint32_t(ad > 1) + uint32_t(ad > 3)) + uint32_t(d > 0);
 }
 
 // Cells of the star in L(x): AND of the "lower" mask over every projection of the offset.
@@ -80,26 +82,43 @@ __host__ __device__ inline uint32_t cell_vertices(int p) {
     return xs & ys & zs & ~(1u << CENTER);
 }
 
-// Per-thread scratch: the order keys of the star's vertices.  On the device it lives in shared
-// memory with a [position][thread] layout (stride = threads per CTA).
-struct Scratch {
-    uint32_t* vkey;
-    int stride;
-    __host__ __device__ uint32_t& v(int p) const { return vkey[p * stride]; }
+// Per-position masks, tabulated once per CTA (shared memory on the device): a 27-entry table of
+// 32-bit words sits in 27 distinct banks, so divergent lanes read it without conflicts.  off[p]
+// is where the key of the vertex at position p sits relative to the key of x in the caller's
+// key array (on the device: the CTA's staged field tile).
+struct Tables {
+    uint32_t cellv[27];
+    uint32_t facet[27];
+    uint32_t cofacet[27];
+    int off[27];
+};
+
+__host__ __device__ inline void fill_tables(Tables& T, int p, int row, int plane) {
+    T.cellv[p] = cell_vertices(p);
+    T.facet[p] = facet_mask(p);
+    T.cofacet[p] = cofacet_mask(p);
+    T.off[p] = pdx(p) + row * pdy(p) + plane * pdz(p);
+}
+
+// One lower star: the key of x and the tables; key(p) is the order key of the vertex at p.
+struct Star {
+    const uint32_t* center;
+    const Tables* T;
+    __host__ __device__ uint32_t key(int p) const { return center[T->off[p]]; }
 };
 
 // True if the cell at position a is smaller than the one at b (a != b): the larger one owns
 // the largest vertex (key, then position) of the symmetric difference of their vertex sets.
-__host__ __device__ inline bool cell_less(int a, int b, const Scratch& sc) {
-    const uint32_t vb = cell_vertices(b);
-    uint32_t d = cell_vertices(a) ^ vb;
+__host__ __device__ __forceinline__ bool cell_less(int a, int b, const Star& st) {
+    const uint32_t vb = st.T->cellv[b];
+    uint32_t d = st.T->cellv[a] ^ vb;
     int w = MSC_FFS(d) - 1;
-    uint32_t kw = sc.v(w);
+    uint32_t kw = st.key(w);
     d &= d - 1;
     while (d) {  // ascending positions: on equal keys the later position wins
         const int q = MSC_FFS(d) - 1;
         d &= d - 1;
-        const uint32_t kq = sc.v(q);
+        const uint32_t kq = st.key(q);
         if (kq >= kw) {
             kw = kq;
             w = q;
@@ -108,19 +127,19 @@ __host__ __device__ inline bool cell_less(int a, int b, const Scratch& sc) {
     return (vb >> w) & 1u;
 }
 
-__host__ __device__ inline int pop_min(uint32_t mask, const Scratch& sc) {
+__host__ __device__ __forceinline__ int pop_min(uint32_t mask, const Star& st) {
     int best = MSC_FFS(mask) - 1;
     mask &= mask - 1;
     while (mask) {
         const int p = MSC_FFS(mask) - 1;
         mask &= mask - 1;
-        if (cell_less(p, best, sc)) best = p;
+        if (cell_less(p, best, st)) best = p;
     }
     return best;
 }
 
-__host__ __device__ inline bool one_free_facet(int q, uint32_t inL, uint32_t cls) {
-    return MSC_POPC(facet_mask(q) & inL & ~cls) == 1;
+__host__ __device__ __forceinline__ bool one_free_facet(int q, uint32_t inL, uint32_t cls, const Tables* T) {
+    return MSC_POPC(T->facet[q] & inL & ~cls) == 1;
 }
 
 // Bit p set iff the vertex at position p is lower than x (value, then index; the index order
@@ -137,29 +156,30 @@ __host__ __device__ inline uint32_t lower_mask(const uint32_t* k) {
     return lower;
 }
 
-// Pairs the cells of L(x) given inL (the lower-star mask, with more than x in it) and the order
-// keys of the vertices of L(x) in sc.v(p) for every p in inL other than 13.  Vertices with equal
-// keys are ordered by position, which is their index order.  emit(p, code) is called for every
-// non-critical cell with its direction code.  Returns false if the procedure did not classify
-// every cell (an internal error).
+// Pairs the cells of L(x) given inL (the lower-star mask, with more than x in it); st.key(p)
+// must be valid for every p in inL.  Vertices with equal keys are ordered by position, which
+// is their index order.  emit(p, code) is called for every non-critical cell with its
+// direction code.  Returns false if the procedure did not classify every cell (an internal
+// error).
 template <class Emit>
-__host__ __device__ bool pair_lower_star(const uint32_t inL, const Scratch& sc, Emit&& emit) {
-    const int delta = pop_min(inL & DIM1, sc);
+__host__ __device__ __forceinline__ bool pair_lower_star(const uint32_t inL, const Star& st, Emit&& emit) {
+    const Tables* T = st.T;
+    const int delta = pop_min(inL & DIM1, st);
     uint32_t cls = (1u << CENTER) | (1u << delta);
     emit(CENTER, dir_code(CENTER, delta));
     emit(delta, dir_code(delta, CENTER));
     uint32_t pq0 = inL & DIM1 & ~(1u << delta);
     uint32_t pq1 = 0;
-    for (uint32_t c = cofacet_mask(delta) & inL & ~cls; c; c &= c - 1) {
+    for (uint32_t c = T->cofacet[delta] & inL & ~cls; c; c &= c - 1) {
         int q = MSC_FFS(c) - 1;
-        if (one_free_facet(q, inL, cls)) pq1 |= 1u << q;
+        if (one_free_facet(q, inL, cls, T)) pq1 |= 1u << q;
     }
     for (int guard = 0; guard < 64; ++guard) {
         while (pq1) {
-            int a = pop_min(pq1, sc);
+            int a = pop_min(pq1, st);
             pq1 &= ~(1u << a);
             if (cls & (1u << a)) continue;
-            uint32_t uf = facet_mask(a) & inL & ~cls;
+            uint32_t uf = T->facet[a] & inL & ~cls;
             if (uf == 0) {
                 pq0 |= 1u << a;
                 continue;
@@ -169,33 +189,31 @@ __host__ __device__ bool pair_lower_star(const uint32_t inL, const Scratch& sc, 
             pq0 &= ~(1u << pf);
             emit(pf, dir_code(pf, a));
             emit(a, dir_code(a, pf));
-            for (uint32_t c = (cofacet_mask(a) | cofacet_mask(pf)) & inL & ~cls; c; c &= c - 1) {
+            for (uint32_t c = (T->cofacet[a] | T->cofacet[pf]) & inL & ~cls; c; c &= c - 1) {
                 int q = MSC_FFS(c) - 1;
-                if (one_free_facet(q, inL, cls)) pq1 |= 1u << q;
+                if (one_free_facet(q, inL, cls, T)) pq1 |= 1u << q;
             }
         }
         if (!pq0) return cls == inL;
-        int c0 = pop_min(pq0, sc);
+        int c0 = pop_min(pq0, st);
         pq0 &= ~(1u << c0);
         if (cls & (1u << c0)) continue;
         cls |= 1u << c0;  // critical
-        for (uint32_t c = cofacet_mask(c0) & inL & ~cls; c; c &= c - 1) {
+        for (uint32_t c = T->cofacet[c0] & inL & ~cls; c; c &= c - 1) {
             int q = MSC_FFS(c) - 1;
-            if (one_free_facet(q, inL, cls)) pq1 |= 1u << q;
+            if (one_free_facet(q, inL, cls, T)) pq1 |= 1u << q;
         }
     }
     return false;
 }
 
 // Pairs the cells of L(x) given the 27 vertex order keys k[] (k[13] = x; an off-grid vertex
-// has key 0xFFFFFFFF).  See pair_lower_star.
+// has key 0xFFFFFFFF) and tables filled with row = 3, plane = 9.  See pair_lower_star.
 template <class Emit>
-__host__ __device__ bool process_lower_star(const uint32_t* k, const Scratch& sc, Emit&& emit) {
+__host__ __device__ bool process_lower_star(const uint32_t* k, const Tables* T, Emit&& emit) {
     const uint32_t inL = lower_star_mask(lower_mask(k));
     if (inL == (1u << CENTER)) return true;  // a minimum: every code stays 0
-    for (int p = 0; p < 27; ++p)
-        if ((inL >> p) & 1u) sc.v(p) = k[p];
-    return pair_lower_star(inL, sc, emit);
+    return pair_lower_star(inL, Star{k + CENTER, T}, emit);
 }
 
 }  // namespace star

@@ -20,8 +20,8 @@ static uint32_t order_key(float f) {
 extern "C" int host_words(const int64_t* d, const float* f, uint32_t* words) {
     const int nx = int(d[0]), ny = int(d[1]), nz = int(d[2]);
     std::memset(words, 0, sizeof(uint32_t) * size_t(nx) * ny * nz);
-    uint32_t vk[27];
-    Scratch sc{vk, 1};
+    Tables T;
+    for (int p = 0; p < 27; p++) fill_tables(T, p, 3, 9);
     int bad = 0;
     for (int z = 0; z < nz; z++)
         for (int y = 0; y < ny; y++)
@@ -38,7 +38,7 @@ extern "C" int host_words(const int64_t* d, const float* f, uint32_t* words) {
                     const int slot = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
                     words[ox + nx * (oy + ny * oz)] |= code << (3 * slot);
                 };
-                if (!process_lower_star(k, sc, emit)) bad++;
+                if (!process_lower_star(k, &T, emit)) bad++;
             }
     for (int z = 0; z < nz; z++)
         for (int y = 0; y < ny; y++)
