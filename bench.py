@@ -331,7 +331,10 @@ def run_gpu(args):
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "dims": [nx, ny, nz],
                    "voxels_per_step": nvox, "parallelism": f"replicas x{world}",
                    "l2": "flushed before every timed step (256 MB write)",
-                   "critical_counts": counts, "nnz_Dstar": last["nnz_Dstar"], "n_iter": last["n_iter"]},
+                   "critical_counts": counts, "nnz_Dstar": last["nnz_Dstar"], "n_iter": last["n_iter"],
+                   "graph": {k: last[k] for k in ("n_reachable", "n_bfs_levels", "n_junctions", "nnz_A", "nnz_B",
+                                                  "nnz_Bstar", "nnz_D", "n_pointer_jumps", "n_frontier_entries")},
+                   "max_path_count": str(last["max_path_count"])},
         "e2e": {"value": agg["e2e_value"], "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(bo)},
         "gpu_launches": launches,

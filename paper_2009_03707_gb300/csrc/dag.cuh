@@ -98,10 +98,14 @@ __host__ __device__ __forceinline__ int dag_out(const Geom& g, const uint32_t* _
     return cnt;
 }
 
-// Per-node record written by the BFS when it expands a 1-cell (indexed by its handle): whether
-// the node is a dead end, a branch point (out-degree > 1), or else its one successor.  A 1-cell
-// successor is its handle; a 2-saddle successor has bit 31 set and (owner << 2 | even axis).
+// Per-node record of every reachable 1-cell that is not a 1-saddle: whether the node is a dead
+// end, a branch point (out-degree > 1), or else its one successor.  A 1-cell successor is its
+// handle; a 2-saddle successor has bit 31 set and (owner << 2 | even axis).  Records are stored
+// one plane per axis (info_index), so a row of cells writes a contiguous run.
 constexpr uint32_t INFO_DEAD = 0xFFFFFFFFu;
+__host__ __device__ __forceinline__ uint32_t info_index(const Geom& g, uint32_t handle) {
+    return (handle & 3u) * uint32_t(g.nverts) + (handle >> 2);
+}
 constexpr uint32_t INFO_BRANCH = 0xFFFFFFFEu;
 
 __host__ __device__ __forceinline__ uint32_t encode_successor(const DagTarget& t) {

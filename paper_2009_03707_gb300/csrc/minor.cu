@@ -39,7 +39,7 @@ struct TraceArgs {
     const uint32_t* junc_prefix;
     const uint32_t* crit_bits;
     const uint32_t* crit_prefix;
-    const uint32_t* info;  // per 1-cell handle: dead end, branch point, or its one successor
+    const uint32_t* info;  // per reachable 1-cell (info_index): dead end, branch point, or its one successor
     uint32_t* tgt;    // 4 per source: destination rank
     uint8_t* kinds;   // 4 per source: 0 none / 1 junction / 2 2-saddle (read as one word per source)
     int64_t max_steps;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
                 atomicOr(a.status, ST_ITER);
                 break;
             }
-            const uint32_t w = a.info[h];
+            const uint32_t w = a.info[info_index(g, h)];
             if (w == INFO_DEAD) break;  // a dead path: dropped
             if (w == INFO_BRANCH) {     // a junction
                 const Vtx q = vtx_of(g, h >> 2);

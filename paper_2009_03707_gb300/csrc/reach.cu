@@ -1,17 +1,28 @@
 // (a4) Saddle-saddle reachability and (a5, first half) junction nodes.
 //
-// Sec. 3.2 and Sec. 3.5 "Saddle-Saddle reachability": a BFS over the DAG of 1-2 gradient
-// pairs from all 1-saddles at once.  The frontier starts as the 1-saddles; each level
-// expands every frontier node along its <= 4 out-edges, marks newly reached 1-cells in a
-// visited bitmap and appends them to the next frontier; the traversal ends when a level
-// adds nothing.  Where the paper stream-compacts a 4x-sized candidate array after each
-// level, here the first thread that sets a visited bit (atomicOr) owns the node and appends
-// it with one warp-aggregated atomic per warp, so the next frontier is already compact.
+// Sec. 3.2 and Sec. 3.5 "Saddle-Saddle reachability": the 1-cells reachable from the
+// 1-saddles in the DAG of 1-2 gradient pairs, level by level; the traversal ends when a level
+// adds nothing.  The paper runs a frontier BFS (expand, then stream-compact a 4x candidate
+// array).  Here the same level sets are computed by pulling instead of pushing, on the 1-cell
+// bitmap itself:
 //
-// Sec. 3.3 / Sec. 3.5 "Gradient path counting": a junction is a reachable 1-cell that is
-// not a 1-saddle and has out-degree > 1.  Junctions are marked in a bitmap with the same
-// row layout as the visited set and stream-compacted in cell-id order (scan.cuh), which
-// also gives O(1) ranks for the minor's matrix indices.
+//  * A 1-cell e has in-edges only if it is paired with a quad q; they come from the other three
+//    facets of q (a facet f of q has the out-edge f -> e because q is a cofacet of f that is not
+//    f's own partner).  So with R_k the set reached within k levels,
+//        R_{k+1} = R_k  u  { e paired with a quad q : some other facet of q is in R_k },
+//    R_0 = the 1-saddles.  That is one data-parallel sweep per level over the bitmap rows:
+//    for each 32-cell word, four pairing-direction masks select which neighbouring rows (shifted
+//    by one bit where the step is along x) feed it.  Sweep k+1 changes the bitmap iff BFS level
+//    k+1 is non-empty, so the level count is the paper's.
+//  * Every access is a coalesced word of a row, where a queue frontier scatters a 4-byte access
+//    per node over the whole grid.  Sweeps run in batches between host checks of their
+//    "changed" flags; a sweep after convergence only copies.
+//
+// Sec. 3.3 / Sec. 3.5 "Gradient path counting": a junction is a reachable 1-cell that is not a
+// 1-saddle and has out-degree > 1.  One warp per bitmap word (a lane per 1-cell) evaluates the
+// out-edges of each reachable cell, marks junctions, and records each node's successor for the
+// path tracer.  Junctions are stream-compacted in cell-id order (scan.cuh), which also gives
+// O(1) ranks for the minor's matrix indices.
 #include "dag.cuh"
 #include "scan.cuh"
 
@@ -20,98 +31,255 @@ namespace msc {
 namespace {
 
 constexpr int THREADS = 256;
+constexpr int SWEEP_BATCH = 4;  // sweeps between host checks
 
-int blocks(int64_t n) { return int((n + THREADS - 1) / THREADS); }
+__device__ __forceinline__ int other_axis(int a, int j) { return j == 0 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2); }
 
-struct CellXYZ {
-    int x, y, z;
+// Word addressing of the bitmaps, per thread: the 1-cell row layout is
+//   edge_word(z, c, y, b, w) = z*sz + y*sy + off[axis] + w   (sz = 4 ny W, sy = 2 W),
+// and the quad bitmaps hold one row per (even axis k, z, y): quad_word = ((k nz + z) ny + y) W + w.
+struct Rows {
+    int w, y, z;      // this thread's word: x = 32w .. 32w+31 of row (y, z)
+    int W, ny, nz;
+    int64_t sy, sz;   // 1-cell layout strides
+    int64_t base;     // z*sz + y*sy + w
+    int64_t qbase;    // (z ny + y) W + w
+    int64_t qplane;   // nz ny W
+    __device__ Rows(const Geom& g, int64_t t) {
+        const uint32_t q = g.div_W.div(uint32_t(t));
+        w = int(uint32_t(t) - q * uint32_t(g.W));
+        const uint32_t q2 = g.div_ny.div(q);
+        y = int(q - q2 * uint32_t(g.ny));
+        z = int(q2);
+        W = g.W;
+        ny = g.ny;
+        nz = g.nz;
+        sy = 2 * int64_t(W);
+        sz = 4 * int64_t(ny) * W;
+        base = z * sz + y * sy + w;
+        qbase = (int64_t(z) * ny + y) * W + w;
+        qplane = int64_t(nz) * ny * W;
+    }
+    template <int AX>
+    __device__ __forceinline__ int64_t edge(int dy, int dz) const {
+        return base + (AX == 1 ? W : AX == 2 ? 2 * int64_t(ny) * W : 0) + dy * sy + dz * sz;
+    }
+    template <int DY, int DZ>
+    __device__ __forceinline__ bool in_range() const {
+        return (DY >= 0 || y > 0) && (DY <= 0 || y < ny - 1) && (DZ >= 0 || z > 0) && (DZ <= 0 || z < nz - 1);
+    }
 };
-__device__ __forceinline__ CellXYZ decode(const Geom& g, uint32_t id) {
-    CellXYZ c;
-    const uint32_t q = g.div_rx.div(id);
-    c.x = int(id - q * g.rx);
-    c.z = int(g.div_ry.div(q));
-    c.y = int(q - uint32_t(c.z) * g.ry);
-    return c;
+
+// Bits of a row word at index `at` (the word of x = 32w..), shifted so that bit i refers to x + DX.
+template <int DX>
+__device__ __forceinline__ uint32_t shifted(const uint32_t* __restrict__ R, int64_t at, const Rows& r) {
+    const uint32_t mid = R[at];
+    if (DX == 0) return mid;
+    if (DX > 0) return __funnelshift_r(mid, r.w + 1 < r.W ? R[at + 1] : 0u, 1);
+    return __funnelshift_l(r.w > 0 ? R[at - 1] : 0u, mid, 1);
 }
 
-// Frontier 0: every 1-saddle (cell id -> handle), marked visited.
-__global__ void __launch_bounds__(THREADS) bfs_seed(Geom g, const uint32_t* __restrict__ s1, int64_t n1,
-                                                    uint32_t* __restrict__ visited, uint32_t* __restrict__ front) {
-    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (i >= n1) return;
-    CellXYZ c = decode(g, s1[i]);
-    const int axis = (c.x & 1) ? 0 : (c.y & 1) ? 1 : 2;
-    const int x = c.x >> 1, y = c.y >> 1, z = c.z >> 1;
-    atomicOr(&visited[edge_bitmap_word(g, x, y, z, axis)], 1u << (x & 31));
-    front[i] = edge_handle(vid32(g, x, y, z), axis);
+// Reach bits of the AX-cells owned by vertex (x + DX, y + DY, z + DZ); 0 outside the grid.
+template <int AX, int DX, int DY, int DZ>
+__device__ __forceinline__ uint32_t reach_row(const uint32_t* __restrict__ R, const Rows& r) {
+    if (!r.in_range<DY, DZ>()) return 0;
+    return shifted<DX>(R, r.edge<AX>(DY, DZ), r);
 }
 
-// One BFS level.  All lanes of a warp reach the aggregated append.
-__global__ void __launch_bounds__(THREADS) bfs_expand(Geom g, const uint32_t* __restrict__ words,
-                                                      const uint32_t* __restrict__ cur, int64_t ncur,
-                                                      uint32_t* __restrict__ visited, uint32_t* __restrict__ info,
-                                                      uint32_t* __restrict__ next,
-                                                      unsigned long long* __restrict__ next_count, uint64_t cap,
-                                                      uint32_t* __restrict__ status) {
-    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    uint32_t found[4];
-    int nf = 0;
-    if (i < ncur) {
-        const uint32_t h = cur[i];
-        const Vtx v = vtx_of(g, h >> 2);
-        DagTarget t[4];
-        const int n = dag_out(g, words, v.x, v.y, v.z, int(h & 3), t);
-        info[h] = node_info(n, t);  // read later by the junction marking and the path tracer
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (t[k].kind != 1) continue;
-            const uint32_t bit = 1u << (t[k].x & 31);
-            const uint32_t old = atomicOr(&visited[edge_bitmap_word(g, t[k].x, t[k].y, t[k].z, t[k].sub)], bit);
-            if (!(old & bit)) found[nf++] = edge_handle(t[k].v, t[k].sub);
-        }
-    }
-    // warp-aggregated append of the newly reached nodes
+// Cells of axis A whose partner is the quad on side S along axis B (mask m) and that have a
+// facet of that quad in R: the quad's other facets are the parallel A-cell one vertex along
+// S u_B and the two B-cells at the ends of the A-cell, owned by v (+ u_A) (- u_B if S < 0).
+template <int A, int B, int S>
+__device__ __forceinline__ uint32_t pull(uint32_t m, const uint32_t* __restrict__ R, const Rows& r) {
+    if (!m) return 0;
+    constexpr int back = S < 0 ? 1 : 0;
+    constexpr int ux = A == 0, uy = A == 1, uz = A == 2, bx = B == 0, by = B == 1, bz = B == 2;
+    const uint32_t p = reach_row<A, S * bx, S * by, S * bz>(R, r) |
+                       reach_row<B, ux - back * bx, uy - back * by, uz - back * bz>(R, r) |
+                       reach_row<B, -back * bx, -back * by, -back * bz>(R, r);
+    return m & p;
+}
+
+// Per vertex-row word (one warp, a lane per x): for each axis the four masks of 1-cells paired
+// with the quad on the - / + side along the first / second other axis, R_0 = the 1-saddles,
+// and for each quad orientation (by its even axis k) the bitmap of quads that are critical or
+// paired with a facet (the quads that give an out-edge to every other facet).
+__global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __restrict__ words,
+                                                      uint4* __restrict__ masks, uint32_t* __restrict__ R0,
+                                                      uint32_t* __restrict__ R1, uint32_t* __restrict__ qdown) {
     const int lane = threadIdx.x & 31;
-    int incl = nf;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && total) base = atomicAdd(next_count, (unsigned long long)total);
-    base = __shfl_sync(0xFFFFFFFFu, base, 31);
-    uint64_t pos = base + uint64_t(incl - nf);
-    for (int k = 0; k < nf; ++k, ++pos) {
-        if (pos < cap) next[pos] = found[k];
-        else atomicOr(status, ST_CAPACITY);
+    const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
+    for (int64_t t = (int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5; t < nrw;
+         t += (int64_t(gridDim.x) * THREADS) >> 5) {  // warp-uniform
+        const Rows r(g, t);
+        const int x = r.w * 32 + lane;
+        const uint32_t word = x < g.nx ? words[vid32(g, x, r.y, r.z)] : 0x00FFFFFFu;  // all codes 7 off-grid
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t code = slot_code(word, 1 << a);
+            const int k = int(code - 1) >> 1;  // axis of the partner (code 1..6)
+            const bool quad = code >= 1 && code <= 6 && k != a;
+            const int sel = quad ? 2 * (k == other_axis(a, 0) ? 0 : 1) + int(!(code & 1u)) : -1;  // odd: - side
+            const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, sel == 0), m1 = __ballot_sync(0xFFFFFFFFu, sel == 1);
+            const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, sel == 2), m3 = __ballot_sync(0xFFFFFFFFu, sel == 3);
+            const uint32_t crit = __ballot_sync(0xFFFFFFFFu, code == 0);
+            if (lane == a) {
+                const int64_t e = g.edge_word(r.z, a == 2, r.y, a == 1, r.w);
+                masks[e] = make_uint4(m0, m1, m2, m3);
+                R0[e] = crit;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t code = slot_code(word, 7 ^ (1 << k));
+            const bool down = code == 0 || (code <= 6 && (int(code - 1) >> 1) != k);
+            const uint32_t qd = __ballot_sync(0xFFFFFFFFu, down);
+            if (lane == 4 + k) qdown[k * r.qplane + r.qbase] = qd;
+        }
+        if (lane == 3) {  // the unused slot of the 1-cell layout stays empty in both buffers
+            const int64_t e = g.edge_word(r.z, 1, r.y, 1, r.w);
+            masks[e] = make_uint4(0, 0, 0, 0);
+            R0[e] = 0;
+            R1[e] = 0;
+        }
     }
 }
 
-// Junction bitmap: one thread per visited word; a set bit whose 1-cell is not critical and
-// has more than one out-edge is a junction.
-__global__ void __launch_bounds__(THREADS) mark_junctions(Geom g, const uint32_t* __restrict__ words,
-                                                          const uint32_t* __restrict__ visited,
-                                                          const uint32_t* __restrict__ info,
-                                                          uint32_t* __restrict__ junc) {
-    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (i >= g.edge_words()) return;
-    uint32_t vis = visited[i];
-    uint32_t out = 0;
-    if (vis) {
-        RowCoord r = decode_row(g, i);
-        const int axis = r.c ? 2 : (r.b ? 1 : 0);
-        while (vis) {
-            const int bit = __ffs(vis) - 1;
-            vis &= vis - 1;
-            const int x = r.w * 32 + bit;
-            const uint32_t v = vid32(g, x, r.y, r.z);
-            if (slot_code(words[v], edge_slot(axis)) == 0) continue;  // a 1-saddle
-            if (info[edge_handle(v, axis)] == INFO_BRANCH) out |= 1u << bit;
+template <int A>
+__device__ __forceinline__ bool sweep_word(const Rows& r, const uint4* __restrict__ masks,
+                                           const uint32_t* __restrict__ Rin, uint32_t* __restrict__ Rout) {
+    constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
+    const int64_t i = r.edge<A>(0, 0);
+    const uint32_t cur = Rin[i];
+    const uint4 m = masks[i];
+    uint32_t add = 0;
+    if ((m.x | m.y | m.z | m.w) & ~cur)
+        add = pull<A, B1, -1>(m.x & ~cur, Rin, r) | pull<A, B1, 1>(m.y & ~cur, Rin, r) |
+              pull<A, B2, -1>(m.z & ~cur, Rin, r) | pull<A, B2, 1>(m.w & ~cur, Rin, r);
+    Rout[i] = cur | add;
+    return add != 0;
+}
+
+// One level: Rout = Rin | cells whose partner quad has another facet in Rin.  blockIdx.y is the
+// axis, so every branch on it is uniform.  Sets *changed if any word grew.
+__global__ void __launch_bounds__(THREADS) reach_sweep(Geom g, const uint4* __restrict__ masks,
+                                                       const uint32_t* __restrict__ Rin, uint32_t* __restrict__ Rout,
+                                                       uint32_t* __restrict__ changed) {
+    const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
+    const int64_t t = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    bool grew = false;
+    if (t < nrw) {
+        const Rows r(g, t);
+        grew = blockIdx.y == 0 ? sweep_word<0>(r, masks, Rin, Rout)
+               : blockIdx.y == 1 ? sweep_word<1>(r, masks, Rin, Rout)
+                                 : sweep_word<2>(r, masks, Rin, Rout);
+    }
+    if (__syncthreads_or(grew) && threadIdx.x == 0) *changed = 1u;
+}
+
+// Down-quad bits of the quads with even axis K owned by vertex (x + DX, y + DY, z + DZ).
+template <int K, int DX, int DY, int DZ>
+__device__ __forceinline__ uint32_t quad_row(const uint32_t* __restrict__ qdown, const Rows& r) {
+    if (!r.in_range<DY, DZ>()) return 0;
+    return shifted<DX>(qdown, K * r.qplane + r.qbase + DY * int64_t(r.W) + DZ * int64_t(r.ny) * r.W, r);
+}
+
+// One warp per word of A-cells (a lane per cell).  The out-edges of a 1-cell e go through its
+// cofacet quads other than its partner that are critical or paired with a facet, so with the
+// down-quad rows (ordered like the partner masks: first/second other axis, - then + side) the
+// out-degree is a popcount.  Reachable cells that are not 1-saddles get their info record; a
+// single successor is decoded from the one quad word it goes through.
+template <int A>
+__device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int lane, const uint32_t* __restrict__ words,
+                                              const uint32_t* __restrict__ visited, const uint4* __restrict__ masks,
+                                              const uint32_t* __restrict__ qdown, const uint32_t* __restrict__ crit_bits,
+                                              uint32_t* __restrict__ info, uint32_t* __restrict__ junc,
+                                              unsigned long long& cnt) {
+    constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
+    constexpr int K1 = 3 - A - B1, K2 = 3 - A - B2;  // even axes of the quads along B1, B2
+    const int64_t i = r.edge<A>(0, 0);
+    const uint32_t vis = visited[i];
+    if (!vis) {  // warp-uniform
+        if (lane == 0) junc[i] = 0;
+        return;
+    }
+    if (lane == 0) cnt += __popc(vis);
+    const uint32_t crit = crit_bits[g.slot_word(1 << A, r.z, r.y, r.w)];
+    const uint4 m = masks[i];
+    const uint32_t q[4] = {quad_row<K1, -(B1 == 0), -(B1 == 1), -(B1 == 2)>(qdown, r), quad_row<K1, 0, 0, 0>(qdown, r),
+                           quad_row<K2, -(B2 == 0), -(B2 == 1), -(B2 == 2)>(qdown, r), quad_row<K2, 0, 0, 0>(qdown, r)};
+    const uint32_t partner = ((m.x >> lane) & 1u) | (((m.y >> lane) & 1u) << 1) | (((m.z >> lane) & 1u) << 2) |
+                             (((m.w >> lane) & 1u) << 3);
+    const uint32_t out = (((q[0] >> lane) & 1u) | (((q[1] >> lane) & 1u) << 1) | (((q[2] >> lane) & 1u) << 2) |
+                          (((q[3] >> lane) & 1u) << 3)) &
+                         ~partner;
+    const int n = __popc(out);
+    const bool mine = ((vis & ~crit) >> lane) & 1u;
+    if (mine) {
+        const int x = r.w * 32 + lane;
+        const uint32_t v = vid32(g, x, r.y, r.z);
+        uint32_t rec = n == 0 ? INFO_DEAD : INFO_BRANCH;
+        if (n == 1) {
+            const int sel = __ffs(out) - 1;
+            const int b = sel < 2 ? B1 : B2;
+            const int k = 3 - A - b;  // the quad's even axis
+            const bool plus = sel & 1;
+            int ox = x, oy = r.y, oz = r.z;
+            if (!plus) {
+                ox -= b == 0;
+                oy -= b == 1;
+                oz -= b == 2;
+            }
+            uint32_t ov = vid32(g, ox, oy, oz);
+            const uint32_t qc = slot_code(words[ov], 7 ^ (1 << k));
+            if (qc == 0) {
+                rec = 0x80000000u | (ov << 2) | uint32_t(k);  // a 2-saddle
+            } else {                                           // the facet the quad is paired with
+                const int kk = int(qc - 1) >> 1;
+                if (!(qc & 1u)) ov += kk == 0 ? 1u : kk == 1 ? uint32_t(g.nx) : uint32_t(g.nx) * uint32_t(g.ny);
+                rec = edge_handle(ov, kk == A ? b : A);
+            }
+        }
+        info[info_index(g, edge_handle(v, A))] = rec;
+    }
+    const uint32_t jw = __ballot_sync(0xFFFFFFFFu, mine && n > 1);
+    if (lane == 0) junc[i] = jw;
+}
+
+__global__ void __launch_bounds__(THREADS) classify_reached(Geom g, const uint32_t* __restrict__ words,
+                                                            const uint32_t* __restrict__ visited,
+                                                            const uint4* __restrict__ masks,
+                                                            const uint32_t* __restrict__ qdown,
+                                                            const uint32_t* __restrict__ crit_bits,
+                                                            uint32_t* __restrict__ info, uint32_t* __restrict__ junc,
+                                                            unsigned long long* __restrict__ n_reached) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
+    unsigned long long cnt = 0;
+    for (int64_t t = (int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5; t < nrw;
+         t += (int64_t(gridDim.x) * THREADS) >> 5) {  // warp-uniform
+        const Rows r(g, t);
+        if (blockIdx.y == 0) classify_word<0>(g, r, lane, words, visited, masks, qdown, crit_bits, info, junc, cnt);
+        else if (blockIdx.y == 1) classify_word<1>(g, r, lane, words, visited, masks, qdown, crit_bits, info, junc, cnt);
+        else classify_word<2>(g, r, lane, words, visited, masks, qdown, crit_bits, info, junc, cnt);
+        if (lane == 0 && blockIdx.y == 0) {  // the unused slot of the 1-cell layout
+            junc[g.edge_word(r.z, 1, r.y, 1, r.w)] = 0;
         }
     }
-    junc[i] = out;
+    __shared__ unsigned long long part[THREADS / 32];
+    if (lane == 0) part[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int k = 0; k < THREADS / 32; ++k) s += part[k];
+        if (s) atomicAdd(n_reached, s);
+    }
+}
+
+int grid_for(const Plan* p, int64_t threads) {
+    const int64_t want = (threads + THREADS - 1) / THREADS;
+    const int64_t cap = int64_t(p->num_sms > 0 ? p->num_sms : 148) * 8;
+    return int(std::max<int64_t>(1, std::min(want, cap)));
 }
 
 }  // namespace
@@ -119,50 +287,46 @@ __global__ void __launch_bounds__(THREADS) mark_junctions(Geom g, const uint32_t
 msc_status run_reachability(Plan* p, cudaStream_t s) {
     const Geom& g = p->g;
     msc_status st;
-    const int64_t n1 = p->counts[1];
-    const int64_t n_edges = int64_t(g.nx - 1) * g.ny * g.nz + int64_t(g.nx) * (g.ny - 1) * g.nz +
-                            int64_t(g.nx) * g.ny * (g.nz - 1);
-    if ((st = ensure(p, p->visited, sizeof(uint32_t) * size_t(g.edge_words())))) return st;
-    if ((st = ensure(p, p->qcount, sizeof(unsigned long long) * 2))) return st;
-    if ((st = ensure(p, p->node_info, sizeof(uint32_t) * 4 * size_t(g.nverts)))) return st;
-    if ((st = ensure(p, p->frontier[0], sizeof(uint32_t) * size_t(n1 ? n1 : 1)))) return st;
-    auto* visited = static_cast<uint32_t*>(p->visited.ptr);
-    auto* qcount = static_cast<unsigned long long*>(p->qcount.ptr);
-    if ((st = check_cuda(p, cudaMemsetAsync(visited, 0, sizeof(uint32_t) * size_t(g.edge_words()), s),
-                         "memset visited")))
-        return st;
+    const int64_t nw = g.edge_words();
+    const int64_t nrw = int64_t(g.nz) * g.ny * g.W;  // vertex-row words
+    if ((st = ensure(p, p->visited, sizeof(uint32_t) * size_t(nw)))) return st;
+    if ((st = ensure(p, p->reach_tmp, sizeof(uint32_t) * size_t(nw)))) return st;
+    if ((st = ensure(p, p->reach_masks, sizeof(uint4) * size_t(nw)))) return st;
+    if ((st = ensure(p, p->reach_qdown, sizeof(uint32_t) * 3 * size_t(nrw)))) return st;
+    if ((st = ensure(p, p->reach_flags, sizeof(uint32_t) * SWEEP_BATCH))) return st;
+    auto* masks = static_cast<uint4*>(p->reach_masks.ptr);
+    auto* flags = static_cast<uint32_t*>(p->reach_flags.ptr);
+    uint32_t* buf[2] = {static_cast<uint32_t*>(p->visited.ptr), static_cast<uint32_t*>(p->reach_tmp.ptr)};
+    reach_init<<<grid_for(p, nrw * 32), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, buf[0],
+                                                         buf[1], static_cast<uint32_t*>(p->reach_qdown.ptr));
+    launched(p);
+    if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
+    const dim3 sweep_grid(unsigned((nrw + THREADS - 1) / THREADS), 3);
     int cur = 0;
-    if (n1) {
-        bfs_seed<<<blocks(n1), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[1].ptr), n1, visited,
-                                                static_cast<uint32_t*>(p->frontier[0].ptr));
-        launched(p);
-    }
-    int64_t ncur = n1, levels = 0, reached = n1;
-    while (ncur > 0) {
-        if (levels >= p->opts.max_iterations) return fail(p, MSC_ERR_ITER_LIMIT, "BFS exceeded the iteration cap");
-        ++levels;
-        const int64_t cap = std::min<int64_t>(4 * ncur, n_edges);
-        if ((st = ensure(p, p->frontier[cur ^ 1], sizeof(uint32_t) * size_t(cap)))) return st;
-        if ((st = check_cuda(p, cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), s), "memset qcount")))
+    int64_t levels = p->counts[1] > 0 ? 1 : 0;
+    bool done = p->counts[1] == 0;
+    while (!done) {
+        if ((st = check_cuda(p, cudaMemsetAsync(flags, 0, sizeof(uint32_t) * SWEEP_BATCH, s), "memset flags")))
             return st;
-        bfs_expand<<<blocks(ncur), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr),
-                                                    static_cast<const uint32_t*>(p->frontier[cur].ptr), ncur, visited,
-                                                    static_cast<uint32_t*>(p->node_info.ptr),
-                                                    static_cast<uint32_t*>(p->frontier[cur ^ 1].ptr), qcount,
-                                                    uint64_t(cap), static_cast<uint32_t*>(p->status.ptr));
-        launched(p);
-        unsigned long long nn = 0;
-        if ((st = check_cuda(p, cudaMemcpyAsync(&nn, qcount, sizeof(nn), cudaMemcpyDeviceToHost, s), "qcount copy")))
+        for (int k = 0; k < SWEEP_BATCH; ++k, cur ^= 1)
+            reach_sweep<<<sweep_grid, THREADS, 0, s>>>(g, masks, buf[cur], buf[cur ^ 1], flags + k);
+        launched(p, SWEEP_BATCH);
+        uint32_t h[SWEEP_BATCH];
+        if ((st = check_cuda(p, cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s), "flags copy")))
             return st;
-        if ((st = check_cuda(p, cudaStreamSynchronize(s), "bfs sync"))) return st;
-        if (int64_t(nn) > cap) return fail(p, MSC_ERR_CUDA, "internal: BFS frontier overflow");
-        cur ^= 1;
-        ncur = int64_t(nn);
-        reached += ncur;
+        if ((st = check_cuda(p, cudaStreamSynchronize(s), "reach sync"))) return st;
+        for (int k = 0; k < SWEEP_BATCH && !done; ++k) {
+            if (!h[k]) {
+                done = true;
+            } else if (++levels > p->opts.max_iterations) {
+                return fail(p, MSC_ERR_ITER_LIMIT, "reachability exceeded the iteration cap");
+            }
+        }
     }
+    // the converged set is in buf[cur]; make it the plan's visited bitmap
+    if (cur == 1) std::swap(p->visited, p->reach_tmp);
     p->stats.n_bfs_levels = levels;
-    p->stats.n_reachable = reached;
-    return check_cuda(p, cudaGetLastError(), "bfs launch");
+    return check_cuda(p, cudaGetLastError(), "reach sweep launch");
 }
 
 msc_status run_junctions(Plan* p, cudaStream_t s) {
@@ -171,19 +335,27 @@ msc_status run_junctions(Plan* p, cudaStream_t s) {
     const int64_t nw = g.edge_words();
     if ((st = ensure(p, p->junc_bits, sizeof(uint32_t) * size_t(nw)))) return st;
     if ((st = ensure(p, p->junc_prefix, sizeof(uint32_t) * size_t(nw)))) return st;
-    mark_junctions<<<blocks(nw), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr),
-                                                  static_cast<const uint32_t*>(p->visited.ptr),
-                                                  static_cast<const uint32_t*>(p->node_info.ptr),
-                                                  static_cast<uint32_t*>(p->junc_bits.ptr));
+    if ((st = ensure(p, p->node_info, sizeof(uint32_t) * 3 * size_t(g.nverts)))) return st;
+    if ((st = ensure(p, p->reach_count, sizeof(unsigned long long)))) return st;
+    auto* cnt = static_cast<unsigned long long*>(p->reach_count.ptr);
+    if ((st = check_cuda(p, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s), "memset count"))) return st;
+    const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
+    const dim3 grid(unsigned(std::max(1, grid_for(p, nrw * 32) / 3)), 3);
+    classify_reached<<<grid, THREADS, 0, s>>>(
+        g, static_cast<const uint32_t*>(p->words.ptr), static_cast<const uint32_t*>(p->visited.ptr),
+        static_cast<const uint4*>(p->reach_masks.ptr), static_cast<const uint32_t*>(p->reach_qdown.ptr),
+        static_cast<const uint32_t*>(p->crit_bits.ptr), static_cast<uint32_t*>(p->node_info.ptr),
+        static_cast<uint32_t*>(p->junc_bits.ptr), cnt);
     launched(p);
-    if ((st = check_cuda(p, cudaGetLastError(), "mark_junctions launch"))) return st;
+    if ((st = check_cuda(p, cudaGetLastError(), "classify_reached launch"))) return st;
     EdgeSource src{};
     src.g = g;
     src.bits = static_cast<const uint32_t*>(p->junc_bits.ptr);
     src.prefix = static_cast<uint32_t*>(p->junc_prefix.ptr);
     src.status = static_cast<uint32_t*>(p->status.ptr);
-    unsigned long long tot = 0;
-    if ((st = compaction_count(p, s, src, 1, &tot))) return st;
+    unsigned long long tot = 0, reached = 0;
+    if ((st = compaction_count(p, s, src, 1, &tot, cnt, &reached))) return st;  // synchronises the stream
+    p->stats.n_reachable = int64_t(reached);
     p->n_junctions = int64_t(tot);
     p->stats.n_junctions = int64_t(tot);
     if ((st = ensure(p, p->junc_cells, sizeof(uint32_t) * size_t(tot ? tot : 1)))) return st;

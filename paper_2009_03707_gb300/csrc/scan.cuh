@@ -206,9 +206,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_emit_kernel(Src src, int64_
     }
 }
 
-// Host driver, phase 1: block sums and per-sequence totals (copied to the host; syncs).
+// Host driver, phase 1: block sums and per-sequence totals (copied to the host; syncs).  An
+// optional extra device counter is copied to *extra_host in the same round trip.
 template <class Src>
-msc_status compaction_count(Plan* p, cudaStream_t s, const Src& src, int nseq, unsigned long long* host_totals) {
+msc_status compaction_count(Plan* p, cudaStream_t s, const Src& src, int nseq, unsigned long long* host_totals,
+                            const unsigned long long* extra_dev = nullptr, unsigned long long* extra_host = nullptr) {
     const int64_t len = seq_length(p->g);
     const int bps = int((len + SCAN_CHUNK - 1) / SCAN_CHUNK);
     msc_status st;
@@ -223,6 +225,10 @@ msc_status compaction_count(Plan* p, cudaStream_t s, const Src& src, int nseq, u
     if ((st = check_cuda(p, cudaMemcpyAsync(host_totals, totals, sizeof(unsigned long long) * size_t(nseq),
                                             cudaMemcpyDeviceToHost, s),
                          "scan totals copy")))
+        return st;
+    if (extra_dev && (st = check_cuda(p, cudaMemcpyAsync(extra_host, extra_dev, sizeof(unsigned long long),
+                                                         cudaMemcpyDeviceToHost, s),
+                                      "counter copy")))
         return st;
     return check_cuda(p, cudaStreamSynchronize(s), "scan sync");
 }
