@@ -108,20 +108,4 @@ __host__ __device__ __forceinline__ uint32_t info_index(const Geom& g, uint32_t 
 }
 constexpr uint32_t INFO_BRANCH = 0xFFFFFFFEu;
 
-__host__ __device__ __forceinline__ uint32_t encode_successor(const DagTarget& t) {
-    if (t.kind == 1) return edge_handle(t.v, t.sub);
-    const uint32_t even = (t.sub & 1u) == 0 ? 0u : (t.sub & 2u) == 0 ? 1u : 2u;  // the quad's even axis
-    return 0x80000000u | (t.v << 2) | even;
-}
-
-__host__ __device__ __forceinline__ uint32_t node_info(int n, const DagTarget out[4]) {
-    if (n == 0) return INFO_DEAD;
-    if (n > 1) return INFO_BRANCH;
-    uint32_t w = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (out[i].kind) w = encode_successor(out[i]);
-    return w;
-}
-
 }  // namespace msc

@@ -42,64 +42,10 @@ struct TraceArgs {
     const uint32_t* info;  // per reachable 1-cell (info_index): dead end, branch point, or its one successor
     uint32_t* tgt;    // 4 per source: destination rank
     uint8_t* kinds;   // 4 per source: 0 none / 1 junction / 2 2-saddle (read as one word per source)
+    uint32_t* cnt[4];  // distinct destinations per row of A, B, B*, D
     int64_t max_steps;
     uint32_t* status;
 };
-
-// One thread per (source, out-edge slot): follows that simple path to its end.
-__global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
-    const int64_t tid = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (tid >= 4 * (a.n1 + a.nj)) return;
-    const int64_t u = tid >> 2;
-    const int slot = int(tid & 3);
-    const Geom& g = a.g;
-    const uint32_t id = u < a.n1 ? a.s1[u] : a.junc_cells[u - a.n1];
-    const uint32_t q1 = g.div_rx.div(id);
-    const int cx = int(id - q1 * g.rx);
-    const int cz = int(g.div_ry.div(q1));
-    const int cy = int(q1 - uint32_t(cz) * g.ry);
-    const int axis = (cx & 1) ? 0 : (cy & 1) ? 1 : 2;
-    DagTarget out[4];
-    dag_out(g, a.words, cx >> 1, cy >> 1, cz >> 1, axis, out);
-    DagTarget cur = out[0];
-#pragma unroll
-    for (int i = 1; i < 4; ++i)
-        if (i == slot) cur = out[i];
-    uint32_t rank = 0, kind = 0;
-    // follow the path with one load per node: the BFS recorded every reachable node's successor
-    if (cur.kind == 2) {
-        rank = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(cur.sub, cur.z, cur.y, cur.x >> 5), cur.x & 31);
-        kind = 2;
-    } else if (cur.kind == 1) {
-        uint32_t h = edge_handle(cur.v, cur.sub);
-        for (int64_t step = 0;; ++step) {
-            if (step > a.max_steps) {
-                atomicOr(a.status, ST_ITER);
-                break;
-            }
-            const uint32_t w = a.info[info_index(g, h)];
-            if (w == INFO_DEAD) break;  // a dead path: dropped
-            if (w == INFO_BRANCH) {     // a junction
-                const Vtx q = vtx_of(g, h >> 2);
-                const int64_t wi = edge_bitmap_word(g, q.x, q.y, q.z, int(h & 3));
-                if (!((a.junc_bits[wi] >> (q.x & 31)) & 1u)) atomicOr(a.status, ST_INTERNAL);
-                rank = bit_rank(a.junc_bits, a.junc_prefix, wi, q.x & 31);
-                kind = 1;
-                break;
-            }
-            if (w & 0x80000000u) {  // the path ends at a 2-saddle
-                const Vtx q = vtx_of(g, (w & 0x7FFFFFFFu) >> 2);
-                const int slot = 7 ^ (1 << (w & 3u));
-                rank = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(slot, q.z, q.y, q.x >> 5), q.x & 31);
-                kind = 2;
-                break;
-            }
-            h = w;
-        }
-    }
-    a.tgt[tid] = rank;
-    a.kinds[tid] = uint8_t(kind);
-}
 
 // Distinct destinations of one source among slots of kind `want`, sorted, with multiplicity.
 __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t kinds, uint32_t want, uint32_t col[4],
@@ -127,6 +73,86 @@ __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t ki
     return m;
 }
 
+// One thread per source (1-saddle or junction): its <= 4 out-edges are found once, then the
+// simple paths are followed in an interleaved loop (one independent record load per live path
+// per step), and the destinations are ranked and counted per matrix row.
+__global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
+    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (u >= a.n1 + a.nj) return;
+    const Geom& g = a.g;
+    const uint32_t id = u < a.n1 ? a.s1[u] : a.junc_cells[u - a.n1];
+    const uint32_t q1 = g.div_rx.div(id);
+    const int cx = int(id - q1 * g.rx);
+    const int cz = int(g.div_ry.div(q1));
+    const int cy = int(q1 - uint32_t(cz) * g.ry);
+    const int axis = (cx & 1) ? 0 : (cy & 1) ? 1 : 2;
+    DagTarget out[4];
+    dag_out(g, a.words, cx >> 1, cy >> 1, cz >> 1, axis, out);
+    // per path: the current 1-cell handle while live; at the end the terminal (a junction's
+    // handle, or a 2-saddle as bit 31 | owner << 2 | even axis)
+    uint32_t h[4], kind[4];
+    uint32_t live = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        kind[k] = out[k].kind;
+        if (out[k].kind == 1) {
+            h[k] = edge_handle(out[k].v, out[k].sub);
+            live |= 1u << k;
+        } else {
+            const uint32_t even = (out[k].sub & 1u) == 0 ? 0u : (out[k].sub & 2u) == 0 ? 1u : 2u;
+            h[k] = 0x80000000u | (out[k].v << 2) | even;
+        }
+    }
+    for (int64_t step = 0; live; ++step) {
+        if (step > a.max_steps) {
+            atomicOr(a.status, ST_ITER);
+            break;
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = (live >> k) & 1u ? a.info[info_index(g, h[k])] : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!((live >> k) & 1u)) continue;
+            if (w[k] == INFO_DEAD) {  // a dead path: dropped
+                kind[k] = 0;
+                live &= ~(1u << k);
+            } else if (w[k] == INFO_BRANCH) {  // ends at the junction h[k]
+                live &= ~(1u << k);
+            } else if (w[k] & 0x80000000u) {  // ends at a 2-saddle
+                kind[k] = 2;
+                h[k] = w[k];
+                live &= ~(1u << k);
+            } else {
+                h[k] = w[k];
+            }
+        }
+    }
+    uint32_t rank[4], kinds = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        rank[k] = 0;
+        if (kind[k] == 1) {
+            const Vtx q = vtx_of(g, h[k] >> 2);
+            const int64_t wi = edge_bitmap_word(g, q.x, q.y, q.z, int(h[k] & 3));
+            if (!((a.junc_bits[wi] >> (q.x & 31)) & 1u)) atomicOr(a.status, ST_INTERNAL);
+            rank[k] = bit_rank(a.junc_bits, a.junc_prefix, wi, q.x & 31);
+        } else if (kind[k] == 2) {
+            const Vtx q = vtx_of(g, (h[k] & 0x7FFFFFFFu) >> 2);
+            const int slot = 7 ^ (1 << (h[k] & 3u));
+            rank[k] = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(slot, q.z, q.y, q.x >> 5), q.x & 31);
+        }
+        kinds |= kind[k] << (8 * k);
+    }
+    reinterpret_cast<uint4*>(a.tgt)[u] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
+    reinterpret_cast<uint32_t*>(a.kinds)[u] = kinds;
+    uint32_t col[4], mult[4];
+    const bool saddle = u < a.n1;
+    const int64_t row = saddle ? u : u - a.n1;
+    a.cnt[saddle ? 0 : 1][row] = uint32_t(distinct_targets(rank, kinds, 1, col, mult));
+    a.cnt[saddle ? 3 : 2][row] = uint32_t(distinct_targets(rank, kinds, 2, col, mult));
+}
+
 // which: 0 A, 1 B, 2 B*, 3 D.  Sources 0..n1-1 are 1-saddles (rows of A and D), n1.. are
 // junctions (rows of B and B*).
 struct CsrArgs {
@@ -138,18 +164,6 @@ struct CsrArgs {
     uint32_t* col[4];
     uint32_t* mult[4];
 };
-
-__global__ void __launch_bounds__(THREADS) csr_count(CsrArgs a) {
-    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (u >= a.n1 + a.nj) return;
-    uint32_t col[4], mult[4];
-    const bool saddle = u < a.n1;
-    const int64_t row = saddle ? u : u - a.n1;
-    const int mj = distinct_targets(a.tgt + 4 * u, a.kinds[u], 1, col, mult);
-    const int m2 = distinct_targets(a.tgt + 4 * u, a.kinds[u], 2, col, mult);
-    a.cnt[saddle ? 0 : 1][row] = uint32_t(mj);
-    a.cnt[saddle ? 3 : 2][row] = uint32_t(m2);
-}
 
 __global__ void __launch_bounds__(THREADS) csr_fill(CsrArgs a) {
     const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
@@ -176,6 +190,17 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     const int64_t n1 = p->counts[1], nj = p->n_junctions, nsrc = n1 + nj;
     if ((st = ensure(p, p->trace, sizeof(uint32_t) * 4 * size_t(nsrc ? nsrc : 1)))) return st;
     if ((st = ensure(p, p->trace_kinds, sizeof(uint32_t) * size_t(nsrc ? nsrc : 1)))) return st;
+    // per-row counts and row pointers of A, B, B*, D
+    const int64_t rows[4] = {n1, nj, nj, n1};
+    size_t cnt_elems = 0, scratch_total = 0;
+    size_t scratch_off[4];
+    for (int w = 0; w < 4; ++w) {
+        cnt_elems += size_t(rows[w]);
+        scratch_off[w] = scratch_total;
+        scratch_total += (row_scan_scratch_bytes(rows[w]) + 255) / 256 * 256;
+    }
+    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * (cnt_elems ? cnt_elems : 1)))) return st;
+    if ((st = ensure(p, p->minor_scan, scratch_total ? scratch_total : 1))) return st;
     TraceArgs ta{};
     ta.g = g;
     ta.words = static_cast<const uint32_t*>(p->words.ptr);
@@ -192,22 +217,6 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     ta.kinds = static_cast<uint8_t*>(p->trace_kinds.ptr);
     ta.max_steps = p->opts.max_iterations;
     ta.status = static_cast<uint32_t*>(p->status.ptr);
-    cudaEventRecord(p->kev0, s);
-    if (nsrc) {
-        trace_kernel<<<blocks(4 * nsrc), THREADS, 0, s>>>(ta);
-        launched(p);
-    }
-    cudaEventRecord(p->kev1, s);
-    if ((st = check_cuda(p, cudaGetLastError(), "trace launch"))) return st;
-
-    // CSR of A, B, B*, D
-    const int64_t rows[4] = {n1, nj, nj, n1};
-    size_t cnt_elems = 0;
-    for (int w = 0; w < 4; ++w) cnt_elems += size_t(rows[w]);
-    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * (cnt_elems ? cnt_elems : 1)))) return st;
-    size_t scratch = 0;
-    for (int w = 0; w < 4; ++w) scratch = std::max(scratch, row_scan_scratch_bytes(rows[w]));
-    if ((st = ensure(p, p->minor_scan, scratch))) return st;
     CsrArgs ca{};
     ca.n1 = n1;
     ca.nj = nj;
@@ -215,30 +224,32 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     ca.kinds = reinterpret_cast<const uint32_t*>(ta.kinds);
     size_t off = 0;
     for (int w = 0; w < 4; ++w) {
-        ca.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
+        ca.cnt[w] = ta.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
         off += size_t(rows[w]);
         if ((st = ensure(p, p->minor_rowptr[w], sizeof(int64_t) * size_t(rows[w] + 1)))) return st;
         ca.rowptr[w] = static_cast<const int64_t*>(p->minor_rowptr[w].ptr);
         p->minor_rows[w] = rows[w];
     }
+    cudaEventRecord(p->kev0, s);
     if (nsrc) {
-        csr_count<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+        trace_kernel<<<blocks(nsrc), THREADS, 0, s>>>(ta);
         launched(p);
     }
+    cudaEventRecord(p->kev1, s);
+    if ((st = check_cuda(p, cudaGetLastError(), "trace launch"))) return st;
     int64_t nnz[4];
     for (int w = 0; w < 4; ++w) {
+        auto* scratch = reinterpret_cast<unsigned long long*>(static_cast<char*>(p->minor_scan.ptr) + scratch_off[w]);
         if ((st = check_cuda(p,
-                             row_scan(p, ca.cnt[w], rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr),
-                                      static_cast<unsigned long long*>(p->minor_scan.ptr), s),
+                             row_scan(p, ca.cnt[w], rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr), scratch, s),
                              "minor row scan")))
             return st;
         if ((st = check_cuda(p, cudaMemcpyAsync(&nnz[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr) + rows[w],
                                                 sizeof(int64_t), cudaMemcpyDeviceToHost, s),
                              "nnz copy")))
             return st;
-        // the scratch is reused by the next matrix: finish this one first
-        if ((st = check_cuda(p, cudaStreamSynchronize(s), "minor sync"))) return st;
     }
+    if ((st = check_cuda(p, cudaStreamSynchronize(s), "minor sync"))) return st;
     for (int w = 0; w < 4; ++w) {
         p->minor_nnz[w] = nnz[w];
         if ((st = ensure(p, p->minor_col[w], sizeof(uint32_t) * size_t(nnz[w] ? nnz[w] : 1)))) return st;

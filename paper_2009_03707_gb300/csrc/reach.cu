@@ -199,7 +199,13 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
     constexpr int K1 = 3 - A - B1, K2 = 3 - A - B2;  // even axes of the quads along B1, B2
     const int64_t i = r.edge<A>(0, 0);
     const uint32_t vis = visited[i];
+    const int x = r.w * 32 + lane;
+    const uint32_t v = vid32(g, x, r.y, r.z);
+    uint32_t* const rec_at = x < g.nx ? info + info_index(g, edge_handle(v, A)) : nullptr;
+    // every record of the row is written (whole sectors: no read-modify-write in L2); cells
+    // that are not reached, or are 1-saddles, get a dead-end record that nothing reads
     if (!vis) {  // warp-uniform
+        if (rec_at) *rec_at = INFO_DEAD;
         if (lane == 0) junc[i] = 0;
         return;
     }
@@ -215,10 +221,9 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
                          ~partner;
     const int n = __popc(out);
     const bool mine = ((vis & ~crit) >> lane) & 1u;
+    uint32_t rec = INFO_DEAD;
     if (mine) {
-        const int x = r.w * 32 + lane;
-        const uint32_t v = vid32(g, x, r.y, r.z);
-        uint32_t rec = n == 0 ? INFO_DEAD : INFO_BRANCH;
+        rec = n == 0 ? INFO_DEAD : INFO_BRANCH;
         if (n == 1) {
             const int sel = __ffs(out) - 1;
             const int b = sel < 2 ? B1 : B2;
@@ -240,8 +245,8 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
                 rec = edge_handle(ov, kk == A ? b : A);
             }
         }
-        info[info_index(g, edge_handle(v, A))] = rec;
     }
+    if (rec_at) *rec_at = rec;
     const uint32_t jw = __ballot_sync(0xFFFFFFFFu, mine && n > 1);
     if (lane == 0) junc[i] = jw;
 }
