@@ -13,8 +13,8 @@
 //
 // Rows are latency-bound chains of dependent gathers, so the work goes to the smallest worker
 // that can hold it, to keep as many rows in flight as possible:
-//   tier 0  one thread per row, frontier (<= 8) and D* row (<= 16) in shared memory, 32-bit
-//           counts;
+//   tier 0  a row per lane, frontier (<= 8) and D* row (<= 16) hash tables in shared memory,
+//           32-bit counts; each frontier step is spread over the warp item by item;
 //   tier 1  one warp per row, 256-slot hash tables in shared memory;
 //   tier 2+ one CTA per row, hash tables in global memory, grown until the row fits.
 // A row that overflows its worker is deferred, intact, to the next tier.  Finished rows are
@@ -27,9 +27,13 @@ namespace msc {
 namespace {
 
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
-constexpr int T0_THREADS = 256;
-constexpr int T0_F = 8;   // frontier slots per thread
-constexpr int T0_D = 16;  // D* row slots per thread
+constexpr int T0_WARPS = 8;
+constexpr int T0_THREADS = T0_WARPS * 32;
+constexpr int T0_F = 8;    // frontier table slots per row (power of two)
+constexpr int T0_LF = 3;   // log2(T0_F)
+constexpr int T0_D = 16;   // D* table slots per row (power of two)
+constexpr int T0_LD = 4;   // log2(T0_D)
+constexpr int T0_OUT_CHUNK = 1024;  // staging slots a warp takes at a time
 constexpr int T1_WARPS = 4;
 constexpr int T1_HASH = 256;  // slots per table (power of two)
 constexpr int T1_LIST = T1_HASH / 2;
@@ -65,35 +69,55 @@ __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
 }
 
 // ---------------------------------------------------------------------------------------
-// tier 0: one thread per row, small maps in shared memory
+// tier 0: a row per lane, frontier steps item-parallel across the warp
 // ---------------------------------------------------------------------------------------
-// Each thread owns columns of [slot][thread] arrays (conflict-free across a warp): two
-// frontier buffers of T0_F entries and a D* row of T0_D entries, keys and 32-bit counts.  Loops
-// run over the entries actually present.  A row that needs more slots, or whose counts outgrow
-// 32 bits, is deferred intact to the uint64 warp tier.
-struct T0Shared {
-    uint32_t fk[2][T0_F][T0_THREADS];
-    uint32_t fv[2][T0_F][T0_THREADS];
-    uint32_t dk[T0_D][T0_THREADS];
-    uint32_t dv[T0_D][T0_THREADS];
+// Each lane owns a row and its tables in shared memory, stored [slot][lane] per warp: two
+// frontier hash tables (current and next, T0_F slots) and the D* row (T0_D slots), keys and
+// 32-bit counts.  A frontier step is run by the whole warp on the list of all its rows'
+// frontier entries (compacted with one ballot per slot): lane i takes entry i, reads the
+// junction's trace and adds each traced path to the owning row's next frontier or D* table
+// with shared-memory atomics.  So a lane's work does not depend on its own row's size, and
+// every per-row loop is a fixed, unrolled one.  A row whose table fills up, or whose counts
+// outgrow 32 bits, is deferred intact to the uint64 warp tier.
+struct T0Warp {
+    uint32_t fk[2][T0_F][32];
+    uint32_t fv[2][T0_F][32];
+    uint32_t dk[T0_D][32];
+    uint32_t dv[T0_D][32];
+    unsigned long long base[32];  // staging offset of each finishing row
+    uint16_t items[32 * T0_D];    // this round's work list: slot << 5 | row
 };
 
-// Adds (key, val) to the column map K/V of n entries; false if full or a count would wrap.
-template <int N>
-__device__ __forceinline__ bool col_add(uint32_t (*K)[T0_THREADS], uint32_t (*V)[T0_THREADS], int& n, int t,
-                                        uint32_t key, uint32_t val) {
-    for (int i = 0; i < n; ++i)
-        if (K[i][t] == key) {
-            const uint32_t v = V[i][t] + val;
-            if (v < val) return false;
-            V[i][t] = v;
-            return true;
+// Adds val to key's entry in row r's table (K, V: [slot][32] arrays of 2^lg slots); false if
+// the table is full or the count wraps.  Lanes may add to the same row at once: keys are
+// claimed with atomicCAS.  Either of a row's tables goes through this one code path.
+__device__ __forceinline__ bool t0_add_rt(uint32_t* K, uint32_t* V, int lg, int r, uint32_t key, uint32_t val) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = (key * 2654435761u) >> (32 - lg);
+#pragma unroll 1
+    for (uint32_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+        uint32_t k = *reinterpret_cast<volatile uint32_t*>(&K[h * 32 + r]);
+        if (k == EMPTY) {
+            k = atomicCAS(&K[h * 32 + r], EMPTY, key);
+            if (k == EMPTY) k = key;
         }
-    if (n >= N) return false;
-    K[n][t] = key;
-    V[n][t] = val;
-    ++n;
-    return true;
+        if (k == key) {
+            const uint32_t old = atomicAdd(&V[h * 32 + r], val);
+            return old + val >= old;
+        }
+    }
+    return false;
+}
+
+// Exclusive prefix of n over the warp; *total gets the sum.
+__device__ __forceinline__ unsigned warp_prefix(unsigned n, int lane, unsigned* total) {
+    unsigned incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    *total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    return incl - n;
 }
 
 __device__ __forceinline__ u64 warp_sum(u64 v) {
@@ -119,110 +143,206 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
     return base + (incl - n);
 }
 
-// Persistent: each round, every lane advances its own row by one frontier step; lanes whose
-// row is finished (or deferred) take new rows with one warp-wide atomic, so lanes do not idle
-// while the longest row of their warp runs to the end.  Finished rows are appended with one
-// warp-aggregated atomic per round.
+// Persistent: lanes without a row take new ones (one atomic per warp); every round advances all
+// of the warp's rows by one frontier step, and finished rows are written out item-parallel,
+// each entry at its rank within the row (rows come out sorted by column).
 __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a, u64* next_row) {
     extern __shared__ __align__(16) unsigned char t0_raw[];
-    T0Shared& sh = *reinterpret_cast<T0Shared*>(t0_raw);
-    const int t = threadIdx.x, lane = t & 31;
+    T0Warp& sh = reinterpret_cast<T0Warp*>(t0_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const uint32_t lane_bit = 1u << lane;
+#pragma unroll
+    for (int j = 0; j < T0_F; ++j) {
+        sh.fk[0][j][lane] = sh.fk[1][j][lane] = EMPTY;
+        sh.fv[0][j][lane] = sh.fv[1][j][lane] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < T0_D; ++j) {
+        sh.dk[j][lane] = EMPTY;
+        sh.dv[j][lane] = 0;
+    }
+    __syncwarp();
     int64_t s = -1;  // the lane's current row (-1: none)
-    int cur = 0, nf = 0, nd = 0;
+    int c = 0;       // which frontier table is current (warp-uniform)
     u64 iter = 0, entries = 0, it_max = 0, en_sum = 0, mx_all = 0;
+    // warp-private pools of row indices and staging slots, refilled in chunks so that the
+    // shared counters see one atomic per chunk rather than one per round
+    const u64 nwarps = u64(gridDim.x) * T0_WARPS;
+    u64 pool_next = 0, pool_end = 0, seen = 0;
+    u64 out_next = 0, out_end = 0;
     bool exhausted = false;
     while (true) {
-        // lanes without a row take the next ones (one atomic for the warp)
+        // lanes without a row take the next ones; a new row starts from A[s,:] and D[s,:]
         const unsigned want = __ballot_sync(0xFFFFFFFFu, s < 0 && !exhausted);
         if (want) {
-            u64 base = 0;
-            if (lane == __ffs(want) - 1) base = atomicAdd(next_row, (u64)__popc(want));
-            base = __shfl_sync(0xFFFFFFFFu, base, __ffs(want) - 1);
-            if (s < 0 && !exhausted) {
-                const u64 mine = base + __popc(want & ((1u << lane) - 1u));
-                if (mine < (u64)a.nrows) {
-                    s = row_of(a, int64_t(mine));
-                    cur = 0;
-                    nf = nd = 0;
-                    iter = entries = 0;
-                    bool fit = true;
-                    const uint32_t kinds = a.kinds[s];
-                    const uint4 t4 = trace_of(a, s);
-                    const uint32_t tg[4] = {t4.x, t4.y, t4.z, t4.w};
+            const u64 k = u64(__popc(want));
+            const u64 rem = pool_end - pool_next;
+            u64 fresh = pool_end;  // start of a newly taken chunk (if any)
+            if (rem < k) {         // guided chunk size: large while much work is left
+                const u64 left = u64(a.nrows) > seen ? u64(a.nrows) - seen : 0;
+                const u64 ch = max(u64(32), min(u64(1024), left / (4 * nwarps)));
+                if (lane == 0) fresh = atomicAdd(next_row, ch);
+                fresh = __shfl_sync(0xFFFFFFFFu, fresh, 0);
+                seen = fresh + ch;
+                const u64 q = u64(__popc(want & (lane_bit - 1u)));
+                const u64 mine = q < rem ? pool_next + q : fresh + (q - rem);
+                pool_next = fresh + (k - rem);
+                pool_end = fresh + ch;
+                if (want & lane_bit) {
+                    if (mine < (u64)a.nrows) s = row_of(a, int64_t(mine));
+                    else exhausted = true;
+                }
+            } else {
+                const u64 mine = pool_next + u64(__popc(want & (lane_bit - 1u)));
+                pool_next += k;
+                if (want & lane_bit) {
+                    if (mine < (u64)a.nrows) s = row_of(a, int64_t(mine));
+                    else exhausted = true;
+                }
+            }
+            if ((want & lane_bit) && s >= 0) {
+                iter = entries = 0;
+                const uint32_t kinds = a.kinds[s];
+                const uint4 t4 = trace_of(a, s);
+                const uint32_t tg[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t kind = trace_kind(kinds, k);
-                        if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[0], sh.fv[0], nf, t, tg[k], 1);
-                        if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tg[k], 1);
-                    }
-                    if (!fit) nf = -1;  // defer
-                } else {
-                    exhausted = true;
+                for (int k2 = 0; k2 < 4; ++k2) {  // at most 4 entries: these tables cannot fill
+                    const uint32_t kind = trace_kind(kinds, k2);
+                    if (!kind) continue;
+                    const bool junction = kind == 1;
+                    t0_add_rt(junction ? &sh.fk[c][0][0] : &sh.dk[0][0], junction ? &sh.fv[c][0][0] : &sh.dv[0][0],
+                              junction ? T0_LF : T0_LD, lane, tg[k2], 1);
                 }
             }
         }
         if (!__any_sync(0xFFFFFFFFu, s >= 0)) break;
-        // one frontier step of the lane's row
-        if (s >= 0 && nf > 0) {
-            if (int64_t(++iter) > a.max_iter) {
-                atomicOr(a.status, ST_ITER);
-                nf = 0;
-            } else {
-                entries += nf;
-                int ng = 0;
-                bool fit = true;
-                for (int e = 0; e < nf && fit; ++e) {
-                    const int64_t j = a.n1 + int64_t(sh.fk[cur][e][t]);
-                    const uint32_t c = sh.fv[cur][e][t];
-                    const uint32_t kj = a.kinds[j];
-                    const uint4 q = trace_of(a, j);
-                    const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
+        __syncwarp();
+        // one frontier step of every row: the list of (slot, row) frontier entries
+        bool expand = false;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t kind = trace_kind(kj, k);
-                        if (kind == 1) fit = fit && col_add<T0_F>(sh.fk[cur ^ 1], sh.fv[cur ^ 1], ng, t, tq[k], c);
-                        if (kind == 2) fit = fit && col_add<T0_D>(sh.dk, sh.dv, nd, t, tq[k], c);
-                    }
-                }
-                cur ^= 1;
-                nf = fit ? ng : -1;
-            }
+        for (int j = 0; j < T0_F; ++j) expand |= s >= 0 && sh.fk[c][j][lane] != EMPTY;
+        if (expand && int64_t(++iter) > a.max_iter) {
+            atomicOr(a.status, ST_ITER);  // the row is cut short; the result is void anyway
+            expand = false;
         }
-        // rows that finished this round (frontier empty) or must be deferred (a map overflowed)
-        const bool done = s >= 0 && nf == 0;
-        const bool defer = s >= 0 && nf < 0;
-        if (done)
-            for (int e = 1; e < nd; ++e) {  // insertion sort of the row by column
-                const uint32_t k = sh.dk[e][t], v = sh.dv[e][t];
-                int f = e;
-                while (f > 0 && sh.dk[f - 1][t] > k) {
-                    sh.dk[f][t] = sh.dk[f - 1][t];
-                    sh.dv[f][t] = sh.dv[f - 1][t];
-                    --f;
+        // the warp's list of (slot, row) frontier entries, then one entry per lane
+        unsigned fm = 0;
+#pragma unroll
+        for (int j = 0; j < T0_F; ++j) fm |= unsigned(expand && sh.fk[c][j][lane] != EMPTY) << j;
+        entries += __popc(fm);
+        unsigned total = 0;
+        unsigned at = warp_prefix(unsigned(__popc(fm)), lane, &total);
+#pragma unroll
+        for (int j = 0; j < T0_F; ++j)
+            if ((fm >> j) & 1u) sh.items[at++] = uint16_t((j << 5) | lane);
+        __syncwarp();
+        uint32_t bad = 0;
+        uint32_t* const nk = &sh.fk[c ^ 1][0][0];
+        uint32_t* const nv = &sh.fv[c ^ 1][0][0];
+        for (unsigned i = lane; i < total; i += 32) {
+            const int it = sh.items[i];
+            const int j = it >> 5, r = it & 31;
+            const uint32_t key = sh.fk[c][j][r];
+            const uint32_t cnt = sh.fv[c][j][r];
+            const int64_t src = a.n1 + int64_t(key);
+            const uint32_t kj = a.kinds[src];
+            const uint4 q = trace_of(a, src);
+            const uint32_t tq[4] = {q.x, q.y, q.z, q.w};
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t kind = trace_kind(kj, k);
+                if (!kind) continue;
+                const bool junction = kind == 1;
+                ok &= t0_add_rt(junction ? nk : &sh.dk[0][0], junction ? nv : &sh.dv[0][0], junction ? T0_LF : T0_LD, r,
+                                tq[k], cnt);
+            }
+            if (!ok) bad |= 1u << r;
+        }
+        bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+        __syncwarp();
+        // the current tables are spent: clear this lane's and swap
+#pragma unroll
+        for (int j = 0; j < T0_F; ++j) {
+            sh.fk[c][j][lane] = EMPTY;
+            sh.fv[c][j][lane] = 0;
+        }
+        c ^= 1;
+        bool more = false;
+#pragma unroll
+        for (int j = 0; j < T0_F; ++j) more |= sh.fk[c][j][lane] != EMPTY;
+        const bool defer = s >= 0 && (bad & lane_bit);
+        const bool done = s >= 0 && !defer && !more;
+        // finished rows: entries of the D* tables, item-parallel, placed by rank within the row
+        unsigned dm = 0;
+#pragma unroll
+        for (int j = 0; j < T0_D; ++j) dm |= unsigned(done && sh.dk[j][lane] != EMPTY) << j;
+        const unsigned mine_n = unsigned(__popc(dm));
+        unsigned nout = 0;
+        const unsigned off = warp_prefix(mine_n, lane, &nout);
+        if (nout) {
+            // staging slots from the warp's chunk (a new chunk when this round's rows do not fit)
+            if (u64(nout) > out_end - out_next) {
+                const u64 ch = max(u64(nout), u64(T0_OUT_CHUNK));
+                u64 b = 0;
+                if (lane == 0) b = atomicAdd(a.out_cursor, ch);
+                out_next = __shfl_sync(0xFFFFFFFFu, b, 0);
+                out_end = out_next + ch;
+            }
+            const u64 base = out_next + off;
+            out_next += u64(nout);
+            sh.base[lane] = base;
+            unsigned o = off;
+#pragma unroll
+            for (int j = 0; j < T0_D; ++j)
+                if ((dm >> j) & 1u) sh.items[o++] = uint16_t((j << 5) | lane);
+            if (done) {
+                a.row_start[s] = int64_t(base);
+                a.row_len[s] = mine_n;
+            }
+            __syncwarp();
+            for (unsigned i = lane; i < nout; i += 32) {
+                const int it = sh.items[i];
+                const int j = it >> 5, r = it & 31;
+                const uint32_t key = sh.dk[j][r];
+                const uint32_t val = sh.dv[j][r];
+                int rank = 0;
+#pragma unroll
+                for (int jj = 0; jj < T0_D; ++jj) rank += sh.dk[jj][r] < key;  // EMPTY sorts last
+                const u64 dst = sh.base[r] + u64(rank);
+                if (dst < a.out_cap) {
+                    a.out_col[dst] = key;
+                    a.out_cnt[dst] = val;
+                } else {
+                    atomicOr(a.status, ST_CAPACITY);
                 }
-                sh.dk[f][t] = k;
-                sh.dv[f][t] = v;
+                mx_all = max(mx_all, (u64)val);
             }
-        const unsigned n_out = done ? unsigned(nd) : 0u;
-        const u64 base = warp_append(a.out_cursor, n_out);
-        for (unsigned e = 0; e < n_out; ++e) {
-            if (base + e < a.out_cap) {
-                a.out_col[base + e] = sh.dk[e][t];
-                a.out_cnt[base + e] = sh.dv[e][t];
-            } else {
-                atomicOr(a.status, ST_CAPACITY);
-            }
-            mx_all = max(mx_all, (u64)sh.dv[e][t]);
+        } else if (done) {
+            a.row_start[s] = 0;
+            a.row_len[s] = 0;
         }
         if (done) {
-            a.row_start[s] = int64_t(base);
-            a.row_len[s] = n_out;
             it_max = max(it_max, iter);
             en_sum += entries;
         }
+        __syncwarp();
         const u64 dpos = warp_append(a.deferred_count, defer ? 1u : 0u);
         if (defer) a.deferred[dpos] = uint32_t(s);
-        if (done || defer) s = -1;
+        if (done || defer) {  // leave this lane's tables clean for its next row
+#pragma unroll
+            for (int j = 0; j < T0_D; ++j) {
+                sh.dk[j][lane] = EMPTY;
+                sh.dv[j][lane] = 0;
+            }
+#pragma unroll
+            for (int j = 0; j < T0_F; ++j) {
+                sh.fk[c][j][lane] = EMPTY;
+                sh.fv[c][j][lane] = 0;
+            }
+            s = -1;
+        }
+        __syncwarp();
     }
     mx_all = warp_max(mx_all);
     it_max = warp_max(it_max);
@@ -510,8 +630,19 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->minor_scan, row_scan_scratch_bytes(n1)))) return st;
     auto* ctr = static_cast<u64*>(p->pc_counters.ptr);
     const int first_tier = std::max(0, std::min(2, int(p->opts.path_count_tier)));
-    // staging capacity: grown and the stage re-run if a run overflows it
-    uint64_t cap = uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1 + 1024));
+    // tier-0 grid: persistent, as many CTAs as fit
+    const size_t t0_smem = sizeof(T0Warp) * T0_WARPS;
+    if ((st = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
+                         "cudaFuncSetAttribute(rows_thread)")))
+        return st;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_thread, T0_THREADS, t0_smem);
+    const int t0_grid = int(std::max<int64_t>(
+        1, std::min<int64_t>((n1 + T0_THREADS - 1) / T0_THREADS, int64_t(std::max(1, per_sm)) * p->num_sms)));
+    // staging capacity, including what tier-0 warps may leave unused at the end of their chunks:
+    // grown and the stage re-run if a run overflows it
+    const uint64_t slack = uint64_t(t0_grid) * T0_WARPS * (T0_OUT_CHUNK + 32 * T0_D);
+    uint64_t cap = uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1 + 1024)) + slack;
     for (int attempt = 0; attempt < 8; ++attempt) {
         if ((st = ensure(p, p->pc_col, sizeof(uint32_t) * cap))) return st;
         if ((st = ensure(p, p->pc_cnt, sizeof(u64) * cap))) return st;
@@ -544,17 +675,9 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             msc_status e;
             if ((e = check_cuda(p, cudaMemsetAsync(a.deferred_count, 0, sizeof(u64), s), "memset"))) return e;
             if (tier == 0) {
-                if ((e = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                            int(sizeof(T0Shared))),
-                                    "cudaFuncSetAttribute(rows_thread)")))
-                    return e;
                 if ((e = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return e;
-                int per_sm = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_thread, T0_THREADS, sizeof(T0Shared));
-                const int64_t want = (nrows + T0_THREADS - 1) / T0_THREADS;
-                const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(1, per_sm)) * p->num_sms)));
                 cudaEventRecord(p->kev0, s);
-                rows_thread<<<grid, T0_THREADS, sizeof(T0Shared), s>>>(a, ctr + C_NEXT);
+                rows_thread<<<t0_grid, T0_THREADS, t0_smem, s>>>(a, ctr + C_NEXT);
                 cudaEventRecord(p->kev1, s);
                 launched(p);
             } else if (tier == 1) {
@@ -598,8 +721,19 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             if (nrows > 0 && lg >= lg_max) return fail(p, MSC_ERR_CUDA, "internal: a path-count row does not fit");
             lg = std::min(lg + 4, lg_max);
         }
+        // row pointers of D* (the scan also gives nnz), then the counters, in one round trip
+        if ((st = check_cuda(p,
+                             row_scan(p, a.row_len, n1, static_cast<int64_t*>(p->dstar_rowptr.ptr),
+                                      static_cast<u64*>(p->minor_scan.ptr), s),
+                             "D* row scan")))
+            return st;
         u64 h[8];
+        int64_t nnz = 0;
         if ((st = check_cuda(p, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s), "counter copy")))
+            return st;
+        if ((st = check_cuda(p, cudaMemcpyAsync(&nnz, static_cast<int64_t*>(p->dstar_rowptr.ptr) + n1, sizeof(nnz),
+                                                cudaMemcpyDeviceToHost, s),
+                             "nnz copy")))
             return st;
         if ((st = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return st;
         if (h[C_CURSOR] > cap) {  // staging overflow: grow and redo the stage
@@ -610,7 +744,6 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             cap = h[C_CURSOR] + h[C_CURSOR] / 4 + 1024;
             continue;
         }
-        const int64_t nnz = int64_t(h[C_CURSOR]);
         p->dstar_nnz = nnz;
         p->stats.nnz_Dstar = nnz;
         p->stats.max_path_count = h[C_MAX];
@@ -618,11 +751,6 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         p->stats.n_frontier_entries = int64_t(h[C_ENTRIES]);
         if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
         if ((st = ensure(p, p->dstar_count, sizeof(u64) * size_t(nnz ? nnz : 1)))) return st;
-        if ((st = check_cuda(p,
-                             row_scan(p, a.row_len, n1, static_cast<int64_t*>(p->dstar_rowptr.ptr),
-                                      static_cast<u64*>(p->minor_scan.ptr), s),
-                             "D* row scan")))
-            return st;
         if (n1) {
             gather_rows<<<int((n1 + 255) / 256), 256, 0, s>>>(
                 n1, a.row_start, static_cast<const int64_t*>(p->dstar_rowptr.ptr), a.out_col, a.out_cnt,
