@@ -302,13 +302,13 @@ def run_gpu(args):
             "rows_thread": 17.0 * (counts[1] + last["n_frontier_entries"]) + 12.0 * last["nnz_Dstar"]}
     units = {"gradient_kernel": nvox, "rows_thread": counts[1] + last["n_frontier_entries"]}
     dom = max(km, key=km.get)
-    achieved = algo[dom] / (km[dom] / 1e3) / 1e9
+    achieved = algo[dom] / (km[dom] / 1e3) / 1e9 if km[dom] > 0 else None
     rec = _traffic_record(dom)
     traffic = None
     if rec and rec.get("workload") == args.workload:
         traffic = rec["bytes_per_unit"] * units[dom]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "frac": achieved / peak if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel_ms": km[dom], "algorithmic_bytes": algo[dom]}
 
     def med(key):

@@ -53,17 +53,22 @@ typedef enum msc_status {
 
 typedef struct msc_plan_s* msc_plan_t;
 
+/* msc_opts.flags: run every msc_compute with host synchronisation between the stages, never as a
+ * replayed CUDA graph (the results are identical; tests use it to compare the two paths). */
+#define MSC_FLAG_NO_GRAPH 1
+
 /* Plan options (all fields may be zero for defaults). */
 typedef struct msc_opts {
     int64_t max_iterations;  /* cap on every iterative stage; 0 = 1<<20 */
-    int32_t flags;           /* reserved, must be 0 */
+    int32_t flags;           /* MSC_FLAG_* bits; other bits must be 0 */
     int32_t path_count_tier; /* first tier of the row-wise path count: 0 = per-thread registers
                                 (default), 1 = per-warp shared-memory tables, 2 = per-CTA global
                                 tables.  Results are identical; tests use it to cover every tier. */
 } msc_opts;
 
 /* Per-stage diagnostics (Sec. 4.2 "performance analysis" quantities). Times are the
- * device time of the last run of each stage, from CUDA events on the plan's stream. */
+ * device time of the last run of each stage, from CUDA events recorded on the stream (inside
+ * the graph when msc_compute replays one); they are read by msc_get_stats. */
 typedef struct msc_stats {
     int64_t counts[4];        /* critical cells by index: min, 1-saddle, 2-saddle, max */
     int64_t n_reachable;      /* 1-cells reachable from 1-saddles (1-saddles included) */
@@ -76,7 +81,7 @@ typedef struct msc_stats {
     int64_t peak_device_bytes;
     int64_t n_launches;       /* kernels this plan launched since the last msc_gradient */
     float ms_gradient, ms_critical, ms_extremum, ms_reachability, ms_minor, ms_path_count;
-    float ms_rows_kernel;      /* the row-wise product kernel alone (tier 1), CUDA events */
+    float ms_rows_kernel;      /* the row-wise product kernel alone (tier 0), CUDA events */
     float ms_trace_kernel;     /* the simple-path tracing kernel alone, CUDA events */
     int64_t n_frontier_entries; /* sum over 1-saddles and iterations of the frontier sizes */
 } msc_stats;
@@ -162,7 +167,17 @@ msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, c
                            const uint32_t** d_col, const uint64_t** d_count);
 
 /* Runs every stage (a1..a6) on `stream` for one field; equivalent to the calls above in
- * order.  Results are read afterwards with the getters (they do no further work). */
+ * order.  Results are read afterwards with the getters (they do no further work, except that
+ * msc_minor builds the CSR of A, B, B*, D on its first call for a field).
+ * The first call on a plan runs the stages with host synchronisation between them and so learns
+ * the sizes of the field's products.  Later calls replay the whole pipeline as one CUDA graph,
+ * captured on a plan-private stream with buffers sized from those sizes plus headroom; the
+ * iterative stages are conditional WHILE nodes, so a replay needs no host round trip until it
+ * ends.  The call returns after one synchronisation of `stream` at the end of the pass.  If a
+ * field needs more room than the graph was captured with, the kernels say so, the pass is run
+ * again synchronised (same results), and the next call captures a larger graph.  d_field must
+ * stay valid while the call runs; a new pointer is captured anew.  MSC_FLAG_NO_GRAPH disables
+ * the replay. */
 msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t stream);
 
 msc_status msc_get_stats(msc_plan_t plan, msc_stats* out);

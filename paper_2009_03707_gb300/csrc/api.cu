@@ -50,21 +50,102 @@ msc_status ensure(Plan* p, DeviceBuffer& b, size_t bytes) {
     return MSC_OK;
 }
 
-msc_status check_status_word(Plan* p, cudaStream_t s) {
-    uint32_t word = 0;
-    msc_status st;
-    if ((st = check_cuda(p, cudaMemcpyAsync(&word, p->status.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
-                         "status copy")))
-        return st;
-    if ((st = check_cuda(p, cudaStreamSynchronize(s), "stream sync"))) return st;
-    if (word == 0) return MSC_OK;
-    if ((st = check_cuda(p, cudaMemsetAsync(p->status.ptr, 0, sizeof(uint32_t), s), "status clear"))) return st;
+msc_status status_error(Plan* p, uint32_t word) {
     if (word & ST_NAN) return fail(p, MSC_ERR_NAN, "the field holds a NaN");
     if (word & ST_OVERFLOW) return fail(p, MSC_ERR_OVERFLOW, "a saddle-saddle path count exceeds 2^64-1");
     if (word & ST_ITER) return fail(p, MSC_ERR_ITER_LIMIT, "an iterative stage reached its iteration cap");
     if (word & ST_TIMEOUT) return fail(p, MSC_ERR_TIMEOUT, "a bounded device wait gave up");
-    if (word & ST_CAPACITY) return fail(p, MSC_ERR_CUDA, "internal: a device buffer was too small");
+    if (word & (ST_CAPACITY | ST_RETRY)) return fail(p, MSC_ERR_CUDA, "internal: a device buffer was too small");
     return fail(p, MSC_ERR_CUDA, "internal: a device-side bounds check failed");
+}
+
+msc_status check_status_word(Plan* p, cudaStream_t s) {
+    uint32_t word = 0;
+    msc_status st;
+    if ((st = check_cuda(p, cudaMemcpyAsync(&word, p->status_word(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
+                         "status copy")))
+        return st;
+    if ((st = check_cuda(p, cudaStreamSynchronize(s), "stream sync"))) return st;
+    if (word == 0) return MSC_OK;
+    if ((st = check_cuda(p, cudaMemsetAsync(p->status_word(), 0, sizeof(uint32_t), s), "status clear"))) return st;
+    return status_error(p, word);
+}
+
+msc_status read_summary(Plan* p, cudaStream_t s) {
+    if (p->capturing) return fail(p, MSC_ERR_CUDA, "internal: host read during graph capture");
+    msc_status st;
+    if ((st = check_cuda(p, cudaMemcpyAsync(p->hsum, p->dsum(), sizeof(Summary), cudaMemcpyDeviceToHost, s),
+                         "summary copy")))
+        return st;
+    return check_cuda(p, cudaStreamSynchronize(s), "stream sync");
+}
+
+__global__ void loop_arm(cudaGraphConditionalHandle h) { cudaGraphSetConditional(h, 1u); }
+
+int grid_cap(const Plan* p, int64_t threads, int block, int per_sm) {
+    const int64_t want = (threads + block - 1) / block;
+    const int64_t cap = int64_t(p->num_sms > 0 ? p->num_sms : 148) * per_sm;
+    return int(std::max<int64_t>(1, std::min(want, cap)));
+}
+
+msc_status run_loop(Plan* p, cudaStream_t s, int which, int body_launches,
+                    void (*body)(Plan*, cudaStream_t, cudaGraphConditionalHandle, void*), void* ctx) {
+    msc_status st;
+    if (!p->capturing) {
+        for (;;) {
+            body(p, s, 0, ctx);
+            launched(p, body_launches);
+            uint32_t more = 0;
+            if ((st = check_cuda(p, cudaGetLastError(), "loop launch"))) return st;
+            if ((st = check_cuda(p, cudaMemcpyAsync(&more, &p->dsum()->loop_flag[3], sizeof(more),
+                                                    cudaMemcpyDeviceToHost, s),
+                                 "loop flag copy")))
+                return st;
+            if ((st = check_cuda(p, cudaStreamSynchronize(s), "loop sync"))) return st;
+            if (!more) return MSC_OK;  // the decision kernel also stops at the iteration cap
+        }
+    }
+    // capturing: a conditional WHILE node after the work captured so far, its body captured on
+    // the plan's second private stream.  The condition defaults to 0 at every launch and a
+    // one-thread kernel just before the node sets it to 1: should the device-side setting ever
+    // not take effect, the loop runs zero times (a wrong result the checks see), never forever.
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    if ((st = check_cuda(p, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edata, &nd), "capture info")))
+        return st;
+    cudaGraphConditionalHandle h;
+    if ((st = check_cuda(p, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault), "conditional handle")))
+        return st;
+    loop_arm<<<1, 1, 0, s>>>(h);
+    launched(p);
+    if ((st = check_cuda(p, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edata, &nd), "capture info")))
+        return st;
+    std::vector<cudaGraphNode_t> dep(deps, deps + nd);
+    std::vector<cudaGraphEdgeData> edge;
+    if (edata) edge.assign(edata, edata + nd);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((st = check_cuda(p, cudaGraphAddNode(&node, g, dep.data(), edata ? edge.data() : nullptr, nd, &np),
+                         "conditional node")))
+        return st;
+    cudaGraph_t body_graph = np.conditional.phGraph_out[0];
+    if ((st = check_cuda(p, cudaStreamBeginCaptureToGraph(p->body_stream, body_graph, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeRelaxed),
+                         "body capture")))
+        return st;
+    body(p, p->body_stream, h, ctx);
+    const cudaError_t e = cudaStreamEndCapture(p->body_stream, &body_graph);
+    if ((st = check_cuda(p, e, "body capture end"))) return st;
+    p->loop_body_launches[which] = body_launches;
+    return check_cuda(p, cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+                      "capture dependencies");
 }
 
 namespace {
@@ -86,22 +167,20 @@ void read_fault(Plan* p) {
 // Raises a status bit on the device exactly as a kernel would (for injected faults).
 void raise_status(Plan* p, uint32_t bit, cudaStream_t s) {
     uint32_t word = bit;
-    cudaMemcpyAsync(p->status.ptr, &word, sizeof(word), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->status_word(), &word, sizeof(word), cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
 }
 
-struct StageTimer {
-    Plan* p;
-    cudaStream_t s;
-    float* out;
-    StageTimer(Plan* plan, cudaStream_t stream, float* dst) : p(plan), s(stream), out(dst) {
-        cudaEventRecord(p->ev0, s);
-    }
-    void stop() {
-        cudaEventRecord(p->ev1, s);
-        if (cudaEventSynchronize(p->ev1) == cudaSuccess) cudaEventElapsedTime(out, p->ev0, p->ev1);
-    }
-};
+// Stage k's device time is read from events recorded at its start and end, when the host next
+// waits (msc_get_stats); recording costs nothing on the stream, and works inside a graph.
+void stage_start(Plan* p, int k, cudaStream_t s) {
+    record_event(p, p->stage_ev[2 * k], s);
+    p->stage_recorded &= ~(1u << k);
+}
+void stage_end(Plan* p, int k, cudaStream_t s) {
+    record_event(p, p->stage_ev[2 * k + 1], s);
+    p->stage_recorded |= 1u << k;
+}
 
 msc_status bind_device(Plan* p) {
     int cur = -1;
@@ -112,7 +191,38 @@ msc_status bind_device(Plan* p) {
 
 void invalidate(Plan* p) {
     p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = false;
-    p->have_junctions = p->have_minor = p->have_dstar = false;
+    p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = false;
+}
+
+// Host mirrors and statistics from the summary last copied to p->hsum.
+void absorb_summary(Plan* p) {
+    const Summary& h = *p->hsum;
+    for (int k = 0; k < 4; ++k) p->stats.counts[k] = p->counts[k] = int64_t(h.counts[k]);
+    p->stats.n_junctions = p->n_junctions = int64_t(h.n_junctions);
+    p->stats.n_reachable = int64_t(h.reached);
+    p->stats.n_bfs_levels = int64_t(h.levels);
+    p->stats.n_pointer_jumps = int64_t(h.jump_rounds);
+    p->stats.nnz_A = int64_t(h.minor_nnz[0]);
+    p->stats.nnz_B = int64_t(h.minor_nnz[1]);
+    p->stats.nnz_Bstar = int64_t(h.minor_nnz[2]);
+    p->stats.nnz_D = int64_t(h.minor_nnz[3]);
+    p->stats.nnz_Dstar = p->dstar_nnz = int64_t(h.dstar_nnz);
+    p->stats.max_path_count = h.pc[PC_MAX];
+    p->stats.n_iter = int64_t(h.pc[PC_ITER]);
+    p->stats.n_frontier_entries = int64_t(h.pc[PC_ENTRIES]);
+}
+
+// End of a stage run with host synchronisation: the summary, then its status word.
+msc_status finish_stage(Plan* p, cudaStream_t s) {
+    msc_status st;
+    if ((st = read_summary(p, s))) return st;
+    const uint32_t word = p->hsum->status;
+    if (word) {
+        if ((st = check_cuda(p, cudaMemsetAsync(p->status_word(), 0, sizeof(uint32_t), s), "status clear"))) return st;
+        return status_error(p, word);
+    }
+    absorb_summary(p);
+    return MSC_OK;
 }
 
 }  // namespace
@@ -125,16 +235,91 @@ msc_status run_critical(Plan* p, cudaStream_t s) {
     src.g = g;
     src.bits = static_cast<const uint32_t*>(p->crit_bits.ptr);
     src.prefix = static_cast<uint32_t*>(p->crit_prefix.ptr);
-    src.status = static_cast<uint32_t*>(p->status.ptr);
-    unsigned long long tot[4] = {0, 0, 0, 0};
-    if ((st = compaction_count(p, s, src, 4, tot))) return st;
+    src.status = p->status_word();
+    if ((st = compaction_sums(p, s, src, 4, p->dsum()->counts))) return st;
+    int64_t cap[4];
+    if (p->capturing) {
+        for (int k = 0; k < 4; ++k) cap[k] = p->caps.cells[k];
+    } else {  // size the lists exactly
+        if ((st = read_summary(p, s))) return st;
+        for (int k = 0; k < 4; ++k) cap[k] = p->counts[k] = int64_t(p->hsum->counts[k]);
+    }
     for (int k = 0; k < 4; ++k) {
-        p->counts[k] = int64_t(tot[k]);
-        if ((st = ensure(p, p->cells[k], sizeof(uint32_t) * size_t(tot[k] ? tot[k] : 1)))) return st;
+        if ((st = ensure(p, p->cells[k], sizeof(uint32_t) * size_t(cap[k] ? cap[k] : 1)))) return st;
         src.out[k] = static_cast<uint32_t*>(p->cells[k].ptr);
-        src.cap[k] = tot[k];
+        src.cap[k] = uint64_t(cap[k]);
     }
     return compaction_emit(p, s, src, 4);
+}
+
+// Every stage, enqueued without host synchronisation (the body of a captured graph).
+msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s) {
+    msc_status st;
+    if ((st = check_cuda(p, cudaMemsetAsync(p->dsum(), 0, sizeof(Summary), s), "summary clear"))) return st;
+    stage_start(p, 0, s);
+    if ((st = run_gradient(p, d_field, s))) return st;
+    stage_end(p, 0, s);
+    stage_start(p, 1, s);
+    if ((st = run_critical(p, s))) return st;
+    stage_end(p, 1, s);
+    stage_start(p, 2, s);
+    if ((st = run_extremum(p, s))) return st;
+    stage_end(p, 2, s);
+    stage_start(p, 3, s);
+    if ((st = run_reachability(p, s))) return st;
+    stage_end(p, 3, s);
+    stage_start(p, 4, s);
+    if ((st = run_junctions(p, s))) return st;
+    if ((st = run_trace(p, s))) return st;
+    stage_end(p, 4, s);
+    stage_start(p, 5, s);
+    if ((st = run_path_count(p, s))) return st;
+    stage_end(p, 5, s);
+    return MSC_OK;
+}
+
+void destroy_graph(Plan* p) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+    p->graph_field = nullptr;
+}
+
+// Captures the pipeline for d_field.  The first capture only sizes the buffers for the
+// capacities (a buffer that grows is reallocated, which must not happen between captured nodes)
+// and is discarded; the second records the graph that is replayed.
+msc_status capture_graph(Plan* p, const float* d_field) {
+    destroy_graph(p);
+    msc_status st = MSC_OK;
+    for (int pass = 0; pass < 2; ++pass) {
+        p->capturing = true;
+        p->stats.n_launches = 0;
+        cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) st = enqueue_pipeline(p, d_field, p->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &g) : e;
+        p->capturing = false;
+        if (!st && e != cudaSuccess) st = check_cuda(p, e, "begin capture");
+        if (!st && e2 != cudaSuccess) st = check_cuda(p, e2, "end capture");
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st;
+        }
+        if (pass == 0) {
+            cudaGraphDestroy(g);
+            continue;
+        }
+        p->graph = g;
+        p->graph_static_launches = p->stats.n_launches;
+        if ((st = check_cuda(p, cudaGraphInstantiate(&p->graph_exec, g, 0), "graph instantiate"))) {
+            destroy_graph(p);
+            return st;
+        }
+    }
+    p->graph_field = d_field;
+    return MSC_OK;
 }
 
 }  // namespace msc
@@ -151,7 +336,7 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
         if (dims[i] < 2 || dims[i] > (int64_t(1) << 30)) return MSC_ERR_ARG;
     const int64_t rx = 2 * dims[0] - 1, ry = 2 * dims[1] - 1, rz = 2 * dims[2] - 1;
     if (rx * ry > (int64_t(1) << 40) || double(rx) * double(ry) * double(rz) >= 4294967295.0) return MSC_ERR_TOO_LARGE;
-    if (opts && opts->flags != 0) return MSC_ERR_ARG;
+    if (opts && (opts->flags & ~MSC_FLAG_NO_GRAPH)) return MSC_ERR_ARG;
     msc_plan_s* p = new (std::nothrow) msc_plan_s();
     if (!p) return MSC_ERR_OOM;
     p->g.nx = int(dims[0]);
@@ -164,12 +349,16 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
     msc_status st = msc::check_cuda(p, cudaGetDevice(&p->device), "cudaGetDevice");
     if (!st) st = msc::check_cuda(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
                                   "cudaDeviceGetAttribute");
-    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->ev0), "cudaEventCreate");
-    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->ev1), "cudaEventCreate");
+    for (int i = 0; i < 12 && !st; ++i) st = msc::check_cuda(p, cudaEventCreate(&p->stage_ev[i]), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->kev0), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->kev1), "cudaEventCreate");
-    if (!st) st = msc::ensure(p, p->status, sizeof(uint32_t) * 4);
-    if (!st) st = msc::check_cuda(p, cudaMemset(p->status.ptr, 0, sizeof(uint32_t) * 4), "cudaMemset(status)");
+    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->tev0), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->tev1), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!st) st = msc::check_cuda(p, cudaMallocHost(&p->hsum, sizeof(msc::Summary)), "cudaMallocHost");
+    if (!st) st = msc::ensure(p, p->status, sizeof(msc::Summary));
+    if (!st) st = msc::check_cuda(p, cudaMemset(p->status.ptr, 0, sizeof(msc::Summary)), "cudaMemset(summary)");
     if (st) {
         msc_plan_destroy(p);
         return st;
@@ -181,15 +370,19 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
 msc_status msc_plan_destroy(msc_plan_t plan) {
     if (!plan) return MSC_ERR_ARG;
     msc_plan_s* p = plan;
+    msc::destroy_graph(p);
     p->for_each_buffer([](msc::DeviceBuffer& b) {
         if (b.ptr) cudaFree(b.ptr);
         b.ptr = nullptr;
         b.bytes = 0;
     });
-    if (p->ev0) cudaEventDestroy(p->ev0);
-    if (p->ev1) cudaEventDestroy(p->ev1);
-    if (p->kev0) cudaEventDestroy(p->kev0);
-    if (p->kev1) cudaEventDestroy(p->kev1);
+    for (cudaEvent_t e : p->stage_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1})
+        if (e) cudaEventDestroy(e);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->body_stream) cudaStreamDestroy(p->body_stream);
+    if (p->hsum) cudaFreeHost(p->hsum);
     delete p;
     return MSC_OK;
 }
@@ -207,9 +400,11 @@ msc_status msc_gradient(msc_plan_t plan, const float* d_field, msc_stream_t stre
     if ((st = msc::bind_device(p))) return st;
     msc::invalidate(p);
     p->stats.n_launches = 0;
-    msc::StageTimer tm(p, s, &p->stats.ms_gradient);
+    p->stage_recorded = 0;
+    if ((st = msc::check_cuda(p, cudaMemsetAsync(p->dsum(), 0, sizeof(msc::Summary), s), "summary clear"))) return st;
+    msc::stage_start(p, 0, s);
     if ((st = msc::run_gradient(p, d_field, s))) return st;
-    cudaEventRecord(p->ev1, s);  // stage time is read when the next stage synchronises
+    msc::stage_end(p, 0, s);
     p->have_gradient = true;
     return MSC_OK;
 }
@@ -225,14 +420,11 @@ static msc_status ensure_critical(Plan* p, cudaStream_t s) {
     if (!p->have_gradient) return msc::fail(p, MSC_ERR_STATE, "msc_gradient has not run");
     if (p->have_critical) return MSC_OK;
     msc_status st;
-    // gradient time: ev0 was recorded before the gradient launch, ev1 after it
-    if (cudaEventSynchronize(p->ev1) == cudaSuccess) cudaEventElapsedTime(&p->stats.ms_gradient, p->ev0, p->ev1);
-    if ((st = msc::check_status_word(p, s))) return st;
-    msc::StageTimer tm(p, s, &p->stats.ms_critical);
+    if ((st = msc::finish_stage(p, s))) return st;  // a NaN in the field stops here
+    msc::stage_start(p, 1, s);
     if ((st = msc::run_critical(p, s))) return st;
-    tm.stop();
-    if ((st = msc::check_status_word(p, s))) return st;
-    for (int k = 0; k < 4; ++k) p->stats.counts[k] = p->counts[k];
+    msc::stage_end(p, 1, s);
+    if ((st = msc::finish_stage(p, s))) return st;
     p->have_critical = true;
     return MSC_OK;
 }
@@ -255,10 +447,10 @@ static msc_status ensure_extremum(Plan* p, cudaStream_t s) {
     msc_status st;
     if ((st = ensure_critical(p, s))) return st;
     if (p->have_extremum) return MSC_OK;
-    msc::StageTimer tm(p, s, &p->stats.ms_extremum);
+    msc::stage_start(p, 2, s);
     if ((st = msc::run_extremum(p, s))) return st;
-    tm.stop();
-    if ((st = msc::check_status_word(p, s))) return st;
+    msc::stage_end(p, 2, s);
+    if ((st = msc::finish_stage(p, s))) return st;
     p->have_extremum = true;
     return MSC_OK;
 }
@@ -283,11 +475,11 @@ static msc_status ensure_reach(Plan* p, cudaStream_t s) {
     msc_status st;
     if ((st = ensure_critical(p, s))) return st;
     if (p->have_reach) return MSC_OK;
-    msc::StageTimer tm(p, s, &p->stats.ms_reachability);
+    msc::stage_start(p, 3, s);
     if ((st = msc::run_reachability(p, s))) return st;
-    tm.stop();
+    msc::stage_end(p, 3, s);
     if (p->fault_kind == 2) msc::raise_status(p, msc::ST_TIMEOUT, s);
-    if ((st = msc::check_status_word(p, s))) return st;
+    if ((st = msc::finish_stage(p, s))) return st;
     p->have_reach = true;
     return MSC_OK;
 }
@@ -310,12 +502,9 @@ static msc_status ensure_junctions(Plan* p, cudaStream_t s) {
     msc_status st;
     if ((st = ensure_reach(p, s))) return st;
     if (p->have_junctions) return MSC_OK;
-    float ms = 0;
-    msc::StageTimer tm(p, s, &ms);
+    msc::stage_start(p, 4, s);
     if ((st = msc::run_junctions(p, s))) return st;
-    tm.stop();
-    p->stats.ms_minor = ms;
-    if ((st = msc::check_status_word(p, s))) return st;
+    if ((st = msc::finish_stage(p, s))) return st;
     p->have_junctions = true;
     return MSC_OK;
 }
@@ -332,17 +521,14 @@ msc_status msc_junctions(msc_plan_t plan, msc_stream_t stream, const uint32_t** 
     return MSC_OK;
 }
 
-static msc_status ensure_minor(Plan* p, cudaStream_t s) {
+static msc_status ensure_trace(Plan* p, cudaStream_t s) {
     msc_status st;
     if ((st = ensure_junctions(p, s))) return st;
-    if (p->have_minor) return MSC_OK;
-    float ms = 0;
-    msc::StageTimer tm(p, s, &ms);
-    if ((st = msc::run_minor(p, s))) return st;
-    tm.stop();
-    p->stats.ms_minor += ms;
-    if ((st = msc::check_status_word(p, s))) return st;
-    p->have_minor = true;
+    if (p->have_trace) return MSC_OK;
+    if ((st = msc::run_trace(p, s))) return st;
+    msc::stage_end(p, 4, s);
+    if ((st = msc::finish_stage(p, s))) return st;
+    p->have_trace = true;
     return MSC_OK;
 }
 
@@ -353,7 +539,12 @@ msc_status msc_minor(msc_plan_t plan, msc_stream_t stream, int which, int64_t* r
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     msc_status st;
     if ((st = msc::bind_device(p))) return st;
-    if ((st = ensure_minor(p, s))) return st;
+    if ((st = ensure_trace(p, s))) return st;
+    if (!p->have_minor) {
+        if ((st = msc::build_minor_csr(p, s))) return st;
+        if ((st = msc::finish_stage(p, s))) return st;
+        p->have_minor = true;
+    }
     if (rows) *rows = p->minor_rows[which];
     if (nnz) *nnz = p->minor_nnz[which];
     if (d_rowptr) *d_rowptr = static_cast<const int64_t*>(p->minor_rowptr[which].ptr);
@@ -364,13 +555,13 @@ msc_status msc_minor(msc_plan_t plan, msc_stream_t stream, int which, int64_t* r
 
 static msc_status ensure_dstar(Plan* p, cudaStream_t s) {
     msc_status st;
-    if ((st = ensure_minor(p, s))) return st;
+    if ((st = ensure_trace(p, s))) return st;
     if (p->have_dstar) return MSC_OK;
-    msc::StageTimer tm(p, s, &p->stats.ms_path_count);
+    msc::stage_start(p, 5, s);
     if ((st = msc::run_path_count(p, s))) return st;
-    tm.stop();
+    msc::stage_end(p, 5, s);
     if (p->fault_kind == 3) msc::raise_status(p, msc::ST_OVERFLOW, s);
-    if ((st = msc::check_status_word(p, s))) return st;
+    if ((st = msc::finish_stage(p, s))) return st;
     p->have_dstar = true;
     return MSC_OK;
 }
@@ -390,20 +581,76 @@ msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, c
     return MSC_OK;
 }
 
+// One pass as a replayed graph; MSC_NOT_READY asks the caller to run the pass synchronised
+// (a capacity fixed at capture was too small).
+static msc_status compute_graph(Plan* p, const float* d_field, cudaStream_t s) {
+    msc_status st;
+    if (!p->graph_exec || p->graph_field != d_field)
+        if ((st = msc::capture_graph(p, d_field))) return st;
+    msc::invalidate(p);
+    p->stage_recorded = 0;
+    if ((st = msc::check_cuda(p, cudaGraphLaunch(p->graph_exec, s), "graph launch"))) return st;
+    if ((st = msc::read_summary(p, s))) return st;
+    const uint32_t word = p->hsum->status;
+    if (word) {
+        if ((st = msc::check_cuda(p, cudaMemsetAsync(p->status_word(), 0, sizeof(uint32_t), s), "status clear")))
+            return st;
+        if ((word & msc::ST_RETRY) && !(word & ~(msc::ST_RETRY | msc::ST_CAPACITY))) {
+            msc::destroy_graph(p);
+            return MSC_NOT_READY;
+        }
+        return msc::status_error(p, word);
+    }
+    msc::absorb_summary(p);
+    p->stage_recorded = 0x3F;
+    p->stats.n_launches = p->graph_static_launches + p->loop_body_launches[0] * int64_t(p->hsum->jump_rounds) +
+                          p->loop_body_launches[1] * int64_t(p->hsum->sweep_iters);
+    p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = true;
+    p->have_junctions = p->have_trace = p->have_dstar = true;
+    ++p->graph_replays;
+    return MSC_OK;
+}
+
 msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t stream) {
     if (!plan || !d_field) return MSC_ERR_ARG;
     Plan* p = plan;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    const bool graphs = !(p->opts.flags & MSC_FLAG_NO_GRAPH) && p->fault_kind == 0;
+    if (graphs && p->caps_ready) {
+        st = compute_graph(p, d_field, s);
+        if (st != MSC_NOT_READY) return st;
+    }
+    // synchronised run: every stage in turn, with exact buffer sizes
     if ((st = msc_gradient(plan, d_field, stream))) return st;
     if ((st = ensure_extremum(p, s))) return st;
-    return ensure_dstar(p, s);
+    if ((st = ensure_dstar(p, s))) return st;
+    // capacities for the graph of the next call: these sizes plus headroom
+    auto room = [](int64_t n) { return n + n / 4 + 1024; };
+    for (int k = 0; k < 4; ++k) p->caps.cells[k] = std::max(p->caps.cells[k], room(p->counts[k]));
+    p->caps.nj = std::max(p->caps.nj, room(p->n_junctions));
+    p->caps.staging = std::max<int64_t>(p->caps.staging, room(p->pc_staging_cap));
+    p->caps_ready = true;
+    msc::destroy_graph(p);
+    return MSC_OK;
 }
 
 msc_status msc_get_stats(msc_plan_t plan, msc_stats* out) {
     if (!plan || !out) return MSC_ERR_ARG;
-    plan->stats.peak_device_bytes = plan->peak_bytes;
-    *out = plan->stats;
+    Plan* p = plan;
+    p->stats.peak_device_bytes = p->peak_bytes;
+    float* dst[6] = {&p->stats.ms_gradient, &p->stats.ms_critical, &p->stats.ms_extremum,
+                     &p->stats.ms_reachability, &p->stats.ms_minor, &p->stats.ms_path_count};
+    for (int k = 0; k < 6; ++k)
+        if ((p->stage_recorded >> k) & 1u && cudaEventSynchronize(p->stage_ev[2 * k + 1]) == cudaSuccess)
+            cudaEventElapsedTime(dst[k], p->stage_ev[2 * k], p->stage_ev[2 * k + 1]);
+    if (p->have_dstar && cudaEventSynchronize(p->kev1) == cudaSuccess)
+        cudaEventElapsedTime(&p->stats.ms_rows_kernel, p->kev0, p->kev1);
+    if (p->have_trace && cudaEventSynchronize(p->tev1) == cudaSuccess)
+        cudaEventElapsedTime(&p->stats.ms_trace_kernel, p->tev0, p->tev1);
+    cudaGetLastError();
+    *out = p->stats;
     return MSC_OK;
 }
 

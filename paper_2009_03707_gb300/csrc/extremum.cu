@@ -10,7 +10,8 @@
 // become cell ids at the end.  Each jump round lets every thread follow up to JUMPS links,
 // updating its own entry in place; the paper's ping-pong buffers are not needed because any
 // value a thread reads is an ancestor of the one it replaces.  Rounds repeat until no entry
-// changes (a device flag, capped by the plan's iteration limit).
+// changes: a device flag decides, so the loop runs without the host when it is part of a
+// captured pipeline (a conditional WHILE node), and is capped by the plan's iteration limit.
 #include "msc_internal.cuh"
 
 namespace msc {
@@ -95,6 +96,21 @@ __global__ void __launch_bounds__(THREADS) jump_round(int64_t n, uint32_t* __res
     if (open) *changed = 1;
 }
 
+// End of one round: the continue decision (more rounds while some chain is still open, up to the
+// iteration cap), the round count, and the graph condition when the loop runs in a graph.
+__global__ void jump_decide(Summary* sum, int64_t max_iter, cudaGraphConditionalHandle h, int use_handle) {
+    const bool open = sum->loop_flag[0] != 0;
+    sum->loop_flag[0] = 0;
+    const unsigned long long r = ++sum->jump_rounds;
+    bool more = open;
+    if (more && int64_t(r) >= max_iter) {
+        sum->status |= ST_ITER;
+        more = false;
+    }
+    sum->loop_flag[3] = more ? 1u : 0u;
+    if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // Vertex indices -> cell ids of the extremum (in place).
 __global__ void __launch_bounds__(THREADS) finish_labels(Geom g, uint32_t* __restrict__ lab_v,
                                                          uint32_t* __restrict__ lab_c) {
@@ -126,24 +142,37 @@ __device__ __forceinline__ CellCoord decode_cell(const Geom& g, uint32_t id) {
 }
 
 // 1-saddle arcs: the minima of the edge's lower-coordinate and upper-coordinate vertices.
-__global__ void __launch_bounds__(THREADS) min_arcs_kernel(Geom g, const uint32_t* __restrict__ s1, int64_t n1,
-                                                           const uint32_t* __restrict__ vmin,
-                                                           uint32_t* __restrict__ out) {
-    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (i >= n1) return;
+// Count of a list produced earlier in the pass, clamped to the capacity the launch was sized for.
+__device__ __forceinline__ int64_t clamp_count(const unsigned long long* n_dev, int64_t cap, uint32_t* status) {
+    const unsigned long long n = *n_dev;
+    if (n > (unsigned long long)cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_RETRY);
+        return cap;
+    }
+    return int64_t(n);
+}
+
+__global__ void __launch_bounds__(THREADS) min_arcs_kernel(Geom g, const uint32_t* __restrict__ s1,
+                                                           const unsigned long long* n_dev, int64_t cap,
+                                                           const uint32_t* __restrict__ vmin, uint32_t* __restrict__ out,
+                                                           uint32_t* __restrict__ status) {
+    const int64_t n1 = clamp_count(n_dev, cap, status);
+    for (int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x; i < n1; i += int64_t(gridDim.x) * THREADS) {
     CellCoord c = decode_cell(g, s1[i]);
     int lo[3] = {c.x >> 1, c.y >> 1, c.z >> 1};
     int hi[3] = {(c.x + 1) >> 1, (c.y + 1) >> 1, (c.z + 1) >> 1};
     out[2 * i] = vmin[g.vid(lo[0], lo[1], lo[2])];
     out[2 * i + 1] = vmin[g.vid(hi[0], hi[1], hi[2])];
+    }
 }
 
 // 2-saddle arcs: the maxima of the quad's cofacet cubes on the - and + side of its even axis.
-__global__ void __launch_bounds__(THREADS) max_arcs_kernel(Geom g, const uint32_t* __restrict__ s2, int64_t n2,
-                                                           const uint32_t* __restrict__ cmax,
-                                                           uint32_t* __restrict__ out) {
-    const int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (i >= n2) return;
+__global__ void __launch_bounds__(THREADS) max_arcs_kernel(Geom g, const uint32_t* __restrict__ s2,
+                                                           const unsigned long long* n_dev, int64_t cap,
+                                                           const uint32_t* __restrict__ cmax, uint32_t* __restrict__ out,
+                                                           uint32_t* __restrict__ status) {
+    const int64_t n2 = clamp_count(n_dev, cap, status);
+    for (int64_t i = int64_t(blockIdx.x) * THREADS + threadIdx.x; i < n2; i += int64_t(gridDim.x) * THREADS) {
     CellCoord c = decode_cell(g, s2[i]);
     int cc[3] = {c.x, c.y, c.z};
     const int axis = !(cc[0] & 1) ? 0 : !(cc[1] & 1) ? 1 : 2;
@@ -155,52 +184,53 @@ __global__ void __launch_bounds__(THREADS) max_arcs_kernel(Geom g, const uint32_
         if (d[axis] >= 0 && d[axis] < extent[axis]) lab = cmax[g.vid(d[0] >> 1, d[1] >> 1, d[2] >> 1)];
         out[2 * i + side] = lab;
     }
+    }
 }
 
 int blocks(int64_t n) { return int((n + THREADS - 1) / THREADS); }
+
+struct JumpCtx {
+    int64_t n;
+    uint32_t* vmin;
+    uint32_t* cmax;
+};
+
+void jump_body(Plan* p, cudaStream_t s, cudaGraphConditionalHandle h, void* ctx) {
+    const JumpCtx& c = *static_cast<JumpCtx*>(ctx);
+    jump_round<<<blocks(c.n), THREADS, 0, s>>>(c.n, c.vmin, c.cmax, &p->dsum()->loop_flag[0]);
+    jump_decide<<<1, 1, 0, s>>>(p->dsum(), p->opts.max_iterations, h, h != 0);
+}
 
 }  // namespace
 
 msc_status run_extremum(Plan* p, cudaStream_t s) {
     const Geom& g = p->g;
     msc_status st;
+    const int64_t cap1 = p->capturing ? p->caps.cells[1] : p->counts[1];
+    const int64_t cap2 = p->capturing ? p->caps.cells[2] : p->counts[2];
     if ((st = ensure(p, p->vmin, sizeof(uint32_t) * size_t(g.nverts)))) return st;
     if ((st = ensure(p, p->cmax, sizeof(uint32_t) * size_t(g.nverts)))) return st;
-    if ((st = ensure(p, p->flag, sizeof(uint32_t) * 4))) return st;
-    if ((st = ensure(p, p->min_arcs, sizeof(uint32_t) * size_t(2 * p->counts[1] + 1)))) return st;
-    if ((st = ensure(p, p->max_arcs, sizeof(uint32_t) * size_t(2 * p->counts[2] + 1)))) return st;
+    if ((st = ensure(p, p->min_arcs, sizeof(uint32_t) * size_t(2 * cap1 + 1)))) return st;
+    if ((st = ensure(p, p->max_arcs, sizeof(uint32_t) * size_t(2 * cap2 + 1)))) return st;
     auto* vmin = static_cast<uint32_t*>(p->vmin.ptr);
     auto* cmax = static_cast<uint32_t*>(p->cmax.ptr);
-    auto* flag = static_cast<uint32_t*>(p->flag.ptr);
     init_links<<<blocks(g.nverts), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), vmin, cmax,
-                                                     static_cast<uint32_t*>(p->status.ptr));
+                                                     p->status_word());
     launched(p);
-    int64_t rounds = 0;
-    uint32_t more = 1;
-    while (more) {
-        if (rounds >= p->opts.max_iterations) return fail(p, MSC_ERR_ITER_LIMIT, "pointer jumping did not converge");
-        if ((st = check_cuda(p, cudaMemsetAsync(flag, 0, sizeof(uint32_t), s), "memset flag"))) return st;
-        jump_round<<<blocks(g.nverts), THREADS, 0, s>>>(g.nverts, vmin, cmax, flag);
-        launched(p);
-        if ((st = check_cuda(p, cudaMemcpyAsync(&more, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
-                             "flag copy")))
-            return st;
-        if ((st = check_cuda(p, cudaStreamSynchronize(s), "jump sync"))) return st;
-        ++rounds;
-    }
-    p->stats.n_pointer_jumps = rounds;
+    JumpCtx ctx{g.nverts, vmin, cmax};
+    if ((st = run_loop(p, s, 0, 2, jump_body, &ctx))) return st;
     finish_labels<<<blocks(g.nverts), THREADS, 0, s>>>(g, vmin, cmax);
     launched(p);
-    if (p->counts[1]) {
-        min_arcs_kernel<<<blocks(p->counts[1]), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[1].ptr),
-                                                                 p->counts[1], vmin,
-                                                                 static_cast<uint32_t*>(p->min_arcs.ptr));
+    if (cap1) {
+        min_arcs_kernel<<<grid_cap(p, cap1, THREADS), THREADS, 0, s>>>(
+            g, static_cast<const uint32_t*>(p->cells[1].ptr), &p->dsum()->counts[1], cap1, vmin,
+            static_cast<uint32_t*>(p->min_arcs.ptr), p->status_word());
         launched(p);
     }
-    if (p->counts[2]) {
-        max_arcs_kernel<<<blocks(p->counts[2]), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->cells[2].ptr),
-                                                                 p->counts[2], cmax,
-                                                                 static_cast<uint32_t*>(p->max_arcs.ptr));
+    if (cap2) {
+        max_arcs_kernel<<<grid_cap(p, cap2, THREADS), THREADS, 0, s>>>(
+            g, static_cast<const uint32_t*>(p->cells[2].ptr), &p->dsum()->counts[2], cap2, cmax,
+            static_cast<uint32_t*>(p->max_arcs.ptr), p->status_word());
         launched(p);
     }
     return check_cuda(p, cudaGetLastError(), "extremum launch");

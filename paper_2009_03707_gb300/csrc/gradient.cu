@@ -216,7 +216,7 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     launched(p, 2);
     return check_cuda(p,
                       launch_gradient(g, d_field, static_cast<uint32_t*>(p->words.ptr),
-                                      static_cast<uint32_t*>(p->crit_bits.ptr), static_cast<uint32_t*>(p->status.ptr), s),
+                                      static_cast<uint32_t*>(p->crit_bits.ptr), p->status_word(), s),
                       "gradient launch");
 }
 

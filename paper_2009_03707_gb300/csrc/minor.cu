@@ -32,9 +32,7 @@ struct TraceArgs {
     Geom g;
     const uint32_t* words;
     const uint32_t* s1;
-    int64_t n1;
     const uint32_t* junc_cells;
-    int64_t nj;
     const uint32_t* junc_bits;
     const uint32_t* junc_prefix;
     const uint32_t* crit_bits;
@@ -43,6 +41,10 @@ struct TraceArgs {
     uint32_t* tgt;    // 4 per source: destination rank
     uint8_t* kinds;   // 4 per source: 0 none / 1 junction / 2 2-saddle (read as one word per source)
     uint32_t* cnt[4];  // distinct destinations per row of A, B, B*, D
+    const unsigned long long* n1_dev;  // 1-saddles and junctions, counted earlier in the pass
+    const unsigned long long* nj_dev;
+    int64_t cap1, capj;                // the capacities the buffers were sized for
+    unsigned long long* nnz;           // distinct entries of A, B, B*, D (summed here)
     int64_t max_steps;
     uint32_t* status;
 };
@@ -75,12 +77,21 @@ __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t ki
 
 // One thread per source (1-saddle or junction): its <= 4 out-edges are found once, then the
 // simple paths are followed in an interleaved loop (one independent record load per live path
-// per step), and the destinations are ranked and counted per matrix row.
+// per step), and the destinations are ranked and counted per matrix row.  Grid-stride over the
+// sources, whose numbers are read on the device.
 __global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
-    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
-    if (u >= a.n1 + a.nj) return;
+    unsigned long long n1 = *a.n1_dev, nj = *a.nj_dev;
+    if (n1 > (unsigned long long)a.cap1 || nj > (unsigned long long)a.capj) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_RETRY);
+        n1 = min(n1, (unsigned long long)a.cap1);
+        nj = min(nj, (unsigned long long)a.capj);
+    }
+    const int64_t N1 = int64_t(n1), NJ = int64_t(nj);
+    unsigned long long nnz[4] = {0, 0, 0, 0};
+    for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < N1 + NJ;
+         u += int64_t(gridDim.x) * THREADS) {
     const Geom& g = a.g;
-    const uint32_t id = u < a.n1 ? a.s1[u] : a.junc_cells[u - a.n1];
+    const uint32_t id = u < N1 ? a.s1[u] : a.junc_cells[u - N1];
     const uint32_t q1 = g.div_rx.div(id);
     const int cx = int(id - q1 * g.rx);
     const int cz = int(g.div_ry.div(q1));
@@ -147,10 +158,29 @@ __global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
     reinterpret_cast<uint4*>(a.tgt)[u] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
     reinterpret_cast<uint32_t*>(a.kinds)[u] = kinds;
     uint32_t col[4], mult[4];
-    const bool saddle = u < a.n1;
-    const int64_t row = saddle ? u : u - a.n1;
-    a.cnt[saddle ? 0 : 1][row] = uint32_t(distinct_targets(rank, kinds, 1, col, mult));
-    a.cnt[saddle ? 3 : 2][row] = uint32_t(distinct_targets(rank, kinds, 2, col, mult));
+    const bool saddle = u < N1;
+    const int64_t row = saddle ? u : u - N1;
+    const uint32_t mj = uint32_t(distinct_targets(rank, kinds, 1, col, mult));
+    const uint32_t m2 = uint32_t(distinct_targets(rank, kinds, 2, col, mult));
+    a.cnt[saddle ? 0 : 1][row] = mj;
+    a.cnt[saddle ? 3 : 2][row] = m2;
+    nnz[saddle ? 0 : 1] += mj;
+    nnz[saddle ? 3 : 2] += m2;
+    }
+    __shared__ unsigned long long part[4][THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        unsigned long long v = nnz[k];
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) part[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        unsigned long long t = 0;
+        for (int w = 0; w < THREADS / 32; ++w) t += part[threadIdx.x][w];
+        if (t) atomicAdd(&a.nnz[threadIdx.x], t);
+    }
 }
 
 // which: 0 A, 1 B, 2 B*, 3 D.  Sources 0..n1-1 are 1-saddles (rows of A and D), n1.. are
@@ -184,30 +214,22 @@ __global__ void __launch_bounds__(THREADS) csr_fill(CsrArgs a) {
 
 }  // namespace
 
-msc_status run_minor(Plan* p, cudaStream_t s) {
+msc_status run_trace(Plan* p, cudaStream_t s) {
     const Geom& g = p->g;
     msc_status st;
-    const int64_t n1 = p->counts[1], nj = p->n_junctions, nsrc = n1 + nj;
+    const int64_t cap1 = p->capturing ? p->caps.cells[1] : p->counts[1];
+    const int64_t capj = p->capturing ? p->caps.nj : p->n_junctions;
+    const int64_t nsrc = cap1 + capj;
     if ((st = ensure(p, p->trace, sizeof(uint32_t) * 4 * size_t(nsrc ? nsrc : 1)))) return st;
     if ((st = ensure(p, p->trace_kinds, sizeof(uint32_t) * size_t(nsrc ? nsrc : 1)))) return st;
-    // per-row counts and row pointers of A, B, B*, D
-    const int64_t rows[4] = {n1, nj, nj, n1};
-    size_t cnt_elems = 0, scratch_total = 0;
-    size_t scratch_off[4];
-    for (int w = 0; w < 4; ++w) {
-        cnt_elems += size_t(rows[w]);
-        scratch_off[w] = scratch_total;
-        scratch_total += (row_scan_scratch_bytes(rows[w]) + 255) / 256 * 256;
-    }
-    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * (cnt_elems ? cnt_elems : 1)))) return st;
-    if ((st = ensure(p, p->minor_scan, scratch_total ? scratch_total : 1))) return st;
+    // per-row counts of A (cap1 rows), B, B* (capj), D (cap1), in that order
+    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * size_t(2 * nsrc ? 2 * nsrc : 1)))) return st;
+    const int64_t rows[4] = {cap1, capj, capj, cap1};
     TraceArgs ta{};
     ta.g = g;
     ta.words = static_cast<const uint32_t*>(p->words.ptr);
     ta.s1 = static_cast<const uint32_t*>(p->cells[1].ptr);
-    ta.n1 = n1;
     ta.junc_cells = static_cast<const uint32_t*>(p->junc_cells.ptr);
-    ta.nj = nj;
     ta.junc_bits = static_cast<const uint32_t*>(p->junc_bits.ptr);
     ta.junc_prefix = static_cast<const uint32_t*>(p->junc_prefix.ptr);
     ta.crit_bits = static_cast<const uint32_t*>(p->crit_bits.ptr);
@@ -215,57 +237,71 @@ msc_status run_minor(Plan* p, cudaStream_t s) {
     ta.info = static_cast<const uint32_t*>(p->node_info.ptr);
     ta.tgt = static_cast<uint32_t*>(p->trace.ptr);
     ta.kinds = static_cast<uint8_t*>(p->trace_kinds.ptr);
+    size_t off = 0;
+    for (int w = 0; w < 4; ++w) {
+        p->minor_cnt_off[w] = int64_t(off);
+        ta.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
+        off += size_t(rows[w]);
+    }
+    ta.n1_dev = &p->dsum()->counts[1];
+    ta.nj_dev = &p->dsum()->n_junctions;
+    ta.cap1 = cap1;
+    ta.capj = capj;
+    ta.nnz = p->dsum()->minor_nnz;
     ta.max_steps = p->opts.max_iterations;
-    ta.status = static_cast<uint32_t*>(p->status.ptr);
+    ta.status = p->status_word();
+    record_event(p, p->tev0, s);
+    if (nsrc) {
+        trace_kernel<<<grid_cap(p, nsrc, THREADS, 6), THREADS, 0, s>>>(ta);
+        launched(p);
+    }
+    record_event(p, p->tev1, s);
+    return check_cuda(p, cudaGetLastError(), "trace launch");
+}
+
+// CSR of A, B, B*, D from the trace and its per-row counts (host synchronised; called when the
+// matrices are asked for -- the path count reads the trace directly).
+msc_status build_minor_csr(Plan* p, cudaStream_t s) {
+    msc_status st;
+    if ((st = read_summary(p, s))) return st;
+    const int64_t n1 = int64_t(p->hsum->counts[1]), nj = int64_t(p->hsum->n_junctions);
+    const int64_t rows[4] = {n1, nj, nj, n1};
+    size_t scratch_total = 0;
+    size_t scratch_off[4];
+    for (int w = 0; w < 4; ++w) {
+        scratch_off[w] = scratch_total;
+        scratch_total += (row_scan_scratch_bytes(rows[w]) + 255) / 256 * 256;
+    }
+    if ((st = ensure(p, p->minor_scan, scratch_total ? scratch_total : 1))) return st;
     CsrArgs ca{};
     ca.n1 = n1;
     ca.nj = nj;
-    ca.tgt = ta.tgt;
-    ca.kinds = reinterpret_cast<const uint32_t*>(ta.kinds);
-    size_t off = 0;
+    ca.tgt = static_cast<const uint32_t*>(p->trace.ptr);
+    ca.kinds = static_cast<const uint32_t*>(p->trace_kinds.ptr);
     for (int w = 0; w < 4; ++w) {
-        ca.cnt[w] = ta.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
-        off += size_t(rows[w]);
+        ca.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + p->minor_cnt_off[w];
         if ((st = ensure(p, p->minor_rowptr[w], sizeof(int64_t) * size_t(rows[w] + 1)))) return st;
         ca.rowptr[w] = static_cast<const int64_t*>(p->minor_rowptr[w].ptr);
         p->minor_rows[w] = rows[w];
-    }
-    cudaEventRecord(p->kev0, s);
-    if (nsrc) {
-        trace_kernel<<<blocks(nsrc), THREADS, 0, s>>>(ta);
-        launched(p);
-    }
-    cudaEventRecord(p->kev1, s);
-    if ((st = check_cuda(p, cudaGetLastError(), "trace launch"))) return st;
-    int64_t nnz[4];
-    for (int w = 0; w < 4; ++w) {
         auto* scratch = reinterpret_cast<unsigned long long*>(static_cast<char*>(p->minor_scan.ptr) + scratch_off[w]);
         if ((st = check_cuda(p,
-                             row_scan(p, ca.cnt[w], rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr), scratch, s),
+                             row_scan(p, ca.cnt[w], nullptr, rows[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr),
+                                      scratch, s),
                              "minor row scan")))
             return st;
-        if ((st = check_cuda(p, cudaMemcpyAsync(&nnz[w], static_cast<int64_t*>(p->minor_rowptr[w].ptr) + rows[w],
-                                                sizeof(int64_t), cudaMemcpyDeviceToHost, s),
-                             "nnz copy")))
-            return st;
     }
-    if ((st = check_cuda(p, cudaStreamSynchronize(s), "minor sync"))) return st;
     for (int w = 0; w < 4; ++w) {
-        p->minor_nnz[w] = nnz[w];
-        if ((st = ensure(p, p->minor_col[w], sizeof(uint32_t) * size_t(nnz[w] ? nnz[w] : 1)))) return st;
-        if ((st = ensure(p, p->minor_mult[w], sizeof(uint32_t) * size_t(nnz[w] ? nnz[w] : 1)))) return st;
+        const int64_t nnz = int64_t(p->hsum->minor_nnz[w]);
+        p->minor_nnz[w] = nnz;
+        if ((st = ensure(p, p->minor_col[w], sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
+        if ((st = ensure(p, p->minor_mult[w], sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
         ca.col[w] = static_cast<uint32_t*>(p->minor_col[w].ptr);
         ca.mult[w] = static_cast<uint32_t*>(p->minor_mult[w].ptr);
     }
-    if (nsrc) {
-        csr_fill<<<blocks(nsrc), THREADS, 0, s>>>(ca);
+    if (n1 + nj) {
+        csr_fill<<<blocks(n1 + nj), THREADS, 0, s>>>(ca);
         launched(p);
     }
-    if (cudaEventSynchronize(p->kev1) == cudaSuccess) cudaEventElapsedTime(&p->stats.ms_trace_kernel, p->kev0, p->kev1);
-    p->stats.nnz_A = nnz[0];
-    p->stats.nnz_B = nnz[1];
-    p->stats.nnz_Bstar = nnz[2];
-    p->stats.nnz_D = nnz[3];
     return check_cuda(p, cudaGetLastError(), "csr launch");
 }
 

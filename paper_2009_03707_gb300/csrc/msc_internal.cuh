@@ -22,6 +22,26 @@ enum StatusBit : uint32_t {
     ST_ITER = 1u << 3,       // an iteration cap was reached
     ST_TIMEOUT = 1u << 4,    // a bounded spin wait gave up
     ST_INTERNAL = 1u << 5,   // an invariant was violated (a bounds check failed)
+    ST_RETRY = 1u << 6,      // a replayed pipeline outgrew a capacity fixed at capture: rerun and re-capture
+};
+
+// ---- per-pass results the host needs, kept on the device and read back in one copy --------
+// Path-count counter slots in Summary::pc.
+enum PcCounter { PC_CURSOR = 0, PC_MAX = 1, PC_ITER = 2, PC_ENTRIES = 3, PC_DEFER0 = 4, PC_DEFER1 = 5, PC_NEXT = 6,
+                 PC_DEFER2 = 7 };
+struct Summary {
+    unsigned long long counts[4];     // critical cells per dimension
+    unsigned long long n_junctions;
+    unsigned long long reached;       // reachable 1-cells (the 1-saddles included)
+    unsigned long long levels;        // non-empty BFS levels (level 0 = the 1-saddles)
+    unsigned long long jump_rounds;   // pointer-jumping rounds
+    unsigned long long sweep_iters;   // iterations of the reachability loop (two sweeps each)
+    unsigned long long minor_nnz[4];  // distinct entries of A, B, B*, D
+    unsigned long long pc[8];         // path-count counters (pathcount.cu)
+    unsigned long long dstar_nnz;
+    uint32_t loop_flag[4];            // "changed" flags of the iterative stages; [3] = continue (host loops)
+    uint32_t status;                  // StatusBit word
+    uint32_t pad;
 };
 
 // ---- the plan ----------------------------------------------------------------------------
@@ -40,38 +60,66 @@ struct Plan {
     int64_t live_bytes = 0;
     int num_sms = 0;
 
-    // stage products and scratch (all grow-only, freed by msc_plan_destroy)
-    DeviceBuffer words, status, crit_bits, crit_prefix, scan_sums, totals;
+    // stage products and scratch (all grow-only, freed by msc_plan_destroy); `status` holds the
+    // Summary (status word included)
+    DeviceBuffer words, status, crit_bits, crit_prefix, scan_sums;
     DeviceBuffer cells[4];
-    DeviceBuffer vmin, cmax, min_arcs, max_arcs, flag;
-    DeviceBuffer visited, reach_tmp, reach_masks, reach_qdown, reach_flags, reach_count, node_info;
+    DeviceBuffer vmin, cmax, min_arcs, max_arcs;
+    DeviceBuffer visited, reach_tmp, reach_masks, reach_qdown, node_info;
     DeviceBuffer junc_bits, junc_prefix, junc_cells;
     DeviceBuffer trace, trace_kinds, minor_rowcnt, minor_scan, minor_rowptr[4], minor_col[4], minor_mult[4];
-    DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_counters, pc_col, pc_cnt, pc_gk, pc_gv, pc_gocc;
+    DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_col, pc_cnt, pc_gk, pc_gv, pc_gocc;
     DeviceBuffer dstar_rowptr, dstar_col, dstar_count;
 
     template <class F>
     void for_each_buffer(F&& f) {
-        DeviceBuffer* all[] = {&words, &status, &crit_bits, &crit_prefix, &scan_sums, &totals, &cells[0], &cells[1],
-                               &cells[2], &cells[3], &vmin, &cmax, &min_arcs, &max_arcs, &flag, &visited, &node_info,
-                               &reach_tmp, &reach_masks, &reach_qdown, &reach_flags, &reach_count, &junc_bits, &junc_prefix, &junc_cells, &trace,
-                               &trace_kinds, &minor_rowcnt, &minor_scan, &minor_rowptr[0], &minor_rowptr[1],
-                               &minor_rowptr[2], &minor_rowptr[3], &minor_col[0], &minor_col[1], &minor_col[2],
-                               &minor_col[3], &minor_mult[0], &minor_mult[1], &minor_mult[2], &minor_mult[3],
-                               &pc_rowstart, &pc_rowlen, &pc_big, &pc_counters, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc,
-                               &dstar_rowptr, &dstar_col, &dstar_count};
+        DeviceBuffer* all[] = {&words, &status, &crit_bits, &crit_prefix, &scan_sums, &cells[0], &cells[1], &cells[2],
+                               &cells[3], &vmin, &cmax, &min_arcs, &max_arcs, &visited, &reach_tmp, &reach_masks,
+                               &reach_qdown, &node_info, &junc_bits, &junc_prefix, &junc_cells, &trace, &trace_kinds,
+                               &minor_rowcnt, &minor_scan, &minor_rowptr[0], &minor_rowptr[1], &minor_rowptr[2],
+                               &minor_rowptr[3], &minor_col[0], &minor_col[1], &minor_col[2], &minor_col[3],
+                               &minor_mult[0], &minor_mult[1], &minor_mult[2], &minor_mult[3], &pc_rowstart, &pc_rowlen,
+                               &pc_big, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc, &dstar_rowptr, &dstar_col,
+                               &dstar_count};
         for (DeviceBuffer* b : all) f(*b);
     }
+
+    Summary* dsum() const { return static_cast<Summary*>(status.ptr); }
+    uint32_t* status_word() const { return &dsum()->status; }
+
+    // Capacities of the count-dependent buffers, fixed when a pipeline graph is captured (from the
+    // exact sizes of the last run with host synchronisation, plus headroom).  Kernels clamp to them
+    // and raise ST_RETRY when a replay needs more.
+    struct Caps {
+        int64_t cells[4] = {0, 0, 0, 0};
+        int64_t nj = 0;
+        int64_t staging = 0;
+    } caps;
+    bool capturing = false;          // enqueueing into a graph: no host synchronisation allowed
+    cudaStream_t cap_stream = nullptr, body_stream = nullptr;  // private capture streams
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    const float* graph_field = nullptr;
+    int64_t graph_static_launches = 0;  // kernels per replay outside the loops
+    int64_t loop_body_launches[2] = {0, 0};  // per iteration: pointer jumping, reachability
+    Summary* hsum = nullptr;          // pinned host mirror of the summary
+    cudaEvent_t stage_ev[12] = {};    // start and end of stages 0..5 (read by msc_get_stats)
+    uint32_t stage_recorded = 0;      // stages whose two events belong to the same pass
+    bool caps_ready = false;          // a synchronised run has measured the sizes
+    int64_t graph_replays = 0;
 
     int64_t counts[4] = {0, 0, 0, 0};
     int64_t n_junctions = 0;
     int64_t minor_nnz[4] = {0, 0, 0, 0};
     int64_t minor_rows[4] = {0, 0, 0, 0};
+    int64_t minor_cnt_off[4] = {0, 0, 0, 0};  // where each matrix's row counts start in minor_rowcnt
     int64_t dstar_nnz = 0;
+    int64_t pc_staging_cap = 0;  // staging slots of the last path-count run
     // which stages are valid for the current field
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
-         have_junctions = false, have_minor = false, have_dstar = false;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;  // stage / kernel timing
+         have_junctions = false, have_trace = false, have_minor = false, have_dstar = false;
+    cudaEvent_t kev0 = nullptr, kev1 = nullptr;  // around the tier-0 path-count kernel
+    cudaEvent_t tev0 = nullptr, tev1 = nullptr;  // around the trace kernel
     // host-side fault injection (MSC_FAULT, read at plan creation; tests only): the failure is
     // made on the host -- a faked allocation failure, or a status bit raised as a kernel would
     int fault_kind = 0;  // 0 none, 1 alloc, 2 timeout (reachability), 3 overflow (path count)
@@ -83,14 +131,31 @@ struct Plan {
 // 0 none, 1 a junction, 2 a 2-saddle.
 __host__ __device__ __forceinline__ uint32_t trace_kind(uint32_t kinds, int k) { return (kinds >> (8 * k)) & 0xFFu; }
 
+// Records a timing event on s; inside a capture it must be an external event-record node (a plain
+// record there only orders captured work and is never recorded when the graph runs).
+inline void record_event(const Plan* p, cudaEvent_t ev, cudaStream_t s) {
+    if (p->capturing) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else cudaEventRecord(ev, s);
+}
+
 // Counts one kernel launch of this plan (reported in msc_stats.n_launches).
 inline void launched(Plan* p, int n = 1) { p->stats.n_launches += n; }
+
+// Runs an iterative stage: body(stream, handle) enqueues one iteration and must end with a
+// kernel that stores the continue decision in summary.loop_flag[3] and, when the handle is
+// non-zero, sets the graph condition to it.  Host synchronised: a loop that reads the flag after
+// every iteration.  Capturing: a conditional WHILE node whose body graph is captured from one
+// call of body, so the loop runs on the device with no host round trip.
+msc_status run_loop(Plan* p, cudaStream_t s, int which, int body_launches,
+                    void (*body)(Plan*, cudaStream_t, cudaGraphConditionalHandle, void*), void* ctx);
 
 // Buffer helpers (api.cu): grow-only device allocations owned by the plan.
 msc_status ensure(Plan* p, DeviceBuffer& b, size_t bytes);
 msc_status fail(Plan* p, msc_status st, const std::string& msg);
 msc_status check_cuda(Plan* p, cudaError_t e, const char* what);
 msc_status check_status_word(Plan* p, cudaStream_t s);  // syncs, reads and clears the status word
+msc_status status_error(Plan* p, uint32_t word);        // the error a non-zero status word stands for
+msc_status read_summary(Plan* p, cudaStream_t s);       // syncs; copies the summary to p->hsum
 
 // Stage launchers
 msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s);
@@ -98,8 +163,10 @@ msc_status run_critical(Plan* p, cudaStream_t s);
 msc_status run_extremum(Plan* p, cudaStream_t s);
 msc_status run_reachability(Plan* p, cudaStream_t s);
 msc_status run_junctions(Plan* p, cudaStream_t s);
-msc_status run_minor(Plan* p, cudaStream_t s);
+msc_status run_trace(Plan* p, cudaStream_t s);      // the minor's 4-slot trace (pipeline)
+msc_status build_minor_csr(Plan* p, cudaStream_t s);  // CSR of A, B, B*, D (on request; syncs)
 msc_status run_path_count(Plan* p, cudaStream_t s);
+int grid_cap(const Plan* p, int64_t threads, int block, int per_sm = 8);  // grid for a count-bounded loop
 
 }  // namespace msc
 

@@ -42,9 +42,13 @@ constexpr int T2_THREADS = 256;
 typedef unsigned long long u64;
 
 struct PcArgs {
-    int64_t n1;
+    int64_t n1;             // 1-saddles (resolved on the device from n1_dev, see resolve)
     const uint32_t* rows;   // the 1-saddle ranks this launch owns (null: 0..nrows-1)
-    int64_t nrows;
+    int64_t nrows;          // rows of this launch (resolved on the device from nrows_dev)
+    const unsigned long long* n1_dev;     // counted earlier in the pass
+    const unsigned long long* nrows_dev;  // the 1-saddle count, or the previous tier's deferrals
+    int64_t n1_cap;                       // the capacity the buffers were sized for
+    int retry_on_defer;     // a deferral means the pass must be rerun (the last tier of a graph)
     const uint32_t* tgt;    // 4 destination ranks per source (1-saddles, then junctions)
     const uint32_t* kinds;  // per source, byte k = kind of slot k: 1 junction, 2 2-saddle
     uint32_t* out_col;      // staging: columns of finished rows
@@ -63,6 +67,17 @@ struct PcArgs {
 };
 
 __device__ __forceinline__ int64_t row_of(const PcArgs& a, int64_t i) { return a.rows ? int64_t(a.rows[i]) : i; }
+
+// The counts a launch works on, read on the device (they are produced earlier in the same pass).
+__device__ __forceinline__ void resolve(PcArgs& a) {
+    unsigned long long n1 = *a.n1_dev;
+    if (n1 > (unsigned long long)a.n1_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_RETRY);
+        n1 = (unsigned long long)a.n1_cap;
+    }
+    a.n1 = int64_t(n1);
+    a.nrows = int64_t(min(*a.nrows_dev, n1));
+}
 
 __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
     return *reinterpret_cast<const uint4*>(a.tgt + 4 * src);
@@ -146,7 +161,9 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
 // Persistent: lanes without a row take new ones (one atomic per warp); every round advances all
 // of the warp's rows by one frontier step, and finished rows are written out item-parallel,
 // each entry at its rank within the row (rows come out sorted by column).
-__global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a, u64* next_row) {
+__global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next_row) {
+    PcArgs a = args;
+    resolve(a);
     extern __shared__ __align__(16) unsigned char t0_raw[];
     T0Warp& sh = reinterpret_cast<T0Warp*>(t0_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -314,7 +331,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs a, u64* next_ro
                     a.out_col[dst] = key;
                     a.out_cnt[dst] = val;
                 } else {
-                    atomicOr(a.status, ST_CAPACITY);
+                    atomicOr(a.status, ST_RETRY);  // staging too small: the host grows it and reruns
                 }
                 mx_all = max(mx_all, (u64)val);
             }
@@ -536,7 +553,7 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
             a.out_col[base + i] = t.lk[i];
             a.out_cnt[base + i] = t.lv[i];
         } else {
-            atomicOr(a.status, ST_CAPACITY);
+            atomicOr(a.status, ST_RETRY);  // staging too small: the host grows it and reruns
         }
         mx = max(mx, t.lv[i]);
     }
@@ -546,7 +563,9 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
 }
 
 // Tier 1: warps pull rows from a shared counter.
-__global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs a, u64* next_row) {
+__global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs args, u64* next_row) {
+    PcArgs a = args;
+    resolve(a);
     __shared__ uint32_t fk[T1_WARPS][T1_HASH], dk[T1_WARPS][T1_HASH];
     __shared__ u64 fv[T1_WARPS][T1_HASH], dv[T1_WARPS][T1_HASH];
     __shared__ uint32_t focc[T1_WARPS][T1_LIST], docc[T1_WARPS][T1_LIST], lk[T1_WARPS][T1_LIST];
@@ -569,14 +588,17 @@ __global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs a, u64* next_r
         const int64_t s = row_of(a, int64_t(i));
         if (!count_row<32>(a, t, s, lane) && lane == 0) {
             const u64 pos = atomicAdd(a.deferred_count, 1ull);
+            if (a.retry_on_defer) atomicOr(a.status, ST_RETRY);
             a.deferred[pos] = uint32_t(s);
         }
     }
 }
 
 // Tiers 2+: one CTA per row, tables in global memory (one set per CTA).
-__global__ void __launch_bounds__(T2_THREADS) rows_block(PcArgs a, uint32_t* gk, u64* gv, uint32_t* gocc, int cap,
+__global__ void __launch_bounds__(T2_THREADS) rows_block(PcArgs args, uint32_t* gk, u64* gv, uint32_t* gocc, int cap,
                                                          int lg) {
+    PcArgs a = args;
+    resolve(a);
     __shared__ int counters[3];
     __shared__ u64 base;
     const size_t per = size_t(cap);
@@ -589,6 +611,7 @@ __global__ void __launch_bounds__(T2_THREADS) rows_block(PcArgs a, uint32_t* gk,
         const int64_t s = row_of(a, i);
         if (!count_row<T2_THREADS>(a, t, s, threadIdx.x) && threadIdx.x == 0) {
             const u64 pos = atomicAdd(a.deferred_count, 1ull);
+            if (a.retry_on_defer) atomicOr(a.status, ST_RETRY);
             a.deferred[pos] = uint32_t(s);
         }
     }
@@ -601,55 +624,66 @@ __global__ void init_tables(uint32_t* k, u64* v, size_t n) {
     }
 }
 
-__global__ void gather_rows(int64_t n1, const int64_t* __restrict__ row_start, const int64_t* __restrict__ rowptr,
-                            const uint32_t* __restrict__ in_col, const u64* __restrict__ in_cnt,
-                            uint32_t* __restrict__ col, u64* __restrict__ cnt) {
-    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= n1) return;
-    const int64_t b = row_start[s], o = rowptr[s], len = rowptr[s + 1] - rowptr[s];
-    for (int64_t i = 0; i < len; ++i) {
-        col[o + i] = in_col[b + i];
-        cnt[o + i] = in_cnt[b + i];
+__global__ void gather_rows(const unsigned long long* n1_dev, int64_t cap, const int64_t* __restrict__ row_start,
+                            const int64_t* __restrict__ rowptr, const uint32_t* __restrict__ in_col,
+                            const u64* __restrict__ in_cnt, uint32_t* __restrict__ col, u64* __restrict__ cnt) {
+    const int64_t n1 = int64_t(min(*n1_dev, (unsigned long long)cap));
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n1; s += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = row_start[s], o = rowptr[s], len = rowptr[s + 1] - rowptr[s];
+        for (int64_t i = 0; i < len; ++i) {
+            col[o + i] = in_col[b + i];
+            cnt[o + i] = in_cnt[b + i];
+        }
     }
 }
 
-// Counter slots in pc_counters.
-enum { C_CURSOR = 0, C_MAX = 1, C_ITER = 2, C_ENTRIES = 3, C_DEFER0 = 4, C_DEFER1 = 5, C_NEXT = 6 };
+// Counter slots in Summary::pc.
+enum { C_CURSOR = PC_CURSOR, C_MAX = PC_MAX, C_ITER = PC_ITER, C_ENTRIES = PC_ENTRIES, C_DEFER0 = PC_DEFER0,
+       C_DEFER1 = PC_DEFER1, C_NEXT = PC_NEXT, C_DEFER2 = PC_DEFER2 };
 
 }  // namespace
 
 msc_status run_path_count(Plan* p, cudaStream_t s) {
     msc_status st;
-    const int64_t n1 = p->counts[1], nj = p->n_junctions, n2 = p->counts[2];
-    const size_t n1c = size_t(n1 ? n1 : 1);
-    if ((st = ensure(p, p->dstar_rowptr, sizeof(int64_t) * size_t(n1 + 1)))) return st;
+    const bool cap_mode = p->capturing;
+    const int64_t n1cap = cap_mode ? p->caps.cells[1] : p->counts[1];
+    const int64_t njcap = cap_mode ? p->caps.nj : p->n_junctions;
+    const int64_t n2cap = cap_mode ? p->caps.cells[2] : p->counts[2];
+    const size_t n1c = size_t(n1cap ? n1cap : 1);
+    if ((st = ensure(p, p->dstar_rowptr, sizeof(int64_t) * size_t(n1cap + 1)))) return st;
     if ((st = ensure(p, p->pc_rowstart, sizeof(int64_t) * n1c))) return st;
     if ((st = ensure(p, p->pc_rowlen, sizeof(uint32_t) * n1c))) return st;
     if ((st = ensure(p, p->pc_big, sizeof(uint32_t) * n1c * 2))) return st;
-    if ((st = ensure(p, p->pc_counters, sizeof(u64) * 8))) return st;
-    if ((st = ensure(p, p->minor_scan, row_scan_scratch_bytes(n1)))) return st;
-    auto* ctr = static_cast<u64*>(p->pc_counters.ptr);
+    if ((st = ensure(p, p->minor_scan, row_scan_scratch_bytes(n1cap)))) return st;
+    u64* ctr = p->dsum()->pc;
     const int first_tier = std::max(0, std::min(2, int(p->opts.path_count_tier)));
     // tier-0 grid: persistent, as many CTAs as fit
     const size_t t0_smem = sizeof(T0Warp) * T0_WARPS;
-    if ((st = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
+    if (!cap_mode &&
+        (st = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
                          "cudaFuncSetAttribute(rows_thread)")))
         return st;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_thread, T0_THREADS, t0_smem);
     const int t0_grid = int(std::max<int64_t>(
-        1, std::min<int64_t>((n1 + T0_THREADS - 1) / T0_THREADS, int64_t(std::max(1, per_sm)) * p->num_sms)));
-    // staging capacity, including what tier-0 warps may leave unused at the end of their chunks:
-    // grown and the stage re-run if a run overflows it
+        1, std::min<int64_t>((n1cap + T0_THREADS - 1) / T0_THREADS, int64_t(std::max(1, per_sm)) * p->num_sms)));
+    // staging capacity, including what tier-0 warps may leave unused at the end of their chunks;
+    // a synchronised run grows it and reruns the stage on overflow, a replayed graph asks for a rerun
     const uint64_t slack = uint64_t(t0_grid) * T0_WARPS * (T0_OUT_CHUNK + 32 * T0_D);
-    uint64_t cap = uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1 + 1024)) + slack;
+    uint64_t cap = cap_mode ? uint64_t(p->caps.staging)
+                            : uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1cap + 1024)) + slack;
+    // a row never needs more slots than 2 x max(junctions, 2-saddles)
+    const int lg_max = 1 + int(std::ceil(std::log2(double(std::max<int64_t>({njcap, n2cap, 64}) + 1))));
+    uint32_t* lists[2] = {static_cast<uint32_t*>(p->pc_big.ptr), static_cast<uint32_t*>(p->pc_big.ptr) + n1c};
     for (int attempt = 0; attempt < 8; ++attempt) {
         if ((st = ensure(p, p->pc_col, sizeof(uint32_t) * cap))) return st;
         if ((st = ensure(p, p->pc_cnt, sizeof(u64) * cap))) return st;
+        if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * cap))) return st;
+        if ((st = ensure(p, p->dstar_count, sizeof(u64) * cap))) return st;
         if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * 8, s), "memset counters"))) return st;
-        uint32_t* lists[2] = {static_cast<uint32_t*>(p->pc_big.ptr), static_cast<uint32_t*>(p->pc_big.ptr) + n1c};
         PcArgs a{};
-        a.n1 = n1;
+        a.n1_dev = &p->dsum()->counts[1];
+        a.n1_cap = n1cap;
         a.tgt = static_cast<const uint32_t*>(p->trace.ptr);
         a.kinds = static_cast<const uint32_t*>(p->trace_kinds.ptr);
         a.out_col = static_cast<uint32_t*>(p->pc_col.ptr);
@@ -662,101 +696,98 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         a.row_start = static_cast<int64_t*>(p->pc_rowstart.ptr);
         a.row_len = static_cast<uint32_t*>(p->pc_rowlen.ptr);
         a.max_iter = p->opts.max_iterations;
-        a.status = static_cast<uint32_t*>(p->status.ptr);
-        // rows of the current tier: all of them, or those the previous tier deferred
-        const uint32_t* rows = nullptr;
-        int64_t nrows = n1;
-        int which = 0;
-        auto run_tier = [&](int tier, int lg) -> msc_status {
+        a.status = p->status_word();
+        // tier 0 takes every row (unless a tier is forced); each tier defers into the other list
+        auto launch = [&](int tier, const uint32_t* rows, const u64* nrows, uint32_t* defer, u64* defer_ctr, int lg,
+                          bool last) {
             a.rows = rows;
-            a.nrows = nrows;
-            a.deferred = lists[which];
-            a.deferred_count = ctr + C_DEFER0 + which;
-            msc_status e;
-            if ((e = check_cuda(p, cudaMemsetAsync(a.deferred_count, 0, sizeof(u64), s), "memset"))) return e;
+            a.nrows_dev = nrows;
+            a.deferred = defer;
+            a.deferred_count = defer_ctr;
+            a.retry_on_defer = last && cap_mode;
             if (tier == 0) {
-                if ((e = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return e;
-                cudaEventRecord(p->kev0, s);
+                record_event(p, p->kev0, s);
                 rows_thread<<<t0_grid, T0_THREADS, t0_smem, s>>>(a, ctr + C_NEXT);
-                cudaEventRecord(p->kev1, s);
+                record_event(p, p->kev1, s);
                 launched(p);
             } else if (tier == 1) {
-                if ((e = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return e;
                 rows_warp<<<std::max(1, p->num_sms) * 8, T1_WARPS * 32, 0, s>>>(a, ctr + C_NEXT);
                 launched(p);
             } else {
                 const int cap_t = 1 << lg;
-                const int ctas = int(std::min<int64_t>(nrows, lg <= 14 ? 1024 : lg <= 18 ? 64 : 2));
+                const int ctas = lg <= 14 ? 128 : lg <= 18 ? 64 : 2;
                 const size_t slots = size_t(ctas) * 3 * size_t(cap_t);
+                msc_status e;
+                // every use leaves the tables empty, so they are initialised only when (re)allocated
+                const bool fresh = p->pc_gk.bytes < sizeof(uint32_t) * slots;
                 if ((e = ensure(p, p->pc_gk, sizeof(uint32_t) * slots))) return e;
                 if ((e = ensure(p, p->pc_gv, sizeof(u64) * slots))) return e;
                 if ((e = ensure(p, p->pc_gocc, sizeof(uint32_t) * size_t(ctas) * size_t(cap_t)))) return e;
-                init_tables<<<1024, 256, 0, s>>>(static_cast<uint32_t*>(p->pc_gk.ptr), static_cast<u64*>(p->pc_gv.ptr),
-                                                 slots);
+                if (fresh) {
+                    init_tables<<<1024, 256, 0, s>>>(static_cast<uint32_t*>(p->pc_gk.ptr),
+                                                     static_cast<u64*>(p->pc_gv.ptr), p->pc_gk.bytes / sizeof(uint32_t));
+                    launched(p);
+                }
                 rows_block<<<ctas, T2_THREADS, 0, s>>>(a, static_cast<uint32_t*>(p->pc_gk.ptr),
                                                       static_cast<u64*>(p->pc_gv.ptr),
                                                       static_cast<uint32_t*>(p->pc_gocc.ptr), cap_t, lg);
-                launched(p, 2);
+                launched(p);
             }
-            if ((e = check_cuda(p, cudaGetLastError(), "path count launch"))) return e;
-            u64 deferred = 0;
-            if ((e = check_cuda(p, cudaMemcpyAsync(&deferred, a.deferred_count, sizeof(deferred),
-                                                   cudaMemcpyDeviceToHost, s),
-                                "counter copy")))
-                return e;
-            if ((e = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return e;
-            if (tier == 0 && nrows) cudaEventElapsedTime(&p->stats.ms_rows_kernel, p->kev0, p->kev1);
-            rows = lists[which];
-            nrows = int64_t(deferred);
-            which ^= 1;
-            return MSC_OK;
+            return check_cuda(p, cudaGetLastError(), "path count launch");
         };
-        if (first_tier <= 0 && nrows > 0 && (st = run_tier(0, 0))) return st;
-        if (first_tier <= 1 && nrows > 0 && (st = run_tier(1, 0))) return st;
-        // a row never needs more slots than 2 x max(junctions, 2-saddles)
-        const int lg_max = 1 + int(std::ceil(std::log2(double(std::max<int64_t>({nj, n2, 64}) + 1))));
+        const u64* all_rows = &p->dsum()->counts[1];
         int lg = std::min(14, lg_max);
-        while (nrows > 0) {
-            if ((st = run_tier(2, lg))) return st;
-            if (nrows > 0 && lg >= lg_max) return fail(p, MSC_ERR_CUDA, "internal: a path-count row does not fit");
-            lg = std::min(lg + 4, lg_max);
+        if (first_tier == 0) {
+            if ((st = launch(0, nullptr, all_rows, lists[0], ctr + C_DEFER0, 0, false))) return st;
+            if ((st = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return st;
+            if ((st = launch(1, lists[0], ctr + C_DEFER0, lists[1], ctr + C_DEFER1, 0, false))) return st;
+            if ((st = launch(2, lists[1], ctr + C_DEFER1, lists[0], ctr + C_DEFER2, lg, true))) return st;
+        } else if (first_tier == 1) {
+            if ((st = launch(1, nullptr, all_rows, lists[1], ctr + C_DEFER1, 0, false))) return st;
+            if ((st = launch(2, lists[1], ctr + C_DEFER1, lists[0], ctr + C_DEFER2, lg, true))) return st;
+        } else {
+            if ((st = launch(2, nullptr, all_rows, lists[0], ctr + C_DEFER2, lg, true))) return st;
         }
-        // row pointers of D* (the scan also gives nnz), then the counters, in one round trip
+        if (!cap_mode) {
+            // rows that outgrow the tier-2 tables: bigger tables, on the host's watch
+            if ((st = read_summary(p, s))) return st;
+            if (p->hsum->pc[C_CURSOR] > cap) {  // staging overflow: grow and redo the stage
+                cap = p->hsum->pc[C_CURSOR] + p->hsum->pc[C_CURSOR] / 4 + 1024 + slack;
+                uint32_t zero = 0;
+                if ((st = check_cuda(p, cudaMemcpyAsync(p->status_word(), &zero, sizeof(zero), cudaMemcpyHostToDevice, s),
+                                     "status reset")))
+                    return st;
+                continue;
+            }
+            int in = 0;
+            u64* in_ctr = ctr + C_DEFER2;
+            u64 left = p->hsum->pc[C_DEFER2];
+            while (left > 0) {
+                if (lg >= lg_max) return fail(p, MSC_ERR_CUDA, "internal: a path-count row does not fit");
+                lg = std::min(lg + 4, lg_max);
+                u64* out_ctr = in_ctr == ctr + C_DEFER2 ? ctr + C_DEFER1 : ctr + C_DEFER2;
+                if ((st = check_cuda(p, cudaMemsetAsync(out_ctr, 0, sizeof(u64), s), "memset"))) return st;
+                if ((st = launch(2, lists[in], in_ctr, lists[in ^ 1], out_ctr, lg, false))) return st;
+                if ((st = read_summary(p, s))) return st;
+                in ^= 1;
+                in_ctr = out_ctr;
+                left = *(p->hsum->pc + (out_ctr - ctr));
+            }
+        }
+        // D* row pointers (the scan also gives nnz), then the rows gathered into CSR
         if ((st = check_cuda(p,
-                             row_scan(p, a.row_len, n1, static_cast<int64_t*>(p->dstar_rowptr.ptr),
-                                      static_cast<u64*>(p->minor_scan.ptr), s),
+                             row_scan(p, static_cast<const uint32_t*>(p->pc_rowlen.ptr), all_rows, n1cap,
+                                      static_cast<int64_t*>(p->dstar_rowptr.ptr), static_cast<u64*>(p->minor_scan.ptr),
+                                      s, &p->dsum()->dstar_nnz),
                              "D* row scan")))
             return st;
-        u64 h[8];
-        int64_t nnz = 0;
-        if ((st = check_cuda(p, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s), "counter copy")))
-            return st;
-        if ((st = check_cuda(p, cudaMemcpyAsync(&nnz, static_cast<int64_t*>(p->dstar_rowptr.ptr) + n1, sizeof(nnz),
-                                                cudaMemcpyDeviceToHost, s),
-                             "nnz copy")))
-            return st;
-        if ((st = check_cuda(p, cudaStreamSynchronize(s), "path count sync"))) return st;
-        if (h[C_CURSOR] > cap) {  // staging overflow: grow and redo the stage
-            uint32_t zero = 0;
-            if ((st = check_cuda(p, cudaMemcpyAsync(p->status.ptr, &zero, sizeof(zero), cudaMemcpyHostToDevice, s),
-                                 "status reset")))
-                return st;
-            cap = h[C_CURSOR] + h[C_CURSOR] / 4 + 1024;
-            continue;
-        }
-        p->dstar_nnz = nnz;
-        p->stats.nnz_Dstar = nnz;
-        p->stats.max_path_count = h[C_MAX];
-        p->stats.n_iter = int64_t(h[C_ITER]);
-        p->stats.n_frontier_entries = int64_t(h[C_ENTRIES]);
-        if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
-        if ((st = ensure(p, p->dstar_count, sizeof(u64) * size_t(nnz ? nnz : 1)))) return st;
-        if (n1) {
-            gather_rows<<<int((n1 + 255) / 256), 256, 0, s>>>(
-                n1, a.row_start, static_cast<const int64_t*>(p->dstar_rowptr.ptr), a.out_col, a.out_cnt,
+        if (n1cap) {
+            gather_rows<<<grid_cap(p, n1cap, 256), 256, 0, s>>>(
+                all_rows, n1cap, a.row_start, static_cast<const int64_t*>(p->dstar_rowptr.ptr), a.out_col, a.out_cnt,
                 static_cast<uint32_t*>(p->dstar_col.ptr), static_cast<u64*>(p->dstar_count.ptr));
             launched(p);
         }
+        p->pc_staging_cap = int64_t(cap);
         return check_cuda(p, cudaGetLastError(), "gather launch");
     }
     return fail(p, MSC_ERR_CUDA, "internal: D* staging did not converge");

@@ -15,8 +15,9 @@
 //    by one bit where the step is along x) feed it.  Sweep k+1 changes the bitmap iff BFS level
 //    k+1 is non-empty, so the level count is the paper's.
 //  * Every access is a coalesced word of a row, where a queue frontier scatters a 4-byte access
-//    per node over the whole grid.  Sweeps run in batches between host checks of their
-//    "changed" flags; a sweep after convergence only copies.
+//    per node over the whole grid.  One loop iteration is two sweeps (A -> B, B -> A, so the
+//    set always ends in A) and a one-thread decision kernel; the loop is a conditional WHILE node
+//    when the pipeline runs as a graph, so no level needs a host round trip.
 //
 // Sec. 3.3 / Sec. 3.5 "Gradient path counting": a junction is a reachable 1-cell that is not a
 // 1-saddle and has out-degree > 1.  One warp per bitmap word (a lane per 1-cell) evaluates the
@@ -31,7 +32,6 @@ namespace msc {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int SWEEP_BATCH = 4;  // sweeps between host checks
 
 __device__ __forceinline__ int other_axis(int a, int j) { return j == 0 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2); }
 
@@ -177,6 +177,26 @@ __global__ void __launch_bounds__(THREADS) reach_sweep(Geom g, const uint4* __re
     if (__syncthreads_or(grew) && threadIdx.x == 0) *changed = 1u;
 }
 
+// Level 0: the 1-saddles, if there are any.
+__global__ void reach_start(Summary* sum) { sum->levels = sum->counts[1] > 0 ? 1 : 0; }
+
+// End of one loop iteration (two sweeps): the non-empty levels found, and the continue decision
+// (while the second sweep still grew the set, up to the iteration cap).
+__global__ void reach_decide(Summary* sum, int64_t max_iter, cudaGraphConditionalHandle h, int use_handle) {
+    const uint32_t c0 = sum->loop_flag[0], c1 = sum->loop_flag[1];
+    sum->loop_flag[0] = 0;
+    sum->loop_flag[1] = 0;
+    ++sum->sweep_iters;
+    sum->levels += (c0 ? 1 : 0) + (c1 ? 1 : 0);
+    bool more = c1 != 0;
+    if (more && int64_t(sum->levels) >= max_iter) {
+        sum->status |= ST_ITER;
+        more = false;
+    }
+    sum->loop_flag[3] = more ? 1u : 0u;
+    if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // Down-quad bits of the quads with even axis K owned by vertex (x + DX, y + DY, z + DZ).
 template <int K, int DX, int DY, int DZ>
 __device__ __forceinline__ uint32_t quad_row(const uint32_t* __restrict__ qdown, const Rows& r) {
@@ -287,6 +307,20 @@ int grid_for(const Plan* p, int64_t threads) {
     return int(std::max<int64_t>(1, std::min(want, cap)));
 }
 
+struct SweepCtx {
+    dim3 grid;
+    const uint4* masks;
+    uint32_t* a;
+    uint32_t* b;
+};
+
+void sweep_body(Plan* p, cudaStream_t s, cudaGraphConditionalHandle h, void* ctx) {
+    const SweepCtx& c = *static_cast<SweepCtx*>(ctx);
+    reach_sweep<<<c.grid, THREADS, 0, s>>>(p->g, c.masks, c.a, c.b, &p->dsum()->loop_flag[0]);
+    reach_sweep<<<c.grid, THREADS, 0, s>>>(p->g, c.masks, c.b, c.a, &p->dsum()->loop_flag[1]);
+    reach_decide<<<1, 1, 0, s>>>(p->dsum(), p->opts.max_iterations, h, h != 0);
+}
+
 }  // namespace
 
 msc_status run_reachability(Plan* p, cudaStream_t s) {
@@ -298,40 +332,16 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->reach_tmp, sizeof(uint32_t) * size_t(nw)))) return st;
     if ((st = ensure(p, p->reach_masks, sizeof(uint4) * size_t(nw)))) return st;
     if ((st = ensure(p, p->reach_qdown, sizeof(uint32_t) * 3 * size_t(nrw)))) return st;
-    if ((st = ensure(p, p->reach_flags, sizeof(uint32_t) * SWEEP_BATCH))) return st;
     auto* masks = static_cast<uint4*>(p->reach_masks.ptr);
-    auto* flags = static_cast<uint32_t*>(p->reach_flags.ptr);
-    uint32_t* buf[2] = {static_cast<uint32_t*>(p->visited.ptr), static_cast<uint32_t*>(p->reach_tmp.ptr)};
-    reach_init<<<grid_for(p, nrw * 32), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, buf[0],
-                                                         buf[1], static_cast<uint32_t*>(p->reach_qdown.ptr));
-    launched(p);
+    uint32_t* A = static_cast<uint32_t*>(p->visited.ptr);
+    uint32_t* B = static_cast<uint32_t*>(p->reach_tmp.ptr);
+    reach_init<<<grid_for(p, nrw * 32), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, A, B,
+                                                         static_cast<uint32_t*>(p->reach_qdown.ptr));
+    reach_start<<<1, 1, 0, s>>>(p->dsum());
+    launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
-    const dim3 sweep_grid(unsigned((nrw + THREADS - 1) / THREADS), 3);
-    int cur = 0;
-    int64_t levels = p->counts[1] > 0 ? 1 : 0;
-    bool done = p->counts[1] == 0;
-    while (!done) {
-        if ((st = check_cuda(p, cudaMemsetAsync(flags, 0, sizeof(uint32_t) * SWEEP_BATCH, s), "memset flags")))
-            return st;
-        for (int k = 0; k < SWEEP_BATCH; ++k, cur ^= 1)
-            reach_sweep<<<sweep_grid, THREADS, 0, s>>>(g, masks, buf[cur], buf[cur ^ 1], flags + k);
-        launched(p, SWEEP_BATCH);
-        uint32_t h[SWEEP_BATCH];
-        if ((st = check_cuda(p, cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s), "flags copy")))
-            return st;
-        if ((st = check_cuda(p, cudaStreamSynchronize(s), "reach sync"))) return st;
-        for (int k = 0; k < SWEEP_BATCH && !done; ++k) {
-            if (!h[k]) {
-                done = true;
-            } else if (++levels > p->opts.max_iterations) {
-                return fail(p, MSC_ERR_ITER_LIMIT, "reachability exceeded the iteration cap");
-            }
-        }
-    }
-    // the converged set is in buf[cur]; make it the plan's visited bitmap
-    if (cur == 1) std::swap(p->visited, p->reach_tmp);
-    p->stats.n_bfs_levels = levels;
-    return check_cuda(p, cudaGetLastError(), "reach sweep launch");
+    SweepCtx ctx{dim3(unsigned((nrw + THREADS - 1) / THREADS), 3), masks, A, B};
+    return run_loop(p, s, 1, 3, sweep_body, &ctx);
 }
 
 msc_status run_junctions(Plan* p, cudaStream_t s) {
@@ -341,31 +351,30 @@ msc_status run_junctions(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->junc_bits, sizeof(uint32_t) * size_t(nw)))) return st;
     if ((st = ensure(p, p->junc_prefix, sizeof(uint32_t) * size_t(nw)))) return st;
     if ((st = ensure(p, p->node_info, sizeof(uint32_t) * 3 * size_t(g.nverts)))) return st;
-    if ((st = ensure(p, p->reach_count, sizeof(unsigned long long)))) return st;
-    auto* cnt = static_cast<unsigned long long*>(p->reach_count.ptr);
-    if ((st = check_cuda(p, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s), "memset count"))) return st;
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
     const dim3 grid(unsigned(std::max(1, grid_for(p, nrw * 32) / 3)), 3);
     classify_reached<<<grid, THREADS, 0, s>>>(
         g, static_cast<const uint32_t*>(p->words.ptr), static_cast<const uint32_t*>(p->visited.ptr),
         static_cast<const uint4*>(p->reach_masks.ptr), static_cast<const uint32_t*>(p->reach_qdown.ptr),
         static_cast<const uint32_t*>(p->crit_bits.ptr), static_cast<uint32_t*>(p->node_info.ptr),
-        static_cast<uint32_t*>(p->junc_bits.ptr), cnt);
+        static_cast<uint32_t*>(p->junc_bits.ptr), &p->dsum()->reached);
     launched(p);
     if ((st = check_cuda(p, cudaGetLastError(), "classify_reached launch"))) return st;
     EdgeSource src{};
     src.g = g;
     src.bits = static_cast<const uint32_t*>(p->junc_bits.ptr);
     src.prefix = static_cast<uint32_t*>(p->junc_prefix.ptr);
-    src.status = static_cast<uint32_t*>(p->status.ptr);
-    unsigned long long tot = 0, reached = 0;
-    if ((st = compaction_count(p, s, src, 1, &tot, cnt, &reached))) return st;  // synchronises the stream
-    p->stats.n_reachable = int64_t(reached);
-    p->n_junctions = int64_t(tot);
-    p->stats.n_junctions = int64_t(tot);
-    if ((st = ensure(p, p->junc_cells, sizeof(uint32_t) * size_t(tot ? tot : 1)))) return st;
+    src.status = p->status_word();
+    if ((st = compaction_sums(p, s, src, 1, &p->dsum()->n_junctions))) return st;
+    int64_t cap = p->caps.nj;
+    if (!p->capturing) {  // size the list exactly
+        if ((st = read_summary(p, s))) return st;
+        cap = int64_t(p->hsum->n_junctions);
+        p->n_junctions = cap;
+    }
+    if ((st = ensure(p, p->junc_cells, sizeof(uint32_t) * size_t(cap ? cap : 1)))) return st;
     src.out = static_cast<uint32_t*>(p->junc_cells.ptr);
-    src.cap = tot;
+    src.cap = uint64_t(cap);
     return compaction_emit(p, s, src, 1);
 }
 

@@ -1,6 +1,8 @@
 // Exclusive scan of uint32 row counts into int64 CSR row pointers (rowptr[n] = nnz), the
 // prefix-sum primitive of Sec. 2.3 for CSR construction.  Three launches: block sums,
-// a single-block scan of those sums, and the block-local scan plus offset.
+// a single-block scan of those sums, and the block-local scan plus offset.  The row count is
+// either known on the host, or read on the device (n_dev, clamped to the capacity the grid was
+// sized for), so that a pipeline can scan a row count it has not synchronised on.
 #pragma once
 
 #include "msc_internal.cuh"
@@ -11,8 +13,14 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 8;
 constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;
 
-static __global__ void __launch_bounds__(RS_THREADS) rowscan_reduce(const uint32_t* __restrict__ cnt, int64_t n,
-                                                             unsigned long long* __restrict__ sums) {
+__device__ __forceinline__ int64_t rows_of(const unsigned long long* n_dev, int64_t cap) {
+    return n_dev ? int64_t(min((unsigned long long)cap, *n_dev)) : cap;
+}
+
+static __global__ void __launch_bounds__(RS_THREADS) rowscan_reduce(const uint32_t* __restrict__ cnt,
+                                                                    const unsigned long long* n_dev, int64_t cap,
+                                                                    unsigned long long* __restrict__ sums) {
+    const int64_t n = rows_of(n_dev, cap);
     const int64_t base = int64_t(blockIdx.x) * RS_CHUNK;
     unsigned long long acc = 0;
     for (int j = 0; j < RS_ITEMS; ++j) {
@@ -65,9 +73,11 @@ static __global__ void __launch_bounds__(1024) rowscan_top(unsigned long long* s
     if (threadIdx.x == 0) *total = (long long)carry;
 }
 
-static __global__ void __launch_bounds__(RS_THREADS) rowscan_emit(const uint32_t* __restrict__ cnt, int64_t n,
-                                                           const unsigned long long* __restrict__ offs,
-                                                           int64_t* __restrict__ rowptr) {
+static __global__ void __launch_bounds__(RS_THREADS) rowscan_emit(const uint32_t* __restrict__ cnt,
+                                                                  const unsigned long long* n_dev, int64_t cap,
+                                                                  const unsigned long long* __restrict__ offs,
+                                                                  int64_t* __restrict__ rowptr) {
+    const int64_t n = rows_of(n_dev, cap);
     const int64_t base = int64_t(blockIdx.x) * RS_CHUNK + int64_t(threadIdx.x) * RS_ITEMS;
     uint32_t v[RS_ITEMS];
     unsigned long long acc = 0;
@@ -102,22 +112,28 @@ static __global__ void __launch_bounds__(RS_THREADS) rowscan_emit(const uint32_t
     }
 }
 
-static __global__ void rowscan_finish(int64_t* rowptr, int64_t n, const long long* total) { rowptr[n] = *total; }
+static __global__ void rowscan_finish(int64_t* rowptr, const unsigned long long* n_dev, int64_t cap,
+                                      const long long* total, unsigned long long* total_out) {
+    rowptr[rows_of(n_dev, cap)] = *total;
+    if (total_out) *total_out = (unsigned long long)*total;
+}
 
-// rowptr (n+1 int64) from cnt (n uint32); scratch holds >= ceil(n/RS_CHUNK) + 1 uint64.
-inline cudaError_t row_scan(Plan* p, const uint32_t* cnt, int64_t n, int64_t* rowptr,
-                            unsigned long long* scratch, cudaStream_t s) {
-    const int nb = int((n + RS_CHUNK - 1) / RS_CHUNK);
+// rowptr (n+1 int64) from cnt (n uint32), n = min(*n_dev, cap), or n = cap when n_dev is null;
+// the total also goes to *total_out when given.  scratch holds >= ceil(cap/RS_CHUNK) + 2 uint64.
+inline cudaError_t row_scan(Plan* p, const uint32_t* cnt, const unsigned long long* n_dev, int64_t cap,
+                            int64_t* rowptr, unsigned long long* scratch, cudaStream_t s,
+                            unsigned long long* total_out = nullptr) {
+    const int nb = int((cap + RS_CHUNK - 1) / RS_CHUNK);
     long long* total = reinterpret_cast<long long*>(scratch + (nb > 0 ? nb : 1));
     if (nb > 0) {
-        rowscan_reduce<<<nb, RS_THREADS, 0, s>>>(cnt, n, scratch);
+        rowscan_reduce<<<nb, RS_THREADS, 0, s>>>(cnt, n_dev, cap, scratch);
         rowscan_top<<<1, 1024, 0, s>>>(scratch, nb, total);
-        rowscan_emit<<<nb, RS_THREADS, 0, s>>>(cnt, n, scratch, rowptr);
+        rowscan_emit<<<nb, RS_THREADS, 0, s>>>(cnt, n_dev, cap, scratch, rowptr);
         launched(p, 3);
     } else {
         cudaMemsetAsync(total, 0, sizeof(long long), s);
     }
-    rowscan_finish<<<1, 1, 0, s>>>(rowptr, n, total);
+    rowscan_finish<<<1, 1, 0, s>>>(rowptr, n_dev, cap, total, total_out);
     launched(p);
     return cudaGetLastError();
 }

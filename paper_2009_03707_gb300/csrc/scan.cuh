@@ -206,31 +206,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_emit_kernel(Src src, int64_
     }
 }
 
-// Host driver, phase 1: block sums and per-sequence totals (copied to the host; syncs).  An
-// optional extra device counter is copied to *extra_host in the same round trip.
+// Host driver, phase 1: block sums, and per-sequence totals into d_totals[0..nseq) (device
+// memory; no host synchronisation).
 template <class Src>
-msc_status compaction_count(Plan* p, cudaStream_t s, const Src& src, int nseq, unsigned long long* host_totals,
-                            const unsigned long long* extra_dev = nullptr, unsigned long long* extra_host = nullptr) {
+msc_status compaction_sums(Plan* p, cudaStream_t s, const Src& src, int nseq, unsigned long long* d_totals) {
     const int64_t len = seq_length(p->g);
     const int bps = int((len + SCAN_CHUNK - 1) / SCAN_CHUNK);
     msc_status st;
     if ((st = ensure(p, p->scan_sums, sizeof(unsigned long long) * size_t(bps) * size_t(nseq)))) return st;
-    if ((st = ensure(p, p->totals, sizeof(unsigned long long) * 8))) return st;
     auto* sums = static_cast<unsigned long long*>(p->scan_sums.ptr);
-    auto* totals = static_cast<unsigned long long*>(p->totals.ptr);
     scan_reduce_kernel<Src><<<bps * nseq, SCAN_THREADS, 0, s>>>(src, len, bps, sums);
-    scan_top_kernel<<<nseq, 1024, 0, s>>>(sums, bps, totals);
+    scan_top_kernel<<<nseq, 1024, 0, s>>>(sums, bps, d_totals);
     launched(p, 2);
-    if ((st = check_cuda(p, cudaGetLastError(), "scan launch"))) return st;
-    if ((st = check_cuda(p, cudaMemcpyAsync(host_totals, totals, sizeof(unsigned long long) * size_t(nseq),
-                                            cudaMemcpyDeviceToHost, s),
-                         "scan totals copy")))
-        return st;
-    if (extra_dev && (st = check_cuda(p, cudaMemcpyAsync(extra_host, extra_dev, sizeof(unsigned long long),
-                                                         cudaMemcpyDeviceToHost, s),
-                                      "counter copy")))
-        return st;
-    return check_cuda(p, cudaStreamSynchronize(s), "scan sync");
+    return check_cuda(p, cudaGetLastError(), "scan launch");
 }
 
 // Host driver, phase 2: prefixes and ids (the Src's output pointers must be sized by now).

@@ -50,6 +50,9 @@ SIGNATURES = {
 }
 
 
+MSC_FLAG_NO_GRAPH = 1
+
+
 class MscOpts(ctypes.Structure):
     _fields_ = [("max_iterations", ctypes.c_int64), ("flags", ctypes.c_int32), ("path_count_tier", ctypes.c_int32)]
 
@@ -124,10 +127,10 @@ def _view(ptr, shape, typestr):
 class Plan:
     """Owns an msc_plan_t for one grid shape (nx, ny, nz)."""
 
-    def __init__(self, dims, max_iterations: int = 0, path_count_tier: int = 0):
+    def __init__(self, dims, max_iterations: int = 0, path_count_tier: int = 0, no_graph: bool = False):
         self.dims = tuple(int(d) for d in dims)
         arr = (ctypes.c_int64 * 3)(*self.dims)
-        opts = MscOpts(int(max_iterations), 0, int(path_count_tier))
+        opts = MscOpts(int(max_iterations), MSC_FLAG_NO_GRAPH if no_graph else 0, int(path_count_tier))
         h = ctypes.c_void_p()
         _check(lib.msc_plan(arr, ctypes.byref(opts), ctypes.byref(h)), what=f"msc_plan{self.dims}")
         self.handle = h
