@@ -148,8 +148,6 @@ msc_status run_loop(Plan* p, cudaStream_t s, int which, int body_launches,
                       "capture dependencies");
 }
 
-namespace {
-
 // MSC_FAULT = alloc@k | timeout | overflow: host-side fault injection for tests.
 void read_fault(Plan* p) {
     const char* f = std::getenv("MSC_FAULT");
@@ -225,8 +223,6 @@ msc_status finish_stage(Plan* p, cudaStream_t s) {
     return MSC_OK;
 }
 
-}  // namespace
-
 msc_status run_critical(Plan* p, cudaStream_t s) {
     const Geom& g = p->g;
     msc_status st;
@@ -284,6 +280,7 @@ void destroy_graph(Plan* p) {
     p->graph_exec = nullptr;
     p->graph = nullptr;
     p->graph_field = nullptr;
+    ++p->capture_epoch;
 }
 
 // Captures the pipeline for d_field.  The first capture only sizes the buffers for the
@@ -319,6 +316,29 @@ msc_status capture_graph(Plan* p, const float* d_field) {
         }
     }
     p->graph_field = d_field;
+    ++p->capture_epoch;
+    return MSC_OK;
+}
+
+msc_status finish_replay(Plan* p, cudaStream_t s) {
+    msc_status st;
+    const uint32_t word = p->hsum->status;
+    if (word) {
+        if ((st = check_cuda(p, cudaMemsetAsync(p->status_word(), 0, sizeof(uint32_t), s), "status clear")))
+            return st;
+        if ((word & ST_RETRY) && !(word & ~(ST_RETRY | ST_CAPACITY))) {
+            destroy_graph(p);
+            return MSC_NOT_READY;
+        }
+        return status_error(p, word);
+    }
+    absorb_summary(p);
+    p->stage_recorded = 0x3F;
+    p->stats.n_launches = p->graph_static_launches + p->loop_body_launches[0] * int64_t(p->hsum->jump_rounds) +
+                          p->loop_body_launches[1] * int64_t(p->hsum->sweep_iters);
+    p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = true;
+    p->have_junctions = p->have_trace = p->have_dstar = true;
+    ++p->graph_replays;
     return MSC_OK;
 }
 
@@ -591,25 +611,30 @@ static msc_status compute_graph(Plan* p, const float* d_field, cudaStream_t s) {
     p->stage_recorded = 0;
     if ((st = msc::check_cuda(p, cudaGraphLaunch(p->graph_exec, s), "graph launch"))) return st;
     if ((st = msc::read_summary(p, s))) return st;
-    const uint32_t word = p->hsum->status;
-    if (word) {
-        if ((st = msc::check_cuda(p, cudaMemsetAsync(p->status_word(), 0, sizeof(uint32_t), s), "status clear")))
-            return st;
-        if ((word & msc::ST_RETRY) && !(word & ~(msc::ST_RETRY | msc::ST_CAPACITY))) {
-            msc::destroy_graph(p);
-            return MSC_NOT_READY;
-        }
-        return msc::status_error(p, word);
-    }
-    msc::absorb_summary(p);
-    p->stage_recorded = 0x3F;
-    p->stats.n_launches = p->graph_static_launches + p->loop_body_launches[0] * int64_t(p->hsum->jump_rounds) +
-                          p->loop_body_launches[1] * int64_t(p->hsum->sweep_iters);
-    p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = true;
-    p->have_junctions = p->have_trace = p->have_dstar = true;
-    ++p->graph_replays;
+    return msc::finish_replay(p, s);
+}
+
+}  // extern "C"
+
+namespace msc {
+// Every stage with host synchronisation and exact buffer sizes; the sizes plus headroom become
+// the capacities of the next captured graph.
+msc_status compute_synchronised(Plan* p, const float* d_field, cudaStream_t s) {
+    msc_status st;
+    if ((st = msc_gradient(static_cast<msc_plan_s*>(p), d_field, reinterpret_cast<msc_stream_t>(s)))) return st;
+    if ((st = ensure_extremum(p, s))) return st;
+    if ((st = ensure_dstar(p, s))) return st;
+    auto room = [](int64_t n) { return n + n / 4 + 1024; };
+    for (int k = 0; k < 4; ++k) p->caps.cells[k] = std::max(p->caps.cells[k], room(p->counts[k]));
+    p->caps.nj = std::max(p->caps.nj, room(p->n_junctions));
+    p->caps.staging = std::max<int64_t>(p->caps.staging, room(p->pc_staging_cap));
+    p->caps_ready = true;
+    destroy_graph(p);
     return MSC_OK;
 }
+}  // namespace msc
+
+extern "C" {
 
 msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t stream) {
     if (!plan || !d_field) return MSC_ERR_ARG;
@@ -617,23 +642,11 @@ msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t strea
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     msc_status st;
     if ((st = msc::bind_device(p))) return st;
-    const bool graphs = !(p->opts.flags & MSC_FLAG_NO_GRAPH) && p->fault_kind == 0;
-    if (graphs && p->caps_ready) {
+    if (msc::graphs_enabled(p) && p->caps_ready) {
         st = compute_graph(p, d_field, s);
         if (st != MSC_NOT_READY) return st;
     }
-    // synchronised run: every stage in turn, with exact buffer sizes
-    if ((st = msc_gradient(plan, d_field, stream))) return st;
-    if ((st = ensure_extremum(p, s))) return st;
-    if ((st = ensure_dstar(p, s))) return st;
-    // capacities for the graph of the next call: these sizes plus headroom
-    auto room = [](int64_t n) { return n + n / 4 + 1024; };
-    for (int k = 0; k < 4; ++k) p->caps.cells[k] = std::max(p->caps.cells[k], room(p->counts[k]));
-    p->caps.nj = std::max(p->caps.nj, room(p->n_junctions));
-    p->caps.staging = std::max<int64_t>(p->caps.staging, room(p->pc_staging_cap));
-    p->caps_ready = true;
-    msc::destroy_graph(p);
-    return MSC_OK;
+    return msc::compute_synchronised(p, d_field, s);
 }
 
 msc_status msc_get_stats(msc_plan_t plan, msc_stats* out) {

@@ -107,6 +107,7 @@ struct Plan {
     uint32_t stage_recorded = 0;      // stages whose two events belong to the same pass
     bool caps_ready = false;          // a synchronised run has measured the sizes
     int64_t graph_replays = 0;
+    int64_t capture_epoch = 0;        // bumped whenever the plan's graph is captured or dropped
 
     int64_t counts[4] = {0, 0, 0, 0};
     int64_t n_junctions = 0;
@@ -155,6 +156,19 @@ msc_status fail(Plan* p, msc_status st, const std::string& msg);
 msc_status check_cuda(Plan* p, cudaError_t e, const char* what);
 msc_status check_status_word(Plan* p, cudaStream_t s);  // syncs, reads and clears the status word
 msc_status status_error(Plan* p, uint32_t word);        // the error a non-zero status word stands for
+
+// Pipeline graphs (api.cu).  enqueue_pipeline issues every stage without host synchronisation
+// (p->capturing set); capture_graph records the plan's own graph; finish_replay takes a replay's
+// summary (already in p->hsum): MSC_OK, MSC_NOT_READY (rerun synchronised) or the error;
+// compute_synchronised runs a pass with host synchronisation and sets the capacities.
+msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s);
+msc_status capture_graph(Plan* p, const float* d_field);
+void destroy_graph(Plan* p);
+msc_status finish_replay(Plan* p, cudaStream_t s);
+msc_status compute_synchronised(Plan* p, const float* d_field, cudaStream_t s);
+msc_status bind_device(Plan* p);
+void invalidate(Plan* p);
+inline bool graphs_enabled(const Plan* p) { return !(p->opts.flags & MSC_FLAG_NO_GRAPH) && p->fault_kind == 0; }
 msc_status read_summary(Plan* p, cudaStream_t s);       // syncs; copies the summary to p->hsum
 
 // Stage launchers

@@ -93,3 +93,44 @@ def test_batch_reports_errors_per_ticket():
     ticket, _ = batch.msc_batch_submit([gpu_field(random_field((8, 8, 8), 2)), gpu_field(bad)])
     assert batch.msc_batch_wait(ticket) == 2  # MSC_ERR_NAN
     batch.close()
+
+
+def test_group_graph_replays_equal_alone():
+    """Once every plan of a submission has run, the submission runs as one graph with a branch per
+    volume; its replays (same plans, same buffers, new contents) must give each volume's own
+    results."""
+    m = msc()
+    vols = _volumes()
+    dev = [gpu_field(f) for f in vols]
+    batch = m.Batch(n_workers=2)
+    ticket, plans = batch.msc_batch_submit(dev)  # first run of every plan: one job per volume
+    assert batch.msc_batch_wait(ticket) == 0
+    for rnd in range(3):  # group capture, then replays
+        if rnd == 2:  # new contents in the same buffers
+            vols = [np.ascontiguousarray(np.roll(f, 3, axis=0)) for f in vols]
+            for d, f in zip(dev, vols):
+                d.copy_(gpu_field(f))
+        ticket, _ = batch.msc_batch_submit(dev, plans)
+        assert batch.msc_batch_wait(ticket) == 0
+        for f, plan in zip(vols, plans):
+            _same(_outputs(m, plan), _alone(m, f))
+    batch.close()
+
+
+def test_group_volume_outgrowing_its_branch_is_rerun():
+    m = msc()
+    smooth = [fields.grf((30, 28, 26), 4.5, seed=20 + i) for i in range(3)]
+    dev = [gpu_field(f) for f in smooth]
+    batch = m.Batch(n_workers=2)
+    ticket, plans = batch.msc_batch_submit(dev)
+    assert batch.msc_batch_wait(ticket) == 0
+    ticket, _ = batch.msc_batch_submit(dev, plans)  # captured with the smooth fields' sizes
+    assert batch.msc_batch_wait(ticket) == 0
+    rough = random_field((30, 28, 26), 31, "normal")
+    dev[1].copy_(gpu_field(rough))
+    for _ in range(2):
+        ticket, _ = batch.msc_batch_submit(dev, plans)
+        assert batch.msc_batch_wait(ticket) == 0
+        for f, plan in zip([smooth[0], rough, smooth[2]], plans):
+            _same(_outputs(m, plan), _alone(m, f))
+    batch.close()
