@@ -334,7 +334,12 @@ def run_gpu(args):
                    "critical_counts": counts, "nnz_Dstar": last["nnz_Dstar"], "n_iter": last["n_iter"],
                    "graph": {k: last[k] for k in ("n_reachable", "n_bfs_levels", "n_junctions", "nnz_A", "nnz_B",
                                                   "nnz_Bstar", "nnz_D", "n_pointer_jumps", "n_frontier_entries")},
-                   "max_path_count": str(last["max_path_count"])},
+                   "max_path_count": str(last["max_path_count"]),
+                   "gradient_tile": "x".join(str(v) for v in (32, last["gradient_tile"] & 0xFF,
+                                                             (last["gradient_tile"] >> 8) & 0xFF))
+                   + f" vertices, {last['gradient_tile'] >> 16} threads (autotuned)",
+                   "path_count_method": {1: "row-wise products", 2: "junction waves"}.get(
+                       last["path_count_method"], "?") + " (chosen automatically)"},
         "e2e": {"value": agg["e2e_value"], "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(bo)},
         "gpu_launches": launches,

@@ -64,6 +64,19 @@ typedef struct msc_opts {
     int32_t path_count_tier; /* first tier of the row-wise path count: 0 = per-thread registers
                                 (default), 1 = per-warp shared-memory tables, 2 = per-CTA global
                                 tables.  Results are identical; tests use it to cover every tier. */
+    int32_t gradient_tile;   /* 0 = autotuned (the lower-star tile variant that runs fastest for the
+                                grid shape on this device, timed once per shape on the first
+                                synchronised run); 1..9 = force variant (TY,TZ,threads) =
+                                (8,8,512), (8,4,256), (4,8,256), (8,16,512), (16,8,512),
+                                (16,8,1024), (16,16,512), (16,16,1024), (32,8,1024); a tile row
+                                is 32 vertices.  Results are identical. */
+    int32_t path_count_method; /* 1 = the paper's iteration A <- A B, row by row (path_count_tier
+                                  picks its first tier); 2 = junction waves: J = B* + B J once per
+                                  junction in topological order of the minor, then D* = D + A J;
+                                  0 = automatic (default): the plan's first run uses the waves and
+                                  later runs use the row-wise products if the minor is at most 64
+                                  levels deep (their work grows with the depth).  The counts are
+                                  identical. */
 } msc_opts;
 
 /* Per-stage diagnostics (Sec. 4.2 "performance analysis" quantities). Times are the
@@ -75,15 +88,20 @@ typedef struct msc_stats {
     int64_t n_bfs_levels;     /* non-empty BFS levels, level 0 = the 1-saddles */
     int64_t n_junctions;      /* junction nodes of the DAG minor */
     int64_t nnz_A, nnz_B, nnz_Bstar, nnz_D, nnz_Dstar;
-    int64_t n_iter;           /* non-zero iterates A B^k of the product loop */
+    int64_t n_iter;           /* non-zero iterates A B^k (junction waves: the same number, 1 + the
+                                 longest chain of junctions) */
     int64_t n_pointer_jumps;  /* pointer-jumping rounds of the extremum forests */
     uint64_t max_path_count;  /* largest entry of D* */
     int64_t peak_device_bytes;
     int64_t n_launches;       /* kernels this plan launched since the last msc_gradient */
     float ms_gradient, ms_critical, ms_extremum, ms_reachability, ms_minor, ms_path_count;
-    float ms_rows_kernel;      /* the row-wise product kernel alone (tier 0), CUDA events */
+    float ms_rows_kernel;      /* the product kernels: the junction waves and D* rows, or the
+                                  row-wise tier 0 (CUDA events) */
     float ms_trace_kernel;     /* the simple-path tracing kernel alone, CUDA events */
-    int64_t n_frontier_entries; /* sum over 1-saddles and iterations of the frontier sizes */
+    int64_t n_frontier_entries; /* row-wise method: sum over 1-saddles and iterations of the frontier
+                                   sizes; junction waves: J-row entries merged (pool slots) */
+    int64_t gradient_tile;      /* the lower-star tile used: TY | TZ << 8 | threads << 16 */
+    int64_t path_count_method;  /* the path-count method of the last run: 1 row-wise, 2 waves */
 } msc_stats;
 
 /* ---- plan ----------------------------------------------------------------------------

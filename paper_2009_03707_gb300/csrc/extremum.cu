@@ -142,13 +142,10 @@ __device__ __forceinline__ CellCoord decode_cell(const Geom& g, uint32_t id) {
 }
 
 // 1-saddle arcs: the minima of the edge's lower-coordinate and upper-coordinate vertices.
-// Count of a list produced earlier in the pass, clamped to the capacity the launch was sized for.
+// Count of a list produced earlier in the pass; 0 (nothing to do) when the pass is to be rerun.
 __device__ __forceinline__ int64_t clamp_count(const unsigned long long* n_dev, int64_t cap, uint32_t* status) {
     const unsigned long long n = *n_dev;
-    if (n > (unsigned long long)cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_RETRY);
-        return cap;
-    }
+    if (pass_retrying(status) || !count_fits(status, n, cap)) return 0;
     return int64_t(n);
 }
 

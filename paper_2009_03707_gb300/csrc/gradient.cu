@@ -20,6 +20,10 @@
 //    warps then claim 32 consecutive stars at a time, largest first.
 //  * A second, bandwidth-bound kernel turns the finished words into per-slot critical bitmaps:
 //    one warp ballot per slot gives 32 vertices' bits -- the input of the ordered compaction.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "lower_star.cuh"
 #include "msc_internal.cuh"
 
@@ -27,10 +31,7 @@ namespace msc {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, TZ = 8;               // owned tile
-constexpr int FX = TX + 2, FY = TY + 2, FZ = TZ + 2;  // field keys staged (x0-1 .. x0+TX)
-constexpr int NOWN = TX * TY * TZ;
-constexpr int THREADS = 512;
+constexpr int TX = 32;  // a tile row is one warp wide
 constexpr uint32_t OUTSIDE_KEY = 0xFFFFFFFFu;
 
 using star::pdx;
@@ -44,7 +45,12 @@ __device__ __forceinline__ uint32_t order_key(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// The owned tile is TX x TY x TZ vertices, run by THREADS threads (a tuning choice: every
+// variant computes the same words).
+template <int TY, int TZ, int THREADS>
 struct Shared {
+    static constexpr int FX = TX + 2, FY = TY + 2, FZ = TZ + 2;  // field keys staged (x0-1 .. x0+TX)
+    static constexpr int NOWN = TX * TY * TZ;
     uint32_t fkey[FZ][FY][FX];   // order keys of the field tile (OUTSIDE_KEY off-grid)
     uint32_t words[TZ][TY][TX];  // packed codes of the owned tile
     uint32_t inl[NOWN];          // lower-star mask of every owned vertex (0: off-grid)
@@ -57,11 +63,14 @@ struct Shared {
     uint32_t emit_info[27];
 };
 
-__global__ void __launch_bounds__(THREADS) gradient_kernel(Geom g, const float* __restrict__ field,
+template <int TY, int TZ, int THREADS>
+__global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS)) gradient_kernel(Geom g, const float* __restrict__ field,
                                                            uint32_t* __restrict__ words_out,
                                                            uint32_t* __restrict__ status) {
+    using S = Shared<TY, TZ, THREADS>;
+    constexpr int FX = S::FX, FY = S::FY, FZ = S::FZ, NOWN = S::NOWN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
+    S& sh = *reinterpret_cast<S*>(smem_raw);
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
 
@@ -192,18 +201,98 @@ __global__ void __launch_bounds__(256) critical_bitmaps(Geom g, const uint32_t* 
     if (lane < 8) crit_bits[g.slot_word(lane, z, y, w)] = mine;
 }
 
-cudaError_t launch_gradient(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
-                            uint32_t* status, cudaStream_t s) {
-    const size_t smem = sizeof(Shared);
+// Tile variants the autotuner chooses from: (TY, TZ, threads).
+struct Variant {
+    int ty, tz, threads;
+};
+constexpr Variant VARIANTS[] = {{8, 8, 512},   {8, 4, 256},   {4, 8, 256},    {8, 16, 512}, {16, 8, 512},
+                                {16, 8, 1024}, {16, 16, 512}, {16, 16, 1024}, {32, 8, 1024}};
+constexpr int N_VARIANTS = int(sizeof(VARIANTS) / sizeof(VARIANTS[0]));
+
+template <int TY, int TZ, int THREADS>
+cudaError_t launch_tile(const Geom& g, const float* d_field, uint32_t* words, uint32_t* status, cudaStream_t s) {
+    const size_t smem = sizeof(Shared<TY, TZ, THREADS>);
     // set on every call: the attribute is per device, and plans may live on several devices
-    cudaError_t e = cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e =
+        cudaFuncSetAttribute(gradient_kernel<TY, TZ, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * size_t(g.nverts), s)) != cudaSuccess) return e;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + TZ - 1) / TZ);
-    gradient_kernel<<<grid, THREADS, smem, s>>>(g, d_field, words, status);
+    gradient_kernel<TY, TZ, THREADS><<<grid, THREADS, smem, s>>>(g, d_field, words, status);
+    return cudaGetLastError();
+}
+
+// The words of a whole grid with tile variant v: zero them, then the lower-star kernel.
+cudaError_t launch_words(int v, const Geom& g, const float* d_field, uint32_t* words, uint32_t* status,
+                         cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * size_t(g.nverts), s);
+    if (e != cudaSuccess) return e;
+    switch (v) {
+        case 1: return launch_tile<8, 4, 256>(g, d_field, words, status, s);
+        case 2: return launch_tile<4, 8, 256>(g, d_field, words, status, s);
+        case 3: return launch_tile<8, 16, 512>(g, d_field, words, status, s);
+        case 4: return launch_tile<16, 8, 512>(g, d_field, words, status, s);
+        case 5: return launch_tile<16, 8, 1024>(g, d_field, words, status, s);
+        case 6: return launch_tile<16, 16, 512>(g, d_field, words, status, s);
+        case 7: return launch_tile<16, 16, 1024>(g, d_field, words, status, s);
+        case 8: return launch_tile<32, 8, 1024>(g, d_field, words, status, s);
+        default: return launch_tile<8, 8, 512>(g, d_field, words, status, s);
+    }
+}
+
+cudaError_t launch_gradient(int v, const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
+                            uint32_t* status, cudaStream_t s) {
+    cudaError_t e = launch_words(v, g, d_field, words, status, s);
+    if (e != cudaSuccess) return e;
     const int64_t warps = int64_t(g.nz) * g.ny * g.W;
     critical_bitmaps<<<int((warps * 32 + 255) / 256), 256, 0, s>>>(g, words, crit_bits);
     return cudaGetLastError();
+}
+
+// Autotuning: the tile variant that computes this grid's words fastest on this device, timed on
+// the field at hand (every variant gives the same words) and remembered per device and shape.
+std::mutex tune_mu;
+std::map<std::tuple<int, int, int, int>, int> tune_cache;
+
+int tune_variant(Plan* p, const float* d_field, cudaStream_t s) {
+    const Geom& g = p->g;
+    const auto key = std::make_tuple(p->device, g.nx, g.ny, g.nz);
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        auto it = tune_cache.find(key);
+        if (it != tune_cache.end()) return it->second;
+    }
+    auto* words = static_cast<uint32_t*>(p->words.ptr);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 0;
+    for (int v = 0; v < N_VARIANTS; ++v) {
+        // one warm-up launch, then the best of two timed ones
+        if (launch_words(v, g, d_field, words, p->status_word(), s) != cudaSuccess) break;
+        float ms = 0;
+        for (int r = 0; r < 2; ++r) {
+            cudaEventRecord(e0, s);
+            launch_words(v, g, d_field, words, p->status_word(), s);
+            cudaEventRecord(e1, s);
+            float t = 0;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) t = 1e30f;
+            ms = r == 0 ? t : std::min(ms, t);
+        }
+        if (v == 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(tune_mu);
+    tune_cache[key] = best;
+    return best;
 }
 
 }  // namespace
@@ -213,9 +302,14 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     msc_status st;
     if ((st = ensure(p, p->words, sizeof(uint32_t) * size_t(g.nverts)))) return st;
     if ((st = ensure(p, p->crit_bits, sizeof(uint32_t) * size_t(g.slot_words())))) return st;
+    // the tile variant: forced by the plan's options, else tuned on the first synchronised run
+    if (p->opts.gradient_tile > 0) p->grad_variant = std::min(int(p->opts.gradient_tile), N_VARIANTS) - 1;
+    else if (p->grad_variant < 0 && !p->capturing) p->grad_variant = tune_variant(p, d_field, s);
+    const int v = std::max(0, p->grad_variant);
+    p->stats.gradient_tile = VARIANTS[v].ty | (VARIANTS[v].tz << 8) | (int64_t(VARIANTS[v].threads) << 16);
     launched(p, 2);
     return check_cuda(p,
-                      launch_gradient(g, d_field, static_cast<uint32_t*>(p->words.ptr),
+                      launch_gradient(v, g, d_field, static_cast<uint32_t*>(p->words.ptr),
                                       static_cast<uint32_t*>(p->crit_bits.ptr), p->status_word(), s),
                       "gradient launch");
 }
@@ -224,7 +318,7 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
 // no-allocation entry point, static_entry.cu).
 cudaError_t launch_gradient_raw(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
                                 uint32_t* status, cudaStream_t s) {
-    return launch_gradient(g, d_field, words, crit_bits, status, s);
+    return launch_gradient(0, g, d_field, words, crit_bits, status, s);
 }
 
 }  // namespace msc

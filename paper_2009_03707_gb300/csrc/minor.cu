@@ -80,12 +80,8 @@ __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t ki
 // per step), and the destinations are ranked and counted per matrix row.  Grid-stride over the
 // sources, whose numbers are read on the device.
 __global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
-    unsigned long long n1 = *a.n1_dev, nj = *a.nj_dev;
-    if (n1 > (unsigned long long)a.cap1 || nj > (unsigned long long)a.capj) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_RETRY);
-        n1 = min(n1, (unsigned long long)a.cap1);
-        nj = min(nj, (unsigned long long)a.capj);
-    }
+    const unsigned long long n1 = *a.n1_dev, nj = *a.nj_dev;
+    if (pass_retrying(a.status) || !count_fits(a.status, n1, a.cap1) || !count_fits(a.status, nj, a.capj)) return;
     const int64_t N1 = int64_t(n1), NJ = int64_t(nj);
     unsigned long long nnz[4] = {0, 0, 0, 0};
     for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < N1 + NJ;

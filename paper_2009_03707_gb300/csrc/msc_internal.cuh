@@ -25,6 +25,19 @@ enum StatusBit : uint32_t {
     ST_RETRY = 1u << 6,      // a replayed pipeline outgrew a capacity fixed at capture: rerun and re-capture
 };
 
+// A count produced earlier in the pass, against the capacity a launch was sized for.  When a count
+// outgrows its capacity (possible only in a replayed graph) the pass is rerun, so every kernel
+// that depends on counts must then do nothing at all -- ranks stored by earlier kernels may point
+// past its buffers.  count_fits raises ST_RETRY and says no; pass_retrying sees an earlier one.
+__device__ __forceinline__ bool pass_retrying(const uint32_t* status) {
+    return (*reinterpret_cast<const volatile uint32_t*>(status) & ST_RETRY) != 0;
+}
+__device__ __forceinline__ bool count_fits(uint32_t* status, unsigned long long n, int64_t cap) {
+    if (n <= (unsigned long long)cap) return true;
+    if (threadIdx.x == 0) atomicOr(status, ST_RETRY);
+    return false;
+}
+
 // ---- per-pass results the host needs, kept on the device and read back in one copy --------
 // Path-count counter slots in Summary::pc.
 enum PcCounter { PC_CURSOR = 0, PC_MAX = 1, PC_ITER = 2, PC_ENTRIES = 3, PC_DEFER0 = 4, PC_DEFER1 = 5, PC_NEXT = 6,
@@ -39,6 +52,12 @@ struct Summary {
     unsigned long long minor_nnz[4];  // distinct entries of A, B, B*, D
     unsigned long long pc[8];         // path-count counters (pathcount.cu)
     unsigned long long dstar_nnz;
+    unsigned long long dp_wave_done;      // junction DP: junctions done in the current wave
+    unsigned long long dp_pool_used;      // junction DP: J-row pool slots taken
+    unsigned long long dp_junctions_done;
+    unsigned long long dp_iters;          // iterations of the wave loop
+    unsigned int dp_wave;                 // the current wave
+    unsigned int pad2;
     uint32_t loop_flag[4];            // "changed" flags of the iterative stages; [3] = continue (host loops)
     uint32_t status;                  // StatusBit word
     uint32_t pad;
@@ -70,6 +89,7 @@ struct Plan {
     DeviceBuffer trace, trace_kinds, minor_rowcnt, minor_scan, minor_rowptr[4], minor_col[4], minor_mult[4];
     DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_col, pc_cnt, pc_gk, pc_gv, pc_gocc;
     DeviceBuffer dstar_rowptr, dstar_col, dstar_count;
+    DeviceBuffer dp_pend, dp_in_cnt, dp_in_ptr, dp_in_idx, dp_j_off, dp_j_len, dp_pool_col, dp_pool_cnt;
 
     template <class F>
     void for_each_buffer(F&& f) {
@@ -80,7 +100,8 @@ struct Plan {
                                &minor_rowptr[3], &minor_col[0], &minor_col[1], &minor_col[2], &minor_col[3],
                                &minor_mult[0], &minor_mult[1], &minor_mult[2], &minor_mult[3], &pc_rowstart, &pc_rowlen,
                                &pc_big, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc, &dstar_rowptr, &dstar_col,
-                               &dstar_count};
+                               &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
+                               &dp_j_len, &dp_pool_col, &dp_pool_cnt};
         for (DeviceBuffer* b : all) f(*b);
     }
 
@@ -94,6 +115,7 @@ struct Plan {
         int64_t cells[4] = {0, 0, 0, 0};
         int64_t nj = 0;
         int64_t staging = 0;
+        int64_t dp_pool = 0;
     } caps;
     bool capturing = false;          // enqueueing into a graph: no host synchronisation allowed
     cudaStream_t cap_stream = nullptr, body_stream = nullptr;  // private capture streams
@@ -101,13 +123,14 @@ struct Plan {
     cudaGraphExec_t graph_exec = nullptr;
     const float* graph_field = nullptr;
     int64_t graph_static_launches = 0;  // kernels per replay outside the loops
-    int64_t loop_body_launches[2] = {0, 0};  // per iteration: pointer jumping, reachability
+    int64_t loop_body_launches[3] = {0, 0, 0};  // per iteration: pointer jumping, reachability, DP waves
     Summary* hsum = nullptr;          // pinned host mirror of the summary
     cudaEvent_t stage_ev[12] = {};    // start and end of stages 0..5 (read by msc_get_stats)
     uint32_t stage_recorded = 0;      // stages whose two events belong to the same pass
     bool caps_ready = false;          // a synchronised run has measured the sizes
     int64_t graph_replays = 0;
     int64_t capture_epoch = 0;        // bumped whenever the plan's graph is captured or dropped
+    int grad_variant = -1;            // gradient tile variant (-1: not tuned yet)
 
     int64_t counts[4] = {0, 0, 0, 0};
     int64_t n_junctions = 0;
@@ -116,6 +139,9 @@ struct Plan {
     int64_t minor_cnt_off[4] = {0, 0, 0, 0};  // where each matrix's row counts start in minor_rowcnt
     int64_t dstar_nnz = 0;
     int64_t pc_staging_cap = 0;  // staging slots of the last path-count run
+    int64_t dp_pool_cap = 0;     // J-row pool slots of the last junction-DP run
+    int pc_method_chosen = 0;    // path-count method once the first run has measured the minor (1, 2)
+    int pc_method_used = 0;      // the method of the last run
     // which stages are valid for the current field
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
          have_junctions = false, have_trace = false, have_minor = false, have_dstar = false;
@@ -180,6 +206,7 @@ msc_status run_junctions(Plan* p, cudaStream_t s);
 msc_status run_trace(Plan* p, cudaStream_t s);      // the minor's 4-slot trace (pipeline)
 msc_status build_minor_csr(Plan* p, cudaStream_t s);  // CSR of A, B, B*, D (on request; syncs)
 msc_status run_path_count(Plan* p, cudaStream_t s);
+msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t out_cap);
 int grid_cap(const Plan* p, int64_t threads, int block, int per_sm = 8);  // grid for a count-bounded loop
 
 }  // namespace msc

@@ -47,7 +47,8 @@ struct PcArgs {
     int64_t nrows;          // rows of this launch (resolved on the device from nrows_dev)
     const unsigned long long* n1_dev;     // counted earlier in the pass
     const unsigned long long* nrows_dev;  // the 1-saddle count, or the previous tier's deferrals
-    int64_t n1_cap;                       // the capacity the buffers were sized for
+    const unsigned long long* nj_dev;     // junctions: their ranks index the trace
+    int64_t n1_cap, nj_cap;               // the capacities the buffers were sized for
     int retry_on_defer;     // a deferral means the pass must be rerun (the last tier of a graph)
     const uint32_t* tgt;    // 4 destination ranks per source (1-saddles, then junctions)
     const uint32_t* kinds;  // per source, byte k = kind of slot k: 1 junction, 2 2-saddle
@@ -68,15 +69,15 @@ struct PcArgs {
 
 __device__ __forceinline__ int64_t row_of(const PcArgs& a, int64_t i) { return a.rows ? int64_t(a.rows[i]) : i; }
 
-// The counts a launch works on, read on the device (they are produced earlier in the same pass).
-__device__ __forceinline__ void resolve(PcArgs& a) {
-    unsigned long long n1 = *a.n1_dev;
-    if (n1 > (unsigned long long)a.n1_cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_RETRY);
-        n1 = (unsigned long long)a.n1_cap;
-    }
+// The counts a launch works on, read on the device (they are produced earlier in the same pass);
+// false (do nothing) when the pass is to be rerun.
+__device__ __forceinline__ bool resolve(PcArgs& a) {
+    const unsigned long long n1 = *a.n1_dev, nj = *a.nj_dev;
+    if (pass_retrying(a.status) || !count_fits(a.status, n1, a.n1_cap) || !count_fits(a.status, nj, a.nj_cap))
+        return false;
     a.n1 = int64_t(n1);
     a.nrows = int64_t(min(*a.nrows_dev, n1));
+    return true;
 }
 
 __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
@@ -163,7 +164,7 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
 // each entry at its rank within the row (rows come out sorted by column).
 __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next_row) {
     PcArgs a = args;
-    resolve(a);
+    if (!resolve(a)) return;
     extern __shared__ __align__(16) unsigned char t0_raw[];
     T0Warp& sh = reinterpret_cast<T0Warp*>(t0_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -565,7 +566,7 @@ __device__ bool count_row(const PcArgs& a, const Tables& t, int64_t s, int r) {
 // Tier 1: warps pull rows from a shared counter.
 __global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs args, u64* next_row) {
     PcArgs a = args;
-    resolve(a);
+    if (!resolve(a)) return;
     __shared__ uint32_t fk[T1_WARPS][T1_HASH], dk[T1_WARPS][T1_HASH];
     __shared__ u64 fv[T1_WARPS][T1_HASH], dv[T1_WARPS][T1_HASH];
     __shared__ uint32_t focc[T1_WARPS][T1_LIST], docc[T1_WARPS][T1_LIST], lk[T1_WARPS][T1_LIST];
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(T1_WARPS * 32) rows_warp(PcArgs args, u64* nex
 __global__ void __launch_bounds__(T2_THREADS) rows_block(PcArgs args, uint32_t* gk, u64* gv, uint32_t* gocc, int cap,
                                                          int lg) {
     PcArgs a = args;
-    resolve(a);
+    if (!resolve(a)) return;
     __shared__ int counters[3];
     __shared__ u64 base;
     const size_t per = size_t(cap);
@@ -626,8 +627,10 @@ __global__ void init_tables(uint32_t* k, u64* v, size_t n) {
 
 __global__ void gather_rows(const unsigned long long* n1_dev, int64_t cap, const int64_t* __restrict__ row_start,
                             const int64_t* __restrict__ rowptr, const uint32_t* __restrict__ in_col,
-                            const u64* __restrict__ in_cnt, uint32_t* __restrict__ col, u64* __restrict__ cnt) {
-    const int64_t n1 = int64_t(min(*n1_dev, (unsigned long long)cap));
+                            const u64* __restrict__ in_cnt, uint32_t* __restrict__ col, u64* __restrict__ cnt,
+                            uint32_t* status) {
+    if (pass_retrying(status) || !count_fits(status, *n1_dev, cap)) return;
+    const int64_t n1 = int64_t(*n1_dev);
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n1; s += int64_t(gridDim.x) * blockDim.x) {
         const int64_t b = row_start[s], o = rowptr[s], len = rowptr[s + 1] - rowptr[s];
         for (int64_t i = 0; i < len; ++i) {
@@ -656,11 +659,63 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->pc_big, sizeof(uint32_t) * n1c * 2))) return st;
     if ((st = ensure(p, p->minor_scan, row_scan_scratch_bytes(n1cap)))) return st;
     u64* ctr = p->dsum()->pc;
+    // method: forced by the options, else chosen after the plan's first run (which uses the
+    // junction waves, whose cost does not grow with the depth of the minor)
+    const int method = p->opts.path_count_method ? int(p->opts.path_count_method)
+                                                 : (p->pc_method_chosen > 0 ? p->pc_method_chosen : 2);
+    p->pc_method_used = method;
+    if (method == 2) {  // junction waves (junction_dp.cu) into the same staging
+        uint64_t cap = cap_mode ? uint64_t(p->caps.staging)
+                                : uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1cap + 1024));
+        uint64_t pool = cap_mode ? uint64_t(p->caps.dp_pool)
+                                 : uint64_t(std::max<int64_t>(p->dp_pool_cap, 4 * njcap + 1024));
+        for (int attempt = 0; attempt < 8; ++attempt) {
+            if ((st = ensure(p, p->pc_col, sizeof(uint32_t) * cap))) return st;
+            if ((st = ensure(p, p->pc_cnt, sizeof(u64) * cap))) return st;
+            if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * cap))) return st;
+            if ((st = ensure(p, p->dstar_count, sizeof(u64) * cap))) return st;
+            if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * 8, s), "memset counters"))) return st;
+            if ((st = run_junction_dp(p, s, pool, cap))) return st;
+            if (!cap_mode) {
+                if ((st = read_summary(p, s))) return st;
+                const u64 used = p->hsum->pc[C_CURSOR], pool_used = p->hsum->dp_pool_used;
+                if (used > cap || pool_used > pool) {  // grow and redo the stage (an overflowing wave
+                    // stops the later ones, so the usage seen is a lower bound)
+                    if (used > cap) cap = std::max<uint64_t>(2 * cap, used + used / 4 + 1024);
+                    if (pool_used > pool) pool = std::max<uint64_t>(2 * pool, pool_used + pool_used / 4 + 1024);
+                    uint32_t zero = 0;
+                    if ((st = check_cuda(p, cudaMemcpyAsync(p->status_word(), &zero, sizeof(zero),
+                                                            cudaMemcpyHostToDevice, s),
+                                         "status reset")))
+                        return st;
+                    continue;
+                }
+                p->dp_pool_cap = int64_t(pool_used);
+            }
+            const u64* all_rows = &p->dsum()->counts[1];
+            if ((st = check_cuda(p,
+                                 row_scan(p, static_cast<const uint32_t*>(p->pc_rowlen.ptr), all_rows, n1cap,
+                                          static_cast<int64_t*>(p->dstar_rowptr.ptr),
+                                          static_cast<u64*>(p->minor_scan.ptr), s, &p->dsum()->dstar_nnz),
+                                 "D* row scan")))
+                return st;
+            if (n1cap) {
+                gather_rows<<<grid_cap(p, n1cap, 256), 256, 0, s>>>(
+                    all_rows, n1cap, static_cast<const int64_t*>(p->pc_rowstart.ptr),
+                    static_cast<const int64_t*>(p->dstar_rowptr.ptr), static_cast<const uint32_t*>(p->pc_col.ptr),
+                    static_cast<const u64*>(p->pc_cnt.ptr), static_cast<uint32_t*>(p->dstar_col.ptr),
+                    static_cast<u64*>(p->dstar_count.ptr), p->status_word());
+                launched(p);
+            }
+            p->pc_staging_cap = int64_t(cap);
+            return check_cuda(p, cudaGetLastError(), "gather launch");
+        }
+        return fail(p, MSC_ERR_CUDA, "internal: D* staging did not converge");
+    }
     const int first_tier = std::max(0, std::min(2, int(p->opts.path_count_tier)));
     // tier-0 grid: persistent, as many CTAs as fit
     const size_t t0_smem = sizeof(T0Warp) * T0_WARPS;
-    if (!cap_mode &&
-        (st = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
+    if ((st = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
                          "cudaFuncSetAttribute(rows_thread)")))
         return st;
     int per_sm = 0;
@@ -683,7 +738,9 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * 8, s), "memset counters"))) return st;
         PcArgs a{};
         a.n1_dev = &p->dsum()->counts[1];
+        a.nj_dev = &p->dsum()->n_junctions;
         a.n1_cap = n1cap;
+        a.nj_cap = njcap;
         a.tgt = static_cast<const uint32_t*>(p->trace.ptr);
         a.kinds = static_cast<const uint32_t*>(p->trace_kinds.ptr);
         a.out_col = static_cast<uint32_t*>(p->pc_col.ptr);
@@ -784,7 +841,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         if (n1cap) {
             gather_rows<<<grid_cap(p, n1cap, 256), 256, 0, s>>>(
                 all_rows, n1cap, a.row_start, static_cast<const int64_t*>(p->dstar_rowptr.ptr), a.out_col, a.out_cnt,
-                static_cast<uint32_t*>(p->dstar_col.ptr), static_cast<u64*>(p->dstar_count.ptr));
+                static_cast<uint32_t*>(p->dstar_col.ptr), static_cast<u64*>(p->dstar_count.ptr), p->status_word());
             launched(p);
         }
         p->pc_staging_cap = int64_t(cap);

@@ -54,7 +54,8 @@ MSC_FLAG_NO_GRAPH = 1
 
 
 class MscOpts(ctypes.Structure):
-    _fields_ = [("max_iterations", ctypes.c_int64), ("flags", ctypes.c_int32), ("path_count_tier", ctypes.c_int32)]
+    _fields_ = [("max_iterations", ctypes.c_int64), ("flags", ctypes.c_int32), ("path_count_tier", ctypes.c_int32),
+                ("gradient_tile", ctypes.c_int32), ("path_count_method", ctypes.c_int32)]
 
 
 class MscStats(ctypes.Structure):
@@ -67,7 +68,8 @@ class MscStats(ctypes.Structure):
                 ("ms_gradient", ctypes.c_float), ("ms_critical", ctypes.c_float), ("ms_extremum", ctypes.c_float),
                 ("ms_reachability", ctypes.c_float), ("ms_minor", ctypes.c_float),
                 ("ms_path_count", ctypes.c_float), ("ms_rows_kernel", ctypes.c_float),
-                ("ms_trace_kernel", ctypes.c_float), ("n_frontier_entries", ctypes.c_int64)]
+                ("ms_trace_kernel", ctypes.c_float), ("n_frontier_entries", ctypes.c_int64),
+                ("gradient_tile", ctypes.c_int64), ("path_count_method", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -127,10 +129,12 @@ def _view(ptr, shape, typestr):
 class Plan:
     """Owns an msc_plan_t for one grid shape (nx, ny, nz)."""
 
-    def __init__(self, dims, max_iterations: int = 0, path_count_tier: int = 0, no_graph: bool = False):
+    def __init__(self, dims, max_iterations: int = 0, path_count_tier: int = 0, no_graph: bool = False,
+                 gradient_tile: int = 0, path_count_method: int = 0):
         self.dims = tuple(int(d) for d in dims)
         arr = (ctypes.c_int64 * 3)(*self.dims)
-        opts = MscOpts(int(max_iterations), MSC_FLAG_NO_GRAPH if no_graph else 0, int(path_count_tier))
+        opts = MscOpts(int(max_iterations), MSC_FLAG_NO_GRAPH if no_graph else 0, int(path_count_tier),
+                       int(gradient_tile), int(path_count_method))
         h = ctypes.c_void_p()
         _check(lib.msc_plan(arr, ctypes.byref(opts), ctypes.byref(h)), what=f"msc_plan{self.dims}")
         self.handle = h

@@ -71,3 +71,30 @@ def test_bad_arguments():
     with pytest.raises(m.MscError) as e:
         m.msc_critical(plan)  # before msc_gradient
     assert e.value.status == 11
+
+
+TILES = [(8, 8, 512), (8, 4, 256), (4, 8, 256), (8, 16, 512), (16, 8, 512), (16, 8, 1024), (16, 16, 512),
+         (16, 16, 1024), (32, 8, 1024)]
+
+
+@pytest.mark.parametrize("tile", range(1, len(TILES) + 1))
+def test_every_tile_variant_matches_oracle(tile):
+    """The autotuner chooses among tile variants; each must compute the same words (ragged tiles
+    on every axis, ties, a smooth field)."""
+    m = msc()
+    cases = [random_field((17, 9, 35), 40 + tile, "normal"), random_field((9, 18, 33), 50 + tile, "ties"),
+             fields.grf((24, 21, 70), 3.0, seed=tile)]
+    for f in cases:
+        plan = m.Plan(dims_of(f), gradient_tile=tile)
+        _, words, counts, lists, _ = run_gradient(f, plan)
+        pair = oracle.gradient(f)
+        assert np.array_equal(words, oracle.pack(dims_of(f), pair))
+        assert counts == [int(c) for c in oracle.critical(dims_of(f), pair)[0]]
+        st = m.msc_get_stats(plan)["gradient_tile"]
+        assert (st & 0xFF, (st >> 8) & 0xFF, st >> 16) == TILES[tile - 1]
+
+
+def test_tile_option_is_validated():
+    m = msc()
+    with pytest.raises(m.MscError):
+        m.Plan((8, 8, 8), gradient_tile=len(TILES) + 1)

@@ -26,10 +26,11 @@ def _outputs(m, plan):
                minor=[tuple(to_np(x) for x in m.msc_minor(plan, w)) for w in range(4)],
                dstar=tuple(to_np(x) for x in m.msc_saddle_arcs(plan)))
     st = m.msc_get_stats(plan)
-    # (the pointer-jumping round count is left out: in-place jumping may finish a round early,
-    # depending on thread scheduling; the labels it produces do not depend on it)
+    # (left out: the pointer-jumping round count -- in-place jumping may finish a round early,
+    # depending on thread scheduling -- and the path-count work count, whose meaning depends on
+    # the method a run used; the outputs depend on neither)
     out["stats"] = {k: st[k] for k in ("n_reachable", "n_bfs_levels", "n_junctions", "nnz_A", "nnz_B", "nnz_Bstar",
-                                       "nnz_D", "nnz_Dstar", "n_iter", "max_path_count", "n_frontier_entries")}
+                                       "nnz_D", "nnz_Dstar", "n_iter", "max_path_count")}
     return out
 
 
@@ -114,3 +115,22 @@ def test_replay_reports_errors():
     buf.copy_(gpu_field(f))
     m.msc_compute(plan, buf)
     _assert_same(_outputs(m, plan), _reference(m, f))
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_replays_with_each_path_count_method(method):
+    """Graph replays run the path count as row-wise products or as junction waves (a WHILE loop of
+    waves); both give the oracle's D* on a field with a deep minor."""
+    m = msc()
+    f = fields.gaussian_blobs(n=40, n_blobs=5, sigma_range=(4, 12), seed=11)
+    e = oracle.compute_all(f, with_minor=True, with_dstar=True)
+    plan = m.Plan(dims_of(f), path_count_method=method)
+    buf = gpu_field(f)
+    for _ in range(3):
+        m.msc_compute(plan, buf)
+        rowptr, col, cnt = (to_np(x) for x in m.msc_saddle_arcs(plan))
+        er, ec, en = e["dstar"]
+        assert np.array_equal(col, ec) and np.array_equal(cnt, en)
+        assert np.array_equal(np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr)), er)
+        st = m.msc_get_stats(plan)
+        assert st["n_iter"] == e["n_iter"] and st["path_count_method"] == method

@@ -96,15 +96,34 @@ def test_dstar(name, results, expected):
     assert r["stats"]["nnz_Dstar"] == len(er)
 
 
-@pytest.mark.parametrize("tier", [1, 2])
-@pytest.mark.parametrize("name", ["grf40", "grf25x30x70", "cos32", "ties(9, 8, 33)"])
-def test_dstar_every_path_count_tier(name, tier, expected):
-    """The warp-table and CTA-table tiers give the same D* as the register tier and the oracle."""
+@pytest.mark.parametrize("tier", [0, 1, 2])
+@pytest.mark.parametrize("name", ["grf40", "grf25x30x70", "cos32", "ties(9, 8, 33)", "blobs36"])
+def test_dstar_row_wise_every_tier(name, tier, expected):
+    """The paper's iteration A <- A B, run row by row from each tier (register, warp-table and
+    CTA-table), gives the same D* and iteration count as the junction waves and the oracle."""
     m = msc()
     f = dict(CASES)[name]
-    plan = m.Plan(dims_of(f), path_count_tier=tier)
+    plan = m.Plan(dims_of(f), path_count_tier=tier, path_count_method=1)
     m.msc_compute(plan, gpu_field(f))
     rows, cols, cnt = csr_to_coo(*(to_np(x) for x in m.msc_saddle_arcs(plan)))
     er, ec, en = expected[name]["dstar"]
     assert np.array_equal(rows, er) and np.array_equal(cols, ec) and np.array_equal(cnt, en)
     assert m.msc_get_stats(plan)["n_iter"] == expected[name]["n_iter"]
+
+
+def test_dstar_methods_agree_on_long_path_networks():
+    """A blob field with long V-path networks (many junction levels, large multiplicities):
+    junction waves, row-wise products and the oracle agree entry by entry."""
+    m = msc()
+    f = fields.gaussian_blobs(n=44, n_blobs=6, sigma_range=(4, 12), seed=9)
+    e = oracle.compute_all(f, with_minor=True, with_dstar=True)
+    got = {}
+    for method in (1, 2):
+        plan = m.Plan(dims_of(f), path_count_method=method)
+        m.msc_compute(plan, gpu_field(f))
+        got[method] = csr_to_coo(*(to_np(x) for x in m.msc_saddle_arcs(plan)))
+        assert m.msc_get_stats(plan)["n_iter"] == e["n_iter"]
+    er, ec, en = e["dstar"]
+    for method in (1, 2):
+        rows, cols, cnt = got[method]
+        assert np.array_equal(rows, er) and np.array_equal(cols, ec) and np.array_equal(cnt, en)
