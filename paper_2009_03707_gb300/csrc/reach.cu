@@ -106,7 +106,8 @@ __device__ __forceinline__ uint32_t pull(uint32_t m, const uint32_t* __restrict_
 // paired with a facet (the quads that give an out-edge to every other facet).
 __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __restrict__ words,
                                                       uint4* __restrict__ masks, uint32_t* __restrict__ R0,
-                                                      uint32_t* __restrict__ R1, uint32_t* __restrict__ qdown) {
+                                                      uint32_t* __restrict__ R1, uint32_t* __restrict__ qdown,
+                                                      uint32_t* __restrict__ stamp) {
     const int lane = threadIdx.x & 31;
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
     for (int64_t t = (int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5; t < nrw;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __
             const uint32_t qd = __ballot_sync(0xFFFFFFFFu, down);
             if (lane == 4 + k) qdown[k * r.qplane + r.qbase] = qd;
         }
+        if (lane == 8 && r.w == 0) stamp[int64_t(r.z) * g.ny + r.y] = 1;  // every row is new at the start
         if (lane == 3) {  // the unused slot of the 1-cell layout stays empty in both buffers
             const int64_t e = g.edge_word(r.z, 1, r.y, 1, r.w);
             masks[e] = make_uint4(0, 0, 0, 0);
@@ -162,17 +164,33 @@ __device__ __forceinline__ bool sweep_word(const Rows& r, const uint4* __restric
 
 // One level: Rout = Rin | cells whose partner quad has another facet in Rin.  blockIdx.y is the
 // axis, so every branch on it is uniform.  Sets *changed if any word grew.
+// Rows (y, z) are stamped with 1 + the last sweep that changed them (1: the start).  A cell's
+// predecessors lie within one step in y and z, so a row none of whose 3 x 3 neighbour rows changed
+// in the previous sweep cannot change now; it is skipped, Rout included: that buffer already
+// holds the row's value from two sweeps ago, which is still its value.  Fronts that move slowly
+// through a large grid (many levels) then cost only the rows near the front.
 __global__ void __launch_bounds__(THREADS) reach_sweep(Geom g, const uint4* __restrict__ masks,
                                                        const uint32_t* __restrict__ Rin, uint32_t* __restrict__ Rout,
-                                                       uint32_t* __restrict__ changed) {
+                                                       uint32_t* __restrict__ stamp, const Summary* __restrict__ sum,
+                                                       int parity, uint32_t* __restrict__ changed) {
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
     const int64_t t = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    const uint32_t k = 2u * uint32_t(sum->sweep_iters) + 1u + uint32_t(parity);  // this sweep
     bool grew = false;
     if (t < nrw) {
         const Rows r(g, t);
-        grew = blockIdx.y == 0 ? sweep_word<0>(r, masks, Rin, Rout)
-               : blockIdx.y == 1 ? sweep_word<1>(r, masks, Rin, Rout)
-                                 : sweep_word<2>(r, masks, Rin, Rout);
+        uint32_t recent = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = r.y + dy, z = r.z + dz;
+                if (y >= 0 && y < g.ny && z >= 0 && z < g.nz) recent = max(recent, stamp[int64_t(z) * g.ny + y]);
+            }
+        if (recent >= k) {
+            grew = blockIdx.y == 0 ? sweep_word<0>(r, masks, Rin, Rout)
+                   : blockIdx.y == 1 ? sweep_word<1>(r, masks, Rin, Rout)
+                                     : sweep_word<2>(r, masks, Rin, Rout);
+            if (grew) stamp[int64_t(r.z) * g.ny + r.y] = k + 1;
+        }
     }
     if (__syncthreads_or(grew) && threadIdx.x == 0) *changed = 1u;
 }
@@ -312,12 +330,13 @@ struct SweepCtx {
     const uint4* masks;
     uint32_t* a;
     uint32_t* b;
+    uint32_t* stamp;
 };
 
 void sweep_body(Plan* p, cudaStream_t s, cudaGraphConditionalHandle h, void* ctx) {
     const SweepCtx& c = *static_cast<SweepCtx*>(ctx);
-    reach_sweep<<<c.grid, THREADS, 0, s>>>(p->g, c.masks, c.a, c.b, &p->dsum()->loop_flag[0]);
-    reach_sweep<<<c.grid, THREADS, 0, s>>>(p->g, c.masks, c.b, c.a, &p->dsum()->loop_flag[1]);
+    reach_sweep<<<c.grid, THREADS, 0, s>>>(p->g, c.masks, c.a, c.b, c.stamp, p->dsum(), 0, &p->dsum()->loop_flag[0]);
+    reach_sweep<<<c.grid, THREADS, 0, s>>>(p->g, c.masks, c.b, c.a, c.stamp, p->dsum(), 1, &p->dsum()->loop_flag[1]);
     reach_decide<<<1, 1, 0, s>>>(p->dsum(), p->opts.max_iterations, h, h != 0);
 }
 
@@ -332,15 +351,17 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->reach_tmp, sizeof(uint32_t) * size_t(nw)))) return st;
     if ((st = ensure(p, p->reach_masks, sizeof(uint4) * size_t(nw)))) return st;
     if ((st = ensure(p, p->reach_qdown, sizeof(uint32_t) * 3 * size_t(nrw)))) return st;
+    if ((st = ensure(p, p->reach_stamp, sizeof(uint32_t) * size_t(g.nz) * size_t(g.ny)))) return st;
     auto* masks = static_cast<uint4*>(p->reach_masks.ptr);
+    auto* stamp = static_cast<uint32_t*>(p->reach_stamp.ptr);
     uint32_t* A = static_cast<uint32_t*>(p->visited.ptr);
     uint32_t* B = static_cast<uint32_t*>(p->reach_tmp.ptr);
     reach_init<<<grid_for(p, nrw * 32), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, A, B,
-                                                         static_cast<uint32_t*>(p->reach_qdown.ptr));
+                                                         static_cast<uint32_t*>(p->reach_qdown.ptr), stamp);
     reach_start<<<1, 1, 0, s>>>(p->dsum());
     launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
-    SweepCtx ctx{dim3(unsigned((nrw + THREADS - 1) / THREADS), 3), masks, A, B};
+    SweepCtx ctx{dim3(unsigned((nrw + THREADS - 1) / THREADS), 3), masks, A, B, stamp};
     return run_loop(p, s, 1, 3, sweep_body, &ctx);
 }
 
