@@ -40,6 +40,7 @@ namespace {
 constexpr int THREADS = 256;
 constexpr uint32_t READY = 0x80000000u;  // pend[j] = READY | wave: j's row is computed in that wave
 constexpr uint32_t DONE = 0xFFFFFFFFu;
+constexpr int SCAN_BATCH = 8;  // pending words a thread reads at once in a wave
 typedef unsigned long long u64;
 
 struct DpArgs {
@@ -205,24 +206,36 @@ __global__ void __launch_bounds__(THREADS) dp_wave(DpArgs a) {
     const uint32_t mine = READY | wave, next = READY | (wave + 1);
     unsigned done = 0;
     u64 mx = 0;
-    for (int64_t j = int64_t(blockIdx.x) * THREADS + threadIdx.x; j < nj; j += int64_t(gridDim.x) * THREADS) {
-        if (a.pend[j] != mine) continue;
-        uint32_t bound;
-        const Inputs in = inputs_of(a, n1 + j, n1, &bound);
-        const u64 off = bump(&a.sum->dp_pool_used, bound);
-        uint32_t len = 0;
-        if (off + bound <= a.pool_cap) {
-            len = merge_into(in, a.pool_col + off, a.pool_cnt + off, bound, &mx, a.status);
-        } else {
-            atomicOr(a.status, ST_RETRY);  // the pool is too small: the host grows it and reruns
+    // the scan reads SCAN_BATCH pending words at a time, all in flight together, so a wave with
+    // few junctions to do costs a few memory latencies rather than one per word
+    const int64_t stride = int64_t(gridDim.x) * THREADS;
+    for (int64_t j0 = int64_t(blockIdx.x) * THREADS + threadIdx.x; j0 < nj; j0 += SCAN_BATCH * stride) {
+        uint32_t hit = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_BATCH; ++k) {
+            const int64_t j = j0 + k * stride;
+            hit |= uint32_t(j < nj && a.pend[j] == mine) << k;
         }
-        a.j_off[j] = off;
-        a.j_len[j] = len;
-        a.pend[j] = DONE;
-        ++done;
-        for (int64_t e = a.in_ptr[j]; e < a.in_ptr[j + 1]; ++e) {
-            const uint32_t p = a.in_idx[e];
-            if (atomicSub(&a.pend[p], 1u) == 1u) a.pend[p] = next;
+#pragma unroll 1
+        for (; hit; hit &= hit - 1) {
+            const int64_t j = j0 + int64_t(__ffs(hit) - 1) * stride;
+            uint32_t bound;
+            const Inputs in = inputs_of(a, n1 + j, n1, &bound);
+            const u64 off = bump(&a.sum->dp_pool_used, bound);
+            uint32_t len = 0;
+            if (off + bound <= a.pool_cap) {
+                len = merge_into(in, a.pool_col + off, a.pool_cnt + off, bound, &mx, a.status);
+            } else {
+                atomicOr(a.status, ST_RETRY);  // the pool is too small: the host grows it and reruns
+            }
+            a.j_off[j] = off;
+            a.j_len[j] = len;
+            a.pend[j] = DONE;
+            ++done;
+            for (int64_t e = a.in_ptr[j]; e < a.in_ptr[j + 1]; ++e) {
+                const uint32_t p = a.in_idx[e];
+                if (atomicSub(&a.pend[p], 1u) == 1u) a.pend[p] = next;
+            }
         }
     }
     for (int o = 16; o; o >>= 1) done += __shfl_xor_sync(0xFFFFFFFFu, done, o);
