@@ -51,6 +51,12 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _num_sms():
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def _field(name):
     from synth import fields
 
@@ -208,7 +214,7 @@ def run_gpu(args):
     f = _field(args.workload)
     nz, ny, nx = f.shape
     nvox = f.size
-    plan = msc.Plan((nx, ny, nz))
+    plan = msc.Plan((nx, ny, nz), no_graph=args.no_graph, gradient_tile=args.gradient_tile)
     d_field = torch.from_numpy(f).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -246,7 +252,7 @@ def run_gpu(args):
             st = msc.msc_get_stats(plan)
             launches += int(st["n_launches"])
             stage_ms.append(st)
-            kernel_ms["gradient_kernel"].append(st["ms_gradient"])
+            kernel_ms["gradient_kernel"].append(st["ms_gradient_kernel"])
             kernel_ms["rows_thread"].append(st["ms_rows_kernel"])
         barrier()
         wall = time.perf_counter() - t_region
@@ -310,6 +316,18 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel_ms": km[dom], "algorithmic_bytes": algo[dom]}
+    # the lower-star pairing is a sequential loop per vertex: beside the HBM figure, the warp
+    # instructions it issues (counted once by ncu, profiles/traffic.json) per second of the live
+    # kernel time, against the SMs' issue rate at the clock sampled during the run
+    grec = _traffic_record("gradient_kernel")
+    sm_mhz = (clk.summary() or {}).get("sm_mhz")
+    if grec and grec.get("workload") == args.workload and grec.get("warp_inst_per_unit") and sm_mhz and km["gradient_kernel"] > 0:
+        inst = grec["warp_inst_per_unit"] * nvox
+        got = inst / (km["gradient_kernel"] / 1e3) / 1e9
+        top = _num_sms() * 4 * float(sm_mhz) / 1e3
+        roofline["issue"] = {"kernel": "gradient_kernel", "warp_inst": inst, "achieved": got, "peak": top,
+                             "unit": "G warp-instructions/s", "frac": got / top,
+                             "peak_basis": "4 schedulers x 1 instruction/clock per SM at the sampled SM clock"}
 
     def med(key):
         return statistics.median(s[key] for s in stage_ms)
@@ -484,6 +502,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workers", type=int, default=8, help="batch/serve worker streams")
     ap.add_argument("--requests", type=int, default=0, help="serve500: truncate the request trace")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run every pass synchronised between stages instead of replaying its CUDA graph "
+                         "(same kernels; profilers list each launch)")
+    ap.add_argument("--gradient-tile", type=int, default=0, help="force a lower-star tile variant (1..9)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps are required")

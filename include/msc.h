@@ -102,6 +102,8 @@ typedef struct msc_stats {
                                    sizes; junction waves: J-row entries merged (pool slots) */
     int64_t gradient_tile;      /* the lower-star tile used: TY | TZ << 8 | threads << 16 */
     int64_t path_count_method;  /* the path-count method of the last run: 1 row-wise, 2 waves */
+    float ms_gradient_kernel;   /* the lower-star kernel alone (CUDA events) */
+    float reserved_f;
 } msc_stats;
 
 /* ---- plan ----------------------------------------------------------------------------

@@ -378,6 +378,8 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->kev1), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->tev0), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->tev1), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->gev0), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->gev1), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!st) st = msc::check_cuda(p, cudaMallocHost(&p->hsum, sizeof(msc::Summary)), "cudaMallocHost");
@@ -402,7 +404,7 @@ msc_status msc_plan_destroy(msc_plan_t plan) {
     });
     for (cudaEvent_t e : p->stage_ev)
         if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1})
+    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1, p->gev0, p->gev1})
         if (e) cudaEventDestroy(e);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->body_stream) cudaStreamDestroy(p->body_stream);
@@ -677,6 +679,8 @@ msc_status msc_get_stats(msc_plan_t plan, msc_stats* out) {
         cudaEventElapsedTime(&p->stats.ms_rows_kernel, p->kev0, p->kev1);
     if (p->have_trace && cudaEventSynchronize(p->tev1) == cudaSuccess)
         cudaEventElapsedTime(&p->stats.ms_trace_kernel, p->tev0, p->tev1);
+    if (p->have_gradient && cudaEventSynchronize(p->gev1) == cudaSuccess)
+        cudaEventElapsedTime(&p->stats.ms_gradient_kernel, p->gev0, p->gev1);
     cudaGetLastError();
     *out = p->stats;
     return MSC_OK;

@@ -240,8 +240,22 @@ cudaError_t launch_words(int v, const Geom& g, const float* d_field, uint32_t* w
 }
 
 cudaError_t launch_gradient(int v, const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
-                            uint32_t* status, cudaStream_t s) {
-    cudaError_t e = launch_words(v, g, d_field, words, status, s);
+                            uint32_t* status, cudaStream_t s, const Plan* p = nullptr) {
+    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * size_t(g.nverts), s);
+    if (e != cudaSuccess) return e;
+    if (p) record_event(p, p->gev0, s);  // the lower-star kernel alone is timed
+    switch (v) {
+        case 1: e = launch_tile<8, 4, 256>(g, d_field, words, status, s); break;
+        case 2: e = launch_tile<4, 8, 256>(g, d_field, words, status, s); break;
+        case 3: e = launch_tile<8, 16, 512>(g, d_field, words, status, s); break;
+        case 4: e = launch_tile<16, 8, 512>(g, d_field, words, status, s); break;
+        case 5: e = launch_tile<16, 8, 1024>(g, d_field, words, status, s); break;
+        case 6: e = launch_tile<16, 16, 512>(g, d_field, words, status, s); break;
+        case 7: e = launch_tile<16, 16, 1024>(g, d_field, words, status, s); break;
+        case 8: e = launch_tile<32, 8, 1024>(g, d_field, words, status, s); break;
+        default: e = launch_tile<8, 8, 512>(g, d_field, words, status, s); break;
+    }
+    if (p) record_event(p, p->gev1, s);
     if (e != cudaSuccess) return e;
     const int64_t warps = int64_t(g.nz) * g.ny * g.W;
     critical_bitmaps<<<int((warps * 32 + 255) / 256), 256, 0, s>>>(g, words, crit_bits);
@@ -310,7 +324,7 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     launched(p, 2);
     return check_cuda(p,
                       launch_gradient(v, g, d_field, static_cast<uint32_t*>(p->words.ptr),
-                                      static_cast<uint32_t*>(p->crit_bits.ptr), p->status_word(), s),
+                                      static_cast<uint32_t*>(p->crit_bits.ptr), p->status_word(), s, p),
                       "gradient launch");
 }
 

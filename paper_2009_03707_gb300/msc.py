@@ -69,7 +69,8 @@ class MscStats(ctypes.Structure):
                 ("ms_reachability", ctypes.c_float), ("ms_minor", ctypes.c_float),
                 ("ms_path_count", ctypes.c_float), ("ms_rows_kernel", ctypes.c_float),
                 ("ms_trace_kernel", ctypes.c_float), ("n_frontier_entries", ctypes.c_int64),
-                ("gradient_tile", ctypes.c_int64), ("path_count_method", ctypes.c_int64)]
+                ("gradient_tile", ctypes.c_int64), ("path_count_method", ctypes.c_int64),
+                ("ms_gradient_kernel", ctypes.c_float), ("reserved_f", ctypes.c_float)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
