@@ -24,10 +24,6 @@ namespace {
 constexpr int THREADS = 256;
 int blocks(int64_t n) { return int((n + THREADS - 1) / THREADS); }
 
-__device__ __forceinline__ uint32_t bit_rank(const uint32_t* bits, const uint32_t* prefix, int64_t wi, int bit) {
-    return prefix[wi] + __popc(bits[wi] & ((1u << bit) - 1u));
-}
-
 struct TraceArgs {
     Geom g;
     const uint32_t* words;
@@ -40,7 +36,6 @@ struct TraceArgs {
     const uint32_t* info;  // per reachable 1-cell (info_index): dead end, branch point, or its one successor
     uint32_t* tgt;    // 4 per source: destination rank
     uint8_t* kinds;   // 4 per source: 0 none / 1 junction / 2 2-saddle (read as one word per source)
-    uint32_t* cnt[4];  // distinct destinations per row of A, B, B*, D
     const unsigned long long* n1_dev;  // 1-saddles and junctions, counted earlier in the pass
     const unsigned long long* nj_dev;
     int64_t cap1, capj;                // the capacities the buffers were sized for
@@ -75,96 +70,146 @@ __device__ __forceinline__ int distinct_targets(const uint32_t* tgt, uint32_t ki
     return m;
 }
 
+// Distinct destinations of kind `want` among a source's four slots (a slot counts if no earlier
+// slot holds the same destination); static indexing keeps everything in registers.
+__device__ __forceinline__ uint32_t distinct_count(const uint32_t rank[4], const uint32_t kind[4], uint32_t want) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        bool first = kind[k] == want;
+#pragma unroll
+        for (int j = 0; j < k; ++j) first = first && !(kind[j] == want && rank[j] == rank[k]);
+        m += first ? 1u : 0u;
+    }
+    return m;
+}
+
 // One thread per source (1-saddle or junction): its <= 4 out-edges are found once, then the
 // simple paths are followed in an interleaved loop (one independent record load per live path
-// per step), and the destinations are ranked and counted per matrix row.  Grid-stride over the
-// sources, whose numbers are read on the device.
-__global__ void __launch_bounds__(THREADS) trace_kernel(TraceArgs a) {
+// per step), and the destinations are ranked in O(1) from the junction and critical-cell
+// bitmaps.  Grid-stride over the sources, whose numbers are read on the device.  The out-edges
+// and the ranks are computed without branches on the slot (selects and predicated loads), and
+// all index arithmetic is 32-bit (a plan's bitmap words and vertex ids fit in 32 bits).
+__global__ void __launch_bounds__(THREADS, 6) trace_kernel(TraceArgs a) {
     const unsigned long long n1 = *a.n1_dev, nj = *a.nj_dev;
     if (pass_retrying(a.status) || !count_fits(a.status, n1, a.cap1) || !count_fits(a.status, nj, a.capj)) return;
-    const int64_t N1 = int64_t(n1), NJ = int64_t(nj);
-    unsigned long long nnz[4] = {0, 0, 0, 0};
-    for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < N1 + NJ;
-         u += int64_t(gridDim.x) * THREADS) {
     const Geom& g = a.g;
-    const uint32_t id = u < N1 ? a.s1[u] : a.junc_cells[u - N1];
-    const uint32_t q1 = g.div_rx.div(id);
-    const int cx = int(id - q1 * g.rx);
-    const int cz = int(g.div_ry.div(q1));
-    const int cy = int(q1 - uint32_t(cz) * g.ry);
-    const int axis = (cx & 1) ? 0 : (cy & 1) ? 1 : 2;
-    DagTarget out[4];
-    dag_out(g, a.words, cx >> 1, cy >> 1, cz >> 1, axis, out);
-    // per path: the current 1-cell handle while live; at the end the terminal (a junction's
-    // handle, or a 2-saddle as bit 31 | owner << 2 | even axis)
-    uint32_t h[4], kind[4];
-    uint32_t live = 0;
+    const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), nz = uint32_t(g.nz), W = uint32_t(g.W);
+    const uint32_t N1 = uint32_t(n1), NS = uint32_t(n1 + nj);
+    unsigned long long nnz_a = 0, nnz_b = 0, nnz_bs = 0, nnz_d = 0;
+    for (uint32_t u = blockIdx.x * THREADS + threadIdx.x; u < NS; u += gridDim.x * THREADS) {
+        const uint32_t id = u < N1 ? a.s1[u] : a.junc_cells[u - N1];
+        const uint32_t q1 = g.div_rx.div(id);
+        const uint32_t cx = id - q1 * g.rx;
+        const uint32_t cz = g.div_ry.div(q1);
+        const uint32_t cy = q1 - cz * g.ry;
+        const int axis = (cx & 1u) ? 0 : (cy & 1u) ? 1 : 2;
+        const uint32_t x = cx >> 1, y = cy >> 1, z = cz >> 1;
+        const uint32_t v = x + nx * (y + ny * z);
+        // the cofacet quads lie along the two other axes (slots 0,1: axis+1, slots 2,3: axis+2,
+        // - then + side); a quad on the + side shares e's owner, one on the - side is owned by the
+        // vertex one step back
+        const int bA = axis == 2 ? 0 : axis + 1, bB = axis == 0 ? 2 : axis - 1;
+        const uint32_t cA = pick3(bA, x, y, z), cB = pick3(bB, x, y, z);
+        const uint32_t nA = pick3(bA, nx, ny, nz), nB = pick3(bB, nx, ny, nz);
+        const uint32_t sA = pick3(bA, 1u, nx, nx * ny), sB = pick3(bB, 1u, nx, nx * ny);
+        const uint32_t w_own = a.words[v];
+        const uint32_t w_A = cA > 0 ? a.words[v - sA] : 0u;
+        const uint32_t w_B = cB > 0 ? a.words[v - sB] : 0u;
+        const uint32_t own = slot_code(w_own, 1 << axis);
+        // per path: the current 1-cell handle while live; at the end the terminal (a junction's
+        // handle, or a 2-saddle as bit 31 | owner << 2 | even axis)
+        uint32_t h[4], kind[4];
+        uint32_t live = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        kind[k] = out[k].kind;
-        if (out[k].kind == 1) {
-            h[k] = edge_handle(out[k].v, out[k].sub);
-            live |= 1u << k;
-        } else {
-            const uint32_t even = (out[k].sub & 1u) == 0 ? 0u : (out[k].sub & 2u) == 0 ? 1u : 2u;
-            h[k] = 0x80000000u | (out[k].v << 2) | even;
-        }
-    }
-    for (int64_t step = 0; live; ++step) {
-        if (step > a.max_steps) {
-            atomicOr(a.status, ST_ITER);
-            break;
-        }
-        uint32_t w[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w[k] = (live >> k) & 1u ? a.info[info_index(g, h[k])] : 0u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!((live >> k) & 1u)) continue;
-            if (w[k] == INFO_DEAD) {  // a dead path: dropped
-                kind[k] = 0;
-                live &= ~(1u << k);
-            } else if (w[k] == INFO_BRANCH) {  // ends at the junction h[k]
-                live &= ~(1u << k);
-            } else if (w[k] & 0x80000000u) {  // ends at a 2-saddle
-                kind[k] = 2;
-                h[k] = w[k];
-                live &= ~(1u << k);
-            } else {
-                h[k] = w[k];
+        for (int i = 0; i < 4; ++i) {
+            const int b = i < 2 ? bA : bB;
+            const bool plus = i & 1;
+            const uint32_t cb = i < 2 ? cA : cB, sb = i < 2 ? sA : sB, nb = i < 2 ? nA : nB;
+            const bool exists = plus ? cb + 1 < nb : cb > 0;
+            const bool partner = own == uint32_t(1 + 2 * b + (plus ? 1 : 0));
+            const uint32_t ow = plus ? w_own : (i < 2 ? w_A : w_B);
+            const uint32_t ov = plus ? v : v - sb;
+            const int other = 3 - axis - b;  // the quad's even axis
+            const uint32_t qc = slot_code(ow, (1 << axis) | (1 << b));
+            const int k = int(qc - 1) >> 1;  // the axis of the quad's partner (when paired)
+            const uint32_t tv = (qc & 1u) ? ov : ov + (k == 0 ? 1u : k == 1 ? nx : nx * ny);
+            kind[i] = 0;
+            h[i] = 0;
+            if (exists && !partner) {
+                if (qc == 0) {
+                    kind[i] = 2;
+                    h[i] = 0x80000000u | (ov << 2) | uint32_t(other);
+                } else if (k != other) {  // paired with a facet: edge to that facet
+                    kind[i] = 1;
+                    h[i] = edge_handle(tv, k == axis ? b : axis);
+                    live |= 1u << i;
+                }
             }
         }
-    }
-    uint32_t rank[4], kinds = 0;
+        for (int64_t step = 0; live; ++step) {
+            if (step > a.max_steps) {
+                atomicOr(a.status, ST_ITER);
+                break;
+            }
+            uint32_t w[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        rank[k] = 0;
-        if (kind[k] == 1) {
-            const Vtx q = vtx_of(g, h[k] >> 2);
-            const int64_t wi = edge_bitmap_word(g, q.x, q.y, q.z, int(h[k] & 3));
-            if (!((a.junc_bits[wi] >> (q.x & 31)) & 1u)) atomicOr(a.status, ST_INTERNAL);
-            rank[k] = bit_rank(a.junc_bits, a.junc_prefix, wi, q.x & 31);
-        } else if (kind[k] == 2) {
-            const Vtx q = vtx_of(g, (h[k] & 0x7FFFFFFFu) >> 2);
-            const int slot = 7 ^ (1 << (h[k] & 3u));
-            rank[k] = bit_rank(a.crit_bits, a.crit_prefix, g.slot_word(slot, q.z, q.y, q.x >> 5), q.x & 31);
+            for (int k = 0; k < 4; ++k) w[k] = (live >> k) & 1u ? a.info[info_index(g, h[k])] : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!((live >> k) & 1u)) continue;
+                if (w[k] == INFO_DEAD) {  // a dead path: dropped
+                    kind[k] = 0;
+                    live &= ~(1u << k);
+                } else if (w[k] == INFO_BRANCH) {  // ends at the junction h[k]
+                    live &= ~(1u << k);
+                } else if (w[k] & 0x80000000u) {  // ends at a 2-saddle
+                    kind[k] = 2;
+                    h[k] = w[k];
+                    live &= ~(1u << k);
+                } else {
+                    h[k] = w[k];
+                }
+            }
         }
-        kinds |= kind[k] << (8 * k);
-    }
-    reinterpret_cast<uint4*>(a.tgt)[u] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
-    reinterpret_cast<uint32_t*>(a.kinds)[u] = kinds;
-    uint32_t col[4], mult[4];
-    const bool saddle = u < N1;
-    const int64_t row = saddle ? u : u - N1;
-    const uint32_t mj = uint32_t(distinct_targets(rank, kinds, 1, col, mult));
-    const uint32_t m2 = uint32_t(distinct_targets(rank, kinds, 2, col, mult));
-    a.cnt[saddle ? 0 : 1][row] = mj;
-    a.cnt[saddle ? 3 : 2][row] = m2;
-    nnz[saddle ? 0 : 1] += mj;
-    nnz[saddle ? 3 : 2] += m2;
+        // ranks: a junction's in the junction bitmap (1-cell row layout), a 2-saddle's in the
+        // critical bitmap of its slot
+        uint32_t rank[4], kinds = 0;
+        bool missing = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool isj = kind[k] == 1;
+            const uint32_t t = h[k] & 3u;
+            const uint32_t tv = (h[k] & 0x7FFFFFFFu) >> 2;
+            const uint32_t q = g.div_nx.div(tv);
+            const uint32_t tx = tv - q * nx;
+            const uint32_t tz = g.div_ny.div(q);
+            const uint32_t ty = q - tz * ny;
+            const uint32_t wi = isj ? (((tz * 2 + (t == 2)) * ny + ty) * 2 + (t == 1)) * W + (tx >> 5)
+                                    : (((7u ^ (1u << t)) * nz + tz) * ny + ty) * W + (tx >> 5);
+            const uint32_t* bits = isj ? a.junc_bits : a.crit_bits;
+            const uint32_t* pre = isj ? a.junc_prefix : a.crit_prefix;
+            rank[k] = 0;
+            if (kind[k]) {
+                const uint32_t bw = bits[wi];
+                rank[k] = pre[wi] + __popc(bw & ((1u << (tx & 31u)) - 1u));
+                missing |= isj && !((bw >> (tx & 31u)) & 1u);
+            }
+            kinds |= kind[k] << (8 * k);
+        }
+        if (missing) atomicOr(a.status, ST_INTERNAL);
+        reinterpret_cast<uint4*>(a.tgt)[u] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
+        reinterpret_cast<uint32_t*>(a.kinds)[u] = kinds;
+        const bool saddle = u < N1;
+        const uint32_t mj = distinct_count(rank, kind, 1), m2 = distinct_count(rank, kind, 2);
+        nnz_a += saddle ? mj : 0u;
+        nnz_b += saddle ? 0u : mj;
+        nnz_bs += saddle ? 0u : m2;
+        nnz_d += saddle ? m2 : 0u;
     }
     __shared__ unsigned long long part[4][THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long nnz[4] = {nnz_a, nnz_b, nnz_bs, nnz_d};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         unsigned long long v = nnz[k];
@@ -190,6 +235,19 @@ struct CsrArgs {
     uint32_t* col[4];
     uint32_t* mult[4];
 };
+
+__global__ void __launch_bounds__(THREADS) csr_count(CsrArgs a) {
+    const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
+    if (u >= a.n1 + a.nj) return;
+    const uint4 t = reinterpret_cast<const uint4*>(a.tgt)[u];
+    const uint32_t kw = a.kinds[u];
+    const uint32_t rank[4] = {t.x, t.y, t.z, t.w};
+    const uint32_t kind[4] = {trace_kind(kw, 0), trace_kind(kw, 1), trace_kind(kw, 2), trace_kind(kw, 3)};
+    const bool saddle = u < a.n1;
+    const int64_t row = saddle ? u : u - a.n1;
+    a.cnt[saddle ? 0 : 1][row] = distinct_count(rank, kind, 1);
+    a.cnt[saddle ? 3 : 2][row] = distinct_count(rank, kind, 2);
+}
 
 __global__ void __launch_bounds__(THREADS) csr_fill(CsrArgs a) {
     const int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x;
@@ -218,9 +276,6 @@ msc_status run_trace(Plan* p, cudaStream_t s) {
     const int64_t nsrc = cap1 + capj;
     if ((st = ensure(p, p->trace, sizeof(uint32_t) * 4 * size_t(nsrc ? nsrc : 1)))) return st;
     if ((st = ensure(p, p->trace_kinds, sizeof(uint32_t) * size_t(nsrc ? nsrc : 1)))) return st;
-    // per-row counts of A (cap1 rows), B, B* (capj), D (cap1), in that order
-    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * size_t(2 * nsrc ? 2 * nsrc : 1)))) return st;
-    const int64_t rows[4] = {cap1, capj, capj, cap1};
     TraceArgs ta{};
     ta.g = g;
     ta.words = static_cast<const uint32_t*>(p->words.ptr);
@@ -233,12 +288,6 @@ msc_status run_trace(Plan* p, cudaStream_t s) {
     ta.info = static_cast<const uint32_t*>(p->node_info.ptr);
     ta.tgt = static_cast<uint32_t*>(p->trace.ptr);
     ta.kinds = static_cast<uint8_t*>(p->trace_kinds.ptr);
-    size_t off = 0;
-    for (int w = 0; w < 4; ++w) {
-        p->minor_cnt_off[w] = int64_t(off);
-        ta.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
-        off += size_t(rows[w]);
-    }
     ta.n1_dev = &p->dsum()->counts[1];
     ta.nj_dev = &p->dsum()->n_junctions;
     ta.cap1 = cap1;
@@ -269,13 +318,22 @@ msc_status build_minor_csr(Plan* p, cudaStream_t s) {
         scratch_total += (row_scan_scratch_bytes(rows[w]) + 255) / 256 * 256;
     }
     if ((st = ensure(p, p->minor_scan, scratch_total ? scratch_total : 1))) return st;
+    // per-row counts of A (n1 rows), B, B* (nj), D (n1), in that order
+    if ((st = ensure(p, p->minor_rowcnt, sizeof(uint32_t) * size_t(2 * (n1 + nj) ? 2 * (n1 + nj) : 1)))) return st;
     CsrArgs ca{};
     ca.n1 = n1;
     ca.nj = nj;
     ca.tgt = static_cast<const uint32_t*>(p->trace.ptr);
     ca.kinds = static_cast<const uint32_t*>(p->trace_kinds.ptr);
+    for (int64_t w = 0, off = 0; w < 4; ++w) {
+        ca.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + off;
+        off += rows[w];
+    }
+    if (n1 + nj) {
+        csr_count<<<blocks(n1 + nj), THREADS, 0, s>>>(ca);
+        launched(p);
+    }
     for (int w = 0; w < 4; ++w) {
-        ca.cnt[w] = static_cast<uint32_t*>(p->minor_rowcnt.ptr) + p->minor_cnt_off[w];
         if ((st = ensure(p, p->minor_rowptr[w], sizeof(int64_t) * size_t(rows[w] + 1)))) return st;
         ca.rowptr[w] = static_cast<const int64_t*>(p->minor_rowptr[w].ptr);
         p->minor_rows[w] = rows[w];

@@ -41,7 +41,7 @@ __device__ __forceinline__ bool count_fits(uint32_t* status, unsigned long long 
 // ---- per-pass results the host needs, kept on the device and read back in one copy --------
 // Path-count counter slots in Summary::pc.
 enum PcCounter { PC_CURSOR = 0, PC_MAX = 1, PC_ITER = 2, PC_ENTRIES = 3, PC_DEFER0 = 4, PC_DEFER1 = 5, PC_NEXT = 6,
-                 PC_DEFER2 = 7 };
+                 PC_DEFER2 = 7, PC_DEFER3 = 8, PC_SLOTS = 10 };
 struct Summary {
     unsigned long long counts[4];     // critical cells per dimension
     unsigned long long n_junctions;
@@ -50,7 +50,7 @@ struct Summary {
     unsigned long long jump_rounds;   // pointer-jumping rounds
     unsigned long long sweep_iters;   // iterations of the reachability loop (two sweeps each)
     unsigned long long minor_nnz[4];  // distinct entries of A, B, B*, D
-    unsigned long long pc[8];         // path-count counters (pathcount.cu)
+    unsigned long long pc[10];        // path-count counters (PcCounter)
     unsigned long long dstar_nnz;
     unsigned long long dp_wave_done;      // junction DP: junctions done in the current wave
     unsigned long long dp_pool_used;      // junction DP: J-row pool slots taken
@@ -136,7 +136,6 @@ struct Plan {
     int64_t n_junctions = 0;
     int64_t minor_nnz[4] = {0, 0, 0, 0};
     int64_t minor_rows[4] = {0, 0, 0, 0};
-    int64_t minor_cnt_off[4] = {0, 0, 0, 0};  // where each matrix's row counts start in minor_rowcnt
     int64_t dstar_nnz = 0;
     int64_t pc_staging_cap = 0;  // staging slots of the last path-count run
     int64_t dp_pool_cap = 0;     // J-row pool slots of the last junction-DP run

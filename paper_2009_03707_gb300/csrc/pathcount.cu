@@ -29,10 +29,11 @@ namespace {
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr int T0_WARPS = 8;
 constexpr int T0_THREADS = T0_WARPS * 32;
-constexpr int T0_F = 8;    // frontier table slots per row (power of two)
-constexpr int T0_LF = 3;   // log2(T0_F)
-constexpr int T0_D = 16;   // D* table slots per row (power of two)
-constexpr int T0_LD = 4;   // log2(T0_D)
+// tier 0: frontier and D* table slots per row (powers of two); tier 0b: the same kernel with
+// larger tables for the few rows that outgrow tier 0 (more shared memory per row, so fewer rows
+// in flight -- which only the deferred rows pay for)
+constexpr int T0_F = 8, T0_LF = 3, T0_D = 16, T0_LD = 4;
+constexpr int T0B_F = 16, T0B_LF = 4, T0B_D = 32, T0B_LD = 5;
 constexpr int T0_OUT_CHUNK = 1024;  // staging slots a warp takes at a time
 constexpr int T1_WARPS = 4;
 constexpr int T1_HASH = 256;  // slots per table (power of two)
@@ -95,13 +96,14 @@ __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
 // with shared-memory atomics.  So a lane's work does not depend on its own row's size, and
 // every per-row loop is a fixed, unrolled one.  A row whose table fills up, or whose counts
 // outgrow 32 bits, is deferred intact to the uint64 warp tier.
+template <int F, int D>
 struct T0Warp {
-    uint32_t fk[2][T0_F][32];
-    uint32_t fv[2][T0_F][32];
-    uint32_t dk[T0_D][32];
-    uint32_t dv[T0_D][32];
+    uint32_t fk[2][F][32];
+    uint32_t fv[2][F][32];
+    uint32_t dk[D][32];
+    uint32_t dv[D][32];
     unsigned long long base[32];  // staging offset of each finishing row
-    uint16_t items[32 * T0_D];    // this round's work list: slot << 5 | row
+    uint16_t items[32 * (F > D ? F : D)];  // this round's work list: slot << 5 | row
 };
 
 // Adds val to key's entry in row r's table (K, V: [slot][32] arrays of 2^lg slots); false if
@@ -162,20 +164,21 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
 // Persistent: lanes without a row take new ones (one atomic per warp); every round advances all
 // of the warp's rows by one frontier step, and finished rows are written out item-parallel,
 // each entry at its rank within the row (rows come out sorted by column).
+template <int F, int LF, int D, int LD>
 __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next_row) {
     PcArgs a = args;
     if (!resolve(a)) return;
     extern __shared__ __align__(16) unsigned char t0_raw[];
-    T0Warp& sh = reinterpret_cast<T0Warp*>(t0_raw)[threadIdx.x >> 5];
+    T0Warp<F, D>& sh = reinterpret_cast<T0Warp<F, D>*>(t0_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint32_t lane_bit = 1u << lane;
 #pragma unroll
-    for (int j = 0; j < T0_F; ++j) {
+    for (int j = 0; j < F; ++j) {
         sh.fk[0][j][lane] = sh.fk[1][j][lane] = EMPTY;
         sh.fv[0][j][lane] = sh.fv[1][j][lane] = 0;
     }
 #pragma unroll
-    for (int j = 0; j < T0_D; ++j) {
+    for (int j = 0; j < D; ++j) {
         sh.dk[j][lane] = EMPTY;
         sh.dv[j][lane] = 0;
     }
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
                     if (!kind) continue;
                     const bool junction = kind == 1;
                     t0_add_rt(junction ? &sh.fk[c][0][0] : &sh.dk[0][0], junction ? &sh.fv[c][0][0] : &sh.dv[0][0],
-                              junction ? T0_LF : T0_LD, lane, tg[k2], 1);
+                              junction ? LF : LD, lane, tg[k2], 1);
                 }
             }
         }
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         // one frontier step of every row: the list of (slot, row) frontier entries
         bool expand = false;
 #pragma unroll
-        for (int j = 0; j < T0_F; ++j) expand |= s >= 0 && sh.fk[c][j][lane] != EMPTY;
+        for (int j = 0; j < F; ++j) expand |= s >= 0 && sh.fk[c][j][lane] != EMPTY;
         if (expand && int64_t(++iter) > a.max_iter) {
             atomicOr(a.status, ST_ITER);  // the row is cut short; the result is void anyway
             expand = false;
@@ -246,12 +249,12 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         // the warp's list of (slot, row) frontier entries, then one entry per lane
         unsigned fm = 0;
 #pragma unroll
-        for (int j = 0; j < T0_F; ++j) fm |= unsigned(expand && sh.fk[c][j][lane] != EMPTY) << j;
+        for (int j = 0; j < F; ++j) fm |= unsigned(expand && sh.fk[c][j][lane] != EMPTY) << j;
         entries += __popc(fm);
         unsigned total = 0;
         unsigned at = warp_prefix(unsigned(__popc(fm)), lane, &total);
 #pragma unroll
-        for (int j = 0; j < T0_F; ++j)
+        for (int j = 0; j < F; ++j)
             if ((fm >> j) & 1u) sh.items[at++] = uint16_t((j << 5) | lane);
         __syncwarp();
         uint32_t bad = 0;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
                 const uint32_t kind = trace_kind(kj, k);
                 if (!kind) continue;
                 const bool junction = kind == 1;
-                ok &= t0_add_rt(junction ? nk : &sh.dk[0][0], junction ? nv : &sh.dv[0][0], junction ? T0_LF : T0_LD, r,
+                ok &= t0_add_rt(junction ? nk : &sh.dk[0][0], junction ? nv : &sh.dv[0][0], junction ? LF : LD, r,
                                 tq[k], cnt);
             }
             if (!ok) bad |= 1u << r;
@@ -281,20 +284,20 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         __syncwarp();
         // the current tables are spent: clear this lane's and swap
 #pragma unroll
-        for (int j = 0; j < T0_F; ++j) {
+        for (int j = 0; j < F; ++j) {
             sh.fk[c][j][lane] = EMPTY;
             sh.fv[c][j][lane] = 0;
         }
         c ^= 1;
         bool more = false;
 #pragma unroll
-        for (int j = 0; j < T0_F; ++j) more |= sh.fk[c][j][lane] != EMPTY;
+        for (int j = 0; j < F; ++j) more |= sh.fk[c][j][lane] != EMPTY;
         const bool defer = s >= 0 && (bad & lane_bit);
         const bool done = s >= 0 && !defer && !more;
         // finished rows: entries of the D* tables, item-parallel, placed by rank within the row
         unsigned dm = 0;
 #pragma unroll
-        for (int j = 0; j < T0_D; ++j) dm |= unsigned(done && sh.dk[j][lane] != EMPTY) << j;
+        for (int j = 0; j < D; ++j) dm |= unsigned(done && sh.dk[j][lane] != EMPTY) << j;
         const unsigned mine_n = unsigned(__popc(dm));
         unsigned nout = 0;
         const unsigned off = warp_prefix(mine_n, lane, &nout);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
             sh.base[lane] = base;
             unsigned o = off;
 #pragma unroll
-            for (int j = 0; j < T0_D; ++j)
+            for (int j = 0; j < D; ++j)
                 if ((dm >> j) & 1u) sh.items[o++] = uint16_t((j << 5) | lane);
             if (done) {
                 a.row_start[s] = int64_t(base);
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
                 const uint32_t val = sh.dv[j][r];
                 int rank = 0;
 #pragma unroll
-                for (int jj = 0; jj < T0_D; ++jj) rank += sh.dk[jj][r] < key;  // EMPTY sorts last
+                for (int jj = 0; jj < D; ++jj) rank += sh.dk[jj][r] < key;  // EMPTY sorts last
                 const u64 dst = sh.base[r] + u64(rank);
                 if (dst < a.out_cap) {
                     a.out_col[dst] = key;
@@ -349,12 +352,12 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         if (defer) a.deferred[dpos] = uint32_t(s);
         if (done || defer) {  // leave this lane's tables clean for its next row
 #pragma unroll
-            for (int j = 0; j < T0_D; ++j) {
+            for (int j = 0; j < D; ++j) {
                 sh.dk[j][lane] = EMPTY;
                 sh.dv[j][lane] = 0;
             }
 #pragma unroll
-            for (int j = 0; j < T0_F; ++j) {
+            for (int j = 0; j < F; ++j) {
                 sh.fk[c][j][lane] = EMPTY;
                 sh.fv[c][j][lane] = 0;
             }
@@ -642,7 +645,7 @@ __global__ void gather_rows(const unsigned long long* n1_dev, int64_t cap, const
 
 // Counter slots in Summary::pc.
 enum { C_CURSOR = PC_CURSOR, C_MAX = PC_MAX, C_ITER = PC_ITER, C_ENTRIES = PC_ENTRIES, C_DEFER0 = PC_DEFER0,
-       C_DEFER1 = PC_DEFER1, C_NEXT = PC_NEXT, C_DEFER2 = PC_DEFER2 };
+       C_DEFER1 = PC_DEFER1, C_NEXT = PC_NEXT, C_DEFER2 = PC_DEFER2, C_DEFER3 = PC_DEFER3 };
 
 }  // namespace
 
@@ -674,7 +677,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             if ((st = ensure(p, p->pc_cnt, sizeof(u64) * cap))) return st;
             if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * cap))) return st;
             if ((st = ensure(p, p->dstar_count, sizeof(u64) * cap))) return st;
-            if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * 8, s), "memset counters"))) return st;
+            if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * PC_SLOTS, s), "memset counters"))) return st;
             if ((st = run_junction_dp(p, s, pool, cap))) return st;
             if (!cap_mode) {
                 if ((st = read_summary(p, s))) return st;
@@ -713,18 +716,27 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         return fail(p, MSC_ERR_CUDA, "internal: D* staging did not converge");
     }
     const int first_tier = std::max(0, std::min(2, int(p->opts.path_count_tier)));
-    // tier-0 grid: persistent, as many CTAs as fit
-    const size_t t0_smem = sizeof(T0Warp) * T0_WARPS;
-    if ((st = check_cuda(p, cudaFuncSetAttribute(rows_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
+    // tier-0 and tier-0b grids: persistent, as many CTAs as fit
+    const size_t t0_smem = sizeof(T0Warp<T0_F, T0_D>) * T0_WARPS;
+    const size_t t0b_smem = sizeof(T0Warp<T0B_F, T0B_D>) * T0_WARPS;
+    auto* k0 = rows_thread<T0_F, T0_LF, T0_D, T0_LD>;
+    auto* k0b = rows_thread<T0B_F, T0B_LF, T0B_D, T0B_LD>;
+    if ((st = check_cuda(p, cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
+                         "cudaFuncSetAttribute(rows_thread)")) ||
+        (st = check_cuda(p, cudaFuncSetAttribute(k0b, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0b_smem)),
                          "cudaFuncSetAttribute(rows_thread)")))
         return st;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_thread, T0_THREADS, t0_smem);
+    int per_sm = 0, per_sm_b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, T0_THREADS, t0_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k0b, T0_THREADS, t0b_smem);
     const int t0_grid = int(std::max<int64_t>(
         1, std::min<int64_t>((n1cap + T0_THREADS - 1) / T0_THREADS, int64_t(std::max(1, per_sm)) * p->num_sms)));
+    const int t0b_grid = int(std::max<int64_t>(
+        1, std::min<int64_t>((n1cap + T0_THREADS - 1) / T0_THREADS, int64_t(std::max(1, per_sm_b)) * p->num_sms)));
     // staging capacity, including what tier-0 warps may leave unused at the end of their chunks;
     // a synchronised run grows it and reruns the stage on overflow, a replayed graph asks for a rerun
-    const uint64_t slack = uint64_t(t0_grid) * T0_WARPS * (T0_OUT_CHUNK + 32 * T0_D);
+    const uint64_t slack = uint64_t(t0_grid) * T0_WARPS * (T0_OUT_CHUNK + 32 * T0_D) +
+                           uint64_t(t0b_grid) * T0_WARPS * (T0_OUT_CHUNK + 32 * T0B_D);
     uint64_t cap = cap_mode ? uint64_t(p->caps.staging)
                             : uint64_t(std::max<int64_t>(p->dstar_nnz + p->dstar_nnz / 4, 8 * n1cap + 1024)) + slack;
     // a row never needs more slots than 2 x max(junctions, 2-saddles)
@@ -735,7 +747,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         if ((st = ensure(p, p->pc_cnt, sizeof(u64) * cap))) return st;
         if ((st = ensure(p, p->dstar_col, sizeof(uint32_t) * cap))) return st;
         if ((st = ensure(p, p->dstar_count, sizeof(u64) * cap))) return st;
-        if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * 8, s), "memset counters"))) return st;
+        if ((st = check_cuda(p, cudaMemsetAsync(ctr, 0, sizeof(u64) * PC_SLOTS, s), "memset counters"))) return st;
         PcArgs a{};
         a.n1_dev = &p->dsum()->counts[1];
         a.nj_dev = &p->dsum()->n_junctions;
@@ -754,7 +766,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         a.row_len = static_cast<uint32_t*>(p->pc_rowlen.ptr);
         a.max_iter = p->opts.max_iterations;
         a.status = p->status_word();
-        // tier 0 takes every row (unless a tier is forced); each tier defers into the other list
+        // each tier takes the rows the previous one deferred; tier 3 here means tier 0b
         auto launch = [&](int tier, const uint32_t* rows, const u64* nrows, uint32_t* defer, u64* defer_ctr, int lg,
                           bool last) {
             a.rows = rows;
@@ -762,10 +774,15 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
             a.deferred = defer;
             a.deferred_count = defer_ctr;
             a.retry_on_defer = last && cap_mode;
+            msc_status e;
+            if (tier != 2 && (e = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return e;
             if (tier == 0) {
                 record_event(p, p->kev0, s);
-                rows_thread<<<t0_grid, T0_THREADS, t0_smem, s>>>(a, ctr + C_NEXT);
+                k0<<<t0_grid, T0_THREADS, t0_smem, s>>>(a, ctr + C_NEXT);
                 record_event(p, p->kev1, s);
+                launched(p);
+            } else if (tier == 3) {
+                k0b<<<t0b_grid, T0_THREADS, t0b_smem, s>>>(a, ctr + C_NEXT);
                 launched(p);
             } else if (tier == 1) {
                 rows_warp<<<std::max(1, p->num_sms) * 8, T1_WARPS * 32, 0, s>>>(a, ctr + C_NEXT);
@@ -774,7 +791,6 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
                 const int cap_t = 1 << lg;
                 const int ctas = lg <= 14 ? 128 : lg <= 18 ? 64 : 2;
                 const size_t slots = size_t(ctas) * 3 * size_t(cap_t);
-                msc_status e;
                 // every use leaves the tables empty, so they are initialised only when (re)allocated
                 const bool fresh = p->pc_gk.bytes < sizeof(uint32_t) * slots;
                 if ((e = ensure(p, p->pc_gk, sizeof(uint32_t) * slots))) return e;
@@ -794,16 +810,19 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         };
         const u64* all_rows = &p->dsum()->counts[1];
         int lg = std::min(14, lg_max);
+        // after the last tier: the list (index) and counter of the rows still left
+        int left_list = 1;
+        u64* left_ctr = ctr + C_DEFER2;
         if (first_tier == 0) {
             if ((st = launch(0, nullptr, all_rows, lists[0], ctr + C_DEFER0, 0, false))) return st;
-            if ((st = check_cuda(p, cudaMemsetAsync(ctr + C_NEXT, 0, sizeof(u64), s), "memset"))) return st;
-            if ((st = launch(1, lists[0], ctr + C_DEFER0, lists[1], ctr + C_DEFER1, 0, false))) return st;
-            if ((st = launch(2, lists[1], ctr + C_DEFER1, lists[0], ctr + C_DEFER2, lg, true))) return st;
+            if ((st = launch(3, lists[0], ctr + C_DEFER0, lists[1], ctr + C_DEFER1, 0, false))) return st;
+            if ((st = launch(1, lists[1], ctr + C_DEFER1, lists[0], ctr + C_DEFER3, 0, false))) return st;
+            if ((st = launch(2, lists[0], ctr + C_DEFER3, lists[1], ctr + C_DEFER2, lg, true))) return st;
         } else if (first_tier == 1) {
-            if ((st = launch(1, nullptr, all_rows, lists[1], ctr + C_DEFER1, 0, false))) return st;
-            if ((st = launch(2, lists[1], ctr + C_DEFER1, lists[0], ctr + C_DEFER2, lg, true))) return st;
+            if ((st = launch(1, nullptr, all_rows, lists[0], ctr + C_DEFER1, 0, false))) return st;
+            if ((st = launch(2, lists[0], ctr + C_DEFER1, lists[1], ctr + C_DEFER2, lg, true))) return st;
         } else {
-            if ((st = launch(2, nullptr, all_rows, lists[0], ctr + C_DEFER2, lg, true))) return st;
+            if ((st = launch(2, nullptr, all_rows, lists[1], ctr + C_DEFER2, lg, true))) return st;
         }
         if (!cap_mode) {
             // rows that outgrow the tier-2 tables: bigger tables, on the host's watch
@@ -816,9 +835,9 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
                     return st;
                 continue;
             }
-            int in = 0;
-            u64* in_ctr = ctr + C_DEFER2;
-            u64 left = p->hsum->pc[C_DEFER2];
+            int in = left_list;
+            u64* in_ctr = left_ctr;
+            u64 left = p->hsum->pc[left_ctr - ctr];
             while (left > 0) {
                 if (lg >= lg_max) return fail(p, MSC_ERR_CUDA, "internal: a path-count row does not fit");
                 lg = std::min(lg + 4, lg_max);
@@ -828,7 +847,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
                 if ((st = read_summary(p, s))) return st;
                 in ^= 1;
                 in_ctr = out_ctr;
-                left = *(p->hsum->pc + (out_ctr - ctr));
+                left = p->hsum->pc[out_ctr - ctr];
             }
         }
         // D* row pointers (the scan also gives nnz), then the rows gathered into CSR

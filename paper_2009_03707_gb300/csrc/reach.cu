@@ -222,11 +222,25 @@ __device__ __forceinline__ uint32_t quad_row(const uint32_t* __restrict__ qdown,
     return shifted<DX>(qdown, K * r.qplane + r.qbase + DY * int64_t(r.W) + DZ * int64_t(r.ny) * r.W, r);
 }
 
+// Gradient word of the vertex one step down axis B from v (0 off the grid), loaded for a whole
+// row of lanes at once.
+template <int B>
+__device__ __forceinline__ uint32_t minus_word(const Geom& g, const uint32_t* __restrict__ words, const Rows& r, int x,
+                                               uint32_t v) {
+    if (x >= g.nx) return 0u;
+    if (B == 0) return x > 0 ? words[v - 1] : 0u;
+    if (B == 1) return r.y > 0 ? words[v - uint32_t(g.nx)] : 0u;
+    return r.z > 0 ? words[v - uint32_t(g.nx) * uint32_t(g.ny)] : 0u;
+}
+
 // One warp per word of A-cells (a lane per cell).  The out-edges of a 1-cell e go through its
 // cofacet quads other than its partner that are critical or paired with a facet, so with the
 // down-quad rows (ordered like the partner masks: first/second other axis, - then + side) the
 // out-degree is a popcount.  Reachable cells that are not 1-saddles get their info record; a
-// single successor is decoded from the one quad word it goes through.
+// single successor is decoded from the one quad it goes through, whose owner is v itself (+ side)
+// or v one step down the quad's other axis (- side).  Every load of a word -- the bitmaps and
+// the three owners' gradient words, coalesced rows -- is independent of the others, so a warp
+// has them all in flight at once.
 template <int A>
 __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int lane, const uint32_t* __restrict__ words,
                                               const uint32_t* __restrict__ visited, const uint4* __restrict__ masks,
@@ -236,22 +250,19 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
     constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
     constexpr int K1 = 3 - A - B1, K2 = 3 - A - B2;  // even axes of the quads along B1, B2
     const int64_t i = r.edge<A>(0, 0);
-    const uint32_t vis = visited[i];
     const int x = r.w * 32 + lane;
     const uint32_t v = vid32(g, x, r.y, r.z);
-    uint32_t* const rec_at = x < g.nx ? info + info_index(g, edge_handle(v, A)) : nullptr;
-    // every record of the row is written (whole sectors: no read-modify-write in L2); cells
-    // that are not reached, or are 1-saddles, get a dead-end record that nothing reads
-    if (!vis) {  // warp-uniform
-        if (rec_at) *rec_at = INFO_DEAD;
-        if (lane == 0) junc[i] = 0;
-        return;
-    }
-    if (lane == 0) cnt += __popc(vis);
+    const uint32_t vis = visited[i];
     const uint32_t crit = crit_bits[g.slot_word(1 << A, r.z, r.y, r.w)];
     const uint4 m = masks[i];
     const uint32_t q[4] = {quad_row<K1, -(B1 == 0), -(B1 == 1), -(B1 == 2)>(qdown, r), quad_row<K1, 0, 0, 0>(qdown, r),
                            quad_row<K2, -(B2 == 0), -(B2 == 1), -(B2 == 2)>(qdown, r), quad_row<K2, 0, 0, 0>(qdown, r)};
+    const uint32_t w_self = x < g.nx ? words[v] : 0u;
+    const uint32_t w_b1 = minus_word<B1>(g, words, r, x, v), w_b2 = minus_word<B2>(g, words, r, x, v);
+    uint32_t* const rec_at = x < g.nx ? info + info_index(g, edge_handle(v, A)) : nullptr;
+    // every record of the row is written (whole sectors: no read-modify-write in L2); cells
+    // that are not reached, or are 1-saddles, get a dead-end record that nothing reads
+    if (lane == 0) cnt += __popc(vis);
     const uint32_t partner = ((m.x >> lane) & 1u) | (((m.y >> lane) & 1u) << 1) | (((m.z >> lane) & 1u) << 2) |
                              (((m.w >> lane) & 1u) << 3);
     const uint32_t out = (((q[0] >> lane) & 1u) | (((q[1] >> lane) & 1u) << 1) | (((q[2] >> lane) & 1u) << 2) |
@@ -267,14 +278,12 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
             const int b = sel < 2 ? B1 : B2;
             const int k = 3 - A - b;  // the quad's even axis
             const bool plus = sel & 1;
-            int ox = x, oy = r.y, oz = r.z;
+            uint32_t ov = v, ow = w_self;
             if (!plus) {
-                ox -= b == 0;
-                oy -= b == 1;
-                oz -= b == 2;
+                ov -= b == 0 ? 1u : b == 1 ? uint32_t(g.nx) : uint32_t(g.nx) * uint32_t(g.ny);
+                ow = sel < 2 ? w_b1 : w_b2;
             }
-            uint32_t ov = vid32(g, ox, oy, oz);
-            const uint32_t qc = slot_code(words[ov], 7 ^ (1 << k));
+            const uint32_t qc = slot_code(ow, 7 ^ (1 << k));
             if (qc == 0) {
                 rec = 0x80000000u | (ov << 2) | uint32_t(k);  // a 2-saddle
             } else {                                           // the facet the quad is paired with
@@ -289,7 +298,7 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
     if (lane == 0) junc[i] = jw;
 }
 
-__global__ void __launch_bounds__(THREADS) classify_reached(Geom g, const uint32_t* __restrict__ words,
+__global__ void __launch_bounds__(THREADS, 6) classify_reached(Geom g, const uint32_t* __restrict__ words,
                                                             const uint32_t* __restrict__ visited,
                                                             const uint4* __restrict__ masks,
                                                             const uint32_t* __restrict__ qdown,
