@@ -19,7 +19,7 @@ namespace msc {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int JUMPS = 16;
+constexpr int JUMPS = 64;
 constexpr uint32_t NO_LINK = 0xFFFFFFFFu;
 
 // Initial links.  lab_v[v] = the vertex across v's paired edge, or v for a minimum.

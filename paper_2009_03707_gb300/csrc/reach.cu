@@ -222,6 +222,32 @@ __device__ __forceinline__ uint32_t quad_row(const uint32_t* __restrict__ qdown,
     return shifted<DX>(qdown, K * r.qplane + r.qbase + DY * int64_t(r.W) + DZ * int64_t(r.ny) * r.W, r);
 }
 
+// The bitmap words one axis of a vertex-row word needs: reached and critical bits, the four
+// partner masks, and the down-quad rows of the quads on the - / + side along the first / second
+// other axis (the order of the masks).
+struct AxisIn {
+    uint32_t vis, crit;
+    uint4 m;
+    uint32_t q[4];
+};
+
+template <int A>
+__device__ __forceinline__ AxisIn load_axis(const Geom& g, const Rows& r, const uint32_t* __restrict__ visited,
+                                            const uint4* __restrict__ masks, const uint32_t* __restrict__ qdown,
+                                            const uint32_t* __restrict__ crit_bits) {
+    constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
+    constexpr int K1 = 3 - A - B1, K2 = 3 - A - B2;  // even axes of the quads along B1, B2
+    AxisIn in;
+    in.vis = visited[r.edge<A>(0, 0)];
+    in.crit = crit_bits[g.slot_word(1 << A, r.z, r.y, r.w)];
+    in.m = masks[r.edge<A>(0, 0)];
+    in.q[0] = quad_row<K1, -(B1 == 0), -(B1 == 1), -(B1 == 2)>(qdown, r);
+    in.q[1] = quad_row<K1, 0, 0, 0>(qdown, r);
+    in.q[2] = quad_row<K2, -(B2 == 0), -(B2 == 1), -(B2 == 2)>(qdown, r);
+    in.q[3] = quad_row<K2, 0, 0, 0>(qdown, r);
+    return in;
+}
+
 // Gradient word of the vertex one step down axis B from v (0 off the grid), loaded for a whole
 // row of lanes at once.
 template <int B>
@@ -233,43 +259,27 @@ __device__ __forceinline__ uint32_t minus_word(const Geom& g, const uint32_t* __
     return r.z > 0 ? words[v - uint32_t(g.nx) * uint32_t(g.ny)] : 0u;
 }
 
-// One warp per word of A-cells (a lane per cell).  The out-edges of a 1-cell e go through its
-// cofacet quads other than its partner that are critical or paired with a facet, so with the
-// down-quad rows (ordered like the partner masks: first/second other axis, - then + side) the
-// out-degree is a popcount.  Reachable cells that are not 1-saddles get their info record; a
-// single successor is decoded from the one quad it goes through, whose owner is v itself (+ side)
-// or v one step down the quad's other axis (- side).  Every load of a word -- the bitmaps and
-// the three owners' gradient words, coalesced rows -- is independent of the others, so a warp
-// has them all in flight at once.
+// The A-cells of one vertex-row word (a lane per cell).  The out-edges of a 1-cell e go through
+// its cofacet quads other than its partner that are critical or paired with a facet, so with the
+// down-quad rows the out-degree is a popcount.  Reachable cells that are not 1-saddles get their
+// info record; a single successor is decoded from the one quad it goes through, whose owner is v
+// itself (+ side) or v one step down the quad's other axis (- side, gradient word w_b1 / w_b2).
 template <int A>
-__device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int lane, const uint32_t* __restrict__ words,
-                                              const uint32_t* __restrict__ visited, const uint4* __restrict__ masks,
-                                              const uint32_t* __restrict__ qdown, const uint32_t* __restrict__ crit_bits,
+__device__ __forceinline__ void classify_axis(const Geom& g, const Rows& r, int lane, int x, uint32_t v,
+                                              const AxisIn& in, uint32_t w_self, uint32_t w_b1, uint32_t w_b2,
                                               uint32_t* __restrict__ info, uint32_t* __restrict__ junc,
                                               unsigned long long& cnt) {
     constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
-    constexpr int K1 = 3 - A - B1, K2 = 3 - A - B2;  // even axes of the quads along B1, B2
-    const int64_t i = r.edge<A>(0, 0);
-    const int x = r.w * 32 + lane;
-    const uint32_t v = vid32(g, x, r.y, r.z);
-    const uint32_t vis = visited[i];
-    const uint32_t crit = crit_bits[g.slot_word(1 << A, r.z, r.y, r.w)];
-    const uint4 m = masks[i];
-    const uint32_t q[4] = {quad_row<K1, -(B1 == 0), -(B1 == 1), -(B1 == 2)>(qdown, r), quad_row<K1, 0, 0, 0>(qdown, r),
-                           quad_row<K2, -(B2 == 0), -(B2 == 1), -(B2 == 2)>(qdown, r), quad_row<K2, 0, 0, 0>(qdown, r)};
-    const uint32_t w_self = x < g.nx ? words[v] : 0u;
-    const uint32_t w_b1 = minus_word<B1>(g, words, r, x, v), w_b2 = minus_word<B2>(g, words, r, x, v);
-    uint32_t* const rec_at = x < g.nx ? info + info_index(g, edge_handle(v, A)) : nullptr;
     // every record of the row is written (whole sectors: no read-modify-write in L2); cells
     // that are not reached, or are 1-saddles, get a dead-end record that nothing reads
-    if (lane == 0) cnt += __popc(vis);
-    const uint32_t partner = ((m.x >> lane) & 1u) | (((m.y >> lane) & 1u) << 1) | (((m.z >> lane) & 1u) << 2) |
-                             (((m.w >> lane) & 1u) << 3);
-    const uint32_t out = (((q[0] >> lane) & 1u) | (((q[1] >> lane) & 1u) << 1) | (((q[2] >> lane) & 1u) << 2) |
-                          (((q[3] >> lane) & 1u) << 3)) &
+    if (lane == 0) cnt += __popc(in.vis);
+    const uint32_t partner = ((in.m.x >> lane) & 1u) | (((in.m.y >> lane) & 1u) << 1) |
+                             (((in.m.z >> lane) & 1u) << 2) | (((in.m.w >> lane) & 1u) << 3);
+    const uint32_t out = (((in.q[0] >> lane) & 1u) | (((in.q[1] >> lane) & 1u) << 1) |
+                          (((in.q[2] >> lane) & 1u) << 2) | (((in.q[3] >> lane) & 1u) << 3)) &
                          ~partner;
     const int n = __popc(out);
-    const bool mine = ((vis & ~crit) >> lane) & 1u;
+    const bool mine = ((in.vis & ~in.crit) >> lane) & 1u;
     uint32_t rec = INFO_DEAD;
     if (mine) {
         rec = n == 0 ? INFO_DEAD : INFO_BRANCH;
@@ -293,12 +303,15 @@ __device__ __forceinline__ void classify_word(const Geom& g, const Rows& r, int 
             }
         }
     }
-    if (rec_at) *rec_at = rec;
+    if (x < g.nx) info[info_index(g, edge_handle(v, A))] = rec;
     const uint32_t jw = __ballot_sync(0xFFFFFFFFu, mine && n > 1);
-    if (lane == 0) junc[i] = jw;
+    if (lane == 0) junc[r.edge<A>(0, 0)] = jw;
 }
 
-__global__ void __launch_bounds__(THREADS, 6) classify_reached(Geom g, const uint32_t* __restrict__ words,
+// One warp per vertex-row word, all three axes: every load of the word (the bitmaps of the three
+// axes and the gradient words of v and of its three down neighbours, coalesced rows) is issued
+// before any result is computed, so a warp has them all in flight at once.
+__global__ void __launch_bounds__(THREADS, 4) classify_reached(Geom g, const uint32_t* __restrict__ words,
                                                             const uint32_t* __restrict__ visited,
                                                             const uint4* __restrict__ masks,
                                                             const uint32_t* __restrict__ qdown,
@@ -311,12 +324,18 @@ __global__ void __launch_bounds__(THREADS, 6) classify_reached(Geom g, const uin
     for (int64_t t = (int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5; t < nrw;
          t += (int64_t(gridDim.x) * THREADS) >> 5) {  // warp-uniform
         const Rows r(g, t);
-        if (blockIdx.y == 0) classify_word<0>(g, r, lane, words, visited, masks, qdown, crit_bits, info, junc, cnt);
-        else if (blockIdx.y == 1) classify_word<1>(g, r, lane, words, visited, masks, qdown, crit_bits, info, junc, cnt);
-        else classify_word<2>(g, r, lane, words, visited, masks, qdown, crit_bits, info, junc, cnt);
-        if (lane == 0 && blockIdx.y == 0) {  // the unused slot of the 1-cell layout
-            junc[g.edge_word(r.z, 1, r.y, 1, r.w)] = 0;
-        }
+        const int x = r.w * 32 + lane;
+        const uint32_t v = vid32(g, x, r.y, r.z);
+        const AxisIn i0 = load_axis<0>(g, r, visited, masks, qdown, crit_bits);
+        const AxisIn i1 = load_axis<1>(g, r, visited, masks, qdown, crit_bits);
+        const AxisIn i2 = load_axis<2>(g, r, visited, masks, qdown, crit_bits);
+        const uint32_t w0 = x < g.nx ? words[v] : 0u;
+        const uint32_t wx = minus_word<0>(g, words, r, x, v), wy = minus_word<1>(g, words, r, x, v),
+                       wz = minus_word<2>(g, words, r, x, v);
+        classify_axis<0>(g, r, lane, x, v, i0, w0, wy, wz, info, junc, cnt);
+        classify_axis<1>(g, r, lane, x, v, i1, w0, wx, wz, info, junc, cnt);
+        classify_axis<2>(g, r, lane, x, v, i2, w0, wx, wy, info, junc, cnt);
+        if (lane == 0) junc[g.edge_word(r.z, 1, r.y, 1, r.w)] = 0;  // the unused slot of the 1-cell layout
     }
     __shared__ unsigned long long part[THREADS / 32];
     if (lane == 0) part[threadIdx.x >> 5] = cnt;
@@ -382,8 +401,7 @@ msc_status run_junctions(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->junc_prefix, sizeof(uint32_t) * size_t(nw)))) return st;
     if ((st = ensure(p, p->node_info, sizeof(uint32_t) * 3 * size_t(g.nverts)))) return st;
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
-    const dim3 grid(unsigned(std::max(1, grid_for(p, nrw * 32) / 3)), 3);
-    classify_reached<<<grid, THREADS, 0, s>>>(
+    classify_reached<<<grid_for(p, nrw * 32), THREADS, 0, s>>>(
         g, static_cast<const uint32_t*>(p->words.ptr), static_cast<const uint32_t*>(p->visited.ptr),
         static_cast<const uint4*>(p->reach_masks.ptr), static_cast<const uint32_t*>(p->reach_qdown.ptr),
         static_cast<const uint32_t*>(p->crit_bits.ptr), static_cast<uint32_t*>(p->node_info.ptr),
