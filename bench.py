@@ -52,6 +52,13 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _rounded(d):
+    """Floats in a (nested) dict to 6 significant digits, for the JSON line."""
+    if isinstance(d, dict):
+        return {k: _rounded(v) for k, v in d.items()}
+    return float(f"{d:.6g}") if isinstance(d, float) else d
+
+
 def _num_sms():
     import torch
 
@@ -382,7 +389,8 @@ def run_gpu(args):
                                                              (last["gradient_tile"] >> 8) & 0xFF))
                    + f" vertices, {last['gradient_tile'] >> 16} threads (autotuned)",
                    "path_count_method": {1: "row-wise products", 2: "junction waves"}.get(
-                       last["path_count_method"], "?") + " (chosen automatically)"},
+                       last["path_count_method"], "?") + " (chosen automatically)",
+                   "diagnostics": _rounded(msc.diagnostics(last))},
         "e2e": {"value": agg["e2e_value"], "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(bo)},
         "gpu_launches": launches,

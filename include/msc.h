@@ -186,6 +186,18 @@ msc_status msc_minor(msc_plan_t plan, msc_stream_t stream, int which, int64_t* r
 msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, const int64_t** d_rowptr,
                            const uint32_t** d_col, const uint64_t** d_count);
 
+/* ---- the same arcs by 2-saddle -------------------------------------------------------
+ * Sec. 3.5 "Data structure": the complex keeps every arc in both directions, so that the arcs
+ * reaching a critical point can be queried as well as those leaving it.  This is D* in
+ * compressed sparse column form: for each 2-saddle (by rank in d_cells[2]; colptr has
+ * counts[2]+1 int64 entries) the 1-saddles (by rank in d_cells[1]) with a gradient path to it,
+ * increasing within a column, and the same uint64 path counts as msc_saddle_arcs.  Built on the
+ * first call after a pass (host-synchronised; a stable radix sort of the CSR's entries by
+ * column) and kept until the next pass.  Plan-owned, valid until the next pass or
+ * msc_plan_destroy.  nnz: host.  MSC_ERR_TOO_LARGE if D* has 2^32 or more entries. */
+msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, const int64_t** d_colptr,
+                               const uint32_t** d_row, const uint64_t** d_count);
+
 /* Runs every stage (a1..a6) on `stream` for one field; equivalent to the calls above in
  * order.  Results are read afterwards with the getters (they do no further work, except that
  * msc_minor builds the CSR of A, B, B*, D on its first call for a field).

@@ -189,7 +189,7 @@ msc_status bind_device(Plan* p) {
 
 void invalidate(Plan* p) {
     p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = false;
-    p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = false;
+    p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = p->have_dstar_csc = false;
 }
 
 // Host mirrors and statistics from the summary last copied to p->hsum.
@@ -604,6 +604,26 @@ msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, c
     if (d_rowptr) *d_rowptr = static_cast<const int64_t*>(p->dstar_rowptr.ptr);
     if (d_col) *d_col = static_cast<const uint32_t*>(p->dstar_col.ptr);
     if (d_count) *d_count = static_cast<const uint64_t*>(p->dstar_count.ptr);
+    return MSC_OK;
+}
+
+msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, const int64_t** d_colptr,
+                               const uint32_t** d_row, const uint64_t** d_count) {
+    if (!plan) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    if ((st = ensure_dstar(p, s))) return st;
+    if (!p->have_dstar_csc) {
+        if ((st = msc::build_dstar_csc(p, s))) return st;
+        if ((st = msc::finish_stage(p, s))) return st;
+        p->have_dstar_csc = true;
+    }
+    if (nnz) *nnz = p->dstar_nnz;
+    if (d_colptr) *d_colptr = static_cast<const int64_t*>(p->csc_colptr.ptr);
+    if (d_row) *d_row = static_cast<const uint32_t*>(p->csc_row.ptr);
+    if (d_count) *d_count = static_cast<const uint64_t*>(p->csc_count.ptr);
     return MSC_OK;
 }
 

@@ -282,25 +282,27 @@ int tune_variant(Plan* p, const float* d_field, cudaStream_t s) {
         cudaEventDestroy(e0);
         return 0;
     }
-    int best = 0;
-    float best_ms = 0;
-    for (int v = 0; v < N_VARIANTS; ++v) {
-        // one warm-up launch, then the best of two timed ones
-        if (launch_words(v, g, d_field, words, p->status_word(), s) != cudaSuccess) break;
-        float ms = 0;
-        for (int r = 0; r < 2; ++r) {
+    // a warm-up launch of every variant, then three rounds over all of them (so that a clock
+    // still ramping up, or a neighbour's burst, does not favour one variant); each variant's
+    // best round counts
+    float best_of[N_VARIANTS];
+    int nv = N_VARIANTS;
+    for (int v = 0; v < nv; ++v) {
+        best_of[v] = 1e30f;
+        if (launch_words(v, g, d_field, words, p->status_word(), s) != cudaSuccess) nv = v;
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int v = 0; v < nv; ++v) {
             cudaEventRecord(e0, s);
             launch_words(v, g, d_field, words, p->status_word(), s);
             cudaEventRecord(e1, s);
             float t = 0;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) t = 1e30f;
-            ms = r == 0 ? t : std::min(ms, t);
+            best_of[v] = std::min(best_of[v], t);
         }
-        if (v == 0 || ms < best_ms) {
-            best = v;
-            best_ms = ms;
-        }
-    }
+    int best = 0;
+    for (int v = 1; v < nv; ++v)
+        if (best_of[v] < best_of[best]) best = v;
     cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

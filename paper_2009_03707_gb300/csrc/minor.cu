@@ -97,8 +97,19 @@ __global__ void __launch_bounds__(THREADS, 6) trace_kernel(TraceArgs a) {
     const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), nz = uint32_t(g.nz), W = uint32_t(g.W);
     const uint32_t N1 = uint32_t(n1), NS = uint32_t(n1 + nj);
     unsigned long long nnz_a = 0, nnz_b = 0, nnz_bs = 0, nnz_d = 0;
-    for (uint32_t u = blockIdx.x * THREADS + threadIdx.x; u < NS; u += gridDim.x * THREADS) {
-        const uint32_t id = u < N1 ? a.s1[u] : a.junc_cells[u - N1];
+    // Both source lists are in cell-id order.  The grid is split between them in proportion
+    // (whole warps), so every grid-stride step covers the same slab of the volume in both lists
+    // and the records of that slab are read from DRAM once rather than once per list.
+    const uint32_t G = gridDim.x * THREADS, t = blockIdx.x * THREADS + threadIdx.x;
+    uint32_t G1 = NS ? uint32_t((uint64_t(G) * N1 + NS / 2) / NS + 16) / 32 * 32 : 0;
+    if (N1 && G1 < 32) G1 = 32;
+    if (NS > N1 && G1 > G - 32) G1 = G - 32;
+    if (NS == N1) G1 = G;
+    const bool sad_thread = t < G1;
+    const uint32_t stride = sad_thread ? G1 : G - G1, lim = sad_thread ? N1 : NS - N1;
+    for (uint32_t i = sad_thread ? t : t - G1; i < lim; i += stride) {
+        const uint32_t u = sad_thread ? i : N1 + i;
+        const uint32_t id = sad_thread ? a.s1[i] : a.junc_cells[i];
         const uint32_t q1 = g.div_rx.div(id);
         const uint32_t cx = id - q1 * g.rx;
         const uint32_t cz = g.div_ry.div(q1);

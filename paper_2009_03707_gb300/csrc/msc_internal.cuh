@@ -89,6 +89,7 @@ struct Plan {
     DeviceBuffer trace, trace_kinds, minor_rowcnt, minor_scan, minor_rowptr[4], minor_col[4], minor_mult[4];
     DeviceBuffer pc_rowstart, pc_rowlen, pc_big, pc_col, pc_cnt, pc_gk, pc_gv, pc_gocc;
     DeviceBuffer dstar_rowptr, dstar_col, dstar_count;
+    DeviceBuffer csc_colptr, csc_row, csc_count, csc_work;  // D* by 2-saddle (transpose.cu)
     DeviceBuffer dp_pend, dp_in_cnt, dp_in_ptr, dp_in_idx, dp_j_off, dp_j_len, dp_pool_col, dp_pool_cnt;
 
     template <class F>
@@ -101,7 +102,7 @@ struct Plan {
                                &minor_mult[0], &minor_mult[1], &minor_mult[2], &minor_mult[3], &pc_rowstart, &pc_rowlen,
                                &pc_big, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc, &dstar_rowptr, &dstar_col,
                                &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
-                               &dp_j_len, &dp_pool_col, &dp_pool_cnt};
+                               &dp_j_len, &dp_pool_col, &dp_pool_cnt, &csc_colptr, &csc_row, &csc_count, &csc_work};
         for (DeviceBuffer* b : all) f(*b);
     }
 
@@ -143,7 +144,8 @@ struct Plan {
     int pc_method_used = 0;      // the method of the last run
     // which stages are valid for the current field
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
-         have_junctions = false, have_trace = false, have_minor = false, have_dstar = false;
+         have_junctions = false, have_trace = false, have_minor = false, have_dstar = false,
+         have_dstar_csc = false;
     cudaEvent_t kev0 = nullptr, kev1 = nullptr;  // around the tier-0 path-count kernel
     cudaEvent_t tev0 = nullptr, tev1 = nullptr;  // around the trace kernel
     cudaEvent_t gev0 = nullptr, gev1 = nullptr;  // around the lower-star kernel
@@ -206,6 +208,7 @@ msc_status run_junctions(Plan* p, cudaStream_t s);
 msc_status run_trace(Plan* p, cudaStream_t s);      // the minor's 4-slot trace (pipeline)
 msc_status build_minor_csr(Plan* p, cudaStream_t s);  // CSR of A, B, B*, D (on request; syncs)
 msc_status run_path_count(Plan* p, cudaStream_t s);
+msc_status build_dstar_csc(Plan* p, cudaStream_t s);  // D* by 2-saddle (on request; syncs)
 msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t out_cap);
 int grid_cap(const Plan* p, int64_t threads, int block, int per_sm = 8);  // grid for a count-bounded loop
 

@@ -38,13 +38,14 @@ __device__ __forceinline__ int other_axis(int a, int j) { return j == 0 ? (a == 
 // Word addressing of the bitmaps, per thread: the 1-cell row layout is
 //   edge_word(z, c, y, b, w) = z*sz + y*sy + off[axis] + w   (sz = 4 ny W, sy = 2 W),
 // and the quad bitmaps hold one row per (even axis k, z, y): quad_word = ((k nz + z) ny + y) W + w.
+// Word indices are 32-bit: a plan's bitmaps have fewer than 2^28 words (nverts < 2^29).
 struct Rows {
-    int w, y, z;      // this thread's word: x = 32w .. 32w+31 of row (y, z)
+    int w, y, z;  // this thread's word: x = 32w .. 32w+31 of row (y, z)
     int W, ny, nz;
-    int64_t sy, sz;   // 1-cell layout strides
-    int64_t base;     // z*sz + y*sy + w
-    int64_t qbase;    // (z ny + y) W + w
-    int64_t qplane;   // nz ny W
+    int sy, sz;   // 1-cell layout strides
+    int base;     // z*sz + y*sy + w
+    int qbase;    // (z ny + y) W + w
+    int qplane;   // nz ny W
     __device__ Rows(const Geom& g, int64_t t) {
         const uint32_t q = g.div_W.div(uint32_t(t));
         w = int(uint32_t(t) - q * uint32_t(g.W));
@@ -54,15 +55,15 @@ struct Rows {
         W = g.W;
         ny = g.ny;
         nz = g.nz;
-        sy = 2 * int64_t(W);
-        sz = 4 * int64_t(ny) * W;
+        sy = 2 * W;
+        sz = 4 * ny * W;
         base = z * sz + y * sy + w;
-        qbase = (int64_t(z) * ny + y) * W + w;
-        qplane = int64_t(nz) * ny * W;
+        qbase = (z * ny + y) * W + w;
+        qplane = nz * ny * W;
     }
     template <int AX>
-    __device__ __forceinline__ int64_t edge(int dy, int dz) const {
-        return base + (AX == 1 ? W : AX == 2 ? 2 * int64_t(ny) * W : 0) + dy * sy + dz * sz;
+    __device__ __forceinline__ int edge(int dy, int dz) const {
+        return base + (AX == 1 ? W : AX == 2 ? 2 * ny * W : 0) + dy * sy + dz * sz;
     }
     template <int DY, int DZ>
     __device__ __forceinline__ bool in_range() const {
@@ -72,7 +73,7 @@ struct Rows {
 
 // Bits of a row word at index `at` (the word of x = 32w..), shifted so that bit i refers to x + DX.
 template <int DX>
-__device__ __forceinline__ uint32_t shifted(const uint32_t* __restrict__ R, int64_t at, const Rows& r) {
+__device__ __forceinline__ uint32_t shifted(const uint32_t* __restrict__ R, int at, const Rows& r) {
     const uint32_t mid = R[at];
     if (DX == 0) return mid;
     if (DX > 0) return __funnelshift_r(mid, r.w + 1 < r.W ? R[at + 1] : 0u, 1);
@@ -151,7 +152,7 @@ template <int A>
 __device__ __forceinline__ bool sweep_word(const Rows& r, const uint4* __restrict__ masks,
                                            const uint32_t* __restrict__ Rin, uint32_t* __restrict__ Rout) {
     constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
-    const int64_t i = r.edge<A>(0, 0);
+    const int i = r.edge<A>(0, 0);
     const uint32_t cur = Rin[i];
     const uint4 m = masks[i];
     uint32_t add = 0;
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool sweep_word(const Rows& r, const uint4* __restric
 // in the previous sweep cannot change now; it is skipped, Rout included: that buffer already
 // holds the row's value from two sweeps ago, which is still its value.  Fronts that move slowly
 // through a large grid (many levels) then cost only the rows near the front.
-__global__ void __launch_bounds__(THREADS) reach_sweep(Geom g, const uint4* __restrict__ masks,
+__global__ void __launch_bounds__(THREADS, 4) reach_sweep(Geom g, const uint4* __restrict__ masks,
                                                        const uint32_t* __restrict__ Rin, uint32_t* __restrict__ Rout,
                                                        uint32_t* __restrict__ stamp, const Summary* __restrict__ sum,
                                                        int parity, uint32_t* __restrict__ changed) {
@@ -219,7 +220,7 @@ __global__ void reach_decide(Summary* sum, int64_t max_iter, cudaGraphConditiona
 template <int K, int DX, int DY, int DZ>
 __device__ __forceinline__ uint32_t quad_row(const uint32_t* __restrict__ qdown, const Rows& r) {
     if (!r.in_range<DY, DZ>()) return 0;
-    return shifted<DX>(qdown, K * r.qplane + r.qbase + DY * int64_t(r.W) + DZ * int64_t(r.ny) * r.W, r);
+    return shifted<DX>(qdown, K * r.qplane + r.qbase + DY * r.W + DZ * r.ny * r.W, r);
 }
 
 // The bitmap words one axis of a vertex-row word needs: reached and critical bits, the four

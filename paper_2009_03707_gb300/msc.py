@@ -39,6 +39,7 @@ SIGNATURES = {
     "msc_junctions": ([_P, _P, _PP, _PI64], _I32),
     "msc_minor": ([_P, _P, _I32, _PI64, _PI64, _PP, _PP, _PP], _I32),
     "msc_saddle_arcs": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
+    "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
     "msc_gradient_critical_static": ([_PI64, _P, _P, _PP, _PI64, _PI64, _P], _I32),
@@ -229,6 +230,17 @@ def msc_saddle_arcs(plan: Plan):
             _view(cnt.value, (nnz.value,), "<u8"))
 
 
+def msc_saddle_arcs_csc(plan: Plan):
+    """D* by 2-saddle: (colptr [counts[2]+1] int64, row [nnz] uint32, count [nnz] uint64)."""
+    nnz = ctypes.c_int64()
+    cp, row, cnt = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.msc_saddle_arcs_csc(plan.handle, _stream(), ctypes.byref(nnz), ctypes.byref(cp), ctypes.byref(row),
+                                   ctypes.byref(cnt)), plan.handle)
+    counts, _ = msc_critical(plan)
+    return (_view(cp.value, (counts[2] + 1,), "<i8"), _view(row.value, (nnz.value,), "<u4"),
+            _view(cnt.value, (nnz.value,), "<u8"))
+
+
 def msc_compute(plan: Plan, field: torch.Tensor) -> None:
     if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
         raise ValueError("field must be a contiguous float32 CUDA tensor")
@@ -241,6 +253,28 @@ def msc_get_stats(plan: Plan) -> dict:
     s = MscStats()
     _check(lib.msc_get_stats(plan.handle, ctypes.byref(s)), plan.handle)
     return s.as_dict()
+
+
+def diagnostics(stats: dict) -> dict:
+    """The statistics of the paper's performance analysis (Sec. 4.2) from a run's msc_get_stats:
+    critical points, saddles and junction nodes (and junctions per critical point), the sparsity
+    ratio (zero entries / all entries) of A (1-saddles x junctions), B (junctions x junctions),
+    B* (junctions x 2-saddles), D and D* (1-saddles x 2-saddles), and the number of iterations of
+    the product loop.  A ratio is None for a matrix with no rows or no columns."""
+    c = [int(x) for x in stats["counts"]]
+    n1, n2, nj = c[1], c[2], int(stats["n_junctions"])
+    ncrit = sum(c)
+
+    def sparsity(nnz, rows, cols):
+        return None if rows * cols == 0 else 1.0 - int(nnz) / (rows * cols)
+
+    return dict(critical=ncrit, saddles=n1 + n2, extrema=c[0] + c[3], junctions=nj,
+                junctions_per_critical=None if ncrit == 0 else nj / ncrit,
+                sparsity=dict(A=sparsity(stats["nnz_A"], n1, nj), B=sparsity(stats["nnz_B"], nj, nj),
+                              Bstar=sparsity(stats["nnz_Bstar"], nj, n2), D=sparsity(stats["nnz_D"], n1, n2),
+                              Dstar=sparsity(stats["nnz_Dstar"], n1, n2)),
+                n_iter=int(stats["n_iter"]), max_path_count=int(stats["max_path_count"]),
+                bfs_levels=int(stats["n_bfs_levels"]), peak_device_bytes=int(stats["peak_device_bytes"]))
 
 
 def msc_gradient_critical_static(field: torch.Tensor, words: torch.Tensor, cells, capacity) -> list:
