@@ -198,6 +198,23 @@ msc_status msc_saddle_arcs(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, c
 msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nnz, const int64_t** d_colptr,
                                const uint32_t** d_row, const uint64_t** d_count);
 
+/* ---- the 1-skeleton as one adjacency, exported to the host -----------------------------
+ * Sec. 3.5 "Data structure": the complex as its critical points, each with the arcs incident on
+ * it in both directions (every arc stored at both ends).  Nodes are the critical cells numbered
+ * minima, then 1-saddles, 2-saddles, maxima, each group in its d_cells order (node id = rank +
+ * the counts of the groups before it).  Node u's neighbours are h_adj[h_nodeptr[u] ..
+ * h_nodeptr[u+1]), increasing, with h_mult the number of arcs between the two: the D* path
+ * count for a pair of saddles; 1 or 2 for a saddle and an extremum (2 when both of the saddle's
+ * arcs reach it).  Arcs that leave the domain (max arcs with NONE) are left out.
+ * Size query: *n_adj on entry is the room in h_adj / h_mult; on return *n_nodes and *n_adj are
+ * set, and with h_nodeptr null nothing is copied.  Otherwise h_nodeptr (n_nodes + 1 int64),
+ * h_adj (uint32) and h_mult (uint64) are caller-owned host buffers, filled after a stream
+ * synchronisation; MSC_ERR_CAPACITY (nothing copied) if the room is smaller than *n_adj.
+ * Built on the device on the first call after a pass (host-synchronised) and kept until the next
+ * pass.  MSC_ERR_TOO_LARGE if there are 2^32 or more critical cells. */
+msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
+                             int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult);
+
 /* Runs every stage (a1..a6) on `stream` for one field; equivalent to the calls above in
  * order.  Results are read afterwards with the getters (they do no further work, except that
  * msc_minor builds the CSR of A, B, B*, D on its first call for a field).

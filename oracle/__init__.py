@@ -291,6 +291,45 @@ def compute_all(f: np.ndarray, with_minor: bool = True, with_dstar: bool = True)
     return res
 
 
+def complex_graph(counts, lists, min_arcs, max_arcs, dstar):
+    """The 1-skeleton as one adjacency with every arc at both ends (Sec. 3.5 "Data structure").
+
+    Nodes: the critical cells, minima, then 1-saddles, 2-saddles, maxima, each group in cell-id
+    order.  Arcs: each 1-saddle's two arcs to minima and each 2-saddle's two arcs to maxima (an
+    arc to NONE, which leaves the domain, is left out), one unit each; each D* entry (1-saddle,
+    2-saddle, count) as `count` arcs.  Returns (nodeptr, adj, mult): node u's neighbours in
+    increasing order, each with the number of arcs joining the two."""
+    c = [int(x) for x in counts]
+    base = np.cumsum([0] + c)
+    us, vs, ms = [], [], []
+
+    def add(u, v, m):  # both directions
+        us.extend([u, v])
+        vs.extend([v, u])
+        ms.extend([m, m])
+
+    s1 = np.repeat(np.arange(c[1], dtype=np.int64), 2)
+    add(base[1] + s1, base[0] + np.searchsorted(lists[0], np.asarray(min_arcs[:2 * c[1]])), np.ones(2 * c[1], np.uint64))
+    ma = np.asarray(max_arcs[:2 * c[2]])
+    keep = ma != NONE
+    s2 = np.repeat(np.arange(c[2], dtype=np.int64), 2)[keep]
+    add(base[2] + s2, base[3] + np.searchsorted(lists[3], ma[keep]), np.ones(int(keep.sum()), np.uint64))
+    rows, cols, cnt = dstar
+    add(base[1] + np.asarray(rows, np.int64), base[2] + np.asarray(cols, np.int64), np.asarray(cnt, np.uint64))
+    u = np.concatenate([np.asarray(x, np.int64) for x in us]) if us else np.zeros(0, np.int64)
+    v = np.concatenate([np.asarray(x, np.int64) for x in vs]) if vs else np.zeros(0, np.int64)
+    m = np.concatenate([np.asarray(x, np.uint64) for x in ms]) if ms else np.zeros(0, np.uint64)
+    n = int(base[4])
+    key = u * max(n, 1) + v
+    uniq, first = np.unique(key, return_index=True)
+    order = np.argsort(key, kind="stable")
+    sums = np.add.reduceat(m[order], np.searchsorted(key[order], uniq)) if len(uniq) else np.zeros(0, np.uint64)
+    uu, vv = uniq // max(n, 1), uniq % max(n, 1)
+    nodeptr = np.zeros(n + 1, np.int64)
+    np.add.at(nodeptr, uu + 1, 1)
+    return np.cumsum(nodeptr), vv.astype(np.uint32), sums.astype(np.uint64)
+
+
 # ---- sampled queries on large volumes (pairs computed lazily, one lower star at a time) ----
 def lazy_pairs(f, cells):
     f = np.ascontiguousarray(f, dtype=np.float32)

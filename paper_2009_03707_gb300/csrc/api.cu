@@ -189,7 +189,7 @@ msc_status bind_device(Plan* p) {
 
 void invalidate(Plan* p) {
     p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = false;
-    p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = p->have_dstar_csc = false;
+    p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = p->have_dstar_csc = p->have_graph = false;
 }
 
 // Host mirrors and statistics from the summary last copied to p->hsum.
@@ -625,6 +625,44 @@ msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nn
     if (d_row) *d_row = static_cast<const uint32_t*>(p->csc_row.ptr);
     if (d_count) *d_count = static_cast<const uint64_t*>(p->csc_count.ptr);
     return MSC_OK;
+}
+
+msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
+                             int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult) {
+    if (!plan || !n_nodes || !n_adj) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    if ((st = ensure_extremum(p, s))) return st;
+    if ((st = ensure_dstar(p, s))) return st;
+    if (!p->have_dstar_csc) {
+        if ((st = msc::build_dstar_csc(p, s))) return st;
+        if ((st = msc::finish_stage(p, s))) return st;
+        p->have_dstar_csc = true;
+    }
+    if (!p->have_graph) {
+        if ((st = msc::build_complex_graph(p, s))) return st;
+        if ((st = msc::finish_stage(p, s))) return st;
+        p->have_graph = true;
+    }
+    const int64_t room = *n_adj;
+    *n_nodes = p->graph_nodes;
+    *n_adj = p->graph_nadj;
+    if (!h_nodeptr) return MSC_OK;  // size query
+    if (!h_adj || !h_mult) return MSC_ERR_ARG;
+    if (room < p->graph_nadj) return MSC_ERR_CAPACITY;
+    if ((st = msc::check_cuda(p, cudaMemcpyAsync(h_nodeptr, p->graph_nodeptr.ptr,
+                                                 sizeof(int64_t) * size_t(p->graph_nodes + 1), cudaMemcpyDeviceToHost, s),
+                              "graph copy")) ||
+        (st = msc::check_cuda(p, cudaMemcpyAsync(h_adj, p->graph_adj.ptr, sizeof(uint32_t) * size_t(p->graph_nadj),
+                                                 cudaMemcpyDeviceToHost, s),
+                              "graph copy")) ||
+        (st = msc::check_cuda(p, cudaMemcpyAsync(h_mult, p->graph_mult.ptr, sizeof(uint64_t) * size_t(p->graph_nadj),
+                                                 cudaMemcpyDeviceToHost, s),
+                              "graph copy")))
+        return st;
+    return msc::check_cuda(p, cudaStreamSynchronize(s), "stream sync");
 }
 
 // One pass as a replayed graph; MSC_NOT_READY asks the caller to run the pass synchronised

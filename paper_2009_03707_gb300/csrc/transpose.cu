@@ -14,17 +14,11 @@
 //   3. rows and counts gathered through the sorted entry indices.
 // Each sort pass is three launches: per-tile digit histograms, one scan of all of them in
 // (digit, tile) order, and a scatter in which each tile ranks its elements stably.
-#include "rowscan.cuh"
+#include "radix.cuh"
 
 namespace msc {
 
 namespace {
-
-constexpr int RX_THREADS = 256;
-constexpr int RX_ITEMS = 16;
-constexpr int RX_TILE = RX_THREADS * RX_ITEMS;  // elements per tile, striped: item j of thread t
-constexpr int RX_BINS = 256;
-constexpr int RX_WARPS = RX_THREADS / 32;
 
 // Row index of every CSR entry (the entries of row r are rowptr[r] .. rowptr[r+1]).
 __global__ void __launch_bounds__(256) expand_rows(const int64_t* __restrict__ rowptr, int64_t nrows,
@@ -42,72 +36,6 @@ __global__ void __launch_bounds__(256) count_cols(const uint32_t* __restrict__ c
         if (c < ncols) atomicAdd(&cnt[c], 1u);
         else atomicOr(status, ST_INTERNAL);
         idx[e] = uint32_t(e);
-    }
-}
-
-// Digit counts of one tile: hist[d * ntiles + tile].
-__global__ void __launch_bounds__(RX_THREADS) radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                         int ntiles, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[RX_BINS];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = int64_t(blockIdx.x) * RX_TILE;
-#pragma unroll 4
-    for (int j = 0; j < RX_ITEMS; ++j) {
-        const int64_t i = base + int64_t(j) * RX_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFFu], 1u);
-    }
-    __syncthreads();
-    hist[int64_t(threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-// Stable scatter of one tile: element i goes to offs[d * ntiles + tile] + (elements of digit d
-// before it in the tile).  The tile is taken in RX_ITEMS rounds of RX_THREADS consecutive
-// elements; within a round a warp ranks equal digits with a match mask, the warps are ordered by
-// a per-digit prefix, and a running count carries the rounds.
-__global__ void __launch_bounds__(RX_THREADS) radix_scatter(const uint32_t* __restrict__ keys_in,
-                                                            const uint32_t* __restrict__ vals_in, int64_t n,
-                                                            int shift, int ntiles, const int64_t* __restrict__ offs,
-                                                            uint32_t* __restrict__ keys_out,
-                                                            uint32_t* __restrict__ vals_out) {
-    __shared__ uint32_t wcnt[RX_WARPS][RX_BINS];
-    __shared__ uint32_t run[RX_BINS];
-    __shared__ int64_t base_of[RX_BINS];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    run[t] = 0;
-    base_of[t] = offs[int64_t(t) * ntiles + blockIdx.x];
-    const int64_t tile = int64_t(blockIdx.x) * RX_TILE;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int j = 0; j < RX_ITEMS; ++j) {
-#pragma unroll
-        for (int w = 0; w < RX_WARPS; ++w) wcnt[w][t] = 0;
-        __syncthreads();
-        const int64_t i = tile + int64_t(j) * RX_THREADS + t;
-        const bool live = i < n;
-        const uint32_t key = live ? keys_in[i] : 0u;
-        const uint32_t val = live ? vals_in[i] : 0u;
-        const uint32_t d = live ? (key >> shift) & 0xFFu : uint32_t(RX_BINS);  // RX_BINS: no element
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (live && rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {  // thread t: digit t's exclusive prefix over the warps, after the earlier rounds
-            uint32_t acc = run[t];
-#pragma unroll
-            for (int w = 0; w < RX_WARPS; ++w) {
-                const uint32_t c = wcnt[w][t];
-                wcnt[w][t] = acc;
-                acc += c;
-            }
-            run[t] = acc;
-        }
-        __syncthreads();
-        if (live) {
-            const int64_t pos = base_of[d] + wcnt[warp][d] + rank;
-            keys_out[pos] = key;
-            vals_out[pos] = val;
-        }
-        __syncthreads();
     }
 }
 
@@ -137,8 +65,7 @@ msc_status build_dstar_csc(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->csc_colptr, sizeof(int64_t) * size_t(n2 + 1)))) return st;
     if ((st = ensure(p, p->csc_row, sizeof(uint32_t) * size_t(nnz ? nnz : 1)))) return st;
     if ((st = ensure(p, p->csc_count, sizeof(unsigned long long) * size_t(nnz ? nnz : 1)))) return st;
-    const int64_t ntiles = (nnz + RX_TILE - 1) / RX_TILE;
-    const int64_t nhist = int64_t(RX_BINS) * ntiles;
+    const int64_t nhist = int64_t(radix_hist_count(nnz));
     // work space: column counts, two key and two value arrays, the row of each entry, the digit
     // histograms and their scan
     const size_t scan_n = size_t(std::max<int64_t>(n2, nhist));
@@ -178,19 +105,11 @@ msc_status build_dstar_csc(Plan* p, cudaStream_t s) {
                          "copy columns")))
         return st;
     // 2. stable sort by column, 8 bits a pass
-    int passes = 0;
-    for (int64_t top = n2 - 1; top > 0; top >>= 8) ++passes;
     int cur = 0;
-    for (int k = 0; k < passes; ++k) {
-        const int shift = 8 * k;
-        radix_hist<<<unsigned(ntiles), RX_THREADS, 0, s>>>(keys[cur], nnz, shift, int(ntiles), cnt);
-        launched(p);
-        if ((st = check_cuda(p, row_scan(p, cnt, nullptr, nhist, offs, scratch, s), "digit scan"))) return st;
-        radix_scatter<<<unsigned(ntiles), RX_THREADS, 0, s>>>(keys[cur], vals[cur], nnz, shift, int(ntiles), offs,
-                                                               keys[cur ^ 1], vals[cur ^ 1]);
-        launched(p);
-        cur ^= 1;
-    }
+    const RadixSpace ws{cnt, offs, scratch};
+    if ((st = check_cuda(p, radix_sort_pairs(p, keys, vals, &cur, nnz, uint32_t(std::max<int64_t>(n2 - 1, 0)), ws, s),
+                         "column sort")))
+        return st;
     // 3. rows and counts in column order
     gather_csc<<<grid_of(p, nnz), 256, 0, s>>>(vals[cur], nnz, row_of,
                                                static_cast<const unsigned long long*>(p->dstar_count.ptr),

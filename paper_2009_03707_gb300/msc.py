@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -40,6 +41,7 @@ SIGNATURES = {
     "msc_minor": ([_P, _P, _I32, _PI64, _PI64, _PP, _PP, _PP], _I32),
     "msc_saddle_arcs": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
+    "msc_complex_graph": ([_P, _P, _PI64, _PI64, _P, _P, _P], _I32),
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
     "msc_gradient_critical_static": ([_PI64, _P, _P, _PP, _PI64, _PI64, _P], _I32),
@@ -239,6 +241,21 @@ def msc_saddle_arcs_csc(plan: Plan):
     counts, _ = msc_critical(plan)
     return (_view(cp.value, (counts[2] + 1,), "<i8"), _view(row.value, (nnz.value,), "<u4"),
             _view(cnt.value, (nnz.value,), "<u8"))
+
+
+def msc_complex_graph(plan: Plan):
+    """The 1-skeleton on the host: (nodeptr [n_nodes+1] int64, adj [n_adj] uint32, mult [n_adj]
+    uint64) over nodes numbered minima, 1-saddles, 2-saddles, maxima."""
+    n_nodes, n_adj = ctypes.c_int64(), ctypes.c_int64(0)
+    _check(lib.msc_complex_graph(plan.handle, _stream(), ctypes.byref(n_nodes), ctypes.byref(n_adj), None, None, None),
+           plan.handle)
+    nodeptr = np.zeros(n_nodes.value + 1, dtype=np.int64)
+    adj = np.zeros(max(n_adj.value, 1), dtype=np.uint32)
+    mult = np.zeros(max(n_adj.value, 1), dtype=np.uint64)
+    _check(lib.msc_complex_graph(plan.handle, _stream(), ctypes.byref(n_nodes), ctypes.byref(n_adj),
+                                 nodeptr.ctypes.data_as(ctypes.c_void_p), adj.ctypes.data_as(ctypes.c_void_p),
+                                 mult.ctypes.data_as(ctypes.c_void_p)), plan.handle)
+    return nodeptr, adj[:n_adj.value], mult[:n_adj.value]
 
 
 def msc_compute(plan: Plan, field: torch.Tensor) -> None:
