@@ -182,23 +182,39 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS
     }
 }
 
-// Per-slot critical bitmaps from finished words: one warp per 32 vertices of a row.
+// Per-slot critical bitmaps from finished words: one warp per CB_WORDS row words of 32 vertices,
+// their loads issued together.
+constexpr int CB_WORDS = 4;
 __global__ void __launch_bounds__(256) critical_bitmaps(Geom g, const uint32_t* __restrict__ words,
                                                         uint32_t* __restrict__ crit_bits) {
-    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nrw = uint32_t(g.nz) * uint32_t(g.ny) * uint32_t(g.W);  // < 2^28 row words
+    const uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * CB_WORDS;
     const int lane = threadIdx.x & 31;
-    if (wid >= int64_t(g.nz) * g.ny * g.W) return;  // warp-uniform
-    const int w = int(wid % g.W), y = int((wid / g.W) % g.ny), z = int(wid / (int64_t(g.W) * g.ny));
-    const int x = w * 32 + lane;
-    const bool valid = x < g.nx;
-    const uint32_t word = valid ? words[g.vid(x, y, z)] : 0x00FFFFFFu;
-    uint32_t mine = 0;
+    if (w0 >= nrw) return;  // warp-uniform
+    uint32_t word[CB_WORDS];
+    int w[CB_WORDS], y[CB_WORDS], z[CB_WORDS];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, valid && slot_code(word, s) == 0);
-        if (lane == s) mine = bits;
+    for (int u = 0; u < CB_WORDS; ++u) {
+        const uint32_t wid = min(w0 + u, nrw - 1);
+        const uint32_t q = g.div_W.div(wid);
+        w[u] = int(wid - q * uint32_t(g.W));
+        z[u] = int(g.div_ny.div(q));
+        y[u] = int(q - uint32_t(z[u]) * uint32_t(g.ny));
+        const int x = w[u] * 32 + lane;
+        word[u] = x < g.nx ? words[uint32_t(x) + uint32_t(g.nx) * (uint32_t(y[u]) + uint32_t(g.ny) * uint32_t(z[u]))]
+                           : 0x00FFFFFFu;  // all codes 7: no cell
     }
-    if (lane < 8) crit_bits[g.slot_word(lane, z, y, w)] = mine;
+#pragma unroll
+    for (int u = 0; u < CB_WORDS; ++u) {
+        if (w0 + u >= nrw) break;  // warp-uniform
+        uint32_t mine = 0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const uint32_t bits = __ballot_sync(0xFFFFFFFFu, slot_code(word[u], s) == 0);
+            if (lane == s) mine = bits;
+        }
+        if (lane < 8) crit_bits[g.slot_word(lane, z[u], y[u], w[u])] = mine;
+    }
 }
 
 // Tile variants the autotuner chooses from: (TY, TZ, threads).
@@ -257,7 +273,7 @@ cudaError_t launch_gradient(int v, const Geom& g, const float* d_field, uint32_t
     }
     if (p) record_event(p, p->gev1, s);
     if (e != cudaSuccess) return e;
-    const int64_t warps = int64_t(g.nz) * g.ny * g.W;
+    const int64_t warps = (int64_t(g.nz) * g.ny * g.W + CB_WORDS - 1) / CB_WORDS;
     critical_bitmaps<<<int((warps * 32 + 255) / 256), 256, 0, s>>>(g, words, crit_bits);
     return cudaGetLastError();
 }

@@ -83,7 +83,7 @@ struct Plan {
     // Summary (status word included)
     DeviceBuffer words, status, crit_bits, crit_prefix, scan_sums;
     DeviceBuffer cells[4];
-    DeviceBuffer vmin, cmax, min_arcs, max_arcs;
+    DeviceBuffer vmin, cmax, min_arcs, max_arcs, ext_lab_v, ext_lab_c;
     DeviceBuffer visited, reach_tmp, reach_masks, reach_qdown, reach_stamp, node_info;
     DeviceBuffer junc_bits, junc_prefix, junc_cells;
     DeviceBuffer trace, trace_kinds, minor_rowcnt, minor_scan, minor_rowptr[4], minor_col[4], minor_mult[4];
@@ -96,7 +96,7 @@ struct Plan {
     template <class F>
     void for_each_buffer(F&& f) {
         DeviceBuffer* all[] = {&words, &status, &crit_bits, &crit_prefix, &scan_sums, &cells[0], &cells[1], &cells[2],
-                               &cells[3], &vmin, &cmax, &min_arcs, &max_arcs, &visited, &reach_tmp, &reach_masks,
+                               &cells[3], &vmin, &cmax, &min_arcs, &max_arcs, &ext_lab_v, &ext_lab_c, &visited, &reach_tmp, &reach_masks,
                                &reach_qdown, &reach_stamp, &node_info, &junc_bits, &junc_prefix, &junc_cells, &trace, &trace_kinds,
                                &minor_rowcnt, &minor_scan, &minor_rowptr[0], &minor_rowptr[1], &minor_rowptr[2],
                                &minor_rowptr[3], &minor_col[0], &minor_col[1], &minor_col[2], &minor_col[3],

@@ -104,46 +104,58 @@ __device__ __forceinline__ uint32_t pull(uint32_t m, const uint32_t* __restrict_
 // Per vertex-row word (one warp, a lane per x): for each axis the four masks of 1-cells paired
 // with the quad on the - / + side along the first / second other axis, R_0 = the 1-saddles,
 // and for each quad orientation (by its even axis k) the bitmap of quads that are critical or
-// paired with a facet (the quads that give an out-edge to every other facet).
+// paired with a facet (the quads that give an out-edge to every other facet).  A warp takes
+// RI_WORDS consecutive row words at a time and issues their loads together.
+constexpr int RI_WORDS = 4;
 __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __restrict__ words,
                                                       uint4* __restrict__ masks, uint32_t* __restrict__ R0,
                                                       uint32_t* __restrict__ R1, uint32_t* __restrict__ qdown,
                                                       uint32_t* __restrict__ stamp) {
     const int lane = threadIdx.x & 31;
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
-    for (int64_t t = (int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5; t < nrw;
-         t += (int64_t(gridDim.x) * THREADS) >> 5) {  // warp-uniform
-        const Rows r(g, t);
-        const int x = r.w * 32 + lane;
-        const uint32_t word = x < g.nx ? words[vid32(g, x, r.y, r.z)] : 0x00FFFFFFu;  // all codes 7 off-grid
+    const int64_t step = ((int64_t(gridDim.x) * THREADS) >> 5) * RI_WORDS;
+    for (int64_t t0 = ((int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5) * RI_WORDS; t0 < nrw; t0 += step) {
+        uint32_t words_of[RI_WORDS];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const uint32_t code = slot_code(word, 1 << a);
-            const int k = int(code - 1) >> 1;  // axis of the partner (code 1..6)
-            const bool quad = code >= 1 && code <= 6 && k != a;
-            const int sel = quad ? 2 * (k == other_axis(a, 0) ? 0 : 1) + int(!(code & 1u)) : -1;  // odd: - side
-            const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, sel == 0), m1 = __ballot_sync(0xFFFFFFFFu, sel == 1);
-            const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, sel == 2), m3 = __ballot_sync(0xFFFFFFFFu, sel == 3);
-            const uint32_t crit = __ballot_sync(0xFFFFFFFFu, code == 0);
-            if (lane == a) {
-                const int64_t e = g.edge_word(r.z, a == 2, r.y, a == 1, r.w);
-                masks[e] = make_uint4(m0, m1, m2, m3);
-                R0[e] = crit;
+        for (int u = 0; u < RI_WORDS; ++u) {
+            const Rows r(g, min(t0 + u, nrw - 1));
+            const int x = r.w * 32 + lane;
+            words_of[u] = x < g.nx ? words[vid32(g, x, r.y, r.z)] : 0x00FFFFFFu;  // all codes 7 off-grid
+        }
+#pragma unroll
+        for (int u = 0; u < RI_WORDS; ++u) {  // warp-uniform
+            if (t0 + u >= nrw) break;
+            const Rows r(g, t0 + u);
+            const uint32_t word = words_of[u];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const uint32_t code = slot_code(word, 1 << a);
+                const int k = int(code - 1) >> 1;  // axis of the partner (code 1..6)
+                const bool quad = code >= 1 && code <= 6 && k != a;
+                const int sel = quad ? 2 * (k == other_axis(a, 0) ? 0 : 1) + int(!(code & 1u)) : -1;  // odd: - side
+                const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, sel == 0), m1 = __ballot_sync(0xFFFFFFFFu, sel == 1);
+                const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, sel == 2), m3 = __ballot_sync(0xFFFFFFFFu, sel == 3);
+                const uint32_t crit = __ballot_sync(0xFFFFFFFFu, code == 0);
+                if (lane == a) {
+                    const int64_t e = g.edge_word(r.z, a == 2, r.y, a == 1, r.w);
+                    masks[e] = make_uint4(m0, m1, m2, m3);
+                    R0[e] = crit;
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const uint32_t code = slot_code(word, 7 ^ (1 << k));
-            const bool down = code == 0 || (code <= 6 && (int(code - 1) >> 1) != k);
-            const uint32_t qd = __ballot_sync(0xFFFFFFFFu, down);
-            if (lane == 4 + k) qdown[k * r.qplane + r.qbase] = qd;
-        }
-        if (lane == 8 && r.w == 0) stamp[int64_t(r.z) * g.ny + r.y] = 1;  // every row is new at the start
-        if (lane == 3) {  // the unused slot of the 1-cell layout stays empty in both buffers
-            const int64_t e = g.edge_word(r.z, 1, r.y, 1, r.w);
-            masks[e] = make_uint4(0, 0, 0, 0);
-            R0[e] = 0;
-            R1[e] = 0;
+            for (int k = 0; k < 3; ++k) {
+                const uint32_t code = slot_code(word, 7 ^ (1 << k));
+                const bool down = code == 0 || (code <= 6 && (int(code - 1) >> 1) != k);
+                const uint32_t qd = __ballot_sync(0xFFFFFFFFu, down);
+                if (lane == 4 + k) qdown[k * r.qplane + r.qbase] = qd;
+            }
+            if (lane == 8 && r.w == 0) stamp[int64_t(r.z) * g.ny + r.y] = 1;  // every row is new at the start
+            if (lane == 3) {  // the unused slot of the 1-cell layout stays empty in both buffers
+                const int64_t e = g.edge_word(r.z, 1, r.y, 1, r.w);
+                masks[e] = make_uint4(0, 0, 0, 0);
+                R0[e] = 0;
+                R1[e] = 0;
+            }
         }
     }
 }
