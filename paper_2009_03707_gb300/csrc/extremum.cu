@@ -76,17 +76,21 @@ __global__ void __launch_bounds__(TL_THREADS) tile_links(Geom g, const uint32_t*
     lc[t] = c;
     __syncthreads();
     if (!valid) return;
-    // local links have the OUTSIDE bit clear (NO_LINK has it set)
+    // local links have the OUTSIDE bit clear (NO_LINK has it set); each thread leaves its end point
+    // in its own entry, a shortcut for the threads that reach it later (any value read is still an
+    // ancestor)
     for (int hop = 0; hop < TL_THREADS && !(a & OUTSIDE); ++hop) {
         const uint32_t b = lv[a];
         if (b == a) break;  // a root
         a = b;
     }
+    lv[t] = a;
     for (int hop = 0; hop < TL_THREADS && !(c & OUTSIDE); ++hop) {
         const uint32_t b = lc[c];
         if (b == c) break;
         c = b;
     }
+    lc[t] = c;
     auto global_of = [&](uint32_t l) -> uint32_t {
         if (l == NO_LINK) return NO_LINK;
         if (l & OUTSIDE) return l & ~OUTSIDE;

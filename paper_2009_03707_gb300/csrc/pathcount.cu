@@ -628,17 +628,37 @@ __global__ void init_tables(uint32_t* k, u64* v, size_t n) {
     }
 }
 
+// One warp per 32 consecutive rows: their CSR range is contiguous, and the warp copies it one
+// output entry per lane (coalesced writes).  A lane finds the row of its entry among the warp's 32
+// row starts by a binary search over the lanes (shuffles); an empty row shares its start with the
+// next one, and the search takes the last row starting at or before the entry.
 __global__ void gather_rows(const unsigned long long* n1_dev, int64_t cap, const int64_t* __restrict__ row_start,
                             const int64_t* __restrict__ rowptr, const uint32_t* __restrict__ in_col,
                             const u64* __restrict__ in_cnt, uint32_t* __restrict__ col, u64* __restrict__ cnt,
                             uint32_t* status) {
     if (pass_retrying(status) || !count_fits(status, *n1_dev, cap)) return;
     const int64_t n1 = int64_t(*n1_dev);
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n1; s += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t b = row_start[s], o = rowptr[s], len = rowptr[s + 1] - rowptr[s];
-        for (int64_t i = 0; i < len; ++i) {
-            col[o + i] = in_col[b + i];
-            cnt[o + i] = in_cnt[b + i];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t s0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; s0 < n1; s0 += nwarps * 32) {
+        const int64_t s = s0 + lane;
+        const int64_t end = rowptr[min(s0 + 32, n1)];
+        const int64_t start = s < n1 ? rowptr[s] : end;  // past the last row: never at or before an entry
+        const int64_t src = s < n1 ? row_start[s] : 0;
+        const int64_t begin = __shfl_sync(0xFFFFFFFFu, start, 0);
+        for (int64_t base = begin; base < end; base += 32) {  // warp-uniform
+            const int64_t o = base + lane;
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const int64_t v = __shfl_sync(0xFFFFFFFFu, start, r + step);
+                if (v <= o) r += step;
+            }
+            const int64_t rs = __shfl_sync(0xFFFFFFFFu, start, r), rsrc = __shfl_sync(0xFFFFFFFFu, src, r);
+            if (o < end) {
+                col[o] = in_col[rsrc + (o - rs)];
+                cnt[o] = in_cnt[rsrc + (o - rs)];
+            }
         }
     }
 }
