@@ -267,11 +267,13 @@ def run_gpu(args):
     ms_local = sum(step_ms) / len(step_ms)
 
     # ---- end to end from pinned host memory -------------------------------------------
-    # Every step copies its field in from pinned host memory, runs msc_compute and reads the whole
-    # 1-skeleton back into pinned host memory.  Two plans on two streams take the steps in turn, so
-    # that one step's copies overlap the next step's compute (the public API's msc_compute waits
-    # only for its own stream); a step's result buffers are reused two steps later, on the same
-    # stream, so the copies of one step are never overwritten before they finish.
+    # Every step copies its field in from pinned host memory, runs the pass and reads the whole
+    # 1-skeleton back into pinned host memory.  Two plans on two streams take the steps in turn
+    # through the public asynchronous entry points: step i's pass is enqueued
+    # (msc_compute_async), then step i-1's is waited for (msc_compute_wait) and its results are
+    # copied out on its stream, and the field of step i+1 goes up into that plan's buffer behind
+    # them.  So the device always has the next pass queued while the host collects the last one; a
+    # plan's result buffers are reused two steps later, on the same stream, after their copies.
     h_field = torch.from_numpy(f).pin_memory()
     counts = stats["counts"]
     lanes = []
@@ -293,12 +295,13 @@ def run_gpu(args):
         with torch.cuda.stream(lane["stream"]):
             lane["field"].copy_(h_field, non_blocking=True)
 
-    def e2e_step(lane, next_lane):
-        # the next step's field goes up on the other stream before this step's pass blocks the host
-        if next_lane is not None:
-            upload(next_lane)
+    def issue(lane):
         with torch.cuda.stream(lane["stream"]):
-            msc.msc_compute(lane["plan"], lane["field"])
+            msc.msc_compute_async(lane["plan"], lane["field"])
+
+    def collect(lane):
+        with torch.cuda.stream(lane["stream"]):
+            msc.msc_compute_wait(lane["plan"])
             _, cells = msc.msc_critical(lane["plan"])
             amin, amax, _, _ = msc.msc_extremum_arcs(lane["plan"])
             rowptr, col, cnt = msc.msc_saddle_arcs(lane["plan"])
@@ -307,18 +310,26 @@ def run_gpu(args):
             n += d2h(lane, "rowptr", rowptr) + d2h(lane, "col", col) + d2h(lane, "cnt", cnt)
         return n
 
+    def run_e2e(k):
+        upload(lanes[0])
+        n = 0
+        for i in range(k):
+            lane, other = lanes[i % 2], lanes[(i + 1) % 2]
+            issue(lane)
+            if i > 0:
+                n = collect(other)
+            if i + 1 < k:
+                upload(other)
+        return collect(lanes[(k - 1) % 2])
+
     warm = max(args.warmup, 2)  # both plans warm (their graphs captured)
-    upload(lanes[0])
-    for i in range(warm):
-        e2e_step(lanes[i % 2], lanes[(i + 1) % 2] if i + 1 < warm else None)
+    for _ in range(2):
+        run_e2e(warm)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(lanes[0]["stream"])
     lanes[1]["stream"].wait_event(e0)
-    upload(lanes[0])  # the first timed step's field, inside the timed region
-    bo = 0
-    for i in range(args.steps):
-        bo = e2e_step(lanes[i % 2], lanes[(i + 1) % 2] if i + 1 < args.steps else None)
+    bo = run_e2e(args.steps)  # the first field's upload is inside the timed region
     done = torch.cuda.Event()
     done.record(lanes[1]["stream"])
     lanes[0]["stream"].wait_event(done)

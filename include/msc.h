@@ -215,6 +215,20 @@ msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nn
 msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
                              int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult);
 
+/* ---- the whole pass without waiting ----------------------------------------------------
+ * msc_compute_async enqueues a pass on `stream` and returns without waiting for it, so that one
+ * thread can keep several plans' passes (on their own streams) in flight -- e.g. upload the next
+ * field and read back the previous results while a pass runs.  It does so when the plan replays a
+ * captured graph (from its second msc_compute on the same grid shape, graphs enabled); otherwise
+ * it runs the pass synchronised, exactly as msc_compute.  msc_compute_wait waits for the pass and
+ * returns its status; a pass that outgrew the capacities of the captured graph is then run again
+ * synchronised (so the wait can take as long as a synchronised pass).  A plan holds one pass in
+ * flight: every other entry point on the plan (msc_get_stats included) waits for it first, and
+ * reports its error if it failed.  The field must stay valid and unchanged until the wait.  The
+ * outputs are those of the pass only once it has been waited for. */
+msc_status msc_compute_async(msc_plan_t plan, const float* d_field, msc_stream_t stream);
+msc_status msc_compute_wait(msc_plan_t plan);
+
 /* Runs every stage (a1..a6) on `stream` for one field; equivalent to the calls above in
  * order.  Results are read afterwards with the getters (they do no further work, except that
  * msc_minor builds the CSR of A, B, B*, D on its first call for a field).

@@ -180,11 +180,18 @@ void stage_end(Plan* p, int k, cudaStream_t s) {
     p->stage_recorded |= 1u << k;
 }
 
+msc_status settle(Plan* p);
+
+// Every entry point starts here: the plan's device is made current, and a pass left in flight by
+// msc_compute_async is waited for (its status is what this call returns if it failed).
 msc_status bind_device(Plan* p) {
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return fail(p, MSC_ERR_CUDA, "cudaGetDevice failed");
-    if (cur != p->device) return check_cuda(p, cudaSetDevice(p->device), "cudaSetDevice");
-    return MSC_OK;
+    if (cur != p->device) {
+        const msc_status st = check_cuda(p, cudaSetDevice(p->device), "cudaSetDevice");
+        if (st) return st;
+    }
+    return p->pending ? settle(p) : MSC_OK;
 }
 
 void invalidate(Plan* p) {
@@ -321,6 +328,18 @@ msc_status capture_graph(Plan* p, const float* d_field) {
     return MSC_OK;
 }
 
+// Waits for the pass msc_compute_async launched and publishes it; a replay that outgrew the
+// graph's capacities is run again synchronised, as msc_compute does.
+msc_status compute_synchronised(Plan* p, const float* d_field, cudaStream_t s);
+msc_status settle(Plan* p) {
+    p->pending = false;
+    msc_status st = check_cuda(p, cudaEventSynchronize(p->pend_ev), "wait for the pass");
+    if (st) return st;
+    st = finish_replay(p, p->pending_stream);
+    if (st != MSC_NOT_READY) return st;
+    return compute_synchronised(p, p->pending_field, p->pending_stream);
+}
+
 msc_status finish_replay(Plan* p, cudaStream_t s) {
     msc_status st;
     const uint32_t word = p->hsum->status;
@@ -380,6 +399,7 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->tev1), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->gev0), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->gev1), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreateWithFlags(&p->pend_ev, cudaEventDisableTiming), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!st) st = msc::check_cuda(p, cudaMallocHost(&p->hsum, sizeof(msc::Summary)), "cudaMallocHost");
@@ -404,7 +424,8 @@ msc_status msc_plan_destroy(msc_plan_t plan) {
     });
     for (cudaEvent_t e : p->stage_ev)
         if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1, p->gev0, p->gev1})
+    if (p->pending) cudaEventSynchronize(p->pend_ev);  // the pass in flight still uses the buffers
+    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1, p->gev0, p->gev1, p->pend_ev})
         if (e) cudaEventDestroy(e);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->body_stream) cudaStreamDestroy(p->body_stream);
@@ -724,9 +745,40 @@ msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t strea
     return msc::compute_synchronised(p, d_field, s);
 }
 
+msc_status msc_compute_async(msc_plan_t plan, const float* d_field, msc_stream_t stream) {
+    if (!plan || !d_field) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;  // also waits for a pass still in flight
+    if (!msc::graphs_enabled(p) || !p->caps_ready) return msc::compute_synchronised(p, d_field, s);
+    if (!p->graph_exec || p->graph_field != d_field)
+        if ((st = msc::capture_graph(p, d_field))) return st;
+    msc::invalidate(p);
+    p->stage_recorded = 0;
+    if ((st = msc::check_cuda(p, cudaGraphLaunch(p->graph_exec, s), "graph launch"))) return st;
+    if ((st = msc::check_cuda(p, cudaMemcpyAsync(p->hsum, p->dsum(), sizeof(msc::Summary), cudaMemcpyDeviceToHost, s),
+                              "summary copy")) ||
+        (st = msc::check_cuda(p, cudaEventRecord(p->pend_ev, s), "event record")))
+        return st;
+    p->pending = true;
+    p->pending_field = d_field;
+    p->pending_stream = s;
+    return MSC_OK;
+}
+
+msc_status msc_compute_wait(msc_plan_t plan) {
+    if (!plan) return MSC_ERR_ARG;
+    return msc::bind_device(plan);
+}
+
 msc_status msc_get_stats(msc_plan_t plan, msc_stats* out) {
     if (!plan || !out) return MSC_ERR_ARG;
     Plan* p = plan;
+    if (p->pending) {
+        const msc_status st = msc::bind_device(p);
+        if (st) return st;
+    }
     p->stats.peak_device_bytes = p->peak_bytes;
     float* dst[6] = {&p->stats.ms_gradient, &p->stats.ms_critical, &p->stats.ms_extremum,
                      &p->stats.ms_reachability, &p->stats.ms_minor, &p->stats.ms_path_count};

@@ -152,6 +152,11 @@ struct Plan {
     cudaEvent_t kev0 = nullptr, kev1 = nullptr;  // around the tier-0 path-count kernel
     cudaEvent_t tev0 = nullptr, tev1 = nullptr;  // around the trace kernel
     cudaEvent_t gev0 = nullptr, gev1 = nullptr;  // around the lower-star kernel
+    // a pass launched by msc_compute_async and not yet waited for: its summary copy ends at pend_ev
+    cudaEvent_t pend_ev = nullptr;
+    bool pending = false;
+    const float* pending_field = nullptr;
+    cudaStream_t pending_stream = nullptr;
     // host-side fault injection (MSC_FAULT, read at plan creation; tests only): the failure is
     // made on the host -- a faked allocation failure, or a status bit raised as a kernel would
     int fault_kind = 0;  // 0 none, 1 alloc, 2 timeout (reachability), 3 overflow (path count)

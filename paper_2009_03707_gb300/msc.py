@@ -42,6 +42,8 @@ SIGNATURES = {
     "msc_saddle_arcs": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_complex_graph": ([_P, _P, _PI64, _PI64, _P, _P, _P], _I32),
+    "msc_compute_async": ([_P, _P, _P], _I32),
+    "msc_compute_wait": ([_P], _I32),
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
     "msc_gradient_critical_static": ([_PI64, _P, _P, _PP, _PI64, _PI64, _P], _I32),
@@ -264,6 +266,19 @@ def msc_compute(plan: Plan, field: torch.Tensor) -> None:
     if tuple(field.shape) != plan.shape_zyx:
         raise ValueError(f"field shape {tuple(field.shape)} does not match the plan {plan.shape_zyx}")
     _check(lib.msc_compute(plan.handle, ctypes.c_void_p(field.data_ptr()), _stream()), plan.handle)
+
+
+def msc_compute_async(plan: Plan, field: torch.Tensor) -> None:
+    """Enqueues the pass on the current stream and returns (see msc_compute_wait)."""
+    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    if tuple(field.shape) != plan.shape_zyx:
+        raise ValueError(f"field shape {tuple(field.shape)} does not match the plan {plan.shape_zyx}")
+    _check(lib.msc_compute_async(plan.handle, ctypes.c_void_p(field.data_ptr()), _stream()), plan.handle)
+
+
+def msc_compute_wait(plan: Plan) -> None:
+    _check(lib.msc_compute_wait(plan.handle), plan.handle)
 
 
 def msc_get_stats(plan: Plan) -> dict:
