@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __
                 const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, sel == 2), m3 = __ballot_sync(0xFFFFFFFFu, sel == 3);
                 const uint32_t crit = __ballot_sync(0xFFFFFFFFu, code == 0);
                 if (lane == a) {
-                    const int64_t e = g.edge_word(r.z, a == 2, r.y, a == 1, r.w);
+                    const int e = a == 0 ? r.edge<0>(0, 0) : a == 1 ? r.edge<1>(0, 0) : r.edge<2>(0, 0);
                     masks[e] = make_uint4(m0, m1, m2, m3);
                     R0[e] = crit;
                 }
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __
                 const uint32_t qd = __ballot_sync(0xFFFFFFFFu, down);
                 if (lane == 4 + k) qdown[k * r.qplane + r.qbase] = qd;
             }
-            if (lane == 8 && r.w == 0) stamp[int64_t(r.z) * g.ny + r.y] = 1;  // every row is new at the start
+            if (lane == 8 && r.w == 0) stamp[r.z * r.ny + r.y] = 1;  // every row is new at the start
             if (lane == 3) {  // the unused slot of the 1-cell layout stays empty in both buffers
-                const int64_t e = g.edge_word(r.z, 1, r.y, 1, r.w);
+                const int e = r.edge<2>(0, 0) + r.W;  // (c, b) = (1, 1)
                 masks[e] = make_uint4(0, 0, 0, 0);
                 R0[e] = 0;
                 R1[e] = 0;
