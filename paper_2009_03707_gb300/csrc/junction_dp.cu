@@ -24,7 +24,11 @@
 //   3. D* row s = the same merge over 1-saddle s's slots, written to staging and gathered into
 //      CSR (pathcount.cu's staging, row scan and gather).
 // Rows are merged sorted by column with exact uint64 sums (an add that wraps raises the overflow
-// flag).  J rows live in one pool, allocated with a warp-aggregated bump pointer.
+// flag).  J rows live in one pool, allocated with a warp-aggregated bump pointer.  A merge is a
+// chain of dependent loads, one step per output entry, so a wave lasts as long as its longest
+// merge: junctions whose inputs hold more than LONG_ROW entries are handed to a second kernel of
+// the same wave, where a warp splits the key range over its 32 lanes (pivots from the longest
+// input row, a binary search per lane and input) and each lane merges its slice.
 #include <cooperative_groups.h>
 
 #include <cstddef>
@@ -41,6 +45,7 @@ constexpr int THREADS = 256;
 constexpr uint32_t READY = 0x80000000u;  // pend[j] = READY | wave: j's row is computed in that wave
 constexpr uint32_t DONE = 0xFFFFFFFFu;
 constexpr int SCAN_BATCH = 8;  // pending words a thread reads at once in a wave
+constexpr uint32_t LONG_ROW = 64;  // merges with more input entries go to the warp kernel
 typedef unsigned long long u64;
 
 struct DpArgs {
@@ -55,6 +60,7 @@ struct DpArgs {
     int64_t* in_ptr;                     // CSR of those predecessors
     uint32_t* in_fill;
     uint32_t* in_idx;
+    uint32_t* long_list;                 // this wave's junctions with long merges (dp_long)
     u64* j_off;                          // per junction: its J row in the pool
     uint32_t* j_len;
     uint32_t* pool_col;                  // J rows: 2-saddle ranks increasing, uint64 counts
@@ -221,6 +227,10 @@ __global__ void __launch_bounds__(THREADS) dp_wave(DpArgs a) {
             const int64_t j = j0 + int64_t(__ffs(hit) - 1) * stride;
             uint32_t bound;
             const Inputs in = inputs_of(a, n1 + j, n1, &bound);
+            if (bound > LONG_ROW) {  // merged by dp_long in this wave, which also releases its predecessors
+                a.long_list[atomicAdd(&a.sum->dp_long_n, 1ull)] = uint32_t(j);
+                continue;
+            }
             const u64 off = bump(&a.sum->dp_pool_used, bound);
             uint32_t len = 0;
             if (off + bound <= a.pool_cap) {
@@ -242,11 +252,140 @@ __global__ void __launch_bounds__(THREADS) dp_wave(DpArgs a) {
     if ((threadIdx.x & 31) == 0 && done) atomicAdd(&a.sum->dp_wave_done, (u64)done);
 }
 
+// First position in col[0..len) whose column is >= key.
+__device__ __forceinline__ uint32_t lower_bound(const uint32_t* col, uint32_t len, uint32_t key) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (col[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One lane's slice of a merge: the columns in [lo, hi) (hi_open: no upper end) of every input,
+// merged with equal columns summed; counts them, and writes them from out_col / out_cnt when
+// `write` is set.
+__device__ __forceinline__ uint32_t slice_merge(const Inputs& in, const uint32_t s[4], const uint32_t e[4],
+                                                uint32_t lo, uint32_t hi, bool hi_open, bool write, uint32_t* out_col,
+                                                u64* out_cnt, u64* max_seen, bool* wrapped) {
+    uint32_t pos[4], end[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        pos[k] = s[k];
+        end[k] = e[k];
+        if (in.kind[k] == 2) {  // a 2-saddle slot: its one column, if it falls in the slice
+            const bool mine = in.single[k] >= lo && (hi_open || in.single[k] < hi);
+            pos[k] = 0;
+            end[k] = mine ? 1 : 0;
+        }
+    }
+    uint32_t n = 0;
+    for (;;) {
+        uint32_t c = 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (pos[k] < end[k]) c = min(c, in.kind[k] == 2 ? in.single[k] : in.col[k][pos[k]]);
+        if (c == 0xFFFFFFFFu) break;
+        u64 sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (pos[k] >= end[k]) continue;
+            const uint32_t ck = in.kind[k] == 2 ? in.single[k] : in.col[k][pos[k]];
+            if (ck != c) continue;
+            const u64 v = in.kind[k] == 2 ? 1ull : in.cnt[k][pos[k]];
+            *wrapped |= sum + v < sum;
+            sum += v;
+            ++pos[k];
+        }
+        if (write) {
+            out_col[n] = c;
+            out_cnt[n] = sum;
+            *max_seen = max(*max_seen, sum);
+        }
+        ++n;
+    }
+    return n;
+}
+
+// The long merges of this wave, a warp each: the longest input row gives 32 pivot columns, lane l
+// merges the columns in [pivot l, pivot l+1) of every input (binary searches for its slice), twice
+// -- to count, then, after a warp prefix of the counts, to write -- and the warp releases the
+// junction's predecessors.
+__global__ void __launch_bounds__(THREADS) dp_long(DpArgs a) {
+    int64_t n1, nj;
+    if (!counts_of(a, n1, nj)) return;
+    const uint32_t next = READY | (a.sum->dp_wave + 1);
+    const u64 n = a.sum->dp_long_n;
+    const int lane = threadIdx.x & 31;
+    const u64 nwarps = (u64(gridDim.x) * THREADS) >> 5;
+    unsigned done = 0;
+    u64 mx = 0;  // (J entries are not D* entries: the largest path count is taken from the D* rows)
+    bool wrapped = false;
+    for (u64 i = (u64(blockIdx.x) * THREADS + threadIdx.x) >> 5; i < n; i += nwarps) {  // warp-uniform
+        const uint32_t j = a.long_list[i];
+        uint32_t bound;
+        const Inputs in = inputs_of(a, n1 + j, n1, &bound);
+        uint32_t L = 0;  // the longest input row
+        const uint32_t* P = nullptr;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (in.kind[k] == 1 && in.len[k] > L) {
+                L = in.len[k];
+                P = in.col[k];
+            }
+        const uint32_t lo = (lane == 0 || L == 0) ? 0u : P[uint32_t((u64(lane) * L) >> 5)];
+        const uint32_t hi = __shfl_down_sync(0xFFFFFFFFu, lo, 1);
+        const bool hi_open = lane == 31;
+        uint32_t s[4], e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            s[k] = e[k] = 0;
+            if (in.kind[k] == 1) {
+                s[k] = lane == 0 ? 0u : lower_bound(in.col[k], in.len[k], lo);
+                e[k] = hi_open ? in.len[k] : lower_bound(in.col[k], in.len[k], hi);
+            }
+        }
+        u64 off = 0;
+        if (lane == 0) off = atomicAdd(&a.sum->dp_pool_used, u64(bound));
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        const bool fits = off + bound <= a.pool_cap;  // uniform
+        uint32_t len = 0;
+        if (fits) {
+            const uint32_t cnt = slice_merge(in, s, e, lo, hi, hi_open, false, nullptr, nullptr, &mx, &wrapped);
+            uint32_t incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            slice_merge(in, s, e, lo, hi, hi_open, true, a.pool_col + off + (incl - cnt),
+                        a.pool_cnt + off + (incl - cnt), &mx, &wrapped);
+            len = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        } else if (lane == 0) {
+            atomicOr(a.status, ST_RETRY);  // the pool is too small: the host grows it and reruns
+        }
+        if (lane == 0) {
+            a.j_off[j] = off;
+            a.j_len[j] = len;
+            a.pend[j] = DONE;
+            ++done;
+        }
+        for (int64_t q = a.in_ptr[j] + lane; q < a.in_ptr[j + 1]; q += 32) {
+            const uint32_t pr = a.in_idx[q];
+            if (atomicSub(&a.pend[pr], 1u) == 1u) a.pend[pr] = next;
+        }
+    }
+    if (wrapped) atomicOr(a.status, ST_OVERFLOW);
+    for (int o = 16; o; o >>= 1) done += __shfl_xor_sync(0xFFFFFFFFu, done, o);
+    if (lane == 0 && done) atomicAdd(&a.sum->dp_wave_done, (u64)done);
+}
+
 // End of a wave: count it, and go on while it found junctions to do (the loop ends after the
 // first empty wave).
 __global__ void dp_decide(Summary* sum, int64_t max_iter, cudaGraphConditionalHandle h, int use_handle) {
     const u64 done = sum->dp_wave_done;
     sum->dp_wave_done = 0;
+    sum->dp_long_n = 0;
     ++sum->dp_iters;
     bool more = done != 0;
     if (more) {
@@ -294,6 +433,7 @@ struct WaveCtx {
 void wave_body(Plan* p, cudaStream_t s, cudaGraphConditionalHandle h, void* ctx) {
     const WaveCtx& c = *static_cast<WaveCtx*>(ctx);
     dp_wave<<<c.grid, THREADS, 0, s>>>(c.a);
+    dp_long<<<c.grid, THREADS, 0, s>>>(c.a);
     dp_decide<<<1, 1, 0, s>>>(p->dsum(), p->opts.max_iterations, h, h != 0);
 }
 
@@ -307,6 +447,7 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     const int64_t capj = p->capturing ? p->caps.nj : p->n_junctions;
     const size_t njc = size_t(capj ? capj : 1);
     if ((st = ensure(p, p->dp_pend, sizeof(uint32_t) * njc))) return st;
+    if ((st = ensure(p, p->dp_long, sizeof(uint32_t) * njc))) return st;
     if ((st = ensure(p, p->dp_in_cnt, sizeof(uint32_t) * 2 * njc))) return st;  // counts, then fill cursors
     if ((st = ensure(p, p->dp_in_ptr, sizeof(int64_t) * (njc + 1)))) return st;
     if ((st = ensure(p, p->dp_in_idx, sizeof(uint32_t) * 4 * njc))) return st;
@@ -323,6 +464,7 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     a.cap1 = cap1;
     a.capj = capj;
     a.pend = static_cast<uint32_t*>(p->dp_pend.ptr);
+    a.long_list = static_cast<uint32_t*>(p->dp_long.ptr);
     a.in_cnt = static_cast<uint32_t*>(p->dp_in_cnt.ptr);
     a.in_fill = a.in_cnt + njc;
     a.in_ptr = static_cast<int64_t*>(p->dp_in_ptr.ptr);
@@ -356,7 +498,7 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     if ((st = check_cuda(p, cudaGetLastError(), "junction dp launch"))) return st;
     record_event(p, p->kev0, s);
     WaveCtx ctx{grid_cap(p, capj, THREADS, 8), a};
-    if ((st = run_loop(p, s, 2, 2, wave_body, &ctx))) return st;
+    if ((st = run_loop(p, s, 2, 3, wave_body, &ctx))) return st;
     dp_rows<<<grid_cap(p, cap1, THREADS, 8), THREADS, 0, s>>>(a);
     record_event(p, p->kev1, s);
     launched(p);
