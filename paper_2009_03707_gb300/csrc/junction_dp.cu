@@ -45,7 +45,7 @@ constexpr int THREADS = 256;
 constexpr uint32_t READY = 0x80000000u;  // pend[j] = READY | wave: j's row is computed in that wave
 constexpr uint32_t DONE = 0xFFFFFFFFu;
 constexpr int SCAN_BATCH = 8;  // pending words a thread reads at once in a wave
-constexpr uint32_t LONG_ROW = 64;  // merges with more input entries go to the warp kernel
+constexpr uint32_t LONG_ROW = 24;  // merges with more input entries go to the warp kernel
 typedef unsigned long long u64;
 
 struct DpArgs {
