@@ -15,10 +15,12 @@
 //   2. waves: wave 0 is the junctions with no junction successor; a junction's J row is the
 //      merge of its 4 trace slots -- a 2-saddle slot is one path to that 2-saddle, a junction
 //      slot adds that junction's J row -- and finishing it decrements the pending counts of its
-//      predecessors; the one that takes a count to 0 stamps it with the next wave's number.  A
-//      wave is one coalesced scan of the pending words for its own stamp (no shared queue, whose
-//      single append counter would serialise millions of atomics), and a junction released during
-//      a wave waits for the next one, when the rows it reads are complete.  The waves run as a
+//      predecessors; the one that takes a count to 0 stamps it with the next wave's number and
+//      flags its chunk of 32 junctions in that wave's chunk bitmap.  A wave reads the bitmap and
+//      scans only the flagged chunks' pending words for its own stamp (no shared queue, whose
+//      single append counter would serialise millions of atomics; no pass over every junction
+//      for a wave with few), and a junction released during a wave waits for the next one, when
+//      the rows it reads are complete.  The waves run as a
 //      device loop (a conditional WHILE node in a graph); the non-empty ones number the paper's
 //      iteration count, 1 + the longest chain of junctions;
 //   3. D* row s = the same merge over 1-saddle s's slots, written to staging and gathered into
@@ -56,6 +58,9 @@ struct DpArgs {
     int64_t cap1, capj;                  // the capacities the buffers were sized for
     uint32_t* pend;                      // per junction: junction slots whose rows are not ready, or
                                          // READY | wave once they all are, or DONE
+    uint32_t* chunk_map;                 // two bitmaps (waves of even / odd number): bit c of word w
+                                         // flags chunk 32 w + c, junctions 32 (32 w + c) ..
+    int64_t map_words;                   // words per bitmap
     uint32_t* in_cnt;                    // per junction: slots of other junctions pointing at it
     int64_t* in_ptr;                     // CSR of those predecessors
     uint32_t* in_fill;
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(THREADS) dp_init(DpArgs a) {
                 atomicAdd(&a.in_cnt[t[k]], 1u);
             }
         a.pend[j] = pending ? pending : READY;
+        if (!pending) atomicOr(&a.chunk_map[j >> 10], 1u << ((j >> 5) & 31));  // wave 0
     }
 }
 
@@ -210,21 +216,33 @@ __global__ void __launch_bounds__(THREADS) dp_wave(DpArgs a) {
     if (!counts_of(a, n1, nj)) return;
     const uint32_t wave = a.sum->dp_wave;
     const uint32_t mine = READY | wave, next = READY | (wave + 1);
+    uint32_t* const map_cur = a.chunk_map + (wave & 1u) * a.map_words;
+    uint32_t* const map_next = a.chunk_map + ((wave + 1) & 1u) * a.map_words;
     unsigned done = 0;
     u64 mx = 0;
-    // the scan reads SCAN_BATCH pending words at a time, all in flight together, so a wave with
-    // few junctions to do costs a few memory latencies rather than one per word
-    const int64_t stride = int64_t(gridDim.x) * THREADS;
-    for (int64_t j0 = int64_t(blockIdx.x) * THREADS + threadIdx.x; j0 < nj; j0 += SCAN_BATCH * stride) {
+    // a lane per chunk of 32 junctions, a warp per bitmap word; a flagged chunk's pending words
+    // are read SCAN_BATCH at a time, all in flight together
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (nj + 31) / 32;
+    const int64_t stride = int64_t(gridDim.x) * THREADS;  // a multiple of 32: warps stay on whole words
+    for (int64_t cbase = int64_t(blockIdx.x) * THREADS + (threadIdx.x & ~31); cbase < nchunks; cbase += stride) {
+        const uint32_t flags = map_cur[cbase >> 5];
+        __syncwarp();
+        if (lane == 0 && flags) map_cur[cbase >> 5] = 0;  // consumed: the next even/odd wave starts clean
+        const int64_t c = cbase + lane;
+        if (c >= nchunks || !((flags >> lane) & 1u)) continue;
         uint32_t hit = 0;
 #pragma unroll
-        for (int k = 0; k < SCAN_BATCH; ++k) {
-            const int64_t j = j0 + k * stride;
-            hit |= uint32_t(j < nj && a.pend[j] == mine) << k;
+        for (int b = 0; b < 32; b += SCAN_BATCH) {
+#pragma unroll
+            for (int k = 0; k < SCAN_BATCH; ++k) {
+                const int64_t j = c * 32 + b + k;
+                hit |= uint32_t(j < nj && a.pend[j] == mine) << (b + k);
+            }
         }
 #pragma unroll 1
         for (; hit; hit &= hit - 1) {
-            const int64_t j = j0 + int64_t(__ffs(hit) - 1) * stride;
+            const int64_t j = c * 32 + (__ffs(hit) - 1);
             uint32_t bound;
             const Inputs in = inputs_of(a, n1 + j, n1, &bound);
             if (bound > LONG_ROW) {  // merged by dp_long in this wave, which also releases its predecessors
@@ -244,7 +262,10 @@ __global__ void __launch_bounds__(THREADS) dp_wave(DpArgs a) {
             ++done;
             for (int64_t e = a.in_ptr[j]; e < a.in_ptr[j + 1]; ++e) {
                 const uint32_t p = a.in_idx[e];
-                if (atomicSub(&a.pend[p], 1u) == 1u) a.pend[p] = next;
+                if (atomicSub(&a.pend[p], 1u) == 1u) {
+                    a.pend[p] = next;
+                    atomicOr(&map_next[p >> 10], 1u << ((p >> 5) & 31));
+                }
             }
         }
     }
@@ -316,6 +337,7 @@ __global__ void __launch_bounds__(THREADS) dp_long(DpArgs a) {
     int64_t n1, nj;
     if (!counts_of(a, n1, nj)) return;
     const uint32_t next = READY | (a.sum->dp_wave + 1);
+    uint32_t* const map_next = a.chunk_map + ((a.sum->dp_wave + 1) & 1u) * a.map_words;
     const u64 n = a.sum->dp_long_n;
     const int lane = threadIdx.x & 31;
     const u64 nwarps = (u64(gridDim.x) * THREADS) >> 5;
@@ -372,7 +394,10 @@ __global__ void __launch_bounds__(THREADS) dp_long(DpArgs a) {
         }
         for (int64_t q = a.in_ptr[j] + lane; q < a.in_ptr[j + 1]; q += 32) {
             const uint32_t pr = a.in_idx[q];
-            if (atomicSub(&a.pend[pr], 1u) == 1u) a.pend[pr] = next;
+            if (atomicSub(&a.pend[pr], 1u) == 1u) {
+                a.pend[pr] = next;
+                atomicOr(&map_next[pr >> 10], 1u << ((pr >> 5) & 31));
+            }
         }
     }
     if (wrapped) atomicOr(a.status, ST_OVERFLOW);
@@ -447,6 +472,8 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     const int64_t capj = p->capturing ? p->caps.nj : p->n_junctions;
     const size_t njc = size_t(capj ? capj : 1);
     if ((st = ensure(p, p->dp_pend, sizeof(uint32_t) * njc))) return st;
+    const int64_t map_words = int64_t((njc + 1023) / 1024);
+    if ((st = ensure(p, p->dp_chunks, sizeof(uint32_t) * 2 * size_t(map_words)))) return st;
     if ((st = ensure(p, p->dp_long, sizeof(uint32_t) * njc))) return st;
     if ((st = ensure(p, p->dp_in_cnt, sizeof(uint32_t) * 2 * njc))) return st;  // counts, then fill cursors
     if ((st = ensure(p, p->dp_in_ptr, sizeof(int64_t) * (njc + 1)))) return st;
@@ -464,6 +491,8 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     a.cap1 = cap1;
     a.capj = capj;
     a.pend = static_cast<uint32_t*>(p->dp_pend.ptr);
+    a.chunk_map = static_cast<uint32_t*>(p->dp_chunks.ptr);
+    a.map_words = map_words;
     a.long_list = static_cast<uint32_t*>(p->dp_long.ptr);
     a.in_cnt = static_cast<uint32_t*>(p->dp_in_cnt.ptr);
     a.in_fill = a.in_cnt + njc;
@@ -482,6 +511,8 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     a.sum = p->dsum();
     a.status = p->status_word();
     if ((st = check_cuda(p, cudaMemsetAsync(a.in_cnt, 0, sizeof(uint32_t) * 2 * njc, s), "memset"))) return st;
+    if ((st = check_cuda(p, cudaMemsetAsync(a.chunk_map, 0, sizeof(uint32_t) * 2 * size_t(map_words), s), "memset")))
+        return st;
     // the wave state of the summary (a rerun of the stage starts it afresh)
     if ((st = check_cuda(p, cudaMemsetAsync(&p->dsum()->dp_wave_done, 0,
                                             offsetof(Summary, loop_flag) - offsetof(Summary, dp_wave_done), s),

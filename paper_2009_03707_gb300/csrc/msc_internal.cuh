@@ -92,7 +92,7 @@ struct Plan {
     DeviceBuffer dstar_rowptr, dstar_col, dstar_count;
     DeviceBuffer csc_colptr, csc_row, csc_count, csc_work;  // D* by 2-saddle (transpose.cu)
     DeviceBuffer graph_nodeptr, graph_adj, graph_mult, graph_work, graph_none;  // the 1-skeleton (graph.cu)
-    DeviceBuffer dp_pend, dp_in_cnt, dp_in_ptr, dp_in_idx, dp_j_off, dp_j_len, dp_pool_col, dp_pool_cnt, dp_long;
+    DeviceBuffer dp_pend, dp_in_cnt, dp_in_ptr, dp_in_idx, dp_j_off, dp_j_len, dp_pool_col, dp_pool_cnt, dp_long, dp_chunks;
 
     template <class F>
     void for_each_buffer(F&& f) {
@@ -104,7 +104,7 @@ struct Plan {
                                &minor_mult[0], &minor_mult[1], &minor_mult[2], &minor_mult[3], &pc_rowstart, &pc_rowlen,
                                &pc_big, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc, &dstar_rowptr, &dstar_col,
                                &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
-                               &dp_j_len, &dp_pool_col, &dp_pool_cnt, &dp_long, &csc_colptr, &csc_row, &csc_count, &csc_work,
+                               &dp_j_len, &dp_pool_col, &dp_pool_cnt, &dp_long, &dp_chunks, &csc_colptr, &csc_row, &csc_count, &csc_work,
                                &graph_nodeptr, &graph_adj, &graph_mult, &graph_work, &graph_none};
         for (DeviceBuffer* b : all) f(*b);
     }
