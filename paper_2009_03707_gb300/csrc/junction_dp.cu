@@ -47,7 +47,7 @@ constexpr int THREADS = 256;
 constexpr uint32_t READY = 0x80000000u;  // pend[j] = READY | wave: j's row is computed in that wave
 constexpr uint32_t DONE = 0xFFFFFFFFu;
 constexpr int SCAN_BATCH = 8;  // pending words a thread reads at once in a wave
-constexpr uint32_t LONG_ROW = 24;  // merges with more input entries go to the warp kernel
+constexpr uint32_t LONG_ROW = 12;  // merges with more input entries go to the warp kernel
 typedef unsigned long long u64;
 
 struct DpArgs {
@@ -452,13 +452,14 @@ __global__ void __launch_bounds__(THREADS) dp_rows(DpArgs a) {
 
 struct WaveCtx {
     int grid;
+    int long_grid;  // the long merges of a wave are few: a smaller grid of warps
     DpArgs a;
 };
 
 void wave_body(Plan* p, cudaStream_t s, cudaGraphConditionalHandle h, void* ctx) {
     const WaveCtx& c = *static_cast<WaveCtx*>(ctx);
     dp_wave<<<c.grid, THREADS, 0, s>>>(c.a);
-    dp_long<<<c.grid, THREADS, 0, s>>>(c.a);
+    dp_long<<<c.long_grid, THREADS, 0, s>>>(c.a);
     dp_decide<<<1, 1, 0, s>>>(p->dsum(), p->opts.max_iterations, h, h != 0);
 }
 
@@ -528,7 +529,7 @@ msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t 
     launched(p);
     if ((st = check_cuda(p, cudaGetLastError(), "junction dp launch"))) return st;
     record_event(p, p->kev0, s);
-    WaveCtx ctx{grid_cap(p, capj, THREADS, 8), a};
+    WaveCtx ctx{grid_cap(p, capj, THREADS, 8), std::max(1, p->num_sms) * 4, a};
     if ((st = run_loop(p, s, 2, 3, wave_body, &ctx))) return st;
     dp_rows<<<grid_cap(p, cap1, THREADS, 8), THREADS, 0, s>>>(a);
     record_event(p, p->kev1, s);
