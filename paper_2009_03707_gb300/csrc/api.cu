@@ -704,7 +704,7 @@ static msc_status compute_graph(Plan* p, const float* d_field, cudaStream_t s) {
 namespace msc {
 // Minors at most this deep (iterations of the product loop) run the row-wise products when the
 // method is automatic: on the 256^3 GRF (26 levels) they take 1.5 ms against 6 ms for the waves,
-// on the 512^3 blob field (197 levels) 1.55 s against 58 ms.
+// on the 512^3 blob field (197 levels) 1.55 s against 24 ms.
 constexpr int64_t kShallowMinor = 64;
 
 // Every stage with host synchronisation and exact buffer sizes; the sizes plus headroom become
