@@ -167,9 +167,11 @@ def cpu_baseline(field, seconds_hint=""):
     oracle.compute_all(crop)
     dt = time.perf_counter() - t
     nvox = crop.size
+    cz, cy, cx = crop.shape
+    what = "the whole field" if crop.shape == field.shape else "the corner crop"
     return {"value": nvox / dt / 1e6, "unit": "Mvoxel/s", "cores": 1, "kind": "oracle",
-            "sample": f"full pipeline on the 96x96x64 corner crop ({nvox} voxels) of the workload field, "
-                      f"one oracle run of {dt:.1f} s on {os.cpu_count()} host cores (oracle uses 1)"}
+            "sample": f"full pipeline on {what}, {cx}x{cy}x{cz} ({nvox} voxels), one oracle run of {dt:.1f} s "
+                      f"on {os.cpu_count()} host cores (oracle uses 1)"}
 
 
 def run_reference(args):

@@ -289,7 +289,7 @@ __device__ __forceinline__ uint32_t lower_bound(const uint32_t* col, uint32_t le
 // `write` is set.
 __device__ __forceinline__ uint32_t slice_merge(const Inputs& in, const uint32_t s[4], const uint32_t e[4],
                                                 uint32_t lo, uint32_t hi, bool hi_open, bool write, uint32_t* out_col,
-                                                u64* out_cnt, u64* max_seen, bool* wrapped) {
+                                                u64* out_cnt, bool* wrapped) {
     uint32_t pos[4], end[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -322,7 +322,6 @@ __device__ __forceinline__ uint32_t slice_merge(const Inputs& in, const uint32_t
         if (write) {
             out_col[n] = c;
             out_cnt[n] = sum;
-            *max_seen = max(*max_seen, sum);
         }
         ++n;
     }
@@ -342,7 +341,6 @@ __global__ void __launch_bounds__(THREADS) dp_long(DpArgs a) {
     const int lane = threadIdx.x & 31;
     const u64 nwarps = (u64(gridDim.x) * THREADS) >> 5;
     unsigned done = 0;
-    u64 mx = 0;  // (J entries are not D* entries: the largest path count is taken from the D* rows)
     bool wrapped = false;
     for (u64 i = (u64(blockIdx.x) * THREADS + threadIdx.x) >> 5; i < n; i += nwarps) {  // warp-uniform
         const uint32_t j = a.long_list[i];
@@ -374,14 +372,14 @@ __global__ void __launch_bounds__(THREADS) dp_long(DpArgs a) {
         const bool fits = off + bound <= a.pool_cap;  // uniform
         uint32_t len = 0;
         if (fits) {
-            const uint32_t cnt = slice_merge(in, s, e, lo, hi, hi_open, false, nullptr, nullptr, &mx, &wrapped);
+            const uint32_t cnt = slice_merge(in, s, e, lo, hi, hi_open, false, nullptr, nullptr, &wrapped);
             uint32_t incl = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                 if (lane >= o) incl += y;
             }
             slice_merge(in, s, e, lo, hi, hi_open, true, a.pool_col + off + (incl - cnt),
-                        a.pool_cnt + off + (incl - cnt), &mx, &wrapped);
+                        a.pool_cnt + off + (incl - cnt), &wrapped);
             len = __shfl_sync(0xFFFFFFFFu, incl, 31);
         } else if (lane == 0) {
             atomicOr(a.status, ST_RETRY);  // the pool is too small: the host grows it and reruns
