@@ -52,6 +52,9 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+E2E_LANES = 3  # plans in flight in the end-to-end leg
+
+
 def _rounded(d):
     """Floats in a (nested) dict to 6 significant digits, for the JSON line."""
     if isinstance(d, dict):
@@ -270,16 +273,17 @@ def run_gpu(args):
 
     # ---- end to end from pinned host memory -------------------------------------------
     # Every step copies its field in from pinned host memory, runs the pass and reads the whole
-    # 1-skeleton back into pinned host memory.  Two plans on two streams take the steps in turn
-    # through the public asynchronous entry points: step i's pass is enqueued
-    # (msc_compute_async), then step i-1's is waited for (msc_compute_wait) and its results are
-    # copied out on its stream, and the field of step i+1 goes up into that plan's buffer behind
-    # them.  So the device always has the next pass queued while the host collects the last one; a
-    # plan's result buffers are reused two steps later, on the same stream, after their copies.
+    # 1-skeleton back into pinned host memory.  E2E_LANES plans on as many streams take the steps in
+    # turn through the public asynchronous entry points: step i's pass is enqueued
+    # (msc_compute_async), then the oldest pass still out, step i - E2E_LANES + 1, is waited for
+    # (msc_compute_wait) and its results are copied out on its stream, and the field of step i+1
+    # goes up into that plan's buffer behind them.  So the device always has the next passes queued
+    # while the host collects an earlier one; a plan's result buffers are reused E2E_LANES steps
+    # later, on the same stream, after their copies.
     h_field = torch.from_numpy(f).pin_memory()
     counts = stats["counts"]
     lanes = []
-    for x in range(2):
+    for x in range(E2E_LANES):
         pl = plan if x == 0 else msc.Plan((nx, ny, nz), no_graph=args.no_graph, gradient_tile=args.gradient_tile)
         lanes.append({"plan": pl, "field": d_field if x == 0 else torch.empty_like(d_field),
                       "stream": stream if x == 0 else torch.cuda.Stream(), "out": {}})
@@ -313,28 +317,33 @@ def run_gpu(args):
         return n
 
     def run_e2e(k):
+        L = len(lanes)
         upload(lanes[0])
         n = 0
         for i in range(k):
-            lane, other = lanes[i % 2], lanes[(i + 1) % 2]
-            issue(lane)
-            if i > 0:
-                n = collect(other)
+            issue(lanes[i % L])
+            nxt = lanes[(i + 1) % L]
+            if i - L + 1 >= 0:
+                n = collect(nxt)  # pass i - L + 1 ran on the lane that takes step i + 1
             if i + 1 < k:
-                upload(other)
-        return collect(lanes[(k - 1) % 2])
+                upload(nxt)
+        for i in range(max(k - L + 1, 0), k):  # the passes still out
+            n = collect(lanes[i % L])
+        return n
 
-    warm = max(args.warmup, 2)  # both plans warm (their graphs captured)
+    warm = max(args.warmup, E2E_LANES)  # every plan warm (its graph captured)
     for _ in range(2):
         run_e2e(warm)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(lanes[0]["stream"])
-    lanes[1]["stream"].wait_event(e0)
+    for lane in lanes[1:]:
+        lane["stream"].wait_event(e0)
     bo = run_e2e(args.steps)  # the first field's upload is inside the timed region
-    done = torch.cuda.Event()
-    done.record(lanes[1]["stream"])
-    lanes[0]["stream"].wait_event(done)
+    for lane in lanes[1:]:
+        done = torch.cuda.Event()
+        done.record(lane["stream"])
+        lanes[0]["stream"].wait_event(done)
     e1.record(lanes[0]["stream"])
     e1.synchronize()
     e2e_ms = [e0.elapsed_time(e1) / args.steps]
