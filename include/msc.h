@@ -215,6 +215,32 @@ msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nn
 msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
                              int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult);
 
+/* ---- outputs into host memory --------------------------------------------------------
+ * Copies one output of the plan's last pass into caller-owned host memory, computing the stage if
+ * it has not run yet (as the accessor above would).  `what` selects the array and its element type:
+ *   MSC_OUT_CELLS0..3      critical k-cell ids (uint32, counts[k])
+ *   MSC_OUT_MIN_ARCS       2 minima per 1-saddle (uint32)       MSC_OUT_MAX_ARCS  2 maxima per 2-saddle (uint32)
+ *   MSC_OUT_VERTEX_MIN     minimum of every vertex (uint32)     MSC_OUT_CUBE_MAX  maximum of every cube (uint32)
+ *   MSC_OUT_DSTAR_ROWPTR   D* row pointers (int64, counts[1]+1) MSC_OUT_DSTAR_COL columns (uint32, nnz)
+ *   MSC_OUT_DSTAR_COUNT    path counts (uint64, nnz)
+ * Size query: *bytes on entry is the room in h_out; on return it is the output's size in bytes.
+ * With h_out null nothing is copied.  Otherwise the copy is made and the stream synchronised;
+ * MSC_ERR_CAPACITY (nothing copied) if the room is smaller.  MSC_ERR_ARG for an unknown `what`. */
+enum {
+    MSC_OUT_CELLS0 = 0,
+    MSC_OUT_CELLS1 = 1,
+    MSC_OUT_CELLS2 = 2,
+    MSC_OUT_CELLS3 = 3,
+    MSC_OUT_MIN_ARCS = 4,
+    MSC_OUT_MAX_ARCS = 5,
+    MSC_OUT_VERTEX_MIN = 6,
+    MSC_OUT_CUBE_MAX = 7,
+    MSC_OUT_DSTAR_ROWPTR = 8,
+    MSC_OUT_DSTAR_COL = 9,
+    MSC_OUT_DSTAR_COUNT = 10
+};
+msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void* h_out, int64_t* bytes);
+
 /* ---- the whole pass without waiting ----------------------------------------------------
  * msc_compute_async enqueues a pass on `stream` and returns without waiting for it, so that one
  * thread can keep several plans' passes (on their own streams) in flight -- e.g. upload the next

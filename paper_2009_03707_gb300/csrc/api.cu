@@ -745,6 +745,47 @@ msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t strea
     return msc::compute_synchronised(p, d_field, s);
 }
 
+msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void* h_out, int64_t* bytes) {
+    if (!plan || !bytes || what < MSC_OUT_CELLS0 || what > MSC_OUT_DSTAR_COUNT) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    const void* src = nullptr;
+    int64_t n = 0;  // bytes
+    if (what <= MSC_OUT_CELLS3) {
+        if ((st = ensure_critical(p, s))) return st;
+        src = p->cells[what].ptr;
+        n = int64_t(sizeof(uint32_t)) * p->counts[what];
+    } else if (what <= MSC_OUT_CUBE_MAX) {
+        if ((st = ensure_extremum(p, s))) return st;
+        const int64_t nv = p->g.nverts;
+        const msc::DeviceBuffer* b[4] = {&p->min_arcs, &p->max_arcs, &p->vmin, &p->cmax};
+        const int64_t len[4] = {2 * p->counts[1], 2 * p->counts[2], nv, nv};
+        src = b[what - MSC_OUT_MIN_ARCS]->ptr;
+        n = int64_t(sizeof(uint32_t)) * len[what - MSC_OUT_MIN_ARCS];
+    } else {
+        if ((st = ensure_dstar(p, s))) return st;
+        if (what == MSC_OUT_DSTAR_ROWPTR) {
+            src = p->dstar_rowptr.ptr;
+            n = int64_t(sizeof(int64_t)) * (p->counts[1] + 1);
+        } else if (what == MSC_OUT_DSTAR_COL) {
+            src = p->dstar_col.ptr;
+            n = int64_t(sizeof(uint32_t)) * p->dstar_nnz;
+        } else {
+            src = p->dstar_count.ptr;
+            n = int64_t(sizeof(uint64_t)) * p->dstar_nnz;
+        }
+    }
+    const int64_t room = *bytes;
+    *bytes = n;
+    if (!h_out) return MSC_OK;
+    if (room < n) return MSC_ERR_CAPACITY;
+    if (n && (st = msc::check_cuda(p, cudaMemcpyAsync(h_out, src, size_t(n), cudaMemcpyDeviceToHost, s), "copy out")))
+        return st;
+    return msc::check_cuda(p, cudaStreamSynchronize(s), "stream sync");
+}
+
 msc_status msc_compute_async(msc_plan_t plan, const float* d_field, msc_stream_t stream) {
     if (!plan || !d_field) return MSC_ERR_ARG;
     Plan* p = plan;

@@ -43,6 +43,7 @@ SIGNATURES = {
     "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_complex_graph": ([_P, _P, _PI64, _PI64, _P, _P, _P], _I32),
     "msc_compute_async": ([_P, _P, _P], _I32),
+    "msc_copy_to_host": ([_P, _P, _I32, _P, _PI64], _I32),
     "msc_compute_wait": ([_P], _I32),
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
@@ -266,6 +267,24 @@ def msc_compute(plan: Plan, field: torch.Tensor) -> None:
     if tuple(field.shape) != plan.shape_zyx:
         raise ValueError(f"field shape {tuple(field.shape)} does not match the plan {plan.shape_zyx}")
     _check(lib.msc_compute(plan.handle, ctypes.c_void_p(field.data_ptr()), _stream()), plan.handle)
+
+
+MSC_OUT = {"cells0": (0, np.uint32), "cells1": (1, np.uint32), "cells2": (2, np.uint32), "cells3": (3, np.uint32),
+           "min_arcs": (4, np.uint32), "max_arcs": (5, np.uint32), "vertex_min": (6, np.uint32),
+           "cube_max": (7, np.uint32), "dstar_rowptr": (8, np.int64), "dstar_col": (9, np.uint32),
+           "dstar_count": (10, np.uint64)}
+
+
+def msc_copy_to_host(plan: Plan, what: str) -> np.ndarray:
+    """One output of the last pass as a host numpy array (size query, then the copy)."""
+    code, dtype = MSC_OUT[what]
+    nbytes = ctypes.c_int64(0)
+    _check(lib.msc_copy_to_host(plan.handle, _stream(), code, None, ctypes.byref(nbytes)), plan.handle)
+    out = np.empty(nbytes.value // np.dtype(dtype).itemsize, dtype=dtype)
+    room = ctypes.c_int64(out.nbytes)
+    _check(lib.msc_copy_to_host(plan.handle, _stream(), code, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(room)),
+           plan.handle)
+    return out
 
 
 def msc_compute_async(plan: Plan, field: torch.Tensor) -> None:
