@@ -175,8 +175,9 @@ __device__ __forceinline__ bool sweep_word(const Rows& r, const uint4* __restric
     return add != 0;
 }
 
-// One level: Rout = Rin | cells whose partner quad has another facet in Rin.  blockIdx.y is the
-// axis, so every branch on it is uniform.  Sets *changed if any word grew.
+// One level: Rout = Rin | cells whose partner quad has another facet in Rin.  A thread takes one
+// vertex-row word for all three axes (one neighbourhood check, three independent chains of
+// loads).  Sets *changed if any word grew.
 // Rows (y, z) are stamped with 1 + the last sweep that changed them (1: the start).  A cell's
 // predecessors lie within one step in y and z, so a row none of whose 3 x 3 neighbour rows changed
 // in the previous sweep cannot change now; it is skipped, Rout included: that buffer already
@@ -199,9 +200,10 @@ __global__ void __launch_bounds__(THREADS, 4) reach_sweep(Geom g, const uint4* _
                 if (y >= 0 && y < g.ny && z >= 0 && z < g.nz) recent = max(recent, stamp[int64_t(z) * g.ny + y]);
             }
         if (recent >= k) {
-            grew = blockIdx.y == 0 ? sweep_word<0>(r, masks, Rin, Rout)
-                   : blockIdx.y == 1 ? sweep_word<1>(r, masks, Rin, Rout)
-                                     : sweep_word<2>(r, masks, Rin, Rout);
+            const bool g0 = sweep_word<0>(r, masks, Rin, Rout);
+            const bool g1 = sweep_word<1>(r, masks, Rin, Rout);
+            const bool g2 = sweep_word<2>(r, masks, Rin, Rout);
+            grew = g0 || g1 || g2;
             if (grew) stamp[int64_t(r.z) * g.ny + r.y] = k + 1;
         }
     }
@@ -402,7 +404,7 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     reach_start<<<1, 1, 0, s>>>(p->dsum());
     launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
-    SweepCtx ctx{dim3(unsigned((nrw + THREADS - 1) / THREADS), 3), masks, A, B, stamp};
+    SweepCtx ctx{dim3(unsigned((nrw + THREADS - 1) / THREADS), 1), masks, A, B, stamp};
     return run_loop(p, s, 1, 3, sweep_body, &ctx);
 }
 
