@@ -321,7 +321,8 @@ def run_gpu(args):
     counts = stats["counts"]
     lanes = []
     for x in range(E2E_LANES):
-        pl = plan if x == 0 else msc.Plan((nx, ny, nz), no_graph=args.no_graph, gradient_tile=args.gradient_tile)
+        # several passes in flight fill the device: each plan replays its pass as one chain
+        pl = msc.Plan((nx, ny, nz), no_graph=args.no_graph, gradient_tile=args.gradient_tile, serial_pass=True)
         lanes.append({"plan": pl, "field": d_field if x == 0 else torch.empty_like(d_field),
                       "stream": stream if x == 0 else torch.cuda.Stream(), "out": {}})
 

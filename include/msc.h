@@ -56,6 +56,14 @@ typedef struct msc_plan_s* msc_plan_t;
 /* msc_opts.flags: run every msc_compute with host synchronisation between the stages, never as a
  * replayed CUDA graph (the results are identical; tests use it to compare the two paths). */
 #define MSC_FLAG_NO_GRAPH 1
+/* msc_opts.flags: replay the pass as one chain of kernels.  By default a replayed pass runs the
+ * saddle-extremum stage (a3) as a branch of its own beside the critical path (reachability, the
+ * minor, the path counts), its kernels at the device's lowest stream priority and those of the
+ * critical path at the highest, which shortens the pass on an otherwise idle device.  When
+ * several passes are kept in flight (msc_compute_async on several plans, or a batch), they already
+ * fill the device, and one chain per pass at the launching stream's priority gives more
+ * throughput.  The results are identical. */
+#define MSC_FLAG_SERIAL_PASS 2
 
 /* Plan options (all fields may be zero for defaults). */
 typedef struct msc_opts {
@@ -95,6 +103,9 @@ typedef struct msc_stats {
     int64_t peak_device_bytes;
     int64_t n_launches;       /* kernels this plan launched since the last msc_gradient */
     float ms_gradient, ms_critical, ms_extremum, ms_reachability, ms_minor, ms_path_count;
+                              /* per stage, CUDA events; in a replayed pass the extremum stage runs
+                                 beside the reachability, minor and path-count stages, so the six
+                                 may add up to more than the pass */
     float ms_rows_kernel;      /* the product kernels: the junction waves and D* rows, or the
                                   row-wise tier 0 (CUDA events) */
     float ms_trace_kernel;     /* the simple-path tracing kernel alone, CUDA events */

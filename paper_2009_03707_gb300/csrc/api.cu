@@ -97,7 +97,8 @@ msc_status run_loop(Plan* p, cudaStream_t s, int which, int body_launches,
             launched(p, body_launches);
             uint32_t more = 0;
             if ((st = check_cuda(p, cudaGetLastError(), "loop launch"))) return st;
-            if ((st = check_cuda(p, cudaMemcpyAsync(&more, &p->dsum()->loop_flag[3], sizeof(more),
+            const uint32_t* cont = which == 0 ? &p->dsum()->jump_flag[1] : &p->dsum()->loop_flag[3];
+            if ((st = check_cuda(p, cudaMemcpyAsync(&more, cont, sizeof(more),
                                                     cudaMemcpyDeviceToHost, s),
                                  "loop flag copy")))
                 return st;
@@ -136,12 +137,13 @@ msc_status run_loop(Plan* p, cudaStream_t s, int which, int body_launches,
                          "conditional node")))
         return st;
     cudaGraph_t body_graph = np.conditional.phGraph_out[0];
-    if ((st = check_cuda(p, cudaStreamBeginCaptureToGraph(p->body_stream, body_graph, nullptr, nullptr, 0,
+    cudaStream_t bs = s == p->side_stream ? p->side_body_stream : p->body_stream;  // the branch's priority
+    if ((st = check_cuda(p, cudaStreamBeginCaptureToGraph(bs, body_graph, nullptr, nullptr, 0,
                                                           cudaStreamCaptureModeRelaxed),
                          "body capture")))
         return st;
-    body(p, p->body_stream, h, ctx);
-    const cudaError_t e = cudaStreamEndCapture(p->body_stream, &body_graph);
+    body(p, bs, h, ctx);
+    const cudaError_t e = cudaStreamEndCapture(bs, &body_graph);
     if ((st = check_cuda(p, e, "body capture end"))) return st;
     p->loop_body_launches[which] = body_launches;
     return check_cuda(p, cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
@@ -256,8 +258,14 @@ msc_status run_critical(Plan* p, cudaStream_t s) {
     return compaction_emit(p, s, src, 4);
 }
 
-// Every stage, enqueued without host synchronisation (the body of a captured graph).
-msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s) {
+// Every stage, enqueued without host synchronisation (the body of a captured graph).  The
+// saddle-extremum stage needs only the gradient and the critical cells, and no later stage reads
+// what it writes.  With `branch` it is a branch of its own, captured at the lowest stream
+// priority beside the critical path (reachability, the minor and the path counts, whose
+// latency-bound kernels leave room on the device), so it fills what they leave free.  The two
+// branches share no buffer and no summary word but the status bits, which every kernel sets
+// atomically.
+msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s, bool branch) {
     msc_status st;
     if ((st = check_cuda(p, cudaMemsetAsync(p->dsum(), 0, sizeof(Summary), s), "summary clear"))) return st;
     stage_start(p, 0, s);
@@ -266,9 +274,17 @@ msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s) {
     stage_start(p, 1, s);
     if ((st = run_critical(p, s))) return st;
     stage_end(p, 1, s);
-    stage_start(p, 2, s);
-    if ((st = run_extremum(p, s))) return st;
-    stage_end(p, 2, s);
+    cudaStream_t side = s;
+    if (branch) {
+        side = p->side_stream;
+        if ((st = check_cuda(p, cudaEventRecord(p->fork_ev, s), "fork")) ||
+            (st = check_cuda(p, cudaStreamWaitEvent(side, p->fork_ev, 0), "fork")))
+            return st;
+    }
+    stage_start(p, 2, side);
+    if ((st = run_extremum(p, side))) return st;
+    stage_end(p, 2, side);
+    if (branch && (st = check_cuda(p, cudaEventRecord(p->join_ev, side), "join"))) return st;
     stage_start(p, 3, s);
     if ((st = run_reachability(p, s))) return st;
     stage_end(p, 3, s);
@@ -279,7 +295,7 @@ msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s) {
     stage_start(p, 5, s);
     if ((st = run_path_count(p, s))) return st;
     stage_end(p, 5, s);
-    return MSC_OK;
+    return branch ? check_cuda(p, cudaStreamWaitEvent(s, p->join_ev, 0), "join") : MSC_OK;
 }
 
 void destroy_graph(Plan* p) {
@@ -297,11 +313,12 @@ void destroy_graph(Plan* p) {
 msc_status capture_graph(Plan* p, const float* d_field) {
     destroy_graph(p);
     msc_status st = MSC_OK;
+    const bool branch = !(p->opts.flags & MSC_FLAG_SERIAL_PASS);
     for (int pass = 0; pass < 2; ++pass) {
         p->capturing = true;
         p->stats.n_launches = 0;
         cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed);
-        if (e == cudaSuccess) st = enqueue_pipeline(p, d_field, p->cap_stream);
+        if (e == cudaSuccess) st = enqueue_pipeline(p, d_field, p->cap_stream, branch);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(p->cap_stream, &g) : e;
         p->capturing = false;
@@ -318,7 +335,7 @@ msc_status capture_graph(Plan* p, const float* d_field) {
         }
         p->graph = g;
         p->graph_static_launches = p->stats.n_launches;
-        if ((st = check_cuda(p, cudaGraphInstantiate(&p->graph_exec, g, 0), "graph instantiate"))) {
+        if ((st = check_cuda(p, cudaGraphInstantiate(&p->graph_exec, g, branch ? cudaGraphInstantiateFlagUseNodePriority : 0), "graph instantiate"))) {
             destroy_graph(p);
             return st;
         }
@@ -377,7 +394,7 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
         if (dims[i] < 2 || dims[i] > (int64_t(1) << 30)) return MSC_ERR_ARG;
     const int64_t rx = 2 * dims[0] - 1, ry = 2 * dims[1] - 1, rz = 2 * dims[2] - 1;
     if (rx * ry > (int64_t(1) << 40) || double(rx) * double(ry) * double(rz) >= 4294967295.0) return MSC_ERR_TOO_LARGE;
-    if (opts && ((opts->flags & ~MSC_FLAG_NO_GRAPH) || opts->gradient_tile < 0 || opts->gradient_tile > 9 ||
+    if (opts && ((opts->flags & ~(MSC_FLAG_NO_GRAPH | MSC_FLAG_SERIAL_PASS)) || opts->gradient_tile < 0 || opts->gradient_tile > 9 ||
                  opts->path_count_method < 0 || opts->path_count_method > 2))
         return MSC_ERR_ARG;
     msc_plan_s* p = new (std::nothrow) msc_plan_s();
@@ -400,8 +417,18 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->gev0), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreate(&p->gev1), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaEventCreateWithFlags(&p->pend_ev, cudaEventDisableTiming), "cudaEventCreate");
-    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
-    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    // the pass's critical path (capture and its loop bodies) at the highest priority, the extremum
+    // branch at the lowest, so that the branch takes only what the critical path leaves free; a
+    // replayed graph with the branch keeps these per-node priorities (one without it runs at the
+    // priority of the stream it is launched into)
+    int lo_prio = 0, hi_prio = 0;
+    if (!st) st = msc::check_cuda(p, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio), "cudaDeviceGetStreamPriorityRange");
+    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithPriority(&p->cap_stream, cudaStreamNonBlocking, hi_prio), "cudaStreamCreate");
+    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithPriority(&p->body_stream, cudaStreamNonBlocking, hi_prio), "cudaStreamCreate");
+    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithPriority(&p->side_stream, cudaStreamNonBlocking, lo_prio), "cudaStreamCreate");
+    if (!st) st = msc::check_cuda(p, cudaStreamCreateWithPriority(&p->side_body_stream, cudaStreamNonBlocking, lo_prio), "cudaStreamCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming), "cudaEventCreate");
+    if (!st) st = msc::check_cuda(p, cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming), "cudaEventCreate");
     if (!st) st = msc::check_cuda(p, cudaMallocHost(&p->hsum, sizeof(msc::Summary)), "cudaMallocHost");
     if (!st) st = msc::ensure(p, p->status, sizeof(msc::Summary));
     if (!st) st = msc::check_cuda(p, cudaMemset(p->status.ptr, 0, sizeof(msc::Summary)), "cudaMemset(summary)");
@@ -416,6 +443,7 @@ msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out
 msc_status msc_plan_destroy(msc_plan_t plan) {
     if (!plan) return MSC_ERR_ARG;
     msc_plan_s* p = plan;
+    if (p->pending) cudaEventSynchronize(p->pend_ev);  // the pass in flight still uses the buffers
     msc::destroy_graph(p);
     p->for_each_buffer([](msc::DeviceBuffer& b) {
         if (b.ptr) cudaFree(b.ptr);
@@ -424,11 +452,10 @@ msc_status msc_plan_destroy(msc_plan_t plan) {
     });
     for (cudaEvent_t e : p->stage_ev)
         if (e) cudaEventDestroy(e);
-    if (p->pending) cudaEventSynchronize(p->pend_ev);  // the pass in flight still uses the buffers
-    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1, p->gev0, p->gev1, p->pend_ev})
+    for (cudaEvent_t e : {p->kev0, p->kev1, p->tev0, p->tev1, p->gev0, p->gev1, p->pend_ev, p->fork_ev, p->join_ev})
         if (e) cudaEventDestroy(e);
-    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    if (p->body_stream) cudaStreamDestroy(p->body_stream);
+    for (cudaStream_t t : {p->cap_stream, p->body_stream, p->side_stream, p->side_body_stream})
+        if (t) cudaStreamDestroy(t);
     if (p->hsum) cudaFreeHost(p->hsum);
     delete p;
     return MSC_OK;

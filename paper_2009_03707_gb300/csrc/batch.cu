@@ -120,7 +120,7 @@ struct msc_batch_s {
             }
             p->capturing = true;
             const int64_t launches = p->stats.n_launches;
-            st = msc::enqueue_pipeline(p, vols[i].second, branches[i]);
+            st = msc::enqueue_pipeline(p, vols[i].second, branches[i], false);  // the volumes fill the device
             p->capturing = false;
             p->stats.n_launches = launches;
             if (!st && (cudaEventRecord(joins[i], branches[i]) != cudaSuccess ||
@@ -273,7 +273,10 @@ msc_status msc_batch_submit(msc_batch_t b, msc_volume* vols, int n, msc_stream_t
     std::vector<Job> jobs;
     for (int i = 0; i < n; ++i) {
         if (!vols[i].plan) {
-            msc_status st = msc_plan(vols[i].dims, nullptr, &vols[i].plan);
+            // the runtime keeps several passes in flight: each replays as one chain
+            msc_opts o{};
+            o.flags = MSC_FLAG_SERIAL_PASS;
+            msc_status st = msc_plan(vols[i].dims, &o, &vols[i].plan);
             if (st) {
                 for (auto& j : jobs) cudaEventDestroy(j.ready);
                 return st;

@@ -152,15 +152,15 @@ __global__ void __launch_bounds__(THREADS) jump_round(Geom g, uint32_t* __restri
 // End of one round: the continue decision (more rounds while some chain is still open, up to the
 // iteration cap), the round count, and the graph condition when the loop runs in a graph.
 __global__ void jump_decide(Summary* sum, int64_t max_iter, cudaGraphConditionalHandle h, int use_handle) {
-    const bool open = sum->loop_flag[0] != 0;
-    sum->loop_flag[0] = 0;
+    const bool open = sum->jump_flag[0] != 0;
+    sum->jump_flag[0] = 0;
     const unsigned long long r = ++sum->jump_rounds;
     bool more = open;
     if (more && int64_t(r) >= max_iter) {
-        sum->status |= ST_ITER;
+        atomicOr(&sum->status, uint32_t(ST_ITER));
         more = false;
     }
-    sum->loop_flag[3] = more ? 1u : 0u;
+    sum->jump_flag[1] = more ? 1u : 0u;
     if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
@@ -232,7 +232,7 @@ struct JumpCtx {
 
 void jump_body(Plan* p, cudaStream_t s, cudaGraphConditionalHandle h, void* ctx) {
     const JumpCtx& c = *static_cast<JumpCtx*>(ctx);
-    jump_round<<<blocks(c.n), THREADS, 0, s>>>(p->g, c.lab_v, c.lab_c, c.vmin, c.cmax, &p->dsum()->loop_flag[0]);
+    jump_round<<<blocks(c.n), THREADS, 0, s>>>(p->g, c.lab_v, c.lab_c, c.vmin, c.cmax, &p->dsum()->jump_flag[0]);
     jump_decide<<<1, 1, 0, s>>>(p->dsum(), p->opts.max_iterations, h, h != 0);
 }
 

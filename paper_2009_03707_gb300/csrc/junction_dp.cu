@@ -416,7 +416,7 @@ __global__ void dp_decide(Summary* sum, int64_t max_iter, cudaGraphConditionalHa
         sum->dp_junctions_done += done;
         ++sum->dp_wave;
         if (int64_t(sum->pc[PC_ITER]) >= max_iter) {
-            sum->status |= ST_ITER;
+            atomicOr(&sum->status, uint32_t(ST_ITER));
             more = false;
         }
     }

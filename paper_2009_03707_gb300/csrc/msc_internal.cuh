@@ -62,6 +62,9 @@ struct Summary {
     uint32_t loop_flag[4];            // "changed" flags of the iterative stages; [3] = continue (host loops)
     uint32_t status;                  // StatusBit word
     uint32_t pad;
+    uint32_t jump_flag[2];            // pointer jumping's own "changed" flag and continue decision: that
+                                      // stage runs beside the reachability loop in a replayed pass
+    uint32_t pad3[2];
 };
 
 // ---- the plan ----------------------------------------------------------------------------
@@ -123,6 +126,9 @@ struct Plan {
     } caps;
     bool capturing = false;          // enqueueing into a graph: no host synchronisation allowed
     cudaStream_t cap_stream = nullptr, body_stream = nullptr;  // private capture streams
+    cudaStream_t side_stream = nullptr;                        // the extremum branch of a captured pass
+    cudaStream_t side_body_stream = nullptr;                   // its loop body
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     const float* graph_field = nullptr;
@@ -180,9 +186,9 @@ inline void record_event(const Plan* p, cudaEvent_t ev, cudaStream_t s) {
 inline void launched(Plan* p, int n = 1) { p->stats.n_launches += n; }
 
 // Runs an iterative stage: body(stream, handle) enqueues one iteration and must end with a
-// kernel that stores the continue decision in summary.loop_flag[3] and, when the handle is
-// non-zero, sets the graph condition to it.  Host synchronised: a loop that reads the flag after
-// every iteration.  Capturing: a conditional WHILE node whose body graph is captured from one
+// kernel that stores the continue decision in summary.loop_flag[3] (jump_flag[1] for pointer
+// jumping, which = 0) and, when the handle is non-zero, sets the graph condition to it.  Host
+// synchronised: a loop that reads the flag after every iteration.  Capturing: a conditional WHILE node whose body graph is captured from one
 // call of body, so the loop runs on the device with no host round trip.
 msc_status run_loop(Plan* p, cudaStream_t s, int which, int body_launches,
                     void (*body)(Plan*, cudaStream_t, cudaGraphConditionalHandle, void*), void* ctx);
@@ -195,10 +201,11 @@ msc_status check_status_word(Plan* p, cudaStream_t s);  // syncs, reads and clea
 msc_status status_error(Plan* p, uint32_t word);        // the error a non-zero status word stands for
 
 // Pipeline graphs (api.cu).  enqueue_pipeline issues every stage without host synchronisation
-// (p->capturing set); capture_graph records the plan's own graph; finish_replay takes a replay's
+// (p->capturing set), the saddle-extremum stage on a branch of its own if `branch`; capture_graph
+// records the plan's own graph; finish_replay takes a replay's
 // summary (already in p->hsum): MSC_OK, MSC_NOT_READY (rerun synchronised) or the error;
 // compute_synchronised runs a pass with host synchronisation and sets the capacities.
-msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s);
+msc_status enqueue_pipeline(Plan* p, const float* d_field, cudaStream_t s, bool branch);
 msc_status capture_graph(Plan* p, const float* d_field);
 void destroy_graph(Plan* p);
 msc_status finish_replay(Plan* p, cudaStream_t s);

@@ -223,7 +223,7 @@ __global__ void reach_decide(Summary* sum, int64_t max_iter, cudaGraphConditiona
     sum->levels += (c0 ? 1 : 0) + (c1 ? 1 : 0);
     bool more = c1 != 0;
     if (more && int64_t(sum->levels) >= max_iter) {
-        sum->status |= ST_ITER;
+        atomicOr(&sum->status, uint32_t(ST_ITER));
         more = false;
     }
     sum->loop_flag[3] = more ? 1u : 0u;

@@ -57,6 +57,7 @@ SIGNATURES = {
 
 
 MSC_FLAG_NO_GRAPH = 1
+MSC_FLAG_SERIAL_PASS = 2
 
 
 class MscOpts(ctypes.Structure):
@@ -137,10 +138,11 @@ class Plan:
     """Owns an msc_plan_t for one grid shape (nx, ny, nz)."""
 
     def __init__(self, dims, max_iterations: int = 0, path_count_tier: int = 0, no_graph: bool = False,
-                 gradient_tile: int = 0, path_count_method: int = 0):
+                 gradient_tile: int = 0, path_count_method: int = 0, serial_pass: bool = False):
         self.dims = tuple(int(d) for d in dims)
         arr = (ctypes.c_int64 * 3)(*self.dims)
-        opts = MscOpts(int(max_iterations), MSC_FLAG_NO_GRAPH if no_graph else 0, int(path_count_tier),
+        flags = (MSC_FLAG_NO_GRAPH if no_graph else 0) | (MSC_FLAG_SERIAL_PASS if serial_pass else 0)
+        opts = MscOpts(int(max_iterations), flags, int(path_count_tier),
                        int(gradient_tile), int(path_count_method))
         h = ctypes.c_void_p()
         _check(lib.msc_plan(arr, ctypes.byref(opts), ctypes.byref(h)), what=f"msc_plan{self.dims}")

@@ -55,3 +55,19 @@ def test_plan_frees_every_buffer_exactly_once():
     listed = re.findall(r"&(\w+(?:\[\d+\])?)", block)
     assert [n for n, c in collections.Counter(listed).items() if c > 1] == []
     assert sorted(listed) == sorted(declared)
+
+
+def test_plan_rejects_unknown_options_before_touching_the_device():
+    """msc_plan checks its options first: unknown flag bits and out-of-range selectors are
+    MSC_ERR_ARG with no plan made (so this runs without a GPU)."""
+    from paper_2009_03707_gb300 import build, msc
+
+    lib = ctypes.CDLL(build.build())
+    lib.msc_plan.restype = ctypes.c_int
+    dims = (ctypes.c_int64 * 3)(8, 8, 8)
+    known = msc.MSC_FLAG_NO_GRAPH | msc.MSC_FLAG_SERIAL_PASS
+    for flags, tile, method in [(4, 0, 0), (known | 8, 0, 0), (0, 10, 0), (0, -1, 0), (0, 0, 3)]:
+        opts = msc.MscOpts(0, flags, 0, tile, method)
+        out = ctypes.c_void_p(1)
+        assert lib.msc_plan(dims, ctypes.byref(opts), ctypes.byref(out)) == 1
+        assert not out.value

@@ -55,12 +55,15 @@ def _reference(m, f):
     return _outputs(m, plan)
 
 
+@pytest.mark.parametrize("serial", [False, True])
 @pytest.mark.parametrize("shape,alpha,seed", [((40, 40, 40), 3.0, 1), ((33, 20, 47), 2.5, 2)])
-def test_replays_match_synchronised_runs(shape, alpha, seed):
+def test_replays_match_synchronised_runs(shape, alpha, seed, serial):
+    """Replays with the saddle-extremum stage on its own branch (the default) and as one chain
+    (MSC_FLAG_SERIAL_PASS)."""
     m = msc()
     fa = fields.grf(shape, alpha, seed=seed)
     fb = fields.grf(shape, alpha, seed=seed + 100)
-    plan = m.Plan(dims_of(fa))
+    plan = m.Plan(dims_of(fa), serial_pass=serial)
     da = gpu_field(fa)
     want_a, want_b = _reference(m, fa), _reference(m, fb)
     for _ in range(3):  # synchronised run, then capture + replay, then replay
