@@ -96,12 +96,17 @@ __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
 // with shared-memory atomics.  So a lane's work does not depend on its own row's size, and
 // every per-row loop is a fixed, unrolled one.  A row whose table fills up, or whose counts
 // outgrow 32 bits, is deferred intact to the uint64 warp tier.
-template <int F, int D>
+//
+// Packed tables (PK): a slot is one word, key << 8 | count, for keys below 2^24 - 1 (then a
+// packed slot never equals EMPTY) and counts up to 255.  That halves the tables, so more warps fit
+// on an SM.  An add whose count would carry into the key defers the row (its corrupted slot is
+// never expanded: the row's tables are cleared at the end of that round).
+template <int F, int D, bool PK>
 struct T0Warp {
     uint32_t fk[2][F][32];
-    uint32_t fv[2][F][32];
+    uint32_t fv[PK ? 1 : 2][PK ? 1 : F][32];
     uint32_t dk[D][32];
-    uint32_t dv[D][32];
+    uint32_t dv[PK ? 1 : D][32];
     unsigned long long base[32];  // staging offset of each finishing row
     uint16_t items[32 * (F > D ? F : D)];  // this round's work list: slot << 5 | row
 };
@@ -125,6 +130,33 @@ __device__ __forceinline__ bool t0_add_rt(uint32_t* K, uint32_t* V, int lg, int 
         }
     }
     return false;
+}
+
+// The packed form of t0_add_rt: K holds key << 8 | count; val <= 255.  A new key is claimed with
+// its count in one atomicCAS.
+__device__ __forceinline__ bool t0_add_pk(uint32_t* K, int lg, int r, uint32_t key, uint32_t val) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = (key * 2654435761u) >> (32 - lg);
+#pragma unroll 1
+    for (uint32_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+        uint32_t k = *reinterpret_cast<volatile uint32_t*>(&K[h * 32 + r]);
+        if (k == EMPTY) {
+            k = atomicCAS(&K[h * 32 + r], EMPTY, (key << 8) | val);
+            if (k == EMPTY) return true;
+        }
+        if ((k >> 8) == key) {
+            const uint32_t old = atomicAdd(&K[h * 32 + r], val);
+            return (old & 0xFFu) + val <= 0xFFu;  // a carry would change the key
+        }
+    }
+    return false;
+}
+
+// One table add of either form; lg is the table's log2 size.
+template <bool PK>
+__device__ __forceinline__ bool t0_add(uint32_t* K, uint32_t* V, int lg, int r, uint32_t key, uint32_t val) {
+    if constexpr (PK) return t0_add_pk(K, lg, r, key, val);
+    else return t0_add_rt(K, V, lg, r, key, val);
 }
 
 // Exclusive prefix of n over the warp; *total gets the sum.
@@ -164,24 +196,32 @@ __device__ __forceinline__ u64 warp_append(u64* counter, unsigned n) {
 // Persistent: lanes without a row take new ones (one atomic per warp); every round advances all
 // of the warp's rows by one frontier step, and finished rows are written out item-parallel,
 // each entry at its rank within the row (rows come out sorted by column).
-template <int F, int LF, int D, int LD>
+template <int F, int LF, int D, int LD, bool PK>
 __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next_row) {
     PcArgs a = args;
     if (!resolve(a)) return;
     extern __shared__ __align__(16) unsigned char t0_raw[];
-    T0Warp<F, D>& sh = reinterpret_cast<T0Warp<F, D>*>(t0_raw)[threadIdx.x >> 5];
+    T0Warp<F, D, PK>& sh = reinterpret_cast<T0Warp<F, D, PK>*>(t0_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint32_t lane_bit = 1u << lane;
+    // a slot's key and count, and clearing a lane's slot, in either table form
+    auto fkey = [&](int c2, int j, int r) { return PK ? sh.fk[c2][j][r] >> 8 : sh.fk[c2][j][r]; };
+    auto fcnt = [&](int c2, int j, int r) { return PK ? sh.fk[c2][j][r] & 0xFFu : sh.fv[PK ? 0 : c2][PK ? 0 : j][r]; };
+    auto fclear = [&](int c2, int j) {
+        sh.fk[c2][j][lane] = EMPTY;
+        if constexpr (!PK) sh.fv[c2][j][lane] = 0;
+    };
+    auto dclear = [&](int j) {
+        sh.dk[j][lane] = EMPTY;
+        if constexpr (!PK) sh.dv[j][lane] = 0;
+    };
 #pragma unroll
     for (int j = 0; j < F; ++j) {
-        sh.fk[0][j][lane] = sh.fk[1][j][lane] = EMPTY;
-        sh.fv[0][j][lane] = sh.fv[1][j][lane] = 0;
+        fclear(0, j);
+        fclear(1, j);
     }
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-        sh.dk[j][lane] = EMPTY;
-        sh.dv[j][lane] = 0;
-    }
+    for (int j = 0; j < D; ++j) dclear(j);
     __syncwarp();
     int64_t s = -1;  // the lane's current row (-1: none)
     int c = 0;       // which frontier table is current (warp-uniform)
@@ -231,8 +271,8 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
                     const uint32_t kind = trace_kind(kinds, k2);
                     if (!kind) continue;
                     const bool junction = kind == 1;
-                    t0_add_rt(junction ? &sh.fk[c][0][0] : &sh.dk[0][0], junction ? &sh.fv[c][0][0] : &sh.dv[0][0],
-                              junction ? LF : LD, lane, tg[k2], 1);
+                    t0_add<PK>(junction ? &sh.fk[c][0][0] : &sh.dk[0][0],
+                               junction ? &sh.fv[PK ? 0 : c][0][0] : &sh.dv[0][0], junction ? LF : LD, lane, tg[k2], 1);
                 }
             }
         }
@@ -259,12 +299,12 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         __syncwarp();
         uint32_t bad = 0;
         uint32_t* const nk = &sh.fk[c ^ 1][0][0];
-        uint32_t* const nv = &sh.fv[c ^ 1][0][0];
+        uint32_t* const nv = &sh.fv[PK ? 0 : c ^ 1][0][0];
         for (unsigned i = lane; i < total; i += 32) {
             const int it = sh.items[i];
             const int j = it >> 5, r = it & 31;
-            const uint32_t key = sh.fk[c][j][r];
-            const uint32_t cnt = sh.fv[c][j][r];
+            const uint32_t key = fkey(c, j, r);
+            const uint32_t cnt = fcnt(c, j, r);
             const int64_t src = a.n1 + int64_t(key);
             const uint32_t kj = a.kinds[src];
             const uint4 q = trace_of(a, src);
@@ -275,8 +315,8 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
                 const uint32_t kind = trace_kind(kj, k);
                 if (!kind) continue;
                 const bool junction = kind == 1;
-                ok &= t0_add_rt(junction ? nk : &sh.dk[0][0], junction ? nv : &sh.dv[0][0], junction ? LF : LD, r,
-                                tq[k], cnt);
+                ok &= t0_add<PK>(junction ? nk : &sh.dk[0][0], junction ? nv : &sh.dv[0][0], junction ? LF : LD, r,
+                                 tq[k], cnt);
             }
             if (!ok) bad |= 1u << r;
         }
@@ -284,10 +324,7 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         __syncwarp();
         // the current tables are spent: clear this lane's and swap
 #pragma unroll
-        for (int j = 0; j < F; ++j) {
-            sh.fk[c][j][lane] = EMPTY;
-            sh.fv[c][j][lane] = 0;
-        }
+        for (int j = 0; j < F; ++j) fclear(c, j);
         c ^= 1;
         bool more = false;
 #pragma unroll
@@ -325,11 +362,12 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
             for (unsigned i = lane; i < nout; i += 32) {
                 const int it = sh.items[i];
                 const int j = it >> 5, r = it & 31;
-                const uint32_t key = sh.dk[j][r];
-                const uint32_t val = sh.dv[j][r];
+                const uint32_t slot = sh.dk[j][r];  // packed slots order by key too
+                const uint32_t key = PK ? slot >> 8 : slot;
+                const uint32_t val = PK ? slot & 0xFFu : sh.dv[PK ? 0 : j][r];
                 int rank = 0;
 #pragma unroll
-                for (int jj = 0; jj < D; ++jj) rank += sh.dk[jj][r] < key;  // EMPTY sorts last
+                for (int jj = 0; jj < D; ++jj) rank += sh.dk[jj][r] < slot;  // EMPTY sorts last
                 const u64 dst = sh.base[r] + u64(rank);
                 if (dst < a.out_cap) {
                     a.out_col[dst] = key;
@@ -352,15 +390,9 @@ __global__ void __launch_bounds__(T0_THREADS) rows_thread(PcArgs args, u64* next
         if (defer) a.deferred[dpos] = uint32_t(s);
         if (done || defer) {  // leave this lane's tables clean for its next row
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                sh.dk[j][lane] = EMPTY;
-                sh.dv[j][lane] = 0;
-            }
+            for (int j = 0; j < D; ++j) dclear(j);
 #pragma unroll
-            for (int j = 0; j < F; ++j) {
-                sh.fk[c][j][lane] = EMPTY;
-                sh.fv[c][j][lane] = 0;
-            }
+            for (int j = 0; j < F; ++j) fclear(c, j);
             s = -1;
         }
         __syncwarp();
@@ -736,11 +768,14 @@ msc_status run_path_count(Plan* p, cudaStream_t s) {
         return fail(p, MSC_ERR_CUDA, "internal: D* staging did not converge");
     }
     const int first_tier = std::max(0, std::min(2, int(p->opts.path_count_tier)));
-    // tier-0 and tier-0b grids: persistent, as many CTAs as fit
-    const size_t t0_smem = sizeof(T0Warp<T0_F, T0_D>) * T0_WARPS;
-    const size_t t0b_smem = sizeof(T0Warp<T0B_F, T0B_D>) * T0_WARPS;
-    auto* k0 = rows_thread<T0_F, T0_LF, T0_D, T0_LD>;
-    auto* k0b = rows_thread<T0B_F, T0B_LF, T0B_D, T0B_LD>;
+    // tier-0 and tier-0b grids: persistent, as many CTAs as fit.  Tier 0 packs key and count into
+    // one word when every junction and 2-saddle rank fits in 24 bits (the capacities bound them);
+    // a row whose counts pass 255 then goes on to tier 0b, which keeps 32-bit counts.
+    const bool pack = njcap < int64_t(0xFFFFFF) && n2cap < int64_t(0xFFFFFF);
+    const size_t t0_smem = (pack ? sizeof(T0Warp<T0_F, T0_D, true>) : sizeof(T0Warp<T0_F, T0_D, false>)) * T0_WARPS;
+    const size_t t0b_smem = sizeof(T0Warp<T0B_F, T0B_D, false>) * T0_WARPS;
+    auto* k0 = pack ? rows_thread<T0_F, T0_LF, T0_D, T0_LD, true> : rows_thread<T0_F, T0_LF, T0_D, T0_LD, false>;
+    auto* k0b = rows_thread<T0B_F, T0B_LF, T0B_D, T0B_LD, false>;
     if ((st = check_cuda(p, cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0_smem)),
                          "cudaFuncSetAttribute(rows_thread)")) ||
         (st = check_cuda(p, cudaFuncSetAttribute(k0b, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t0b_smem)),

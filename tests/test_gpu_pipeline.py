@@ -127,3 +127,20 @@ def test_dstar_methods_agree_on_long_path_networks():
     for method in (1, 2):
         rows, cols, cnt = got[method]
         assert np.array_equal(rows, er) and np.array_equal(cols, ec) and np.array_equal(cnt, en)
+
+
+def test_dstar_row_wise_counts_beyond_one_byte():
+    """Tier 0 keeps a count in 8 bits beside its key when the ranks fit in 24; a row whose counts
+    pass 255 must go on to the 32-bit tiers.  This blob field has rows with counts in the
+    thousands, and the row-wise products must still give the oracle's D*."""
+    m = msc()
+    f = fields.gaussian_blobs(n=48, n_blobs=3, sigma_range=(10, 20), seed=2)
+    e = oracle.compute_all(f, with_minor=False, with_dstar=True)
+    er, ec, en = e["dstar"]
+    assert en.max() > 255
+    plan = m.Plan(dims_of(f), path_count_tier=0, path_count_method=1)
+    for _ in range(3):  # synchronised, then replayed
+        m.msc_compute(plan, gpu_field(f))
+        rows, cols, cnt = csr_to_coo(*(to_np(x) for x in m.msc_saddle_arcs(plan)))
+        assert np.array_equal(rows, er) and np.array_equal(cols, ec) and np.array_equal(cnt, en)
+        assert m.msc_get_stats(plan)["max_path_count"] == int(en.max())
