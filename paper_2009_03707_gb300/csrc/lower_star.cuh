@@ -138,8 +138,34 @@ __host__ __device__ __forceinline__ int pop_min(uint32_t mask, const Star& st) {
     return best;
 }
 
-__host__ __device__ __forceinline__ bool one_free_facet(int q, uint32_t inL, uint32_t cls, const Tables* T) {
-    return MSC_POPC(T->facet[q] & inL & ~cls) == 1;
+// The least edge of a non-empty set of edges (positions with one non-zero component): an edge's
+// only vertex other than x is the one at its own position, so edges compare as their vertices do
+// (key, then position).
+__host__ __device__ __forceinline__ int pop_min_edge(uint32_t mask, const Star& st) {
+    int best = MSC_FFS(mask) - 1;
+    uint32_t kb = st.key(best);
+    mask &= mask - 1;
+    while (mask) {  // ascending positions: a later position wins only with a smaller key
+        const int p = MSC_FFS(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t kp = st.key(p);
+        if (kp < kb) {
+            kb = kp;
+            best = p;
+        }
+    }
+    return best;
+}
+
+// The positions whose cell has exactly one facet (through x) in `free`, for all 27 at once: a
+// cell's facet along an axis on which its offset is d = +-1 sits one step back towards 0 on that
+// axis (position p - d, p - 3d, p - 9d), so a shift of `free` by 1, 3 or 9 brings each facet's bit
+// to its cofacet's position; the result is "exactly one of the three".
+__host__ __device__ __forceinline__ uint32_t one_free_facet_mask(uint32_t free) {
+    const uint32_t fx = ((free << 1) & XP) | ((free >> 1) & XN);
+    const uint32_t fy = ((free << 3) & YP) | ((free >> 3) & YN);
+    const uint32_t fz = ((free << 9) & ZP) | ((free >> 9) & ZN);
+    return (fx ^ fy ^ fz) & ~((fx & fy) | (fz & (fx | fy)));
 }
 
 // Bit p set iff the vertex at position p is lower than x (value, then index; the index order
@@ -164,16 +190,13 @@ __host__ __device__ inline uint32_t lower_mask(const uint32_t* k) {
 template <class Emit>
 __host__ __device__ __forceinline__ bool pair_lower_star(const uint32_t inL, const Star& st, Emit&& emit) {
     const Tables* T = st.T;
-    const int delta = pop_min(inL & DIM1, st);
+    const int delta = pop_min_edge(inL & DIM1, st);
     uint32_t cls = (1u << CENTER) | (1u << delta);
     emit(CENTER, dir_code(CENTER, delta));
     emit(delta, dir_code(delta, CENTER));
     uint32_t pq0 = inL & DIM1 & ~(1u << delta);
-    uint32_t pq1 = 0;
-    for (uint32_t c = T->cofacet[delta] & inL & ~cls; c; c &= c - 1) {
-        int q = MSC_FFS(c) - 1;
-        if (one_free_facet(q, inL, cls, T)) pq1 |= 1u << q;
-    }
+    // cofacets (in L(x), unclassified) of a newly classified cell with one unclassified facet
+    uint32_t pq1 = T->cofacet[delta] & inL & ~cls & one_free_facet_mask(inL & ~cls);
     for (int guard = 0; guard < 64; ++guard) {
         while (pq1) {
             int a = pop_min(pq1, st);
@@ -189,20 +212,14 @@ __host__ __device__ __forceinline__ bool pair_lower_star(const uint32_t inL, con
             pq0 &= ~(1u << pf);
             emit(pf, dir_code(pf, a));
             emit(a, dir_code(a, pf));
-            for (uint32_t c = (T->cofacet[a] | T->cofacet[pf]) & inL & ~cls; c; c &= c - 1) {
-                int q = MSC_FFS(c) - 1;
-                if (one_free_facet(q, inL, cls, T)) pq1 |= 1u << q;
-            }
+            pq1 |= (T->cofacet[a] | T->cofacet[pf]) & inL & ~cls & one_free_facet_mask(inL & ~cls);
         }
         if (!pq0) return cls == inL;
         int c0 = pop_min(pq0, st);
         pq0 &= ~(1u << c0);
         if (cls & (1u << c0)) continue;
         cls |= 1u << c0;  // critical
-        for (uint32_t c = T->cofacet[c0] & inL & ~cls; c; c &= c - 1) {
-            int q = MSC_FFS(c) - 1;
-            if (one_free_facet(q, inL, cls, T)) pq1 |= 1u << q;
-        }
+        pq1 |= T->cofacet[c0] & inL & ~cls & one_free_facet_mask(inL & ~cls);
     }
     return false;
 }
