@@ -101,11 +101,12 @@ __device__ __forceinline__ uint32_t pull(uint32_t m, const uint32_t* __restrict_
     return m & p;
 }
 
-// Per vertex-row word (one warp, a lane per x): for each axis the four masks of 1-cells paired
-// with the quad on the - / + side along the first / second other axis, R_0 = the 1-saddles,
-// and for each quad orientation (by its even axis k) the bitmap of quads that are critical or
-// paired with a facet (the quads that give an out-edge to every other facet).  A warp takes
-// RI_WORDS consecutive row words at a time and issues their loads together.
+// Per vertex-row word: for each axis the four masks of 1-cells paired with the quad on the - / +
+// side along the first / second other axis, R_0 = the 1-saddles, and for each quad orientation (by
+// its even axis k) the bitmap of quads that are critical or paired with a facet (the quads that
+// give an out-edge to every other facet).  A warp takes 32 consecutive row words: it builds each
+// word's bitmaps with one ballot apiece (a lane per x), RI_WORDS words' loads issued together,
+// keeps word u's bitmaps in lane u, and then writes all 32 words' with one store per array.
 constexpr int RI_WORDS = 4;
 __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __restrict__ words,
                                                       uint4* __restrict__ masks, uint32_t* __restrict__ R0,
@@ -113,49 +114,62 @@ __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __
                                                       uint32_t* __restrict__ stamp) {
     const int lane = threadIdx.x & 31;
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
-    const int64_t step = ((int64_t(gridDim.x) * THREADS) >> 5) * RI_WORDS;
-    for (int64_t t0 = ((int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5) * RI_WORDS; t0 < nrw; t0 += step) {
-        uint32_t words_of[RI_WORDS];
+    const int64_t step = ((int64_t(gridDim.x) * THREADS) >> 5) * 32;
+    for (int64_t t0 = ((int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5) * 32; t0 < nrw; t0 += step) {
+        uint4 m[3];
+        uint32_t crit[3], qd[3];
+        for (int u0 = 0; u0 < 32 && t0 + u0 < nrw; u0 += RI_WORDS) {  // warp-uniform
+            uint32_t words_of[RI_WORDS];
 #pragma unroll
-        for (int u = 0; u < RI_WORDS; ++u) {
-            const Rows r(g, min(t0 + u, nrw - 1));
-            const int x = r.w * 32 + lane;
-            words_of[u] = x < g.nx ? words[vid32(g, x, r.y, r.z)] : 0x00FFFFFFu;  // all codes 7 off-grid
-        }
+            for (int v = 0; v < RI_WORDS; ++v) {
+                const Rows r(g, min(t0 + u0 + v, nrw - 1));
+                const int x = r.w * 32 + lane;
+                words_of[v] = x < g.nx ? words[vid32(g, x, r.y, r.z)] : 0x00FFFFFFu;  // all codes 7 off-grid
+            }
 #pragma unroll
-        for (int u = 0; u < RI_WORDS; ++u) {  // warp-uniform
-            if (t0 + u >= nrw) break;
-            const Rows r(g, t0 + u);
-            const uint32_t word = words_of[u];
+            for (int v = 0; v < RI_WORDS; ++v) {
+                const bool mine = lane == u0 + v;  // this lane keeps word u0 + v's bitmaps
+                const uint32_t word = words_of[v];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const uint32_t code = slot_code(word, 1 << a);
-                const int k = int(code - 1) >> 1;  // axis of the partner (code 1..6)
-                const bool quad = code >= 1 && code <= 6 && k != a;
-                const int sel = quad ? 2 * (k == other_axis(a, 0) ? 0 : 1) + int(!(code & 1u)) : -1;  // odd: - side
-                const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, sel == 0), m1 = __ballot_sync(0xFFFFFFFFu, sel == 1);
-                const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, sel == 2), m3 = __ballot_sync(0xFFFFFFFFu, sel == 3);
-                const uint32_t crit = __ballot_sync(0xFFFFFFFFu, code == 0);
-                if (lane == a) {
-                    const int e = a == 0 ? r.edge<0>(0, 0) : a == 1 ? r.edge<1>(0, 0) : r.edge<2>(0, 0);
-                    masks[e] = make_uint4(m0, m1, m2, m3);
-                    R0[e] = crit;
+                for (int a = 0; a < 3; ++a) {
+                    const uint32_t code = slot_code(word, 1 << a);
+                    const int k = int(code - 1) >> 1;  // axis of the partner (code 1..6)
+                    const bool quad = code >= 1 && code <= 6 && k != a;
+                    const int sel = quad ? 2 * (k == other_axis(a, 0) ? 0 : 1) + int(!(code & 1u)) : -1;  // odd: - side
+                    const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, sel == 0), m1 = __ballot_sync(0xFFFFFFFFu, sel == 1);
+                    const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, sel == 2), m3 = __ballot_sync(0xFFFFFFFFu, sel == 3);
+                    const uint32_t c0 = __ballot_sync(0xFFFFFFFFu, code == 0);
+                    if (mine) {
+                        m[a] = make_uint4(m0, m1, m2, m3);
+                        crit[a] = c0;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const uint32_t code = slot_code(word, 7 ^ (1 << k));
+                    const bool down = code == 0 || (code <= 6 && (int(code - 1) >> 1) != k);
+                    const uint32_t q = __ballot_sync(0xFFFFFFFFu, down);
+                    if (mine) qd[k] = q;
                 }
             }
+        }
+        const int64_t t = t0 + lane;
+        if (t < nrw) {
+            const Rows r(g, t);
+            const int e0 = r.edge<0>(0, 0), e1 = r.edge<1>(0, 0), e2 = r.edge<2>(0, 0);
+            masks[e0] = m[0];
+            masks[e1] = m[1];
+            masks[e2] = m[2];
+            R0[e0] = crit[0];
+            R0[e1] = crit[1];
+            R0[e2] = crit[2];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const uint32_t code = slot_code(word, 7 ^ (1 << k));
-                const bool down = code == 0 || (code <= 6 && (int(code - 1) >> 1) != k);
-                const uint32_t qd = __ballot_sync(0xFFFFFFFFu, down);
-                if (lane == 4 + k) qdown[k * r.qplane + r.qbase] = qd;
-            }
-            if (lane == 8 && r.w == 0) stamp[r.z * r.ny + r.y] = 1;  // every row is new at the start
-            if (lane == 3) {  // the unused slot of the 1-cell layout stays empty in both buffers
-                const int e = r.edge<2>(0, 0) + r.W;  // (c, b) = (1, 1)
-                masks[e] = make_uint4(0, 0, 0, 0);
-                R0[e] = 0;
-                R1[e] = 0;
-            }
+            for (int k = 0; k < 3; ++k) qdown[k * r.qplane + r.qbase] = qd[k];
+            if (r.w == 0) stamp[r.z * r.ny + r.y] = 1;  // every row is new at the start
+            // the unused slot of the 1-cell layout stays empty in both buffers
+            masks[e2 + r.W] = make_uint4(0, 0, 0, 0);
+            R0[e2 + r.W] = 0;
+            R1[e2 + r.W] = 0;
         }
     }
 }
@@ -399,7 +413,7 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     auto* stamp = static_cast<uint32_t*>(p->reach_stamp.ptr);
     uint32_t* A = static_cast<uint32_t*>(p->visited.ptr);
     uint32_t* B = static_cast<uint32_t*>(p->reach_tmp.ptr);
-    reach_init<<<grid_for(p, nrw * 32), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, A, B,
+    reach_init<<<grid_for(p, nrw), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, A, B,
                                                          static_cast<uint32_t*>(p->reach_qdown.ptr), stamp);
     reach_start<<<1, 1, 0, s>>>(p->dsum());
     launched(p, 2);
