@@ -104,21 +104,23 @@ __device__ __forceinline__ uint32_t pull(uint32_t m, const uint32_t* __restrict_
 // Per vertex-row word: for each axis the four masks of 1-cells paired with the quad on the - / +
 // side along the first / second other axis, R_0 = the 1-saddles, and for each quad orientation (by
 // its even axis k) the bitmap of quads that are critical or paired with a facet (the quads that
-// give an out-edge to every other facet).  A warp takes 32 consecutive row words: it builds each
-// word's bitmaps with one ballot apiece (a lane per x), RI_WORDS words' loads issued together,
-// keeps word u's bitmaps in lane u, and then writes all 32 words' with one store per array.
+// give an out-edge to every other facet).  A warp takes `chunk` (4..32, a multiple of RI_WORDS)
+// consecutive row words: it builds each word's bitmaps with one ballot apiece (a lane per x),
+// RI_WORDS words' loads issued together, keeps word u's bitmaps in lane u, and then writes all of
+// them with one store per array.  Large grids take chunks of 32 (the stores fully coalesced), small
+// ones smaller chunks so that enough warps share the work.
 constexpr int RI_WORDS = 4;
 __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __restrict__ words,
                                                       uint4* __restrict__ masks, uint32_t* __restrict__ R0,
                                                       uint32_t* __restrict__ R1, uint32_t* __restrict__ qdown,
-                                                      uint32_t* __restrict__ stamp) {
+                                                      uint32_t* __restrict__ stamp, int chunk) {
     const int lane = threadIdx.x & 31;
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
-    const int64_t step = ((int64_t(gridDim.x) * THREADS) >> 5) * 32;
-    for (int64_t t0 = ((int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5) * 32; t0 < nrw; t0 += step) {
+    const int64_t step = ((int64_t(gridDim.x) * THREADS) >> 5) * chunk;
+    for (int64_t t0 = ((int64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5) * chunk; t0 < nrw; t0 += step) {
         uint4 m[3];
         uint32_t crit[3], qd[3];
-        for (int u0 = 0; u0 < 32 && t0 + u0 < nrw; u0 += RI_WORDS) {  // warp-uniform
+        for (int u0 = 0; u0 < chunk && t0 + u0 < nrw; u0 += RI_WORDS) {  // warp-uniform
             uint32_t words_of[RI_WORDS];
 #pragma unroll
             for (int v = 0; v < RI_WORDS; ++v) {
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(THREADS) reach_init(Geom g, const uint32_t* __
             }
         }
         const int64_t t = t0 + lane;
-        if (t < nrw) {
+        if (lane < chunk && t < nrw) {
             const Rows r(g, t);
             const int e0 = r.edge<0>(0, 0), e1 = r.edge<1>(0, 0), e2 = r.edge<2>(0, 0);
             masks[e0] = m[0];
@@ -413,8 +415,12 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     auto* stamp = static_cast<uint32_t*>(p->reach_stamp.ptr);
     uint32_t* A = static_cast<uint32_t*>(p->visited.ptr);
     uint32_t* B = static_cast<uint32_t*>(p->reach_tmp.ptr);
-    reach_init<<<grid_for(p, nrw), THREADS, 0, s>>>(g, static_cast<const uint32_t*>(p->words.ptr), masks, A, B,
-                                                         static_cast<uint32_t*>(p->reach_qdown.ptr), stamp);
+    // row words per warp: 32 when every SM still gets 32 warps' worth, else fewer (at least 4)
+    int chunk = 32;
+    while (chunk > RI_WORDS && nrw < int64_t(chunk) * 32 * std::max(1, p->num_sms)) chunk >>= 1;
+    reach_init<<<grid_for(p, (nrw + chunk - 1) / chunk * 32), THREADS, 0, s>>>(
+        g, static_cast<const uint32_t*>(p->words.ptr), masks, A, B, static_cast<uint32_t*>(p->reach_qdown.ptr), stamp,
+        chunk);
     reach_start<<<1, 1, 0, s>>>(p->dsum());
     launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
