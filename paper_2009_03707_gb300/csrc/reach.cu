@@ -192,8 +192,8 @@ __device__ __forceinline__ bool sweep_word(const Rows& r, const uint4* __restric
 }
 
 // One level: Rout = Rin | cells whose partner quad has another facet in Rin.  A thread takes one
-// vertex-row word for all three axes (one neighbourhood check, three independent chains of
-// loads).  Sets *changed if any word grew.
+// vertex-row word at a time for all three axes (one neighbourhood check, three independent chains
+// of loads).  Sets *changed if any word grew.
 // Rows (y, z) are stamped with 1 + the last sweep that changed them (1: the start).  A cell's
 // predecessors lie within one step in y and z, so a row none of whose 3 x 3 neighbour rows changed
 // in the previous sweep cannot change now; it is skipped, Rout included: that buffer already
@@ -204,10 +204,11 @@ __global__ void __launch_bounds__(THREADS, 4) reach_sweep(Geom g, const uint4* _
                                                        uint32_t* __restrict__ stamp, const Summary* __restrict__ sum,
                                                        int parity, uint32_t* __restrict__ changed) {
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
-    const int64_t t = int64_t(blockIdx.x) * THREADS + threadIdx.x;
     const uint32_t k = 2u * uint32_t(sum->sweep_iters) + 1u + uint32_t(parity);  // this sweep
     bool grew = false;
-    if (t < nrw) {
+    // grid-stride over the row words (one resident wave of CTAs): a sweep in which few rows are
+    // near a front then costs no CTA launches for the rest
+    for (int64_t t = int64_t(blockIdx.x) * THREADS + threadIdx.x; t < nrw; t += int64_t(gridDim.x) * THREADS) {
         const Rows r(g, t);
         uint32_t recent = 0;
         for (int dz = -1; dz <= 1; ++dz)
@@ -219,8 +220,10 @@ __global__ void __launch_bounds__(THREADS, 4) reach_sweep(Geom g, const uint4* _
             const bool g0 = sweep_word<0>(r, masks, Rin, Rout);
             const bool g1 = sweep_word<1>(r, masks, Rin, Rout);
             const bool g2 = sweep_word<2>(r, masks, Rin, Rout);
-            grew = g0 || g1 || g2;
-            if (grew) stamp[int64_t(r.z) * g.ny + r.y] = k + 1;
+            if (g0 || g1 || g2) {
+                stamp[int64_t(r.z) * g.ny + r.y] = k + 1;
+                grew = true;
+            }
         }
     }
     if (__syncthreads_or(grew) && threadIdx.x == 0) *changed = 1u;
@@ -424,7 +427,9 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     reach_start<<<1, 1, 0, s>>>(p->dsum());
     launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
-    SweepCtx ctx{dim3(unsigned((nrw + THREADS - 1) / THREADS), 1), masks, A, B, stamp};
+    const int64_t tiles = (nrw + THREADS - 1) / THREADS;
+    SweepCtx ctx{dim3(unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, int64_t(std::max(1, p->num_sms)) * 4))), 1),
+                 masks, A, B, stamp};
     return run_loop(p, s, 1, 3, sweep_body, &ctx);
 }
 
