@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(THREADS, 4) reach_sweep(Geom g, const uint4* _
     const int64_t nrw = int64_t(g.nz) * g.ny * g.W;
     const uint32_t k = 2u * uint32_t(sum->sweep_iters) + 1u + uint32_t(parity);  // this sweep
     bool grew = false;
-    // grid-stride over the row words (one resident wave of CTAs): a sweep in which few rows are
-    // near a front then costs no CTA launches for the rest
+    // grid-stride over the row words (a few tiles of THREADS words per CTA): a sweep in which few
+    // rows are near a front then costs fewer CTA launches for the rest
     for (int64_t t = int64_t(blockIdx.x) * THREADS + threadIdx.x; t < nrw; t += int64_t(gridDim.x) * THREADS) {
         const Rows r(g, t);
         uint32_t recent = 0;
@@ -427,9 +427,11 @@ msc_status run_reachability(Plan* p, cudaStream_t s) {
     reach_start<<<1, 1, 0, s>>>(p->dsum());
     launched(p, 2);
     if ((st = check_cuda(p, cudaGetLastError(), "reach_init launch"))) return st;
+    // sweep grid: at most 4 tiles per CTA and at least one resident wave (4 CTAs per SM).  Fewer,
+    // longer CTAs would cost little alone but leave long tails when other passes share the device.
     const int64_t tiles = (nrw + THREADS - 1) / THREADS;
-    SweepCtx ctx{dim3(unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, int64_t(std::max(1, p->num_sms)) * 4))), 1),
-                 masks, A, B, stamp};
+    const int64_t sweep_ctas = std::min<int64_t>(tiles, std::max<int64_t>(int64_t(std::max(1, p->num_sms)) * 4, (tiles + 3) / 4));
+    SweepCtx ctx{dim3(unsigned(std::max<int64_t>(1, sweep_ctas)), 1), masks, A, B, stamp};
     return run_loop(p, s, 1, 3, sweep_body, &ctx);
 }
 
