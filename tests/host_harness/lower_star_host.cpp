@@ -49,3 +49,23 @@ extern "C" int host_words(const int64_t* d, const float* f, uint32_t* words) {
                 }
     return bad;
 }
+
+// The bit-parallel "exactly one unclassified facet" test of the core against its definition (a
+// popcount of the cell's facet mask) for every cell position and every one of `n` free-cell sets
+// drawn from a fixed 64-bit LCG; returns the number of disagreements.
+extern "C" int host_one_free_facet_mismatches(int n) {
+    Tables T;
+    for (int p = 0; p < 27; p++) fill_tables(T, p, 3, 9);
+    uint64_t s = 0x9E3779B97F4A7C15ull;
+    int bad = 0;
+    for (int i = 0; i < n; i++) {
+        s = s * 6364136223846793005ull + 1442695040888963407ull;
+        const uint32_t free = uint32_t(s >> 37) & ALL;
+        const uint32_t m = one_free_facet_mask(free);
+        for (int q = 0; q < 27; q++) {
+            const bool want = __builtin_popcount(T.facet[q] & free) == 1;
+            if (bool((m >> q) & 1u) != want) bad++;
+        }
+    }
+    return bad;
+}

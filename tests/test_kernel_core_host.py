@@ -46,3 +46,11 @@ def test_kernel_core_matches_oracle(host_lib, f):
     bad = host_lib.host_words(d.ctypes.data, f.ctypes.data, words.ctypes.data)
     assert bad == 0
     assert np.array_equal(words, oracle.pack(d, oracle.gradient(f)))
+
+
+def test_one_free_facet_mask_matches_its_definition(host_lib):
+    """The core finds the cells with exactly one unclassified facet for all 27 positions at once
+    (shifts by 1, 3 and 9); it must agree with counting each cell's facets one by one."""
+    host_lib.host_one_free_facet_mismatches.argtypes = [ctypes.c_int]
+    host_lib.host_one_free_facet_mismatches.restype = ctypes.c_int
+    assert host_lib.host_one_free_facet_mismatches(200000) == 0
