@@ -69,3 +69,25 @@ extern "C" int host_one_free_facet_mismatches(int n) {
     }
     return bad;
 }
+
+// The least edge by vertex keys against the general least-cell rule, on random keys (with many
+// ties) and random non-empty sets of edges; returns the number of disagreements.
+extern "C" int host_edge_min_mismatches(int n) {
+    Tables T;
+    for (int p = 0; p < 27; p++) fill_tables(T, p, 3, 9);
+    uint64_t s = 0x243F6A8885A308D3ull;
+    int bad = 0;
+    for (int i = 0; i < n; i++) {
+        uint32_t k[27];
+        for (int p = 0; p < 27; p++) {
+            s = s * 6364136223846793005ull + 1442695040888963407ull;
+            k[p] = (i & 1) ? uint32_t(s >> 61) : uint32_t(s >> 32);  // odd rounds: keys 0..7
+        }
+        s = s * 6364136223846793005ull + 1442695040888963407ull;
+        const uint32_t edges = uint32_t(s >> 40) & DIM1;
+        if (!edges) continue;
+        const Star st{k + CENTER, &T};
+        if (pop_min_edge(edges, st) != pop_min(edges, st)) bad++;
+    }
+    return bad;
+}

@@ -54,3 +54,11 @@ def test_one_free_facet_mask_matches_its_definition(host_lib):
     host_lib.host_one_free_facet_mismatches.argtypes = [ctypes.c_int]
     host_lib.host_one_free_facet_mismatches.restype = ctypes.c_int
     assert host_lib.host_one_free_facet_mismatches(200000) == 0
+
+
+def test_least_edge_by_keys_matches_the_cell_order(host_lib):
+    """The core picks x's lowest edge by comparing the edges' vertex keys directly; that must be
+    the least edge under the general cell order (vertex lists sorted downwards, ties by index)."""
+    host_lib.host_edge_min_mismatches.argtypes = [ctypes.c_int]
+    host_lib.host_edge_min_mismatches.restype = ctypes.c_int
+    assert host_lib.host_edge_min_mismatches(200000) == 0
