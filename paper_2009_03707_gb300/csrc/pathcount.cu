@@ -95,12 +95,14 @@ __device__ __forceinline__ uint4 trace_of(const PcArgs& a, int64_t src) {
 // junction's trace and adds each traced path to the owning row's next frontier or D* table
 // with shared-memory atomics.  So a lane's work does not depend on its own row's size, and
 // every per-row loop is a fixed, unrolled one.  A row whose table fills up, or whose counts
-// outgrow 32 bits, is deferred intact to the uint64 warp tier.
+// outgrow 32 bits, is deferred intact to the next tier (tier 0b, the same kernel with larger
+// tables, then the uint64 warp tier).
 //
 // Packed tables (PK): a slot is one word, key << 8 | count, for keys below 2^24 - 1 (then a
 // packed slot never equals EMPTY) and counts up to 255.  That halves the tables, so more warps fit
-// on an SM.  An add whose count would carry into the key defers the row (its corrupted slot is
-// never expanded: the row's tables are cleared at the end of that round).
+// on an SM.  An add whose count would carry into the key defers the row to tier 0b, which keeps
+// 32-bit counts (the corrupted slot is never expanded: the row's tables are cleared at the end of
+// that round).  The count arrays shrink to one unused slot.
 template <int F, int D, bool PK>
 struct T0Warp {
     uint32_t fk[2][F][32];
