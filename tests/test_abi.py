@@ -71,3 +71,14 @@ def test_plan_rejects_unknown_options_before_touching_the_device():
         out = ctypes.c_void_p(1)
         assert lib.msc_plan(dims, ctypes.byref(opts), ctypes.byref(out)) == 1
         assert not out.value
+
+
+def test_binding_flag_values_match_the_header():
+    """Every MSC_FLAG_* the header defines has the same value in the binding."""
+    from paper_2009_03707_gb300 import msc
+
+    text = open(os.path.join(ROOT, "include", "msc.h")).read()
+    flags = dict(re.findall(r"^#define\s+(MSC_FLAG_\w+)\s+(\d+)", text, re.M))
+    assert {"MSC_FLAG_NO_GRAPH", "MSC_FLAG_SERIAL_PASS"} <= set(flags)
+    for name, value in flags.items():
+        assert getattr(msc, name) == int(value), name
