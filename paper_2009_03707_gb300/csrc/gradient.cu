@@ -6,18 +6,22 @@
 // (the lower star L(x)) are paired among themselves, so every vertex is independent work.
 //
 // GB300 design (not the paper's texture-object kernel):
-//  * One CTA owns a 32 x 8 x 8 tile of vertices and computes exactly their lower stars.  The
-//    field tile plus a one-vertex halo is staged in shared memory as order-preserving uint32 keys.
+//  * One CTA owns a 32 x TY x TZ tile of vertices (a tuned choice) and computes exactly their lower
+//    stars.  The field tile plus a one-vertex halo is staged in shared memory as order-preserving
+//    uint32 keys.
 //  * A cell's 3-bit code lives in the word of its lowest corner vertex (its owner) but is decided
 //    by its highest vertex.  Codes whose owner is in the tile are OR-ed into shared words; codes
 //    whose owner is in the neighbouring tile on the - side go straight to global memory with
-//    atomicOr.  So the tile's words on its + faces are finished with atomicOr too, into words
-//    zeroed beforehand, and every other word is a plain coalesced store.
+//    atomicOr.  So the tile's words on its + faces are finished with atomicOr too, into words a
+//    small kernel zeroes beforehand (about a quarter of all words, mostly whole rows and planes),
+//    and every other word is a plain coalesced store.
 //  * A lower star is handled as 27-bit masks over the offsets d in {-1,0,1}^3 (lower_star.cuh),
 //    with the per-position masks tabulated in shared memory and the vertex keys read straight
-//    from the staged tile.  Stars differ widely in size (1..27 cells) and a warp runs as long as
-//    its largest, so the CTA first sizes every star and counting-sorts its vertices by size;
-//    warps then claim 32 consecutive stars at a time, largest first.
+//    from the staged tile.  Large stars rank their vertices once with a sorting network and keep
+//    their cells' integer keys in a per-thread column of shared memory.  Stars differ widely in
+//    size (1..27 cells) and a warp runs as long as its largest, so the CTA first sizes every star
+//    and counting-sorts its vertices by size; warps then claim 32 consecutive stars at a time,
+//    largest first.
 //  * A second, bandwidth-bound kernel turns the finished words into per-slot critical bitmaps:
 //    one warp ballot per slot gives 32 vertices' bits -- the input of the ordered compaction.
 #include <map>
@@ -55,6 +59,7 @@ struct Shared {
     uint32_t words[TZ][TY][TX];  // packed codes of the owned tile
     uint32_t inl[NOWN];          // lower-star mask of every owned vertex (0: off-grid)
     uint16_t order[NOWN];        // non-minimal vertices, largest stars first
+    uint32_t ckey[27][THREADS];  // per-thread cell keys of the star in hand (ranked path)
     int bin[28];                 // counting-sort bins by star size
     int next;                    // next unclaimed entry of `order`
     star::Tables tab;            // per-position masks; key offsets within fkey
@@ -64,7 +69,7 @@ struct Shared {
 };
 
 template <int TY, int TZ, int THREADS>
-__global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS)) gradient_kernel(Geom g, const float* __restrict__ field,
+__global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kernel(Geom g, const float* __restrict__ field,
                                                            uint32_t* __restrict__ words_out,
                                                            uint32_t* __restrict__ status) {
     using S = Shared<TY, TZ, THREADS>;
@@ -83,7 +88,9 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS
         const uint32_t slot = (pdx(t) != 0) | ((pdy(t) != 0) << 1) | ((pdz(t) != 0) << 2);
         sh.emit_info[t] = slot | (xn << 3) | (yn << 4) | (zn << 5) | ((xn + yn * TX + zn * TX * TY) << 8);
     }
+    // stage the field tile with its one-vertex halo as order keys
     bool saw_nan = false;
+    const int lane = t & 31, warp = t >> 5;
     for (int i = t; i < FX * FY * FZ; i += THREADS) {
         const int fx = i % FX, fy = (i / FX) % FY, fz = i / (FX * FY);
         const int gx = x0 - 1 + fx, gy = y0 - 1 + fy, gz = z0 - 1 + fz;
@@ -98,7 +105,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS
     if (saw_nan) atomicOr(status, ST_NAN);
     __syncthreads();
 
-    // size every star (cheap mask arithmetic) and counting-sort the non-minimal ones
+    // size every star (cheap mask arithmetic) and counting-sort the non-minimal ones (a ballot-based
+    // warp histogram instead of the per-vertex atomics measured slower)
     for (int i = t; i < NOWN; i += THREADS) {
         const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
         uint32_t inL = 0;
@@ -133,7 +141,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS
     // warps claim 32 consecutive stars at a time, largest first, so the CTA's stars are
     // spread over its warps by longest-processing-time order
     bool ok = true;
-    const int lane = t & 31;
     uint32_t* const wtile = &sh.words[0][0][0];
     for (;;) {
         int base = 0;
@@ -158,7 +165,9 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS
                 atomicOr(words_out + g.vid(gx - xn, gy - yn, gz - zn), bits);
             }
         };
-        ok &= star::pair_lower_star(inL, st, emit);
+        // the scratch word of position p of this thread, in its own bank column
+        auto ckey = [&](int p) -> uint32_t& { return sh.ckey[p][t]; };
+        ok &= star::pair_lower_star<FX, FX * FY>(inL, st, ckey, emit);
         }
     }
     if (!ok) atomicOr(status, ST_INTERNAL);
@@ -166,19 +175,18 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 1024 ? 1 : 1536 / THREADS
 
     // epilogue: far-boundary codes, then plain stores -- or atomicOr on the tile's + faces,
     // whose words also receive codes from the neighbouring tiles
-    const int warp = t >> 5;
+    // (code 7 in the slots with a = 1, b = 1 or c = 1 of a vertex on the last x, y or z layer)
+    constexpr uint32_t OUT_X = 0xE38E38u, OUT_Y = 0xFC0FC0u, OUT_Z = 0xFFF000u;
     const int gx = x0 + lane;
     for (int r = warp; r < TY * TZ; r += THREADS / 32) {
         const int ly = r % TY, lz = r / TY;
         const int gy = y0 + ly, gz = z0 + lz;
         if (gy >= g.ny || gz >= g.nz || gx >= g.nx) continue;
-        uint32_t w = sh.words[lz][ly][lane];
-        for (int s = 0; s < 8; ++s) {
-            const bool out = ((s & 1) && gx == g.nx - 1) || ((s & 2) && gy == g.ny - 1) || ((s & 4) && gz == g.nz - 1);
-            if (out) w |= 7u << (3 * s);
-        }
-        if (lane == TX - 1 || ly == TY - 1 || lz == TZ - 1) atomicOr(words_out + g.vid(gx, gy, gz), w);
-        else words_out[g.vid(gx, gy, gz)] = w;
+        const uint32_t w = sh.words[lz][ly][lane] | (gx == g.nx - 1 ? OUT_X : 0u) | (gy == g.ny - 1 ? OUT_Y : 0u) |
+                           (gz == g.nz - 1 ? OUT_Z : 0u);
+        uint32_t* dst = words_out + g.vid(gx, gy, gz);
+        if (lane == TX - 1 || ly == TY - 1 || lz == TZ - 1) atomicOr(dst, w);
+        else *dst = w;
     }
 }
 
@@ -217,12 +225,29 @@ __global__ void __launch_bounds__(256) critical_bitmaps(Geom g, const uint32_t* 
     }
 }
 
+// Zeroes the words that the lower-star kernel finishes with atomicOr: those on the + faces of its
+// tiles (x = 31 mod 32, y = TY-1 mod TY, z = TZ-1 mod TZ), which receive codes from the next tiles'
+// stars.  Every other word gets one plain store, so it needs no zeroing.  A warp per (y, z) row:
+// a row on a y or z face is cleared whole, any other row only at x = 31 mod 32.
+__global__ void __launch_bounds__(256) zero_face_words(Geom g, uint32_t* __restrict__ words, int ty, int tz) {
+    const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= int64_t(g.ny) * g.nz) return;  // warp-uniform
+    const int y = int(row % g.ny), z = int(row / g.ny);
+    uint32_t* w = words + row * g.nx;
+    if (y % ty == ty - 1 || z % tz == tz - 1) {
+        for (int x = lane; x < g.nx; x += 32) w[x] = 0;
+    } else {
+        for (int x = 32 * lane + 31; x < g.nx; x += 32 * 32) w[x] = 0;
+    }
+}
+
 // Tile variants the autotuner chooses from: (TY, TZ, threads).
 struct Variant {
     int ty, tz, threads;
 };
-constexpr Variant VARIANTS[] = {{8, 8, 512},   {8, 4, 256},   {4, 8, 256},    {8, 16, 512}, {16, 8, 512},
-                                {16, 8, 1024}, {16, 16, 512}, {16, 16, 1024}, {32, 8, 1024}};
+constexpr Variant VARIANTS[] = {{8, 8, 512},   {8, 4, 256},  {4, 8, 256},  {8, 16, 512}, {16, 8, 512},
+                                {16, 8, 1024}, {16, 16, 512}, {8, 8, 256}, {16, 8, 256}};
 constexpr int N_VARIANTS = int(sizeof(VARIANTS) / sizeof(VARIANTS[0]));
 
 template <int TY, int TZ, int THREADS>
@@ -237,10 +262,17 @@ cudaError_t launch_tile(const Geom& g, const float* d_field, uint32_t* words, ui
     return cudaGetLastError();
 }
 
-// The words of a whole grid with tile variant v: zero them, then the lower-star kernel.
+cudaError_t launch_zero_faces(int v, const Geom& g, uint32_t* words, cudaStream_t s) {
+    if (v < 0 || v >= N_VARIANTS) v = 0;
+    const int64_t rows = int64_t(g.ny) * g.nz;
+    zero_face_words<<<unsigned((rows * 32 + 255) / 256), 256, 0, s>>>(g, words, VARIANTS[v].ty, VARIANTS[v].tz);
+    return cudaGetLastError();
+}
+
+// The words of a whole grid with tile variant v: zero the face words, then the lower-star kernel.
 cudaError_t launch_words(int v, const Geom& g, const float* d_field, uint32_t* words, uint32_t* status,
                          cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * size_t(g.nverts), s);
+    const cudaError_t e = launch_zero_faces(v, g, words, s);
     if (e != cudaSuccess) return e;
     switch (v) {
         case 1: return launch_tile<8, 4, 256>(g, d_field, words, status, s);
@@ -249,15 +281,15 @@ cudaError_t launch_words(int v, const Geom& g, const float* d_field, uint32_t* w
         case 4: return launch_tile<16, 8, 512>(g, d_field, words, status, s);
         case 5: return launch_tile<16, 8, 1024>(g, d_field, words, status, s);
         case 6: return launch_tile<16, 16, 512>(g, d_field, words, status, s);
-        case 7: return launch_tile<16, 16, 1024>(g, d_field, words, status, s);
-        case 8: return launch_tile<32, 8, 1024>(g, d_field, words, status, s);
+        case 7: return launch_tile<8, 8, 256>(g, d_field, words, status, s);
+        case 8: return launch_tile<16, 8, 256>(g, d_field, words, status, s);
         default: return launch_tile<8, 8, 512>(g, d_field, words, status, s);
     }
 }
 
 cudaError_t launch_gradient(int v, const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
                             uint32_t* status, cudaStream_t s, const Plan* p = nullptr) {
-    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * size_t(g.nverts), s);
+    cudaError_t e = launch_zero_faces(v, g, words, s);
     if (e != cudaSuccess) return e;
     if (p) record_event(p, p->gev0, s);  // the lower-star kernel alone is timed
     switch (v) {
@@ -267,8 +299,8 @@ cudaError_t launch_gradient(int v, const Geom& g, const float* d_field, uint32_t
         case 4: e = launch_tile<16, 8, 512>(g, d_field, words, status, s); break;
         case 5: e = launch_tile<16, 8, 1024>(g, d_field, words, status, s); break;
         case 6: e = launch_tile<16, 16, 512>(g, d_field, words, status, s); break;
-        case 7: e = launch_tile<16, 16, 1024>(g, d_field, words, status, s); break;
-        case 8: e = launch_tile<32, 8, 1024>(g, d_field, words, status, s); break;
+        case 7: e = launch_tile<8, 8, 256>(g, d_field, words, status, s); break;
+        case 8: e = launch_tile<16, 8, 256>(g, d_field, words, status, s); break;
         default: e = launch_tile<8, 8, 512>(g, d_field, words, status, s); break;
     }
     if (p) record_event(p, p->gev1, s);
@@ -339,7 +371,7 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
     else if (p->grad_variant < 0 && !p->capturing) p->grad_variant = tune_variant(p, d_field, s);
     const int v = std::max(0, p->grad_variant);
     p->stats.gradient_tile = VARIANTS[v].ty | (VARIANTS[v].tz << 8) | (int64_t(VARIANTS[v].threads) << 16);
-    launched(p, 2);
+    launched(p, 3);
     return check_cuda(p,
                       launch_gradient(v, g, d_field, static_cast<uint32_t*>(p->words.ptr),
                                       static_cast<uint32_t*>(p->crit_bits.ptr), p->status_word(), s, p),

@@ -10,13 +10,30 @@
 // (pairing each popped cell with its free facet), then the least cell of "zero" becomes
 // critical; a popped cell that is already classified is skipped.
 //
+// The queues are not kept.  A cell enters "one" when one of its facets is classified and it
+// is left with exactly one unclassified facet, and the number of unclassified facets only
+// falls; a popped cell whose count has reached zero moves to "zero"; and edges sit in "zero"
+// from the start.  So whenever "one" is drained, "zero" holds exactly the unclassified cells
+// with no unclassified facet, and the live part of "one" is exactly the unclassified cells with
+// one.  The procedure is therefore: pair the least unclassified cell that has exactly one
+// unclassified facet with that facet; if there is none, declare the least unclassified cell
+// with no unclassified facet critical; repeat.  The counts are kept as two bit planes (a 2-bit
+// counter per position), so each step is a few mask operations and one "least cell of a set".
+//
 // Everything is a 27-bit mask: membership in L(x) (a cell is in L(x) iff all its vertices
 // other than x are lower, i.e. every sub-offset is lower), facets through x (clear one
 // non-zero component), cofacets (set one zero component), a cell's vertex set (its
-// sub-offsets), the classified set and both queues.  Two cells are compared by their vertex
-// lists sorted downwards, lexicographically: the cell whose vertex set holds the largest vertex
-// of the symmetric difference is the larger one (a proper prefix is therefore smaller), so a
-// comparison costs one key lookup per vertex in the symmetric difference and no ranking.
+// sub-offsets) and the unclassified set.  Two cells are compared by their vertex lists sorted
+// downwards, lexicographically.  Two ways of finding the least cell of a set give the same
+// answer:
+//  * small stars compare two cells directly: the cell whose vertex set holds the largest vertex
+//    of the symmetric difference is the larger one (a proper prefix is therefore smaller);
+//  * large stars first rank the vertices of L(x) once (a sorting network over the packed
+//    keys), give every cell the integer key "OR of 1 << rank over its vertices" -- comparing
+//    those integers is exactly the lexicographic order above -- and take minima of integers.
+// The vertices of L(x) other than x correspond one to one to its cells other than x (the cell
+// at position p is in L(x) iff the vertex at p and every sub-offset of p are lower), so a
+// star with m cells besides x has m vertices to rank.
 #pragma once
 
 #include <stdint.h>
@@ -24,9 +41,11 @@
 #ifdef __CUDA_ARCH__
 #define MSC_FFS(x) __ffs(x)
 #define MSC_POPC(x) __popc(x)
+#define MSC_UMIN(a, b) min(a, b)
 #else
 #define MSC_FFS(x) __builtin_ffs(int(x))
 #define MSC_POPC(x) __builtin_popcount(x)
+#define MSC_UMIN(a, b) ((a) < (b) ? (a) : (b))
 #endif
 
 namespace msc {
@@ -127,6 +146,7 @@ __host__ __device__ __forceinline__ bool cell_less(int a, int b, const Star& st)
     return (vb >> w) & 1u;
 }
 
+// The least cell of a non-empty set, by pairwise comparisons.
 __host__ __device__ __forceinline__ int pop_min(uint32_t mask, const Star& st) {
     int best = MSC_FFS(mask) - 1;
     mask &= mask - 1;
@@ -182,46 +202,174 @@ __host__ __device__ inline uint32_t lower_mask(const uint32_t* k) {
     return lower;
 }
 
-// Pairs the cells of L(x) given inL (the lower-star mask, with more than x in it); st.key(p)
-// must be valid for every p in inL.  Vertices with equal keys are ordered by position, which
-// is their index order.  emit(p, code) is called for every non-critical cell with its
-// direction code.  Returns false if the procedure did not classify every cell (an internal
-// error).
-template <class Emit>
-__host__ __device__ __forceinline__ bool pair_lower_star(const uint32_t inL, const Star& st, Emit&& emit) {
-    const Tables* T = st.T;
-    const int delta = pop_min_edge(inL & DIM1, st);
-    uint32_t cls = (1u << CENTER) | (1u << delta);
+// Number of unclassified facets (through x) of every position, as a 2-bit counter in two bit
+// planes: a cube of L(x) starts at 3, a quad at 2, an edge at 0 (its one facet, x, is classified
+// first).  dec() takes one off every position of a mask; counts never go below zero because each
+// facet is classified once.
+struct FacetCount {
+    uint32_t c0, c1;
+    __host__ __device__ __forceinline__ void dec(uint32_t d) {
+        c1 ^= d & ~c0;
+        c0 ^= d;
+    }
+    __host__ __device__ __forceinline__ uint32_t one(uint32_t u) const { return u & c0 & ~c1; }
+    __host__ __device__ __forceinline__ uint32_t zero(uint32_t u) const { return u & ~(c0 | c1); }
+};
+
+// Classifies the cells of L(x) (inL, with more than x in it) once x's lowest edge delta is known.
+// least(S) returns the least cell of a non-empty set S; emit(p, code) is called for every
+// non-critical cell with its direction code.  Returns false if a cell was left unclassified (an
+// internal error).
+template <class Least, class Emit>
+__host__ __device__ __forceinline__ bool classify_star(const uint32_t inL, const int delta, const Tables* T,
+                                                       Least&& least, Emit&& emit) {
     emit(CENTER, dir_code(CENTER, delta));
     emit(delta, dir_code(delta, CENTER));
-    uint32_t pq0 = inL & DIM1 & ~(1u << delta);
-    // cofacets (in L(x), unclassified) of a newly classified cell with one unclassified facet
-    uint32_t pq1 = T->cofacet[delta] & inL & ~cls & one_free_facet_mask(inL & ~cls);
-    for (int guard = 0; guard < 64; ++guard) {
-        while (pq1) {
-            int a = pop_min(pq1, st);
-            pq1 &= ~(1u << a);
-            if (cls & (1u << a)) continue;
-            uint32_t uf = T->facet[a] & inL & ~cls;
-            if (uf == 0) {
-                pq0 |= 1u << a;
-                continue;
-            }
-            int pf = MSC_FFS(uf) - 1;  // the only unclassified facet
-            cls |= (1u << pf) | (1u << a);
-            pq0 &= ~(1u << pf);
-            emit(pf, dir_code(pf, a));
-            emit(a, dir_code(a, pf));
-            pq1 |= (T->cofacet[a] | T->cofacet[pf]) & inL & ~cls & one_free_facet_mask(inL & ~cls);
+    uint32_t U = inL & ~((1u << CENTER) | (1u << delta));
+    FacetCount n{inL & DIM3, inL & (DIM2 | DIM3)};
+    n.dec(T->cofacet[delta] & U);
+    for (int guard = 0; guard < 27 && U; ++guard) {
+        const uint32_t one = n.one(U);
+        if (one) {
+            const int a = least(one);
+            const int f = MSC_FFS(T->facet[a] & U) - 1;  // the only unclassified facet
+            emit(f, dir_code(f, a));
+            emit(a, dir_code(a, f));
+            U &= ~((1u << a) | (1u << f));
+            // a cell with both a and f as facets would have two dimensions: the sets are disjoint
+            n.dec((T->cofacet[a] | T->cofacet[f]) & U);
+        } else {
+            const uint32_t zero = n.zero(U);
+            if (!zero) return false;
+            const int c = least(zero);  // critical: its code stays 0
+            U &= ~(1u << c);
+            n.dec(T->cofacet[c] & U);
         }
-        if (!pq0) return cls == inL;
-        int c0 = pop_min(pq0, st);
-        pq0 &= ~(1u << c0);
-        if (cls & (1u << c0)) continue;
-        cls |= 1u << c0;  // critical
-        pq1 |= T->cofacet[c0] & inL & ~cls & one_free_facet_mask(inL & ~cls);
     }
-    return false;
+    return U == 0;
+}
+
+// ---- the ranked path for large stars -------------------------------------------------------
+
+// Batcher's odd-even merge sort for n inputs (Knuth, TAOCP vol. 3, 5.3.4), enumerated at compile
+// time: oem_comparator(c) is the c-th comparator (lower index * 256 + upper index), or -1 past
+// the last one.  A comparator leaves the smaller value at its lower index.
+template <int N>
+__host__ __device__ constexpr int oem_comparator(int c) {
+    int n = 0;
+    for (int p = 1; p < N; p <<= 1)
+        for (int k = p; k >= 1; k >>= 1)
+            for (int j = k % p; j + k < N; j += 2 * k)
+                for (int i = 0; i < k && i < N - j - k; ++i)
+                    if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                        if (n == c) return (i + j) * 256 + (i + j + k);
+                        ++n;
+                    }
+    return -1;
+}
+
+template <int C>
+__host__ __device__ __forceinline__ void sort26_from(uint32_t* v) {
+    constexpr int ab = oem_comparator<26>(C);
+    if constexpr (ab >= 0) {
+        constexpr int A = ab >> 8, B = ab & 255;
+        const uint32_t x = v[A], y = v[B];
+        v[A] = MSC_UMIN(x, y);
+        v[B] = x ^ y ^ MSC_UMIN(x, y);
+        sort26_from<C + 1>(v);
+    }
+}
+
+// The 26 positions other than x, in index order: i -> position.
+__host__ __device__ constexpr int star_pos(int i) { return i < CENTER ? i : i + 1; }
+
+// Integer keys of the cells of L(x) (inL, at least two cells besides x) for the large-star path.
+// center points at x's key; ROW and PLANE are the key array's strides along y and z.
+//  1. Each vertex of L(x) gets the 32-bit word (key with its low 5 bits cleared) | position, and
+//     each other position a padding word above all of them (spaced 32 apart).  A sorting
+//     network orders the 26 words; these words order two vertices exactly as (key, position)
+//     does unless both keys agree in all but their low 5 bits -- then two adjacent sorted words
+//     agree above bit 4, and the function returns false (the caller uses the pairwise
+//     comparisons instead; on smooth float data this is rare).
+//  2. The vertex of rank r gets the bit 1 << r; a cell's key is the OR of its vertices' bits,
+//     built edge -> quad -> cube from the facets through x.
+//  3. K(p) receives (key << 5) | p for every position of L(x) (K(p) is scratch of the caller,
+//     one 32-bit word per position; other positions are left with unspecified values).
+template <int ROW, int PLANE, class Scratch>
+__host__ __device__ __forceinline__ bool rank_cell_keys(const uint32_t inL, const uint32_t* center, Scratch&& K) {
+    uint32_t v[26];
+#pragma unroll
+    for (int i = 0; i < 26; ++i) {
+        const int p = star_pos(i);
+        const uint32_t k = center[pdx(p) + ROW * pdy(p) + PLANE * pdz(p)];
+        v[i] = ((inL >> p) & 1u) ? ((k & ~31u) | uint32_t(p)) : (0xFFFFFFFFu - 32u * uint32_t(i));
+    }
+    sort26_from<0>(v);
+    uint32_t gap = 0xFFFFFFFFu;  // adjacent words with equal high parts differ below bit 5
+#pragma unroll
+    for (int j = 0; j < 25; ++j) gap = MSC_UMIN(gap, v[j + 1] ^ v[j]);
+    if (gap < 32u) return false;
+    const int m = MSC_POPC(inL) - 1;
+#pragma unroll
+    for (int j = 0; j < 26; ++j)
+        if (j < m) K(int(v[j] & 31u)) = uint32_t(j);
+    uint32_t key[27];
+#pragma unroll
+    for (int p = 0; p < 27; ++p) {  // dimension order within each position's facets: edges first
+        if (p == CENTER) continue;
+        key[p] = 1u << (K(p) & 31u);
+    }
+    // quads then cubes: a cell's vertices are its own position's vertex and its facets' vertices
+#pragma unroll
+    for (int pass = 2; pass <= 3; ++pass)
+#pragma unroll
+        for (int p = 0; p < 27; ++p) {
+            const int dim = (pdx(p) != 0) + (pdy(p) != 0) + (pdz(p) != 0);
+            if (dim != pass) continue;
+            uint32_t k = key[p];
+            if (pdx(p)) k |= key[p - pdx(p)];
+            if (pdy(p)) k |= key[p - 3 * pdy(p)];
+            if (pdz(p)) k |= key[p - 9 * pdz(p)];
+            key[p] = k;
+        }
+#pragma unroll
+    for (int p = 0; p < 27; ++p) {
+        if (p == CENTER) continue;
+        K(p) = (key[p] << 5) | uint32_t(p);
+    }
+    return true;
+}
+
+// The least cell of a non-empty set under the integer keys left in K by rank_cell_keys.
+template <class Scratch>
+__host__ __device__ __forceinline__ int least_by_keys(uint32_t s, Scratch&& K) {
+    uint32_t best = K(MSC_FFS(s) - 1);
+    s &= s - 1;
+    while (s) {
+        best = MSC_UMIN(best, K(MSC_FFS(s) - 1));
+        s &= s - 1;
+    }
+    return int(best & 31u);
+}
+
+// Stars with at least this many cells besides x take the ranked path.
+constexpr int RANKED_MIN_CELLS = 12;
+
+// Pairs the cells of L(x) given inL (the lower-star mask, with more than x in it); st.key(p)
+// must be valid for every p in inL, and the key array must have strides ROW and PLANE.
+// Vertices with equal keys are ordered by position, which is their index order.  emit(p, code)
+// is called for every non-critical cell with its direction code; K is per-star scratch of 27
+// words (see rank_cell_keys).  Returns false if the procedure did not classify every cell (an
+// internal error).
+template <int ROW, int PLANE, class Scratch, class Emit>
+__host__ __device__ __forceinline__ bool pair_lower_star(const uint32_t inL, const Star& st, Scratch&& K,
+                                                         Emit&& emit) {
+    if (MSC_POPC(inL) - 1 >= RANKED_MIN_CELLS && rank_cell_keys<ROW, PLANE>(inL, st.center, K)) {
+        const int delta = least_by_keys(inL & DIM1, K);
+        return classify_star(inL, delta, st.T, [&](uint32_t s) { return least_by_keys(s, K); }, emit);
+    }
+    const int delta = pop_min_edge(inL & DIM1, st);
+    return classify_star(inL, delta, st.T, [&](uint32_t s) { return pop_min(s, st); }, emit);
 }
 
 // Pairs the cells of L(x) given the 27 vertex order keys k[] (k[13] = x; an off-grid vertex
@@ -230,7 +378,8 @@ template <class Emit>
 __host__ __device__ bool process_lower_star(const uint32_t* k, const Tables* T, Emit&& emit) {
     const uint32_t inL = lower_star_mask(lower_mask(k));
     if (inL == (1u << CENTER)) return true;  // a minimum: every code stays 0
-    return pair_lower_star(inL, Star{k + CENTER, T}, emit);
+    uint32_t scratch[27];
+    return pair_lower_star<3, 9>(inL, Star{k + CENTER, T}, [&](int p) -> uint32_t& { return scratch[p]; }, emit);
 }
 
 }  // namespace star

@@ -91,6 +91,9 @@ def random_field(shape_zyx, seed, kind="normal"):
         return rng.standard_normal(shape_zyx).astype(np.float32)
     if kind == "ties":  # few distinct values: exercises the index tie-break
         return rng.integers(0, 3, size=shape_zyx).astype(np.float32)
+    if kind == "near":  # 1 + k ulp, k < 64: order keys that differ only in their lowest bits, and ties
+        ulp = np.float32(2.0 ** -23)
+        return (np.float32(1.0) + rng.integers(0, 64, size=shape_zyx).astype(np.float32) * ulp).astype(np.float32)
     raise KeyError(kind)
 
 

@@ -34,6 +34,7 @@ def _cases():
     for i, shp in enumerate([(2, 2, 2), (3, 5, 7), (9, 8, 33), (6, 6, 6), (4, 3, 2)]):
         out.append(random_field(shp, 40 + i, "normal"))
         out.append(random_field(shp, 60 + i, "ties"))
+        out.append(random_field(shp, 80 + i, "near"))
     return out
 
 
