@@ -401,6 +401,52 @@ def test_nan_rejected_and_infinities_ordered():
     assert list(oracle.critical((2, 2, 2), oracle.gradient(z))[0]) == [1, 0, 0, 0]
 
 
+def _decode_packed_words(dims, words):
+    """The partner of every cell, read from packed words by the word layout's definition (one
+    uint32 per vertex; vertex (x,y,z) owns the cells (2x+a, 2y+b, 2z+c), slot s = a + 2b + 4c,
+    3-bit code in bits [3s, 3s+3): 0 critical, 1..6 partner one step along -x, +x, -y, +y, -z, +z
+    of the refined grid, 7 no such cell).  Returns (cell ids, partner ids or NONE) for every
+    existing cell, and whether every non-existing cell carries code 7."""
+    nx, ny, nz = (int(v) for v in dims)
+    rx, ry, rz = 2 * nx - 1, 2 * ny - 1, 2 * nz - 1
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    words = words.astype(np.int64)
+    step = {1: (-1, 0, 0), 2: (1, 0, 0), 3: (0, -1, 0), 4: (0, 1, 0), 5: (0, 0, -1), 6: (0, 0, 1)}
+    cells, partners, off_grid_ok = [], [], True
+    for s in range(8):
+        a, b, c = s & 1, (s >> 1) & 1, (s >> 2) & 1
+        cx, cy, cz = 2 * x + a, 2 * y + b, 2 * z + c
+        code = (words >> (3 * s)) & 7
+        inside = (cx < rx) & (cy < ry) & (cz < rz)
+        off_grid_ok &= bool(np.all(code[~inside] == 7))
+        cid = cx + rx * (cy + ry * cz)
+        part = np.full(code.shape, 0xFFFFFFFF, dtype=np.int64)
+        for k, (dx, dy, dz) in step.items():
+            sel = code == k
+            part[sel] = ((cx + dx) + rx * ((cy + dy) + ry * (cz + dz)))[sel]
+        bad = inside & (code == 7)  # an existing cell must be critical or paired
+        part[bad] = -1
+        cells.append(cid[inside])
+        partners.append(part[inside])
+    return np.concatenate(cells), np.concatenate(partners), off_grid_ok
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_packed_words_decode_to_the_gradient_pairs(seed):
+    """The packed-word convention (the library's exchange format) against the pairs it encodes:
+    every word of oracle.pack, decoded by the layout's definition, names each cell's partner as
+    oracle.gradient does; every cell of the refined grid appears exactly once."""
+    shapes = [(5, 6, 7), (3, 9, 4), (8, 8, 2), (2, 5, 11)]
+    for kind in ("normal", "ties"):
+        f = random_field(shapes[seed], 300 + seed, kind)
+        dims = (f.shape[2], f.shape[1], f.shape[0])
+        pair = oracle.gradient(f)
+        cells, partners, off_grid_ok = _decode_packed_words(dims, oracle.pack(dims, pair))
+        assert off_grid_ok
+        assert np.array_equal(np.sort(cells), np.arange(pair.size))
+        assert np.array_equal(partners, pair[cells].astype(np.int64))
+
+
 def test_packed_at_matches_full_pack():
     f = fields.grf((9, 10, 11), 3.0, seed=9)
     pair = oracle.gradient(f)
