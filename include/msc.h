@@ -48,7 +48,9 @@ typedef enum msc_status {
     MSC_ERR_CUDA = 9,       /* a CUDA runtime error (message in msc_last_error_string) */
     MSC_NOT_READY = 10,     /* msc_poll: the ticket has not finished yet */
     MSC_ERR_STATE = 11,     /* a stage was requested before msc_gradient */
-    MSC_ERR_CAPACITY = 12   /* a caller-provided output buffer is too small (counts are still reported) */
+    MSC_ERR_CAPACITY = 12,  /* a caller-provided output buffer is too small (counts are still reported) */
+    MSC_ERR_INTERNAL = 13   /* a device-side invariant failed (a lower-star cell left unclassified, a
+                               bounds check): a defect of the library, not of the input */
 } msc_status;
 
 typedef struct msc_plan_s* msc_plan_t;
@@ -76,7 +78,7 @@ typedef struct msc_opts {
                                 grid shape on this device, timed once per shape on the first
                                 synchronised run); 1..9 = force variant (TY,TZ,threads) =
                                 (8,8,512), (8,4,256), (4,8,256), (8,16,512), (16,8,512),
-                                (16,8,1024), (16,16,512), (16,16,1024), (32,8,1024); a tile row
+                                (16,8,1024), (16,16,512), (8,8,256), (16,8,256); a tile row
                                 is 32 vertices.  Results are identical. */
     int32_t path_count_method; /* 1 = the paper's iteration A <- A B, row by row (path_count_tier
                                   picks its first tier); 2 = junction waves: J = B* + B J once per
@@ -118,8 +120,11 @@ typedef struct msc_stats {
 } msc_stats;
 
 /* ---- plan ----------------------------------------------------------------------------
- * Creates a plan for one grid shape on the current CUDA device.  The plan owns every
- * device buffer of the pipeline; they are grown on demand and reused across runs.
+ * Sec. 3.5 (implementation): the pipeline keeps the gradient, the critical cells, the
+ * reachability and the matrices of Sec. 3.3 in device arrays sized from the grid and from the
+ * counts of earlier stages.  A plan holds those arrays for one grid shape on the current CUDA
+ * device; they are grown on demand and reused across runs (a time series on one shape
+ * allocates once).
  * dims: host array {nx, ny, nz}, each >= 2.  opts: nullable.  *out receives the plan. */
 msc_status msc_plan(const int64_t dims[3], const msc_opts* opts, msc_plan_t* out);
 msc_status msc_plan_destroy(msc_plan_t plan);
@@ -227,7 +232,8 @@ msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_no
                              int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult);
 
 /* ---- outputs into host memory --------------------------------------------------------
- * Copies one output of the plan's last pass into caller-owned host memory, computing the stage if
+ * Sec. 3.5 "Data structure": the complex is assembled on the host from the arrays the GPU
+ * stages produce.  This copies one of those arrays into caller-owned host memory, computing the stage if
  * it has not run yet (as the accessor above would).  `what` selects the array and its element type:
  *   MSC_OUT_CELLS0..3      critical k-cell ids (uint32, counts[k])
  *   MSC_OUT_MIN_ARCS       2 minima per 1-saddle (uint32)       MSC_OUT_MAX_ARCS  2 maxima per 2-saddle (uint32)
@@ -282,33 +288,9 @@ msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t strea
 
 msc_status msc_get_stats(msc_plan_t plan, msc_stats* out);
 
-/* ---- (a1)+(a2) without any device allocation ---------------------------------------------
- * The paper has no counterpart: this is a convenience for callers that cannot allocate device
- * memory -- a host program that has already reserved the whole GPU for its own memory pool, or
- * code running in a callback or a deadline-bound loop where a cudaMalloc (which may synchronise
- * the device, and may fail) is not allowed.  It computes the same packed gradient and critical
- * lists as msc_gradient + msc_critical, but needs no plan: all of its scratch (critical-cell
- * bitmaps, their word prefixes, scan block sums and a status word) lives in one static device
- * array of MSC_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until exit.
- * It calls no cudaMalloc, cudaFree or allocating library routine.
- *
- * dims: host {nx, ny, nz}.  d_field: caller-owned float32 field (as msc_gradient).
- * d_words: caller-owned output, nx*ny*nz uint32 in the msc_gradient word layout.
- * d_cells[k], capacity[k]: caller-owned output lists of the critical k-cells (increasing cell
- *   id) and their capacities in entries.  counts: host int64[4], filled before returning.
- * Size limit: 8 * (8 * nz * ny * ceil(nx/32)) bytes of bitmaps and prefixes plus the scan sums
- *   must fit in MSC_STATIC_SCRATCH_BYTES (about 200^3 vertices); larger grids return
- *   MSC_ERR_TOO_LARGE before any GPU work.  If a count exceeds its capacity the lists are not
- *   written, counts are still filled, and MSC_ERR_CAPACITY is returned.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All calls share
- * the one array, which keeps the last call's contents: calls that overlap on the GPU (two
- * streams, or two host threads) race on it and must be serialised by the caller.  The call
- * synchronises `stream` once (to read the counts); the lists are complete when `stream`
- * reaches the end of the call. */
 /* ---- batching and serving ------------------------------------------------------------------
- * Many volumes of uneven size, processed concurrently (the paper's time-varying use, Sec. 1:
- * "each time step may have to be analyzed within a short time budget").  A batch owns a pool of
+ * Many volumes of uneven size, processed concurrently (the time-varying, interactive use that
+ * motivates the paper, Sec. 1, where every time step must be analysed quickly).  A batch owns a pool of
  * host worker threads, each driving its own CUDA stream on the batch's device; submitted
  * volumes are queued and started as workers and device memory free up (continuous batching):
  * a volume is admitted while the summed working-set estimates of the volumes in flight stay
@@ -341,7 +323,39 @@ msc_status msc_batch_submit(msc_batch_t batch, msc_volume* vols, int n, msc_stre
 msc_status msc_poll(msc_batch_t batch, uint64_t ticket, int* done, int* status);
 msc_status msc_batch_wait(msc_batch_t batch, uint64_t ticket, int* status);
 
+/* ---- (a1)+(a2) without any device allocation ---------------------------------------------
+ * The paper has no counterpart: this is a convenience for callers that cannot allocate device
+ * memory -- a host program that has already reserved the whole GPU for its own memory pool, or
+ * code running in a callback or a deadline-bound loop where a cudaMalloc (which may synchronise
+ * the device, and may fail) is not allowed.  It computes the same packed gradient and critical
+ * lists as msc_gradient + msc_critical, but needs no plan: all of its scratch (critical-cell
+ * bitmaps, their word prefixes, scan block sums and a status word) lives in one static device
+ * array of MSC_STATIC_SCRATCH_BYTES.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ * dims: host {nx, ny, nz}.  d_field: caller-owned float32 field (as msc_gradient).
+ * d_words: caller-owned output, nx*ny*nz uint32 in the msc_gradient word layout.
+ * d_cells[k], capacity[k]: caller-owned output lists of the critical k-cells (increasing cell
+ *   id) and their capacities in entries.  counts: host int64[4], filled before returning.
+ * Size limit: the scratch holds 64 * nz * ny * ceil(nx/32) bytes of bitmaps and prefixes, the
+ *   scan's block sums and 512 bytes of status; it must fit in MSC_STATIC_SCRATCH_BYTES.  Cubes up
+ *   to 193^3 fit; 194^3 and larger return MSC_ERR_TOO_LARGE before any GPU work.  If a count
+ *   exceeds its capacity the lists are not written, counts are still filled, and
+ *   MSC_ERR_CAPACITY is returned.  MSC_ERR_INTERNAL if the gradient kernel reports a broken
+ *   invariant.
+ * Loading: CUDA loads the library's device code, and so creates the array, lazily -- when a
+ *   device first needs it.  msc_static_prepare(device) does that for one device (and looks up
+ *   the array's address) without running anything; call it while device memory is still free,
+ *   before the caller reserves the rest of the GPU.  The first msc_gradient_critical_static on a
+ *   device not prepared does the same itself.
+ * Streams: the call synchronises `stream` once (to read the counts) and so cannot be recorded
+ *   into a CUDA graph; the lists are complete when `stream` reaches the end of the call.  All
+ *   calls share the one array, which keeps the last call's contents: calls that overlap on the
+ *   GPU (two streams, or two host threads) race on it and must be serialised by the caller.
+ *   The array's address is remembered per device for the life of the process; do not use the
+ *   entry point on a device after cudaDeviceReset. */
 #define MSC_STATIC_SCRATCH_BYTES (16u << 20)
+msc_status msc_static_prepare(int device);
 msc_status msc_gradient_critical_static(const int64_t dims[3], const float* d_field, uint32_t* d_words,
                                         uint32_t* const d_cells[4], const int64_t capacity[4], int64_t counts[4],
                                         msc_stream_t stream);

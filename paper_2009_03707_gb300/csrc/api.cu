@@ -55,8 +55,8 @@ msc_status status_error(Plan* p, uint32_t word) {
     if (word & ST_OVERFLOW) return fail(p, MSC_ERR_OVERFLOW, "a saddle-saddle path count exceeds 2^64-1");
     if (word & ST_ITER) return fail(p, MSC_ERR_ITER_LIMIT, "an iterative stage reached its iteration cap");
     if (word & ST_TIMEOUT) return fail(p, MSC_ERR_TIMEOUT, "a bounded device wait gave up");
-    if (word & (ST_CAPACITY | ST_RETRY)) return fail(p, MSC_ERR_CUDA, "internal: a device buffer was too small");
-    return fail(p, MSC_ERR_CUDA, "internal: a device-side bounds check failed");
+    if (word & (ST_CAPACITY | ST_RETRY)) return fail(p, MSC_ERR_INTERNAL, "internal: a device buffer was too small");
+    return fail(p, MSC_ERR_INTERNAL, "internal: a device-side invariant or bounds check failed");
 }
 
 msc_status check_status_word(Plan* p, cudaStream_t s) {

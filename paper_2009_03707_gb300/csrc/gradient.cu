@@ -378,6 +378,20 @@ msc_status run_gradient(Plan* p, const float* d_field, cudaStream_t s) {
                       "gradient launch");
 }
 
+// Loads the kernels of launch_gradient_raw on the current device now (under lazy module loading
+// CUDA would load them, and take device memory for their code, at their first launch) and sets
+// the lower-star kernel's shared-memory limit there.
+cudaError_t load_gradient_raw() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, zero_face_words);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gradient_kernel<8, 8, 512>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gradient_kernel<8, 8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sizeof(Shared<8, 8, 512>)));
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, critical_bitmaps);
+    return e;
+}
+
 // The same launches on caller-supplied buffers, with no plan and no allocation (used by the
 // no-allocation entry point, static_entry.cu).
 cudaError_t launch_gradient_raw(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,

@@ -9,8 +9,10 @@
 //
 // In host code the array's name is only a host-side stand-in, not a device address, so the
 // address is looked up once per device with cudaGetSymbolAddress (with that device current)
-// and passed to the kernels.  Every call shares the array and overwrites it; overlapping calls
-// race, which the header documents.
+// and passed to the kernels.  Under lazy module loading that lookup is also what loads the
+// library's device code on the device and creates the array, which is why msc_static_prepare
+// exists: a caller runs it before reserving the rest of the GPU.  Every call shares the array
+// and overwrites it; overlapping calls race, which the header documents.
 #include <mutex>
 
 #include "scan.cuh"
@@ -19,6 +21,7 @@ namespace msc {
 
 cudaError_t launch_gradient_raw(const Geom& g, const float* d_field, uint32_t* words, uint32_t* crit_bits,
                                 uint32_t* status, cudaStream_t s);
+cudaError_t load_gradient_raw();
 
 namespace {
 
@@ -46,6 +49,34 @@ size_t round_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 }  // namespace
 }  // namespace msc
+
+extern "C" msc_status msc_static_prepare(int device) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return MSC_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return MSC_ERR_ARG;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return MSC_ERR_CUDA;
+    }
+    unsigned char* base = nullptr;
+    cudaError_t e = msc::scratch_address(device, &base);
+    // load every kernel the entry point launches, so none is loaded lazily later
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = msc::load_gradient_raw();
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, msc::scan_reduce_kernel<msc::CritSource>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, msc::scan_top_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, msc::scan_emit_kernel<msc::CritSource>);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MSC_ERR_CUDA;
+    }
+    return MSC_OK;
+}
 
 extern "C" msc_status msc_gradient_critical_static(const int64_t dims[3], const float* d_field, uint32_t* d_words,
                                                    uint32_t* const d_cells[4], const int64_t capacity[4],
@@ -107,7 +138,7 @@ extern "C" msc_status msc_gradient_critical_static(const int64_t dims[3], const 
         return MSC_ERR_CUDA;
     }
     if (word & ST_NAN) return MSC_ERR_NAN;
-    if (word) return MSC_ERR_CUDA;
+    if (word) return MSC_ERR_INTERNAL;  // a lower-star cell left unclassified or a bounds check
     bool fits = true;
     for (int k = 0; k < 4; ++k) {
         counts[k] = int64_t(tot[k]);

@@ -20,8 +20,9 @@ from . import build as _build
 MSC_OK = 0
 STATUS_NAMES = {0: "MSC_OK", 1: "MSC_ERR_ARG", 2: "MSC_ERR_NAN", 3: "MSC_ERR_OOM", 4: "MSC_ERR_TOO_LARGE",
                 6: "MSC_ERR_OVERFLOW", 7: "MSC_ERR_ITER_LIMIT", 8: "MSC_ERR_TIMEOUT", 9: "MSC_ERR_CUDA",
-                10: "MSC_NOT_READY", 11: "MSC_ERR_STATE", 12: "MSC_ERR_CAPACITY"}
+                10: "MSC_NOT_READY", 11: "MSC_ERR_STATE", 12: "MSC_ERR_CAPACITY", 13: "MSC_ERR_INTERNAL"}
 MSC_ERR_CAPACITY = 12
+MSC_ERR_INTERNAL = 13
 MSC_STATIC_SCRATCH_BYTES = 16 << 20
 
 # Every symbol declared in include/msc.h with its ctypes signature.
@@ -47,6 +48,7 @@ SIGNATURES = {
     "msc_compute_wait": ([_P], _I32),
     "msc_compute": ([_P, _P, _P], _I32),
     "msc_get_stats": ([_P, _P], _I32),
+    "msc_static_prepare": ([_I32], _I32),
     "msc_gradient_critical_static": ([_PI64, _P, _P, _PP, _PI64, _PI64, _P], _I32),
     "msc_batch_create": ([_I32, _I64, _PP], _I32),
     "msc_batch_destroy": ([_P], _I32),
@@ -339,11 +341,23 @@ def msc_gradient_critical_static(field: torch.Tensor, words: torch.Tensor, cells
     output tensors; capacity: their entry capacities.  Returns the 4 critical counts.  Scratch
     lives in one static device array shared by every call, so overlapping calls race.
     """
-    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
-        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous() or field.dim() != 3:
+        raise ValueError("field must be a contiguous 3-D float32 CUDA tensor")
+    dev = field.device
+    if dev.index != torch.cuda.current_device():
+        raise ValueError(f"field is on {dev}, but the current device is cuda:{torch.cuda.current_device()}")
     nz, ny, nx = field.shape
-    if tuple(words.shape) != (nz, ny, nx) or words.dtype != torch.uint32 or not words.is_contiguous():
-        raise ValueError("words must be a contiguous uint32 tensor shaped like the field")
+    if (tuple(words.shape) != (nz, ny, nx) or words.dtype != torch.uint32 or not words.is_contiguous()
+            or words.device != dev):
+        raise ValueError("words must be a contiguous uint32 tensor shaped like the field, on its device")
+    if len(cells) != 4 or len(capacity) != 4:
+        raise ValueError("cells and capacity need one entry per cell dimension (4)")
+    for k in range(4):
+        c, cap_k = cells[k], int(capacity[k])
+        if c.dtype != torch.uint32 or not c.is_contiguous() or c.device != dev:
+            raise ValueError(f"cells[{k}] must be a contiguous uint32 tensor on {dev}")
+        if cap_k < 0 or cap_k > c.numel():
+            raise ValueError(f"capacity[{k}] = {cap_k} exceeds cells[{k}].numel() = {c.numel()}")
     dims = (ctypes.c_int64 * 3)(nx, ny, nz)
     ptrs = (ctypes.c_void_p * 4)(*[c.data_ptr() if c.numel() else None for c in cells])
     cap = (ctypes.c_int64 * 4)(*[int(c) for c in capacity])
@@ -353,6 +367,13 @@ def msc_gradient_critical_static(field: torch.Tensor, words: torch.Tensor, cells
     if st != MSC_OK:
         raise MscError(st, f"msc_gradient_critical_static{(nx, ny, nz)} counts={list(counts)}")
     return [int(c) for c in counts]
+
+
+def msc_static_prepare(device: int) -> None:
+    """Loads the library's device code on `device` and looks up the static scratch array of
+    msc_gradient_critical_static there, without running anything (call it before the rest of the
+    GPU's memory is reserved)."""
+    _check(lib.msc_static_prepare(int(device)), what=f"msc_static_prepare({device})")
 
 
 class MscVolume(ctypes.Structure):
