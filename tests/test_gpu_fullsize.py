@@ -1,8 +1,11 @@
 """Full-size parity on the bench workload (256^3 k^-3 GRF) and the 512^3 Gaussian-blob field,
-in the configuration bench.py times (one plan, default options, the current stream).  The
-oracle cannot run these volumes whole in test time, so it checks sampled outputs one by one
-(its lower-star pairs are computed lazily, one vertex's star at a time), and properties that
-hold at any size cover the rest."""
+in the configuration bench.py times: one plan with default options, on the current stream, and
+its third msc_compute -- the replayed CUDA graph with the autotuned lower-star tile, the
+saddle-extremum branch beside the critical path, and the path-count method the plan chose after
+its first pass (row-wise products on the shallow GRF minor, junction waves on the deep blob
+minor).  The oracle cannot run these volumes whole in test time, so it checks sampled outputs
+one by one (its lower-star pairs are computed lazily, one vertex's star at a time), and
+properties that hold at any size cover the rest."""
 from __future__ import annotations
 
 import numpy as np
@@ -20,7 +23,9 @@ NONE = 0xFFFFFFFF
 def _run(f):
     m = msc()
     plan = m.Plan(dims_of(f))
-    m.msc_compute(plan, gpu_field(f))
+    d = gpu_field(f)
+    for _ in range(3):  # synchronised first pass, graph capture, then a replay (as the bench)
+        m.msc_compute(plan, d)
     counts, cells = m.msc_critical(plan)
     amin, amax, vmin, cmax = m.msc_extremum_arcs(plan)
     vis, levels = m.msc_reachability(plan)
@@ -32,7 +37,7 @@ def _run(f):
                 stats=m.msc_get_stats(plan))
 
 
-def _check(f, r, n_samples, seed):
+def _check(f, r, n_samples, seed, n_rows=None):
     rng = np.random.default_rng(seed)
     nz, ny, nx = f.shape
     rx, ry = 2 * nx - 1, 2 * ny - 1
@@ -97,10 +102,18 @@ def _check(f, r, n_samples, seed):
     assert np.all(facts[:, 0] == 1) and np.all(facts[:, 1] == 0) and np.all(facts[:, 2] > 1)
     assert np.all(visited(js))
     assert np.all(visited(r["cells"][1]))  # every 1-saddle is a BFS seed
-    # (a6) D* rows of sampled 1-saddles against the oracle's per-source path counts
-    rows = rng.integers(0, counts[1], size=min(counts[1], n_samples // 8))
-    want = oracle.lazy_dstar_rows(f, r["cells"][1][rows])
+    # (a6) D* rows of sampled 1-saddles against the oracle's per-source path counts.  The row-wise
+    # products defer a row to the next tier when its tables overflow: a row of more than 16 entries
+    # cannot finish in tier 0, of more than 32 not in tier 0b, of more than 256 not in tier 1.  So
+    # beside random rows, every row longer than 16 entries (up to 400 of them, the longest first)
+    # is checked too.
     rp = r["rowptr"]
+    n_rows = n_rows or n_samples // 8
+    lens = np.diff(rp.astype(np.int64))
+    long_rows = np.argsort(-lens, kind="stable")[:400]
+    long_rows = long_rows[lens[long_rows] > 16]
+    rows = np.unique(np.concatenate([rng.integers(0, counts[1], size=min(counts[1], n_rows)), long_rows]))
+    want = oracle.lazy_dstar_rows(f, r["cells"][1][rows])
     for s in rows:
         a, b = int(rp[s]), int(rp[s + 1])
         got = {int(r["cells"][2][c]): int(k) for c, k in zip(r["col"][a:b], r["cnt"][a:b])}
@@ -110,9 +123,13 @@ def _check(f, r, n_samples, seed):
 
 def test_grf256_bench_workload():
     f = fields.config_field("grf256")
-    _check(f, _run(f), n_samples=4000, seed=1)
+    r = _run(f)
+    assert r["stats"]["path_count_method"] == 1  # the replay timed by the bench: row-wise products
+    _check(f, r, n_samples=4000, seed=1, n_rows=2000)
 
 
 def test_blobs512():
     f = fields.config_field("blobs512")
-    _check(f, _run(f), n_samples=2000, seed=2)
+    r = _run(f)
+    assert r["stats"]["path_count_method"] == 2  # a minor of ~200 levels: junction waves
+    _check(f, r, n_samples=2000, seed=2)
