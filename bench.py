@@ -5,10 +5,19 @@ saddle-saddle reachability, DAG minor, D* path counts) over one synthetic volume
 the library's C ABI.  The default workload is the 256^3 float32 Gaussian random field with
 P(k) ~ k^-3 (seed 1).  The timed region starts with the field resident in HBM; the L2 is
 flushed (a 256 MB write) before every timed step.  A second pass times the same steps
-end to end from pinned host memory (H2D of the field, D2H of the whole 1-skeleton every step),
-with two plans on two streams taking the steps in turn so that copies overlap compute.
+end to end from pinned host memory: the field goes up every step, and every output of the
+pass (critical lists, both arc arrays, both label arrays, D* CSR) comes back through
+msc_copy_to_host into caller-owned pinned buffers, with three plans on three streams taking
+the steps in turn so that copies overlap compute.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+The default run adds the metric's other workloads to the same JSON line ("legs"), each with
+the clocks sampled while it ran: the 512^3 blob field (the largest single volume); the
+64-volume uneven batch as one submission against the same volumes one msc_compute at a time;
+and the serving trace (the first 200 requests of the Poisson stream) through the
+continuous-batching runtime against the same trace served one request at a time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-legs]
+  python bench.py --workload blobs512 | batch64 | serve500 | cos32
 
 --impl reference times the plain CPU oracle (the only other implementation of this path)
 on bounded crops of the same workload on the host cores.  With N > 1 (torchrun) every rank
@@ -34,7 +43,7 @@ WORKLOADS = {
     "blobs512": "512^3 float32 sum of 2000 Gaussian blobs (sigma 2-20, amplitude U[-1,1]) + N(0,1e-3), seed 2",
     "cos32": "32^3 float32 cos(2 pi x/16)+cos(2 pi y/16)+cos(2 pi z/16) + U[0,1e-3], seed 0",
     "batch64": "64 float32 GRFs, P(k) ~ k^-2.5, seeds 100-163, each axis uniform in 48-192",
-    "serve500": "500 requests over 8 advected k^-3 GRF streams sized 64^3-384^3, Poisson 200 req/s, 8 GiB admission",
+    "serve500": "500 requests over 8 advected k^-3 GRF streams sized 64^3-384^3, Poisson 200 req/s, HBM-budget admission",
 }
 METRIC = "end-to-end MS-complex Mvoxel/s on 1 GB300 (batched vs plain) + per-stage HBM GB/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -53,6 +62,9 @@ def _peaks():
 
 
 E2E_LANES = 3  # plans in flight in the end-to-end leg
+# every output of a pass, copied to the host by the end-to-end leg (msc_copy_to_host selectors)
+E2E_OUTPUTS = ("cells0", "cells1", "cells2", "cells3", "min_arcs", "max_arcs", "vertex_min", "cube_max",
+               "dstar_rowptr", "dstar_col", "dstar_count")
 
 
 def _rounded(d):
@@ -326,14 +338,13 @@ def run_gpu(args):
         lanes.append({"plan": pl, "field": d_field if x == 0 else torch.empty_like(d_field),
                       "stream": stream if x == 0 else torch.cuda.Stream(), "out": {}})
 
-    def d2h(lane, name, t):
-        n = t.numel() * t.element_size()
-        buf = lane["out"].get(name)
+    def d2h(lane, what):
+        """One output into the lane's caller-owned pinned buffer through msc_copy_to_host."""
+        n = msc.msc_copy_to_host_size(lane["plan"], what)
+        buf = lane["out"].get(what)
         if buf is None or buf.numel() < n:
-            buf = lane["out"][name] = torch.empty(max(n, 1), dtype=torch.uint8, pin_memory=True)
-        if n:
-            buf[:n].copy_(t.view(torch.uint8).reshape(-1), non_blocking=True)
-        return n
+            buf = lane["out"][what] = torch.empty(max(n, 1), dtype=torch.uint8, pin_memory=True)
+        return msc.msc_copy_to_host_into(lane["plan"], what, buf) if n else 0
 
     def upload(lane):
         with torch.cuda.stream(lane["stream"]):
@@ -346,13 +357,7 @@ def run_gpu(args):
     def collect(lane):
         with torch.cuda.stream(lane["stream"]):
             msc.msc_compute_wait(lane["plan"])
-            _, cells = msc.msc_critical(lane["plan"])
-            amin, amax, _, _ = msc.msc_extremum_arcs(lane["plan"])
-            rowptr, col, cnt = msc.msc_saddle_arcs(lane["plan"])
-            n = sum(d2h(lane, f"cells{k}", cells[k]) for k in range(4))
-            n += d2h(lane, "amin", amin) + d2h(lane, "amax", amax)
-            n += d2h(lane, "rowptr", rowptr) + d2h(lane, "col", col) + d2h(lane, "cnt", cnt)
-        return n
+            return sum(d2h(lane, what) for what in E2E_OUTPUTS)
 
     def run_e2e(k):
         L = len(lanes)
@@ -431,7 +436,19 @@ def run_gpu(args):
     stages = {}
     for name in stage_bytes:
         t = med("ms_" + name)
-        stages[name] = {"ms": t, "GB/s": stage_bytes[name] / (t / 1e3) / 1e9 if t > 0 else None}
+        gbs = stage_bytes[name] / (t / 1e3) / 1e9 if t > 0 else None
+        stages[name] = {"ms": t, "GB/s": gbs, "frac": gbs / peak if gbs else None}
+    # the whole pass: every stage's algorithmic bytes over the step time
+    total_bytes = sum(stage_bytes.values())
+    stages["end_to_end"] = {"ms": ms, "GB/s": total_bytes / (ms / 1e3) / 1e9,
+                            "frac": total_bytes / (ms / 1e3) / 1e9 / peak,
+                            "note": "sum of the stages' algorithmic bytes over the device-resident step time"}
+    # both candidates for the dominant kernel, each against its own algorithmic bytes
+    kernels = {}
+    for k in km:
+        a = algo[k] / (km[k] / 1e3) / 1e9 if km[k] > 0 else None
+        kernels[k] = {"ms": km[k], "algorithmic_bytes": algo[k], "achieved": a, "frac": a / peak if a else None}
+    roofline["kernels"] = kernels
 
     clocks = clk.summary()
     line = {
@@ -461,80 +478,130 @@ def run_gpu(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f)
+    if world == 1 and args.workload == "grf256" and not args.no_legs:
+        # the other workloads of the metric, in the same run: the largest single volume, batched
+        # against one volume at a time, served against one request at a time
+        del lanes, plan, d_field
+        torch.cuda.empty_cache()
+        line["legs"] = {
+            "blobs512": leg_single(msc, torch, "blobs512", steps=5, warmup=3, uuid=uuid),
+            "batch64": leg_batch(msc, torch, steps=3, workers=args.workers, uuid=uuid),
+            "serve": leg_serve(msc, torch, args.requests, args.workers, args.serve_budget, uuid),
+        }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batch(args):
-    """Batching workload: 64 uneven volumes, one batched submission vs 64 sequential runs."""
-    import torch
+def _events_ms(torch, fn, reps):
+    """Median over reps of fn() bracketed by CUDA events on the current stream, device synced on
+    both sides (fn may leave the stream and wait on the host: the events then see the wall time
+    the stream spent, idle gaps included)."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
 
-    from paper_2009_03707_gb300 import msc
+
+def leg_single(msc, torch, name, steps, warmup, uuid):
+    """A single-volume workload timed like the main leg (device-resident, L2 flushed per step)."""
+    f = _field(name)
+    nz, ny, nx = f.shape
+    plan = msc.Plan((nx, ny, nz))
+    d = torch.from_numpy(f).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        msc.msc_compute(plan, d)
+
+    def step():
+        flush.fill_(3.0)
+        msc.msc_compute(plan, d)
+
+    with ClockSampler(uuid) as clk:
+        ms = _events_ms(torch, step, steps)  # the flush write is inside; it takes ~0.05 ms
+    st = msc.msc_get_stats(plan)
+    return {"workload": f"{name}: {WORKLOADS[name]}", "value": f.size / (ms / 1e3) / 1e6, "unit": "Mvoxel/s",
+            "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "stages_ms": {k: st["ms_" + k] for k in ("gradient", "critical", "extremum", "reachability", "minor",
+                                                    "path_count")},
+            "gradient_kernel_ms": st["ms_gradient_kernel"],
+            "path_count_method": {1: "row-wise products", 2: "junction waves"}.get(st["path_count_method"], "?"),
+            "n_iter": st["n_iter"], "n_bfs_levels": st["n_bfs_levels"], "max_path_count": str(st["max_path_count"]),
+            "clocks": clk.summary()}
+
+
+def leg_batch(msc, torch, steps, workers, uuid, with_cpu=False):
+    """Batching: 64 uneven volumes as one submission (one group graph, one launch) against the same
+    64 volumes one msc_compute at a time on one stream, each on its own default plan.  Both arms
+    are timed by CUDA events on the launching stream around the whole 64-volume job."""
     from synth import fields
 
     vols = fields.batch_volumes(64)
     dev = [torch.from_numpy(v).cuda() for v in vols]
     nvox = sum(v.size for v in vols)
-    plans = [msc.Plan((v.shape[2], v.shape[1], v.shape[0])) for v in vols]
-    for _ in range(args.warmup):  # allocates every plan's buffers
-        for p, d in zip(plans, dev):
+    single = [msc.Plan((v.shape[2], v.shape[1], v.shape[0])) for v in vols]
+    batch = msc.Batch(n_workers=workers)
+    ticket, grouped = batch.msc_batch_submit(dev)  # the runtime's own plans: one job per volume
+    assert batch.msc_batch_wait(ticket) == 0
+    for _ in range(2):  # group capture, then a replay; the single plans capture their graphs
+        ticket, _ = batch.msc_batch_submit(dev, grouped)
+        assert batch.msc_batch_wait(ticket) == 0
+        for p, d in zip(single, dev):
             msc.msc_compute(p, d)
-    torch.cuda.synchronize()
-    plain, batched = [], []
-    batch = msc.Batch(n_workers=args.workers)
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for p, d in zip(plans, dev):
+
+    def one_at_a_time():
+        for p, d in zip(single, dev):
             msc.msc_compute(p, d)
-        torch.cuda.synchronize()
-        plain.append(time.perf_counter() - t)
-        t = time.perf_counter()
-        ticket, _ = batch.msc_batch_submit(dev, plans)
-        st = batch.msc_batch_wait(ticket)
-        torch.cuda.synchronize()
-        batched.append(time.perf_counter() - t)
-        assert st == 0, st
+
+    def batched():
+        t, _ = batch.msc_batch_submit(dev, grouped)
+        assert batch.msc_batch_wait(t) == 0
+
+    with ClockSampler(uuid) as clk:
+        t_one = _events_ms(torch, one_at_a_time, steps)
+        t_bat = _events_ms(torch, batched, steps)
     batch.close()
-    tp, tb = statistics.median(plain), statistics.median(batched)
-    line = {"metric": METRIC, "value": nvox / tb / 1e6, "unit": "Mvoxel/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32-compare/u64-count", "data": "synthetic",
-            "config": {"workload": f"batch64: {WORKLOADS['batch64']}", "voxels_per_step": nvox,
-                       "workers": args.workers, "timing": "host wall clock around each pass, device synced"},
-            "plain": {"value": nvox / tp / 1e6, "unit": "Mvoxel/s", "ms_per_step": 1e3 * tp,
-                      "how": "64 msc_compute calls one after another on one stream"},
-            "batched_over_plain": tp / tb}
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_batch(vols)
-    print(json.dumps(line), flush=True)
+    out = {"workload": f"batch64: {WORKLOADS['batch64']}", "voxels": nvox,
+           "batched": {"value": nvox / t_bat * 1e-3, "unit": "Mvoxel/s", "ms": t_bat,
+                       "how": "one msc_batch_submit of the 64 volumes (a CUDA graph with a branch per volume, "
+                              "one launch) and msc_batch_wait"},
+           "one_at_a_time": {"value": nvox / t_one * 1e-3, "unit": "Mvoxel/s", "ms": t_one,
+                             "how": "64 msc_compute calls one after another on one stream (each a replayed "
+                                    "graph and a host wait)"},
+           "batched_over_one_at_a_time": t_one / t_bat, "repetitions": steps,
+           "timing": "CUDA events on the launching stream around each 64-volume job, median",
+           "clocks": clk.summary()}
+    if with_cpu:
+        out["cpu_baseline"] = cpu_baseline_batch(vols)
+    return out
 
 
-def run_serve(args):
-    """Serving workload: Poisson arrivals over 8 advected streams, HBM-budget admission."""
+def _serve_arm(msc, torch, trace, inputs, plans, batch, saturated):
+    """Runs the request trace; batch None = one request at a time (msc_compute in arrival order).
+    Returns per-request (arrival, completion) host times relative to the start."""
     import threading
 
-    import torch
-
-    from paper_2009_03707_gb300 import msc
-    from synth import fields
-
-    streams = fields.serving_streams()
-    trace = fields.request_trace()
-    if args.requests:
-        trace = trace[:args.requests]
-    budget = 8 << 30
-    batch = msc.Batch(n_workers=args.workers, hbm_budget_bytes=budget)
-    plans = [None] * len(streams)
-    for s in range(len(streams)):  # warm-up: one step per stream creates and sizes its plan
-        ticket, out = batch.msc_batch_submit([streams[s].step_device(0)], [plans[s]])
-        plans[s] = out[0]
-        assert batch.msc_batch_wait(ticket) == 0
+    n = len(trace)
+    arrive = [0.0 if saturated else at for at, _, _ in trace]
+    done = [None] * n
     torch.cuda.synchronize()
-    done_at, lock = {}, threading.Lock()
-    pending = []
-    stop = threading.Event()
+    if batch is None:
+        t0 = time.perf_counter()
+        for i, (_, s, _) in enumerate(trace):
+            wait = arrive[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            msc.msc_compute(plans[s], inputs[i])
+            done[i] = time.perf_counter() - t0
+        return arrive, done
+    pending, lock, stop = [], threading.Lock(), threading.Event()
 
     def poller():
         while not stop.is_set() or pending:
@@ -545,45 +612,110 @@ def run_serve(args):
                 if ok:
                     assert status == 0, status
                     with lock:
-                        done_at[i] = time.perf_counter()
+                        done[i] = time.perf_counter() - t0
                         pending.remove((i, ticket))
-            time.sleep(0.0002)
+            time.sleep(0.0001)
 
     th = threading.Thread(target=poller)
-    th.start()
     t0 = time.perf_counter()
-    arrive = {}
-    for i, (at, s, step) in enumerate(trace):
-        now = time.perf_counter() - t0
-        if at > now:
-            time.sleep(at - now)
-        arrive[i] = t0 + at
-        field = streams[s].step_device(step + 1)
-        ticket, _ = batch.msc_batch_submit([field], [plans[s]])
+    th.start()
+    for i, (_, s, _) in enumerate(trace):
+        wait = arrive[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ticket, _ = batch.msc_batch_submit([inputs[i]], [plans[s]])
         with lock:
             pending.append((i, ticket))
     while True:
         with lock:
             if not pending:
                 break
-        time.sleep(0.001)
+        time.sleep(0.0005)
     stop.set()
     th.join()
-    t_end = max(done_at.values())
+    return arrive, done
+
+
+def _serve_summary(trace, sizes, arrive, done):
+    nvox = sum(sizes[s] ** 3 for _, s, _ in trace)
+    lat = sorted(1e3 * (d - a) for a, d in zip(arrive, done))
+    span = max(done) - min(arrive)
+    return {"value": nvox / span / 1e6, "unit": "Mvoxel/s", "span_s": span,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1], "mean": sum(lat) / len(lat)}}
+
+
+def leg_serve(msc, torch, n_requests, workers, budget, uuid):
+    """Serving: the first n_requests of the Poisson trace (200 req/s over the 8 advected streams),
+    each request's field synthesised on the device before the timed region, served by the
+    continuous-batching runtime (HBM-budget admission, each stream keeping its plan on the device)
+    and, on the same trace, one request at a time in arrival order on default plans; both arms also
+    with every request available at once (saturated)."""
+    from synth import fields
+
+    streams = fields.serving_streams()
+    sizes = [st.size for st in streams]
+    trace = fields.request_trace()[:n_requests]
+    inputs = [streams[s].step_device(step + 1) for _, s, step in trace]
+    single = [msc.Plan((n, n, n)) for n in sizes]
+    batch = msc.Batch(n_workers=workers, hbm_budget_bytes=budget)
+    served = [None] * len(streams)
+    for s in range(len(streams)):  # each stream's plans: first pass, graph capture
+        for _ in range(2):
+            ticket, out = batch.msc_batch_submit([inputs[s]], [served[s]])
+            served[s] = out[0]
+            assert batch.msc_batch_wait(ticket) == 0
+            msc.msc_compute(single[s], inputs[s])
+    torch.cuda.synchronize()
+    res = {}
+    with ClockSampler(uuid) as clk:
+        for mode, sat in (("poisson", False), ("saturated", True)):
+            a, d = _serve_arm(msc, torch, trace, inputs, served, batch, sat)
+            res[f"served_{mode}"] = _serve_summary(trace, sizes, a, d)
+            a, d = _serve_arm(msc, torch, trace, inputs, single, None, sat)
+            res[f"one_at_a_time_{mode}"] = _serve_summary(trace, sizes, a, d)
     batch.close()
-    lat = sorted(1e3 * (done_at[i] - arrive[i]) for i in done_at)
-    nvox = sum(streams[s].size ** 3 for _, s, _ in trace)
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
-    line = {"metric": METRIC, "value": nvox / (t_end - t0) / 1e6, "unit": "Mvoxel/s", "n_gpus": 1,
-            "steps": len(trace), "warmup": len(streams), "ms_per_step": 1e3 * (t_end - t0) / len(trace),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-compare/u64-count",
-            "data": "synthetic",
-            "config": {"workload": f"serve500: {WORKLOADS['serve500']}", "requests": len(trace),
-                       "voxels": nvox, "workers": args.workers, "hbm_budget_bytes": budget,
-                       "offered_mvoxel_s": nvox / trace[-1][0] / 1e6,
-                       "inputs": "synthesised on the GPU at arrival (Fourier shift of each stream's base field)"},
-            "latency_ms": {"p50": p50, "p99": p99, "max": lat[-1], "mean": sum(lat) / len(lat)}}
+    nvox = sum(sizes[s] ** 3 for _, s, _ in trace)
+    res.update({"workload": f"serve: {WORKLOADS['serve500']} (first {len(trace)} requests)",
+                "requests": len(trace), "voxels": nvox, "workers": workers, "hbm_budget_bytes": budget,
+                "offered_mvoxel_s": nvox / trace[-1][0] / 1e6,
+                "inputs": "every request's field synthesised on the GPU before the timed region",
+                "timing": "host clock from the first arrival to the last completion; latency = completion - "
+                          "arrival; saturated = every request available at t = 0",
+                "served_over_one_at_a_time": {m: res[f"one_at_a_time_{m}"]["span_s"] / res[f"served_{m}"]["span_s"]
+                                              for m in ("poisson", "saturated")},
+                "clocks": clk.summary()})
+    return res
+
+
+def _standalone_line(args, leg, value, ms, steps):
+    return {"metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-compare/u64-count", "data": "synthetic",
+            "config": {"workload": leg["workload"]}, "leg": leg, "clocks": leg.get("clocks")}
+
+
+def run_multi(args):
+    """--workload batch64 | serve500 alone: the leg's JSON line."""
+    import torch
+
+    from paper_2009_03707_gb300 import msc
+
+    torch.cuda.set_device(0)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    if args.workload == "batch64":
+        leg = leg_batch(msc, torch, args.steps, args.workers, uuid, with_cpu=not args.no_cpu_baseline)
+        line = _standalone_line(args, leg, leg["batched"]["value"], leg["batched"]["ms"], args.steps)
+    else:
+        leg = leg_serve(msc, torch, args.requests, args.workers, args.serve_budget, uuid)
+        line = _standalone_line(args, leg, leg["served_poisson"]["value"],
+                                1e3 * leg["served_poisson"]["span_s"] / leg["requests"], leg["requests"])
+    if "cpu_baseline" in leg:
+        line["cpu_baseline"] = leg.pop("cpu_baseline")
     print(json.dumps(line), flush=True)
 
 
@@ -596,7 +728,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="grf256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workers", type=int, default=8, help="batch/serve worker streams")
-    ap.add_argument("--requests", type=int, default=0, help="serve500: truncate the request trace")
+    ap.add_argument("--requests", type=int, default=200, help="serving: the first R requests of the 500-request trace")
+    ap.add_argument("--serve-budget", type=int, default=24 << 30, help="serving: HBM admission budget in bytes")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="grf256: skip the blobs512, batch64 and serving legs that the default run adds")
     ap.add_argument("--no-graph", action="store_true",
                     help="run every pass synchronised between stages instead of replaying its CUDA graph "
                          "(same kernels; profilers list each launch)")
@@ -606,10 +741,8 @@ def main():
         ap.error("at least 3 warm-up steps are required")
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch64":
-        run_batch(args)
-    elif args.workload == "serve500":
-        run_serve(args)
+    elif args.workload in ("batch64", "serve500"):
+        run_multi(args)
     else:
         run_gpu(args)
 

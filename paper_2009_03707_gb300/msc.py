@@ -291,6 +291,24 @@ def msc_copy_to_host(plan: Plan, what: str) -> np.ndarray:
     return out
 
 
+def msc_copy_to_host_size(plan: Plan, what: str) -> int:
+    """Size in bytes of one output of the last pass (msc_copy_to_host's size query)."""
+    nbytes = ctypes.c_int64(0)
+    _check(lib.msc_copy_to_host(plan.handle, _stream(), MSC_OUT[what][0], None, ctypes.byref(nbytes)), plan.handle)
+    return int(nbytes.value)
+
+
+def msc_copy_to_host_into(plan: Plan, what: str, out: torch.Tensor) -> int:
+    """Copies one output of the last pass into a caller-owned host tensor (pinned memory for a
+    direct DMA); returns the bytes copied.  MSC_ERR_CAPACITY if the tensor is too small."""
+    if out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous host tensor")
+    room = ctypes.c_int64(out.numel() * out.element_size())
+    _check(lib.msc_copy_to_host(plan.handle, _stream(), MSC_OUT[what][0], ctypes.c_void_p(out.data_ptr()),
+                                ctypes.byref(room)), plan.handle)
+    return int(room.value)
+
+
 def msc_compute_async(plan: Plan, field: torch.Tensor) -> None:
     """Enqueues the pass on the current stream and returns (see msc_compute_wait)."""
     if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
