@@ -230,12 +230,12 @@ __global__ void __launch_bounds__(256) critical_bitmaps(Geom g, const uint32_t* 
 // stars.  Every other word gets one plain store, so it needs no zeroing.  A warp per (y, z) row:
 // a row on a y or z face is cleared whole, any other row only at x = 31 mod 32.
 __global__ void __launch_bounds__(256) zero_face_words(Geom g, uint32_t* __restrict__ words, int ty, int tz) {
-    const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // ny * nz < 2^31
     const int lane = threadIdx.x & 31;
-    if (row >= int64_t(g.ny) * g.nz) return;  // warp-uniform
-    const int y = int(row % g.ny), z = int(row / g.ny);
-    uint32_t* w = words + row * g.nx;
-    if (y % ty == ty - 1 || z % tz == tz - 1) {
+    if (row >= uint32_t(g.ny) * uint32_t(g.nz)) return;  // warp-uniform
+    const uint32_t z = g.div_ny.div(row), y = row - z * uint32_t(g.ny);
+    uint32_t* w = words + int64_t(row) * g.nx;
+    if (int(y) % ty == ty - 1 || int(z) % tz == tz - 1) {
         for (int x = lane; x < g.nx; x += 32) w[x] = 0;
     } else {
         for (int x = 32 * lane + 31; x < g.nx; x += 32 * 32) w[x] = 0;
