@@ -77,6 +77,13 @@ _SIGNATURES = {
                           ctypes.c_int),
     "ora_lazy_nodes": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "ora_lazy_dstar_rows": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_void_p),
+    "ora_arc_cells": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                       ctypes.c_void_p], ctypes.c_void_p),
+    "ora_arc_status": ([ctypes.c_void_p], ctypes.c_int),
+    "ora_arc_count": ([ctypes.c_void_p], ctypes.c_int64),
+    "ora_arc_cells_size": ([ctypes.c_void_p], ctypes.c_int64),
+    "ora_arc_copy": ([ctypes.c_void_p] * 3, None),
+    "ora_arc_free": ([ctypes.c_void_p], None),
 }
 
 
@@ -189,6 +196,26 @@ def extremum(dims, pair, s1, s2):
     lib.ora_min_arcs(_p(d), _p(vmin), len(s1), _p(s1), _p(amin))
     lib.ora_max_arcs(_p(d), _p(cmax), len(s2), _p(s2), _p(amax))
     return vmin, cmax, amin, amax
+
+
+def arc_cells(dims, pair, s1, s2):
+    """The cells along every saddle-extremum arc (Sec. 3.4): (offsets int64[n_arcs + 1], cells
+    uint32), arcs ordered as the arc lists (2 per 1-saddle, then 2 per 2-saddle)."""
+    d = _dims(dims)
+    s1 = np.ascontiguousarray(s1, dtype=np.uint32)
+    s2 = np.ascontiguousarray(s2, dtype=np.uint32)
+    lib = _load()
+    h = lib.ora_arc_cells(_p(d), _p(pair), len(s1), _p(s1), len(s2), _p(s2))
+    try:
+        st = lib.ora_arc_status(h)
+        if st:
+            raise OracleError(st, "arc_cells")
+        offsets = np.empty(lib.ora_arc_count(h) + 1, dtype=np.int64)
+        cells = np.empty(lib.ora_arc_cells_size(h), dtype=np.uint32)
+        lib.ora_arc_copy(h, _p(offsets), _p(cells))
+    finally:
+        lib.ora_arc_free(h)
+    return offsets, cells
 
 
 def reachable(dims, pair):

@@ -638,6 +638,94 @@ int ora_max_arcs(const int64_t* dims, const uint32_t* cube_max, int64_t n2, cons
     return OK;
 }
 
+// Cells along the saddle-extremum arcs (Sec. 3.4 and Sec. 3.5 "Data structure"): the V-path
+// (Sec. 2.2) that each arc follows, walked from its saddle.  Arcs come in the order of the arc
+// lists: two per 1-saddle (its lower-coordinate vertex, then its upper one), then two per
+// 2-saddle (its cofacet cube on the - side, then the + side, of the quad's even axis).
+//   Descending: the 1-saddle, its vertex v, then alternately the edge v is paired with and that
+//   edge's other vertex, until a vertex that is not paired (a minimum).
+//   Ascending: the 2-saddle, its cofacet cube c, then alternately the quad c is paired with and
+//   the cube across that quad, until a cube that is not paired (a maximum); a quad with no cube
+//   across it ends the path there (R4: it leaves the domain); the 2-saddle alone when the cube
+//   on that side does not exist.
+struct ArcCells {
+    std::vector<int64_t> offsets;
+    std::vector<uint32_t> cells;
+    int status = OK;
+};
+
+void* ora_arc_cells(const int64_t* dims, const uint32_t* pair_of, int64_t n1, const uint32_t* s1, int64_t n2,
+                    const uint32_t* s2) {
+    ArcCells* res = new ArcCells();
+    if (!check_dims(dims) || !pair_of || (n1 > 0 && !s1) || (n2 > 0 && !s2)) {
+        res->status = ERR_ARG;
+        return res;
+    }
+    Grid g(dims, nullptr);
+    const int64_t limit = g.ncells();  // a longer walk would have to repeat a cell
+    res->offsets.push_back(0);
+    for (int64_t i = 0; i < n1; ++i) {
+        std::vector<int64_t> vs = g.vertices(int64_t(s1[i]));
+        if (vs.size() != 2) { res->status = ERR_ARG; return res; }
+        for (int side = 0; side < 2; ++side) {
+            int64_t v = side ? std::max(vs[0], vs[1]) : std::min(vs[0], vs[1]);
+            res->cells.push_back(s1[i]);
+            res->cells.push_back(uint32_t(g.vertex_cell(v)));
+            for (int64_t steps = 0;; ++steps) {
+                uint32_t e = pair_of[g.vertex_cell(v)];
+                if (e == NONE) break;  // a minimum
+                if (steps > limit) { res->status = ERR_INTERNAL; return res; }
+                int64_t w = -1;
+                for (int64_t u : g.vertices(int64_t(e)))
+                    if (u != v) w = u;
+                res->cells.push_back(e);
+                res->cells.push_back(uint32_t(g.vertex_cell(w)));
+                v = w;
+            }
+            res->offsets.push_back(int64_t(res->cells.size()));
+        }
+    }
+    for (int64_t i = 0; i < n2; ++i) {
+        int64_t cc[3];
+        g.coords(int64_t(s2[i]), cc[0], cc[1], cc[2]);
+        int axis = !(cc[0] & 1) ? 0 : (!(cc[1] & 1) ? 1 : 2);
+        for (int side = 0; side < 2; ++side) {
+            res->cells.push_back(s2[i]);
+            int64_t d[3] = {cc[0], cc[1], cc[2]};
+            d[axis] += side ? 1 : -1;
+            if (g.inside(d[0], d[1], d[2])) {
+                int64_t c = g.cell(d[0], d[1], d[2]);
+                res->cells.push_back(uint32_t(c));
+                for (int64_t steps = 0;; ++steps) {
+                    uint32_t q = pair_of[c];
+                    if (q == NONE) break;  // a maximum
+                    if (steps > limit) { res->status = ERR_INTERNAL; return res; }
+                    res->cells.push_back(q);
+                    int64_t cx, cy, cz, qx, qy, qz;
+                    g.coords(c, cx, cy, cz);
+                    g.coords(int64_t(q), qx, qy, qz);
+                    int64_t ax = 2 * qx - cx, ay = 2 * qy - cy, az = 2 * qz - cz;  // across the quad
+                    if (!g.inside(ax, ay, az)) break;  // R4: the path leaves the domain here
+                    c = g.cell(ax, ay, az);
+                    res->cells.push_back(uint32_t(c));
+                }
+            }
+            res->offsets.push_back(int64_t(res->cells.size()));
+        }
+    }
+    return res;
+}
+
+int ora_arc_status(void* h) { return static_cast<ArcCells*>(h)->status; }
+int64_t ora_arc_count(void* h) { return int64_t(static_cast<ArcCells*>(h)->offsets.size()) - 1; }
+int64_t ora_arc_cells_size(void* h) { return int64_t(static_cast<ArcCells*>(h)->cells.size()); }
+void ora_arc_copy(void* h, int64_t* offsets, uint32_t* cells) {
+    ArcCells* r = static_cast<ArcCells*>(h);
+    std::copy(r->offsets.begin(), r->offsets.end(), offsets);
+    std::copy(r->cells.begin(), r->cells.end(), cells);
+}
+void ora_arc_free(void* h) { delete static_cast<ArcCells*>(h); }
+
 // Saddle-saddle reachability (Sec. 3.2): multi-source BFS over the DAG from all 1-saddles.
 // visited[v] bit a (a = 0,1,2) marks the 1-cell of vertex v along axis a as reachable
 // (the 1-saddles themselves included).  Returns the number of non-empty BFS levels

@@ -33,6 +33,8 @@ MUTANTS = [
     ("junction_threshold", "if (dag_out(g, pair_of, c).size() > 1) {", "if (dag_out(g, pair_of, c).size() > 0) {"),
     ("dead_paths_kept", "                if (nxt.empty()) break;  // dead path",
      "                if (nxt.empty()) { mn->m[u_is_saddle ? 3 : 2][{urank, 0}] += 1; break; }"),
+    ("arc_walk_repeats_the_vertex", "                res->cells.push_back(uint32_t(g.vertex_cell(w)));\n                v = w;",
+     "                res->cells.push_back(uint32_t(g.vertex_cell(v)));\n                v = w;"),
     ("packed_codes_x_sides_swapped", "    if (bx == ax - 1) return 1;\n    if (bx == ax + 1) return 2;",
      "    if (bx == ax - 1) return 2;\n    if (bx == ax + 1) return 1;"),
 ]
@@ -50,6 +52,7 @@ def _run_pins():
     checks += [lambda s=s: pins.test_reachable_and_junctions(s) for s in range(2)]
     checks.append(pins.test_cosine_lattice_counts)
     checks += [lambda s=s: pins.test_packed_words_decode_to_the_gradient_pairs(s) for s in range(2)]
+    checks += [lambda s=s: pins.test_arc_cells_are_the_v_paths_of_the_arcs(s) for s in range(2)]
     failed = 0
     for c in checks:
         try:

@@ -447,6 +447,93 @@ def test_packed_words_decode_to_the_gradient_pairs(seed):
         assert np.array_equal(partners, pair[cells].astype(np.int64))
 
 
+def _cell_coords(dims, c):
+    nx, ny, nz = dims
+    rx, ry = 2 * nx - 1, 2 * ny - 1
+    return (int(c) % rx, (int(c) // rx) % ry, int(c) // (rx * ry))
+
+
+def _facets(dims, c):
+    """Facets of a cell by the definition: move one odd coordinate by -1 or +1."""
+    nx, ny, nz = dims
+    rx, ry = 2 * nx - 1, 2 * ny - 1
+    cc = _cell_coords(dims, c)
+    out = set()
+    for a in range(3):
+        if cc[a] % 2:
+            for s in (-1, 1):
+                d = list(cc)
+                d[a] += s
+                out.add(d[0] + rx * (d[1] + ry * d[2]))
+    return out
+
+
+def _dim(dims, c):
+    return sum(v % 2 for v in _cell_coords(dims, c))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_arc_cells_are_the_v_paths_of_the_arcs(seed):
+    """Every arc's cells form the V-path of Sec. 2.2 between its saddle and its extremum: a
+    descending path alternates a vertex and the edge it is paired with, each next vertex being the
+    other facet of that edge; an ascending path alternates a cube and the quad it is paired with
+    (a facet of the cube), each next cube being the other cofacet of that quad.  Paths end at an
+    unpaired extremum equal to the arc lists' endpoint, or, ascending, at a quad with no cube beyond
+    it (endpoint NONE); no cell repeats."""
+    shapes = [(5, 6, 7), (3, 9, 4), (8, 8, 2), (2, 5, 11)]
+    for kind in ("normal", "ties"):
+        f = random_field(shapes[seed], 400 + seed, kind)
+        dims = (f.shape[2], f.shape[1], f.shape[0])
+        nx, ny, nz = dims
+        rx, ry, rz = 2 * nx - 1, 2 * ny - 1, 2 * nz - 1
+        pair = oracle.gradient(f)
+        _, lists = oracle.critical(dims, pair)
+        _, _, amin, amax = oracle.extremum(dims, pair, lists[1], lists[2])
+        off, cells = oracle.arc_cells(dims, pair, lists[1], lists[2])
+        n1, n2 = len(lists[1]), len(lists[2])
+        assert len(off) == 2 * (n1 + n2) + 1 and off[-1] == len(cells)
+        NONE = 0xFFFFFFFF
+        for a in range(2 * (n1 + n2)):
+            path = [int(c) for c in cells[off[a]:off[a + 1]]]
+            assert len(set(path)) == len(path)
+            if a < 2 * n1:
+                e = int(lists[1][a // 2])
+                assert path[0] == e and len(path) % 2 == 0
+                lo, hi = sorted(_facets(dims, e))
+                assert path[1] == (hi if a % 2 else lo)  # lower-coordinate vertex first
+                for k in range(1, len(path) - 1, 2):
+                    v, ed, w = path[k], path[k + 1], path[k + 2]
+                    assert _dim(dims, v) == 0 and int(pair[v]) == ed
+                    assert w in _facets(dims, ed) and w != v
+                assert int(pair[path[-1]]) == NONE and path[-1] == int(amin[a])
+            else:
+                b = a - 2 * n1
+                q = int(lists[2][b // 2])
+                assert path[0] == q
+                if len(path) == 1:  # no cube on that side
+                    assert int(amax[b]) == NONE
+                    continue
+                assert q in _facets(dims, path[1])
+                qc = _cell_coords(dims, q)
+                axis = [qc[i] % 2 for i in range(3)].index(0)
+                assert _cell_coords(dims, path[1])[axis] - qc[axis] == (1 if b % 2 else -1)
+                for k in range(1, len(path) - 1, 2):
+                    c, quad = path[k], path[k + 1]
+                    assert _dim(dims, c) == 3 and int(pair[c]) == quad and quad in _facets(dims, c)
+                    if k + 2 < len(path):
+                        nxt = path[k + 2]
+                        assert quad in _facets(dims, nxt) and nxt != c
+                last = path[-1]
+                if _dim(dims, last) == 3:
+                    assert int(pair[last]) == NONE and last == int(amax[b])
+                else:  # left the domain through this quad: it has one cofacet cube
+                    lc = _cell_coords(dims, last)
+                    ext = (rx, ry, rz)
+                    even = [i for i in range(3) if lc[i] % 2 == 0][0]
+                    inside = [0 <= lc[even] + s < ext[even] for s in (-1, 1)]
+                    assert sum(inside) == 1 and int(amax[b]) == NONE
+
+
 def test_packed_at_matches_full_pack():
     f = fields.grf((9, 10, 11), 3.0, seed=9)
     pair = oracle.gradient(f)
