@@ -231,6 +231,25 @@ msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nn
 msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
                              int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult);
 
+/* ---- the cells along the saddle-extremum arcs (on request) -----------------------------
+ * Sec. 3.4 and Sec. 3.5 "Data structure": besides its end points, each saddle-extremum arc has a
+ * geometry, the V-path (Sec. 2.2) it follows from its saddle.  Arcs are numbered as the arc lists:
+ * arc 2i and 2i+1 (i < counts[1]) start at the 1-saddle of rank i, from its lower-coordinate and
+ * upper-coordinate vertex (as d_min_arcs); arc 2*counts[1] + 2j + s starts at the 2-saddle of rank j,
+ * into its cofacet cube on the - (s = 0) or + (s = 1) side of its even axis (as d_max_arcs).
+ *   Descending arc: the 1-saddle, its vertex, then alternately the edge that vertex is paired with
+ *     and that edge's other vertex, ending at the minimum.
+ *   Ascending arc: the 2-saddle, the cube, then alternately the quad the cube is paired with and the
+ *     cube across that quad, ending at the maximum -- or at the quad through which the path leaves
+ *     the domain (the arc's maximum is NONE), or at the 2-saddle alone when that side has no cube.
+ * Arc a's cells are d_cells[d_offsets[a] .. d_offsets[a+1]) (cell ids).  *n_arcs = 2*(counts[1] +
+ * counts[2]); d_offsets has n_arcs+1 int64 entries; *n_cells = d_offsets[n_arcs].  Built on the
+ * first call after a pass (host-synchronised: a thread per arc walks the gradient words to count,
+ * a scan, a second walk to write) and kept until the next pass.  Plan-owned.  Any output pointer may
+ * be null. */
+msc_status msc_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_arcs, int64_t* n_cells,
+                            const int64_t** d_offsets, const uint32_t** d_cells);
+
 /* ---- outputs into host memory --------------------------------------------------------
  * Sec. 3.5 "Data structure": the complex is assembled on the host from the arrays the GPU
  * stages produce.  This copies one of those arrays into caller-owned host memory, computing the stage if
@@ -240,6 +259,7 @@ msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_no
  *   MSC_OUT_VERTEX_MIN     minimum of every vertex (uint32)     MSC_OUT_CUBE_MAX  maximum of every cube (uint32)
  *   MSC_OUT_DSTAR_ROWPTR   D* row pointers (int64, counts[1]+1) MSC_OUT_DSTAR_COL columns (uint32, nnz)
  *   MSC_OUT_DSTAR_COUNT    path counts (uint64, nnz)
+ *   MSC_OUT_ARC_OFFSETS    arc geometry offsets (int64, n_arcs+1)  MSC_OUT_ARC_CELLS  cells along the arcs (uint32)
  * Size query: *bytes on entry is the room in h_out; on return it is the output's size in bytes.
  * With h_out null nothing is copied.  Otherwise the copy is made and the stream synchronised;
  * MSC_ERR_CAPACITY (nothing copied) if the room is smaller.  MSC_ERR_ARG for an unknown `what`. */
@@ -254,7 +274,9 @@ enum {
     MSC_OUT_CUBE_MAX = 7,
     MSC_OUT_DSTAR_ROWPTR = 8,
     MSC_OUT_DSTAR_COL = 9,
-    MSC_OUT_DSTAR_COUNT = 10
+    MSC_OUT_DSTAR_COUNT = 10,
+    MSC_OUT_ARC_OFFSETS = 11,
+    MSC_OUT_ARC_CELLS = 12
 };
 msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void* h_out, int64_t* bytes);
 

@@ -199,6 +199,7 @@ msc_status bind_device(Plan* p) {
 void invalidate(Plan* p) {
     p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = false;
     p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = p->have_dstar_csc = p->have_graph = false;
+    p->have_geometry = false;
 }
 
 // Host mirrors and statistics from the summary last copied to p->hsum.
@@ -675,6 +676,31 @@ msc_status msc_saddle_arcs_csc(msc_plan_t plan, msc_stream_t stream, int64_t* nn
     return MSC_OK;
 }
 
+static msc_status ensure_geometry(Plan* p, cudaStream_t s) {
+    msc_status st;
+    if ((st = ensure_critical(p, s))) return st;
+    if (p->have_geometry) return MSC_OK;
+    if ((st = msc::build_arc_geometry(p, s))) return st;
+    if ((st = msc::finish_stage(p, s))) return st;
+    p->have_geometry = true;
+    return MSC_OK;
+}
+
+msc_status msc_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_arcs, int64_t* n_cells,
+                            const int64_t** d_offsets, const uint32_t** d_cells) {
+    if (!plan) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    if ((st = ensure_geometry(p, s))) return st;
+    if (n_arcs) *n_arcs = 2 * (p->counts[1] + p->counts[2]);
+    if (n_cells) *n_cells = p->geo_cells_n;
+    if (d_offsets) *d_offsets = static_cast<const int64_t*>(p->geo_off.ptr);
+    if (d_cells) *d_cells = static_cast<const uint32_t*>(p->geo_cells.ptr);
+    return MSC_OK;
+}
+
 msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
                              int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult) {
     if (!plan || !n_nodes || !n_adj) return MSC_ERR_ARG;
@@ -773,7 +799,7 @@ msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t strea
 }
 
 msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void* h_out, int64_t* bytes) {
-    if (!plan || !bytes || what < MSC_OUT_CELLS0 || what > MSC_OUT_DSTAR_COUNT) return MSC_ERR_ARG;
+    if (!plan || !bytes || what < MSC_OUT_CELLS0 || what > MSC_OUT_ARC_CELLS) return MSC_ERR_ARG;
     Plan* p = plan;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     msc_status st;
@@ -791,6 +817,12 @@ msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void
         const int64_t len[4] = {2 * p->counts[1], 2 * p->counts[2], nv, nv};
         src = b[what - MSC_OUT_MIN_ARCS]->ptr;
         n = int64_t(sizeof(uint32_t)) * len[what - MSC_OUT_MIN_ARCS];
+    } else if (what >= MSC_OUT_ARC_OFFSETS) {
+        if ((st = ensure_geometry(p, s))) return st;
+        const int64_t n_arcs = 2 * (p->counts[1] + p->counts[2]);
+        src = what == MSC_OUT_ARC_OFFSETS ? p->geo_off.ptr : p->geo_cells.ptr;
+        n = what == MSC_OUT_ARC_OFFSETS ? int64_t(sizeof(int64_t)) * (n_arcs + 1)
+                                        : int64_t(sizeof(uint32_t)) * p->geo_cells_n;
     } else {
         if ((st = ensure_dstar(p, s))) return st;
         if (what == MSC_OUT_DSTAR_ROWPTR) {

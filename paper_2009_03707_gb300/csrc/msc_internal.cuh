@@ -95,6 +95,7 @@ struct Plan {
     DeviceBuffer dstar_rowptr, dstar_col, dstar_count;
     DeviceBuffer csc_colptr, csc_row, csc_count, csc_work;  // D* by 2-saddle (transpose.cu)
     DeviceBuffer graph_nodeptr, graph_adj, graph_mult, graph_work, graph_none;  // the 1-skeleton (graph.cu)
+    DeviceBuffer geo_len, geo_off, geo_scan, geo_cells;  // cells along the saddle-extremum arcs (geometry.cu)
     DeviceBuffer dp_pend, dp_in_cnt, dp_in_ptr, dp_in_idx, dp_j_off, dp_j_len, dp_pool_col, dp_pool_cnt, dp_long, dp_chunks;
 
     template <class F>
@@ -108,7 +109,8 @@ struct Plan {
                                &pc_big, &pc_col, &pc_cnt, &pc_gk, &pc_gv, &pc_gocc, &dstar_rowptr, &dstar_col,
                                &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
                                &dp_j_len, &dp_pool_col, &dp_pool_cnt, &dp_long, &dp_chunks, &csc_colptr, &csc_row, &csc_count, &csc_work,
-                               &graph_nodeptr, &graph_adj, &graph_mult, &graph_work, &graph_none};
+                               &graph_nodeptr, &graph_adj, &graph_mult, &graph_work, &graph_none,
+                               &geo_len, &geo_off, &geo_scan, &geo_cells};
         for (DeviceBuffer* b : all) f(*b);
     }
 
@@ -154,8 +156,9 @@ struct Plan {
     // which stages are valid for the current field
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
          have_junctions = false, have_trace = false, have_minor = false, have_dstar = false,
-         have_dstar_csc = false, have_graph = false;
+         have_dstar_csc = false, have_graph = false, have_geometry = false;
     int64_t graph_nodes = 0, graph_nadj = 0;
+    int64_t geo_cells_n = 0;  // cells along all arcs (geometry.cu)
     cudaEvent_t kev0 = nullptr, kev1 = nullptr;  // around the tier-0 path-count kernel
     cudaEvent_t tev0 = nullptr, tev1 = nullptr;  // around the trace kernel
     cudaEvent_t gev0 = nullptr, gev1 = nullptr;  // around the lower-star kernel
@@ -226,6 +229,7 @@ msc_status build_minor_csr(Plan* p, cudaStream_t s);  // CSR of A, B, B*, D (on 
 msc_status run_path_count(Plan* p, cudaStream_t s);
 msc_status build_dstar_csc(Plan* p, cudaStream_t s);  // D* by 2-saddle (on request; syncs)
 msc_status build_complex_graph(Plan* p, cudaStream_t s);  // the 1-skeleton adjacency (on request; syncs)
+msc_status build_arc_geometry(Plan* p, cudaStream_t s);   // cells along the saddle-extremum arcs (on request; syncs)
 msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t out_cap);
 int grid_cap(const Plan* p, int64_t threads, int block, int per_sm = 8);  // grid for a count-bounded loop
 

@@ -43,6 +43,7 @@ SIGNATURES = {
     "msc_saddle_arcs": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_complex_graph": ([_P, _P, _PI64, _PI64, _P, _P, _P], _I32),
+    "msc_arc_geometry": ([_P, _P, _PI64, _PI64, _PP, _PP], _I32),
     "msc_compute_async": ([_P, _P, _P], _I32),
     "msc_copy_to_host": ([_P, _P, _I32, _P, _PI64], _I32),
     "msc_compute_wait": ([_P], _I32),
@@ -250,6 +251,16 @@ def msc_saddle_arcs_csc(plan: Plan):
             _view(cnt.value, (nnz.value,), "<u8"))
 
 
+def msc_arc_geometry(plan: Plan):
+    """The cells along every saddle-extremum arc: (offsets [n_arcs+1] int64, cells [n_cells] uint32),
+    arcs numbered as the arc lists (2 per 1-saddle, then 2 per 2-saddle)."""
+    n_arcs, n_cells = ctypes.c_int64(), ctypes.c_int64()
+    off, cells = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.msc_arc_geometry(plan.handle, _stream(), ctypes.byref(n_arcs), ctypes.byref(n_cells), ctypes.byref(off),
+                                ctypes.byref(cells)), plan.handle)
+    return _view(off.value, (n_arcs.value + 1,), "<i8"), _view(cells.value, (n_cells.value,), "<u4")
+
+
 def msc_complex_graph(plan: Plan):
     """The 1-skeleton on the host: (nodeptr [n_nodes+1] int64, adj [n_adj] uint32, mult [n_adj]
     uint64) over nodes numbered minima, 1-saddles, 2-saddles, maxima."""
@@ -276,7 +287,7 @@ def msc_compute(plan: Plan, field: torch.Tensor) -> None:
 MSC_OUT = {"cells0": (0, np.uint32), "cells1": (1, np.uint32), "cells2": (2, np.uint32), "cells3": (3, np.uint32),
            "min_arcs": (4, np.uint32), "max_arcs": (5, np.uint32), "vertex_min": (6, np.uint32),
            "cube_max": (7, np.uint32), "dstar_rowptr": (8, np.int64), "dstar_col": (9, np.uint32),
-           "dstar_count": (10, np.uint64)}
+           "dstar_count": (10, np.uint64), "arc_offsets": (11, np.int64), "arc_cells": (12, np.uint32)}
 
 
 def msc_copy_to_host(plan: Plan, what: str) -> np.ndarray:
