@@ -84,6 +84,13 @@ _SIGNATURES = {
     "ora_arc_cells_size": ([ctypes.c_void_p], ctypes.c_int64),
     "ora_arc_copy": ([ctypes.c_void_p] * 3, None),
     "ora_arc_free": ([ctypes.c_void_p], None),
+    "ora_simplify": ([ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_void_p),
+    "ora_simplify_status": ([ctypes.c_void_p], ctypes.c_int),
+    "ora_simplify_cancelled": ([ctypes.c_void_p], ctypes.c_int64),
+    "ora_simplify_arcs": ([ctypes.c_void_p], ctypes.c_int64),
+    "ora_simplify_copy": ([ctypes.c_void_p] * 8, None),
+    "ora_simplify_free": ([ctypes.c_void_p], None),
 }
 
 
@@ -355,6 +362,64 @@ def complex_graph(counts, lists, min_arcs, max_arcs, dstar):
     nodeptr = np.zeros(n + 1, np.int64)
     np.add.at(nodeptr, uu + 1, 1)
     return np.cumsum(nodeptr), vv.astype(np.uint32), sums.astype(np.uint64)
+
+
+def cell_values(f: np.ndarray, cells) -> np.ndarray:
+    """Value of each cell (reading S1 of the simplification): the value of its highest vertex."""
+    nz, ny, nx = f.shape
+    rx, ry = 2 * nx - 1, 2 * ny - 1
+    c = np.asarray(cells, dtype=np.int64)
+    cx, cy, cz = c % rx, (c // rx) % ry, c // (rx * ry)
+    flat = np.ascontiguousarray(f, dtype=np.float32).reshape(-1)
+    best = np.full(len(c), -np.inf)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                x, y, z = (cx + dx * (cx & 1)) // 2, (cy + dy * (cy & 1)) // 2, (cz + dz * (cz & 1)) // 2
+                best = np.maximum(best, flat[x + nx * (y + ny * z)].astype(np.float64))
+    return best
+
+
+def skeleton(f: np.ndarray, e: dict | None = None) -> dict:
+    """The 1-skeleton of f as simplification input: nodes (critical cells numbered minima,
+    1-saddles, 2-saddles, maxima) with index, cell id and value, and arcs (u < v) with their
+    multiplicity (complex_graph's adjacency)."""
+    e = e or compute_all(f, with_minor=False)
+    counts, lists = e["counts"], e["lists"]
+    nodeptr, adj, mult = complex_graph(counts, lists, e["min_arcs"], e["max_arcs"], e["dstar"])
+    index = np.concatenate([np.full(int(counts[k]), k, np.int32) for k in range(4)])
+    cells = np.concatenate([np.asarray(lists[k], np.uint32) for k in range(4)])
+    u = np.repeat(np.arange(len(nodeptr) - 1, dtype=np.int64), np.diff(nodeptr))
+    keep = u < adj
+    return dict(index=index, cell=cells, value=cell_values(f, cells), arc_u=u[keep].astype(np.uint32),
+                arc_v=adj[keep].astype(np.uint32), arc_mult=mult[keep].astype(np.uint64))
+
+
+def simplify(sk: dict, threshold: float) -> dict:
+    """Persistence-ordered cancellation of the skeleton's single-arc pairs up to `threshold`
+    (Sec. 4; readings S1-S4 in the source).  Returns the cancellation log (upper node, lower node,
+    persistence, in order), the surviving nodes and the surviving arcs (u < v, multiplicity)."""
+    n = len(sk["index"])
+    index = np.ascontiguousarray(sk["index"], np.int32)
+    value = np.ascontiguousarray(sk["value"], np.float64)
+    cell = np.ascontiguousarray(sk["cell"], np.uint32)
+    au = np.ascontiguousarray(sk["arc_u"], np.uint32)
+    av = np.ascontiguousarray(sk["arc_v"], np.uint32)
+    am = np.ascontiguousarray(sk["arc_mult"], np.uint64)
+    lib = _load()
+    h = lib.ora_simplify(n, _p(index), _p(value), _p(cell), len(au), _p(au), _p(av), _p(am), float(threshold))
+    try:
+        st = lib.ora_simplify_status(h)
+        if st:
+            raise OracleError(st, "simplify")
+        k, m = lib.ora_simplify_cancelled(h), lib.ora_simplify_arcs(h)
+        up, lo, pers = np.empty(k, np.uint32), np.empty(k, np.uint32), np.empty(k, np.float64)
+        alive = np.empty(n, np.uint8)
+        u, v, mult = np.empty(m, np.uint32), np.empty(m, np.uint32), np.empty(m, np.uint64)
+        lib.ora_simplify_copy(h, _p(up), _p(lo), _p(pers), _p(alive), _p(u), _p(v), _p(mult))
+    finally:
+        lib.ora_simplify_free(h)
+    return dict(upper=up, lower=lo, persistence=pers, alive=alive.astype(bool), arc_u=u, arc_v=v, arc_mult=mult)
 
 
 # ---- sampled queries on large volumes (pairs computed lazily, one lower star at a time) ----

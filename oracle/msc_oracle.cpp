@@ -45,6 +45,7 @@
 #include <set>
 #include <unordered_map>
 #include <unordered_set>
+#include <tuple>
 #include <vector>
 
 namespace {
@@ -1086,5 +1087,122 @@ void* ora_lazy_dstar_rows(const int64_t* dims, const float* f, int64_t n, const 
     if (lp.status) res->status = lp.status;
     return res;
 }
+
+// ---------------------------------------------------------------------------------
+// Persistence-ordered simplification of the 1-skeleton (Sec. 4 "Parallel Simplification",
+// "Grid subdivision": the cancellation it performs in each subgrid, here serially over the whole
+// complex).  Nodes are critical cells with their index (dimension) and value; an arc joins
+// nodes of consecutive index and carries a multiplicity (the number of gradient paths).
+//   S1 value of a critical cell = the value of its highest vertex (the vertex whose lower star
+//      holds it); persistence of an arc = value(upper) - value(lower), never negative for an arc
+//      of the complex, taken as an absolute difference here.
+//   S2 a pair (p, q), index(p) = index(q) + 1, may be cancelled iff both are alive and exactly one
+//      arc joins them (several arcs: a strangulation, Sec. 4).
+//   S3 order: the least valid arc by (persistence, cell id of its upper node, cell id of its lower
+//      node) is cancelled next, while its persistence <= threshold.
+//   S4 cancelling (p, q): every node a joined to p by m_pa arcs (a != q, index(q)) and every node
+//      b joined to q by m_qb arcs (b != p, index(p)) gain m_pa * m_qb arcs between b and a (the
+//      descending arcs of p rerouted to the ends of the ascending arcs of q); then p, q and all
+//      their arcs are removed.  Multiplicities are exact uint64 (an overflow is status 6).
+// A multiplicity only grows while its arc lives, so an arc that is not valid when it is the least
+// one never becomes valid later: a key-ordered set with lazy deletion gives exactly "repeatedly
+// cancel the least valid arc".
+struct Simplified {
+    std::vector<uint32_t> log_upper, log_lower;  // cancelled pairs, in order (node indices)
+    std::vector<double> log_persistence;
+    std::vector<uint32_t> arc_u, arc_v;          // surviving arcs, u < v (node indices)
+    std::vector<uint64_t> arc_mult;
+    std::vector<uint8_t> alive;
+    int status = OK;
+};
+
+void* ora_simplify(int64_t n_nodes, const int32_t* index, const double* value, const uint32_t* cell,
+                   int64_t n_arcs, const uint32_t* arc_u, const uint32_t* arc_v, const uint64_t* arc_mult,
+                   double threshold) {
+    Simplified* res = new Simplified();
+    if (n_nodes < 0 || n_arcs < 0 || (n_nodes > 0 && (!index || !value || !cell)) ||
+        (n_arcs > 0 && (!arc_u || !arc_v || !arc_mult))) {
+        res->status = ERR_ARG;
+        return res;
+    }
+    std::vector<std::map<int64_t, uint64_t>> adj(static_cast<size_t>(n_nodes));
+    for (int64_t i = 0; i < n_arcs; ++i) {
+        const int64_t u = arc_u[i], v = arc_v[i];
+        if (u < 0 || v < 0 || u >= n_nodes || v >= n_nodes || u == v || std::abs(index[u] - index[v]) != 1) {
+            res->status = ERR_ARG;
+            return res;
+        }
+        adj[size_t(u)][v] += arc_mult[i];
+        adj[size_t(v)][u] += arc_mult[i];
+    }
+    std::vector<uint8_t> alive(size_t(n_nodes), 1);
+    // key: (persistence, upper cell, lower cell) -> (upper node, lower node)
+    using Key = std::tuple<double, uint32_t, uint32_t, int64_t, int64_t>;
+    auto key_of = [&](int64_t a, int64_t b) {
+        const int64_t up = index[a] > index[b] ? a : b, lo = up == a ? b : a;
+        return Key(std::fabs(value[up] - value[lo]), cell[up], cell[lo], up, lo);
+    };
+    std::set<Key> queue;
+    for (int64_t u = 0; u < n_nodes; ++u)
+        for (const auto& kv : adj[size_t(u)])
+            if (u < kv.first) queue.insert(key_of(u, kv.first));
+    while (!queue.empty()) {
+        const Key k = *queue.begin();
+        queue.erase(queue.begin());
+        if (std::get<0>(k) > threshold) break;
+        const int64_t p = std::get<3>(k), q = std::get<4>(k);
+        if (!alive[size_t(p)] || !alive[size_t(q)]) continue;
+        auto it = adj[size_t(p)].find(q);
+        if (it == adj[size_t(p)].end() || it->second != 1) continue;  // S2
+        std::vector<std::pair<int64_t, uint64_t>> down, up;
+        for (const auto& kv : adj[size_t(p)])
+            if (kv.first != q && index[kv.first] == index[q]) down.push_back(kv);
+        for (const auto& kv : adj[size_t(q)])
+            if (kv.first != p && index[kv.first] == index[p]) up.push_back(kv);
+        for (const auto& a : down)
+            for (const auto& b : up) {
+                const uint64_t add = a.second * b.second;
+                if (b.second != 0 && add / b.second != a.second) { res->status = ERR_OVERFLOW; return res; }
+                uint64_t& m = adj[size_t(b.first)][a.first];
+                if (m + add < m) { res->status = ERR_OVERFLOW; return res; }
+                m += add;
+                adj[size_t(a.first)][b.first] = m;
+                queue.insert(key_of(b.first, a.first));
+            }
+        for (int64_t x : {p, q}) {
+            for (const auto& kv : adj[size_t(x)]) adj[size_t(kv.first)].erase(x);
+            adj[size_t(x)].clear();
+            alive[size_t(x)] = 0;
+        }
+        res->log_upper.push_back(uint32_t(p));
+        res->log_lower.push_back(uint32_t(q));
+        res->log_persistence.push_back(std::get<0>(k));
+    }
+    for (int64_t u = 0; u < n_nodes; ++u)
+        for (const auto& kv : adj[size_t(u)])
+            if (u < kv.first) {
+                res->arc_u.push_back(uint32_t(u));
+                res->arc_v.push_back(uint32_t(kv.first));
+                res->arc_mult.push_back(kv.second);
+            }
+    res->alive = alive;
+    return res;
+}
+
+int ora_simplify_status(void* h) { return static_cast<Simplified*>(h)->status; }
+int64_t ora_simplify_cancelled(void* h) { return int64_t(static_cast<Simplified*>(h)->log_upper.size()); }
+int64_t ora_simplify_arcs(void* h) { return int64_t(static_cast<Simplified*>(h)->arc_u.size()); }
+void ora_simplify_copy(void* h, uint32_t* log_upper, uint32_t* log_lower, double* log_persistence, uint8_t* alive,
+                       uint32_t* arc_u, uint32_t* arc_v, uint64_t* arc_mult) {
+    Simplified* r = static_cast<Simplified*>(h);
+    std::copy(r->log_upper.begin(), r->log_upper.end(), log_upper);
+    std::copy(r->log_lower.begin(), r->log_lower.end(), log_lower);
+    std::copy(r->log_persistence.begin(), r->log_persistence.end(), log_persistence);
+    std::copy(r->alive.begin(), r->alive.end(), alive);
+    std::copy(r->arc_u.begin(), r->arc_u.end(), arc_u);
+    std::copy(r->arc_v.begin(), r->arc_v.end(), arc_v);
+    std::copy(r->arc_mult.begin(), r->arc_mult.end(), arc_mult);
+}
+void ora_simplify_free(void* h) { delete static_cast<Simplified*>(h); }
 
 }  // extern "C"

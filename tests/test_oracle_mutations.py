@@ -35,6 +35,12 @@ MUTANTS = [
      "                if (nxt.empty()) { mn->m[u_is_saddle ? 3 : 2][{urank, 0}] += 1; break; }"),
     ("arc_walk_repeats_the_vertex", "                res->cells.push_back(uint32_t(g.vertex_cell(w)));\n                v = w;",
      "                res->cells.push_back(uint32_t(g.vertex_cell(v)));\n                v = w;"),
+    ("simplify_allows_strangulations", "if (it == adj[size_t(p)].end() || it->second != 1) continue;  // S2",
+     "if (it == adj[size_t(p)].end() || it->second < 1) continue;  // S2"),
+    ("simplify_reroutes_sum_not_product", "const uint64_t add = a.second * b.second;",
+     "const uint64_t add = a.second + b.second;"),
+    ("simplify_most_persistent_first", "const Key k = *queue.begin();\n        queue.erase(queue.begin());",
+     "const Key k = *std::prev(queue.end());\n        queue.erase(std::prev(queue.end()));"),
     ("packed_codes_x_sides_swapped", "    if (bx == ax - 1) return 1;\n    if (bx == ax + 1) return 2;",
      "    if (bx == ax - 1) return 2;\n    if (bx == ax + 1) return 1;"),
 ]
@@ -53,6 +59,8 @@ def _run_pins():
     checks.append(pins.test_cosine_lattice_counts)
     checks += [lambda s=s: pins.test_packed_words_decode_to_the_gradient_pairs(s) for s in range(2)]
     checks += [lambda s=s: pins.test_arc_cells_are_the_v_paths_of_the_arcs(s) for s in range(2)]
+    checks += [lambda s=s: pins.test_simplification_matches_brute_force_replay(s) for s in range(2)]
+    checks += [pins.test_simplification_two_wells_closed_form, pins.test_simplification_cosine_lattice_closed_form]
     failed = 0
     for c in checks:
         try:

@@ -572,3 +572,101 @@ def test_lazy_sampled_queries_equal_whole_volume(seed):
         visited = bool((vis[cz // 2, cy // 2, cx // 2] >> axis) & 1)
         assert (int(c) in jset) == (visited and node and not crit and deg > 1)
         assert crit == (r["pair"][c] == 0xFFFFFFFF)
+
+
+# ----------------------------------------------------------------------------------
+# persistence-ordered simplification (Sec. 4)
+# ----------------------------------------------------------------------------------
+def _replay_simplification(sk, threshold):
+    """Brute force, written from the cancellation rule: repeatedly take the least valid arc (consecutive
+    index, both ends alive, exactly one arc between them) by (persistence, upper cell, lower cell),
+    while its persistence <= threshold; reroute every descending neighbour a of the upper node p
+    (a != q) to every ascending neighbour b of the lower node q (b != p) with m(p,a) * m(q,b) new
+    arcs, then delete p and q.  Checks the Euler characteristic after every cancellation."""
+    index, value, cell = [int(i) for i in sk["index"]], [float(v) for v in sk["value"]], [int(c) for c in sk["cell"]]
+    n = len(index)
+    adj = [dict() for _ in range(n)]
+    for u, v, m in zip(sk["arc_u"], sk["arc_v"], sk["arc_mult"]):
+        u, v, m = int(u), int(v), int(m)
+        adj[u][v] = adj[u].get(v, 0) + m
+        adj[v][u] = adj[v].get(u, 0) + m
+    alive = [True] * n
+    euler = lambda: sum((-1) ** index[i] for i in range(n) if alive[i])
+    e0 = euler()
+    log = []
+    while True:
+        best = None
+        for p in range(n):
+            if not alive[p]:
+                continue
+            for q, m in adj[p].items():
+                if alive[q] and index[p] == index[q] + 1 and m == 1:
+                    key = (abs(value[p] - value[q]), cell[p], cell[q])
+                    if key[0] <= threshold and (best is None or key < best[0]):
+                        best = (key, p, q)
+        if best is None:
+            break
+        key, p, q = best
+        down = [(a, m) for a, m in adj[p].items() if a != q and index[a] == index[q]]
+        up = [(b, m) for b, m in adj[q].items() if b != p and index[b] == index[p]]
+        for a, ma in down:
+            for b, mb in up:
+                adj[b][a] = adj[b].get(a, 0) + ma * mb
+                adj[a][b] = adj[b][a]
+        for x in (p, q):
+            for y in list(adj[x]):
+                del adj[y][x]
+            adj[x].clear()
+            alive[x] = False
+        log.append((p, q, key[0]))
+        assert euler() == e0
+    arcs = sorted((u, v, m) for u in range(n) for v, m in adj[u].items() if u < v)
+    return log, alive, arcs
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_simplification_matches_brute_force_replay(seed):
+    shapes = [(4, 5, 6), (3, 7, 4), (6, 6, 2), (2, 5, 9)]
+    for kind in ("normal", "ties"):
+        f = random_field(shapes[seed], 500 + seed, kind)
+        sk = oracle.skeleton(f)
+        pers = np.abs(sk["value"][sk["arc_u"]] - sk["value"][sk["arc_v"]])
+        for threshold in (0.0, float(np.median(pers)) if len(pers) else 0.0, 1e9):
+            r = oracle.simplify(sk, threshold)
+            log, alive, arcs = _replay_simplification(sk, threshold)
+            assert [(int(a), int(b)) for a, b in zip(r["upper"], r["lower"])] == [(p, q) for p, q, _ in log]
+            assert np.allclose(r["persistence"], [x for _, _, x in log])
+            assert list(r["alive"]) == alive
+            assert sorted(zip(r["arc_u"].tolist(), r["arc_v"].tolist(), r["arc_mult"].tolist())) == arcs
+
+
+def test_simplification_two_wells_closed_form():
+    """Two parabolic wells along x, depths 0 and 10, meeting at x = 15 where the barrier is 49: the
+    complex is two minima and one 1-saddle, and the only pair, (saddle, the shallower minimum), has
+    persistence 49 - 10 = 39: it is cancelled exactly when the threshold reaches 39."""
+    x = np.arange(31)[None, None, :]
+    y = np.arange(9)[None, :, None]
+    z = np.arange(9)[:, None, None]
+    f = (np.minimum((x - 8.0) ** 2, (x - 22.0) ** 2 + 10.0) + (y - 4.0) ** 2 + (z - 4.0) ** 2).astype(np.float32)
+    sk = oracle.skeleton(f)
+    assert list(np.bincount(sk["index"], minlength=4)) == [2, 1, 0, 0]
+    r = oracle.simplify(sk, 38.999)
+    assert len(r["upper"]) == 0
+    r = oracle.simplify(sk, 39.0)
+    assert len(r["upper"]) == 1 and r["persistence"][0] == 39.0
+    assert sk["value"][r["lower"][0]] == 10.0 and sk["index"][r["upper"][0]] == 1
+    assert list(np.bincount(sk["index"][r["alive"]], minlength=4)) == [1, 0, 0, 0] and len(r["arc_u"]) == 0
+
+
+def test_simplification_cosine_lattice_closed_form():
+    """The cosine lattice's pairs differ by one cosine step, persistence 2 (up to its 1e-3 noise): below
+    it the complex stays (8, 12, 6, 1) with all its arcs; above it every pair cancels and a single
+    minimum is left, the complex of the box."""
+    f = fields.cosine_lattice()
+    sk = oracle.skeleton(f)
+    assert list(np.bincount(sk["index"], minlength=4)) == [8, 12, 6, 1]
+    r = oracle.simplify(sk, 1.99)
+    assert len(r["upper"]) == 0 and len(r["arc_u"]) == len(sk["arc_u"])
+    r = oracle.simplify(sk, 2.01)
+    assert len(r["upper"]) == 13 and np.all(np.abs(r["persistence"] - 2.0) < 2e-3)
+    assert list(np.bincount(sk["index"][r["alive"]], minlength=4)) == [1, 0, 0, 0] and len(r["arc_u"]) == 0
