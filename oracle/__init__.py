@@ -91,6 +91,10 @@ _SIGNATURES = {
     "ora_simplify_arcs": ([ctypes.c_void_p], ctypes.c_int64),
     "ora_simplify_copy": ([ctypes.c_void_p] * 8, None),
     "ora_simplify_free": ([ctypes.c_void_p], None),
+    "ora_simplify_rounds": ([ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_void_p),
+    "ora_simplify_rounds_count": ([ctypes.c_void_p], ctypes.c_int64),
+    "ora_simplify_rounds_of": ([ctypes.c_void_p, ctypes.c_void_p], None),
 }
 
 
@@ -395,10 +399,12 @@ def skeleton(f: np.ndarray, e: dict | None = None) -> dict:
                 arc_v=adj[keep].astype(np.uint32), arc_mult=mult[keep].astype(np.uint64))
 
 
-def simplify(sk: dict, threshold: float) -> dict:
+def simplify(sk: dict, threshold: float, rounds: bool = False) -> dict:
     """Persistence-ordered cancellation of the skeleton's single-arc pairs up to `threshold`
     (Sec. 4; readings S1-S4 in the source).  Returns the cancellation log (upper node, lower node,
-    persistence, in order), the surviving nodes and the surviving arcs (u < v, multiplicity)."""
+    persistence, in order), the surviving nodes and the surviving arcs (u < v, multiplicity).
+    rounds=True: in rounds of independent cancellations (reading S5), with each cancellation's
+    round in "round" and the number of rounds in "n_rounds"."""
     n = len(sk["index"])
     index = np.ascontiguousarray(sk["index"], np.int32)
     value = np.ascontiguousarray(sk["value"], np.float64)
@@ -407,7 +413,9 @@ def simplify(sk: dict, threshold: float) -> dict:
     av = np.ascontiguousarray(sk["arc_v"], np.uint32)
     am = np.ascontiguousarray(sk["arc_mult"], np.uint64)
     lib = _load()
-    h = lib.ora_simplify(n, _p(index), _p(value), _p(cell), len(au), _p(au), _p(av), _p(am), float(threshold))
+    fn = lib.ora_simplify_rounds if rounds else lib.ora_simplify
+    h = fn(n, _p(index), _p(value), _p(cell), len(au), _p(au), _p(av), _p(am), float(threshold))
+    extra = {}
     try:
         st = lib.ora_simplify_status(h)
         if st:
@@ -417,9 +425,14 @@ def simplify(sk: dict, threshold: float) -> dict:
         alive = np.empty(n, np.uint8)
         u, v, mult = np.empty(m, np.uint32), np.empty(m, np.uint32), np.empty(m, np.uint64)
         lib.ora_simplify_copy(h, _p(up), _p(lo), _p(pers), _p(alive), _p(u), _p(v), _p(mult))
+        if rounds:
+            rnd = np.empty(k, np.uint32)
+            lib.ora_simplify_rounds_of(h, _p(rnd))
+            extra = dict(round=rnd, n_rounds=int(lib.ora_simplify_rounds_count(h)))
     finally:
         lib.ora_simplify_free(h)
-    return dict(upper=up, lower=lo, persistence=pers, alive=alive.astype(bool), arc_u=u, arc_v=v, arc_mult=mult)
+    return dict(upper=up, lower=lo, persistence=pers, alive=alive.astype(bool), arc_u=u, arc_v=v, arc_mult=mult,
+                **extra)
 
 
 # ---- sampled queries on large volumes (pairs computed lazily, one lower star at a time) ----

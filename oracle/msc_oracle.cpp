@@ -1205,4 +1205,130 @@ void ora_simplify_copy(void* h, uint32_t* log_upper, uint32_t* log_lower, double
 }
 void ora_simplify_free(void* h) { delete static_cast<Simplified*>(h); }
 
+// ---------------------------------------------------------------------------------
+// Simplification in rounds of independent cancellations (the data-parallel scheme Sec. 4
+// "Discussion" describes: an independent set of arcs under the 3-link neighbourhood, cancelled
+// together).  Same keys (S3), validity (S2) and cancellation (S4) as ora_simplify; the order is:
+//   S5 a round cancels every valid arc (persistence <= threshold) whose key is the least among the
+//      valid arcs that have an endpoint within two links of one of its endpoints; rounds repeat
+//      until no valid arc is left.
+// Two arcs selected in one round are more than two links apart, so the nodes whose arcs each
+// cancellation changes (the two ends and their neighbours) are disjoint and the round's
+// cancellations do not depend on their order; the globally least valid arc is always selected.
+// The round structure is kept: round_of_log[i] is the round of the i-th cancellation.
+struct Rounds : Simplified {
+    std::vector<uint32_t> round_of_log;
+    int64_t rounds = 0;
+};
+
+void* ora_simplify_rounds(int64_t n_nodes, const int32_t* index, const double* value, const uint32_t* cell,
+                          int64_t n_arcs, const uint32_t* arc_u, const uint32_t* arc_v, const uint64_t* arc_mult,
+                          double threshold) {
+    Rounds* res = new Rounds();
+    if (n_nodes < 0 || n_arcs < 0 || (n_nodes > 0 && (!index || !value || !cell)) ||
+        (n_arcs > 0 && (!arc_u || !arc_v || !arc_mult))) {
+        res->status = ERR_ARG;
+        return res;
+    }
+    std::vector<std::map<int64_t, uint64_t>> adj(static_cast<size_t>(n_nodes));
+    for (int64_t i = 0; i < n_arcs; ++i) {
+        const int64_t u = arc_u[i], v = arc_v[i];
+        if (u < 0 || v < 0 || u >= n_nodes || v >= n_nodes || u == v || std::abs(index[u] - index[v]) != 1) {
+            res->status = ERR_ARG;
+            return res;
+        }
+        adj[size_t(u)][v] += arc_mult[i];
+        adj[size_t(v)][u] += arc_mult[i];
+    }
+    std::vector<uint8_t> alive(size_t(n_nodes), 1);
+    using Key = std::tuple<double, uint32_t, uint32_t>;
+    const Key NO_KEY(HUGE_VAL, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    while (true) {
+        // the valid arcs and, per node, the least key of the valid arcs incident on it
+        std::vector<std::tuple<Key, int64_t, int64_t>> valid;
+        std::vector<Key> m0(size_t(n_nodes), NO_KEY);
+        for (int64_t p = 0; p < n_nodes; ++p) {
+            if (!alive[size_t(p)]) continue;
+            for (const auto& kv : adj[size_t(p)]) {
+                const int64_t q = kv.first;
+                if (!alive[size_t(q)] || index[p] != index[q] + 1 || kv.second != 1) continue;
+                const double pers = std::fabs(value[p] - value[q]);
+                if (pers > threshold) continue;
+                const Key k(pers, cell[p], cell[q]);
+                valid.emplace_back(k, p, q);
+                m0[size_t(p)] = std::min(m0[size_t(p)], k);
+                m0[size_t(q)] = std::min(m0[size_t(q)], k);
+            }
+        }
+        if (valid.empty()) break;
+        // least key within one, then two links (closed neighbourhoods)
+        std::vector<Key> m1 = m0, m2;
+        for (int64_t u = 0; u < n_nodes; ++u)
+            for (const auto& kv : adj[size_t(u)]) m1[size_t(u)] = std::min(m1[size_t(u)], m0[size_t(kv.first)]);
+        m2 = m1;
+        for (int64_t u = 0; u < n_nodes; ++u)
+            for (const auto& kv : adj[size_t(u)]) m2[size_t(u)] = std::min(m2[size_t(u)], m1[size_t(kv.first)]);
+        std::vector<std::pair<int64_t, int64_t>> picked;
+        std::vector<std::tuple<Key, int64_t, int64_t>> chosen;
+        for (const auto& t : valid) {
+            const int64_t p = std::get<1>(t), q = std::get<2>(t);
+            if (std::get<0>(t) == std::min(m2[size_t(p)], m2[size_t(q)])) chosen.push_back(t);
+        }
+        // the footprints (both ends and their neighbours) must be disjoint
+        std::vector<uint8_t> touched(size_t(n_nodes), 0);
+        for (const auto& t : chosen) {
+            const int64_t p = std::get<1>(t), q = std::get<2>(t);
+            std::set<int64_t> fp{p, q};
+            for (const auto& kv : adj[size_t(p)]) fp.insert(kv.first);
+            for (const auto& kv : adj[size_t(q)]) fp.insert(kv.first);
+            for (int64_t x : fp) {
+                if (touched[size_t(x)]) { res->status = ERR_INTERNAL; return res; }
+                touched[size_t(x)] = 1;
+            }
+        }
+        for (const auto& t : chosen) {
+            const int64_t p = std::get<1>(t), q = std::get<2>(t);
+            std::vector<std::pair<int64_t, uint64_t>> down, up;
+            for (const auto& kv : adj[size_t(p)])
+                if (kv.first != q && index[kv.first] == index[q]) down.push_back(kv);
+            for (const auto& kv : adj[size_t(q)])
+                if (kv.first != p && index[kv.first] == index[p]) up.push_back(kv);
+            for (const auto& a : down)
+                for (const auto& b : up) {
+                    const uint64_t add = a.second * b.second;
+                    if (b.second != 0 && add / b.second != a.second) { res->status = ERR_OVERFLOW; return res; }
+                    uint64_t& m = adj[size_t(b.first)][a.first];
+                    if (m + add < m) { res->status = ERR_OVERFLOW; return res; }
+                    m += add;
+                    adj[size_t(a.first)][b.first] = m;
+                }
+            for (int64_t x : {p, q}) {
+                for (const auto& kv : adj[size_t(x)]) adj[size_t(kv.first)].erase(x);
+                adj[size_t(x)].clear();
+                alive[size_t(x)] = 0;
+            }
+            res->log_upper.push_back(uint32_t(p));
+            res->log_lower.push_back(uint32_t(q));
+            res->log_persistence.push_back(std::get<0>(std::get<0>(t)));
+            res->round_of_log.push_back(uint32_t(res->rounds));
+        }
+        ++res->rounds;
+    }
+    for (int64_t u = 0; u < n_nodes; ++u)
+        for (const auto& kv : adj[size_t(u)])
+            if (u < kv.first) {
+                res->arc_u.push_back(uint32_t(u));
+                res->arc_v.push_back(uint32_t(kv.first));
+                res->arc_mult.push_back(kv.second);
+            }
+    res->alive = alive;
+    return res;
+}
+
+int64_t ora_simplify_rounds_count(void* h) { return static_cast<Rounds*>(h)->rounds; }
+void ora_simplify_rounds_of(void* h, uint32_t* round_of_log) {
+    Rounds* r = static_cast<Rounds*>(h);
+    std::copy(r->round_of_log.begin(), r->round_of_log.end(), round_of_log);
+}
+
 }  // extern "C"

@@ -41,6 +41,8 @@ MUTANTS = [
      "const uint64_t add = a.second + b.second;"),
     ("simplify_most_persistent_first", "const Key k = *queue.begin();\n        queue.erase(queue.begin());",
      "const Key k = *std::prev(queue.end());\n        queue.erase(std::prev(queue.end()));"),
+    ("rounds_select_one_link_minima", "for (const auto& kv : adj[size_t(u)]) m2[size_t(u)] = std::min(m2[size_t(u)], m1[size_t(kv.first)]);",
+     "for (const auto& kv : adj[size_t(u)]) m2[size_t(u)] = std::min(m2[size_t(u)], m0[size_t(kv.first)]);"),
     ("packed_codes_x_sides_swapped", "    if (bx == ax - 1) return 1;\n    if (bx == ax + 1) return 2;",
      "    if (bx == ax - 1) return 2;\n    if (bx == ax + 1) return 1;"),
 ]
@@ -61,6 +63,7 @@ def _run_pins():
     checks += [lambda s=s: pins.test_arc_cells_are_the_v_paths_of_the_arcs(s) for s in range(2)]
     checks += [lambda s=s: pins.test_simplification_matches_brute_force_replay(s) for s in range(2)]
     checks += [pins.test_simplification_two_wells_closed_form, pins.test_simplification_cosine_lattice_closed_form]
+    checks += [lambda s=s: pins.test_simplification_rounds_match_brute_force_and_the_serial_order(s) for s in range(2)]
     failed = 0
     for c in checks:
         try:

@@ -670,3 +670,96 @@ def test_simplification_cosine_lattice_closed_form():
     r = oracle.simplify(sk, 2.01)
     assert len(r["upper"]) == 13 and np.all(np.abs(r["persistence"] - 2.0) < 2e-3)
     assert list(np.bincount(sk["index"][r["alive"]], minlength=4)) == [1, 0, 0, 0] and len(r["arc_u"]) == 0
+
+
+def _replay_rounds(sk, threshold):
+    """Brute force of the round rule: each round, the valid arcs whose key is the least among the valid
+    arcs with an endpoint within two links (breadth-first distances) of one of theirs are cancelled
+    together; their footprints (ends and neighbours) must be disjoint."""
+    index, value, cell = [int(i) for i in sk["index"]], [float(v) for v in sk["value"]], [int(c) for c in sk["cell"]]
+    n = len(index)
+    adj = [dict() for _ in range(n)]
+    for u, v, m in zip(sk["arc_u"], sk["arc_v"], sk["arc_mult"]):
+        u, v, m = int(u), int(v), int(m)
+        adj[u][v] = adj[u].get(v, 0) + m
+        adj[v][u] = adj[v].get(u, 0) + m
+    alive = [True] * n
+    rounds = []
+    while True:
+        valid = {}
+        for p in range(n):
+            for q, m in adj[p].items():
+                if alive[p] and alive[q] and index[p] == index[q] + 1 and m == 1:
+                    k = (abs(value[p] - value[q]), cell[p], cell[q])
+                    if k[0] <= threshold:
+                        valid[(p, q)] = k
+
+        def near(x):  # nodes within two links of x
+            seen, front = {x}, [x]
+            for _ in range(2):
+                front = [y for z in front for y in adj[z] if y not in seen]
+                seen.update(front)
+            return seen
+
+        chosen = []
+        for (p, q), k in valid.items():
+            zone = near(p) | near(q)
+            if all(k2 >= k for (a, b), k2 in valid.items() if a in zone or b in zone):
+                chosen.append((p, q))
+        if not chosen:
+            break
+        fps = [{p, q} | set(adj[p]) | set(adj[q]) for p, q in chosen]
+        assert sum(len(x) for x in fps) == len(set().union(*fps))
+        for p, q in chosen:
+            down = [(a, m) for a, m in adj[p].items() if a != q and index[a] == index[q]]
+            up = [(b, m) for b, m in adj[q].items() if b != p and index[b] == index[p]]
+            for a, ma in down:
+                for b, mb in up:
+                    adj[b][a] = adj[b].get(a, 0) + ma * mb
+                    adj[a][b] = adj[b][a]
+            for x in (p, q):
+                for y in list(adj[x]):
+                    del adj[y][x]
+                adj[x].clear()
+                alive[x] = False
+        rounds.append(sorted(chosen))
+    arcs = sorted((u, v, m) for u in range(n) for v, m in adj[u].items() if u < v)
+    return rounds, alive, arcs
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_simplification_rounds_match_brute_force_and_the_serial_order(seed):
+    """The round rule against its brute-force replay (round by round); on these fields it also ends
+    in exactly the complex that the serial order gives (same survivors, arcs and cancelled pairs)."""
+    shapes = [(4, 5, 6), (3, 7, 4), (6, 6, 3)]
+    for kind in ("normal", "ties"):
+        f = random_field(shapes[seed], 600 + seed, kind)
+        sk = oracle.skeleton(f)
+        pers = np.abs(sk["value"][sk["arc_u"]] - sk["value"][sk["arc_v"]])
+        for threshold in (0.0, float(np.median(pers)) if len(pers) else 0.0, 1e9):
+            r = oracle.simplify(sk, threshold, rounds=True)
+            rounds, alive, arcs = _replay_rounds(sk, threshold)
+            assert r["n_rounds"] == len(rounds)
+            got = [sorted((int(a), int(b)) for a, b, k in zip(r["upper"], r["lower"], r["round"]) if k == i)
+                   for i in range(r["n_rounds"])]
+            assert got == rounds
+            assert list(r["alive"]) == alive
+            assert sorted(zip(r["arc_u"].tolist(), r["arc_v"].tolist(), r["arc_mult"].tolist())) == arcs
+            s = oracle.simplify(sk, threshold)
+            assert np.array_equal(s["alive"], r["alive"])
+            assert set(zip(s["upper"].tolist(), s["lower"].tolist())) == set(zip(r["upper"].tolist(), r["lower"].tolist()))
+
+
+def test_simplification_rounds_closed_forms():
+    x = np.arange(31)[None, None, :]
+    y = np.arange(9)[None, :, None]
+    z = np.arange(9)[:, None, None]
+    f = (np.minimum((x - 8.0) ** 2, (x - 22.0) ** 2 + 10.0) + (y - 4.0) ** 2 + (z - 4.0) ** 2).astype(np.float32)
+    sk = oracle.skeleton(f)
+    assert len(oracle.simplify(sk, 38.999, rounds=True)["upper"]) == 0
+    r = oracle.simplify(sk, 39.0, rounds=True)
+    assert r["n_rounds"] == 1 and r["persistence"].tolist() == [39.0]
+    sk = oracle.skeleton(fields.cosine_lattice())
+    assert oracle.simplify(sk, 1.99, rounds=True)["n_rounds"] == 0
+    r = oracle.simplify(sk, 2.01, rounds=True)
+    assert len(r["upper"]) == 13 and list(np.bincount(sk["index"][r["alive"]], minlength=4)) == [1, 0, 0, 0]
