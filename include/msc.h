@@ -250,6 +250,38 @@ msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_no
 msc_status msc_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_arcs, int64_t* n_cells,
                             const int64_t** d_offsets, const uint32_t** d_cells);
 
+/* ---- simplification of the 1-skeleton (on request) --------------------------------------
+ * Sec. 4 "Parallel Simplification": critical-point pairs of consecutive index joined by exactly one
+ * arc are cancelled in order of persistence; a cancellation reroutes the upper point's descending
+ * arcs to the end points of the lower point's ascending arcs (multiplicities multiply) and deletes
+ * both points.  Pairs joined by several arcs are never cancelled (strangulations).  This runs the
+ * paper's data-parallel form on the GPU, in rounds: a round cancels every valid arc whose key
+ * (persistence, cell id of the upper point, cell id of the lower point) is the least among the valid
+ * arcs with an end within two links of one of its ends; those arcs are independent (their
+ * cancellations touch disjoint points), and rounds repeat until no arc with persistence <= threshold
+ * can be cancelled.  The value of a critical cell is the field's value at its highest vertex;
+ * persistence = |value(upper) - value(lower)|.
+ * d_field: the field of the plan's last pass (caller-owned; its values are read).  threshold >= 0
+ *   (absolute, in the field's units).
+ * The complex starts as msc_complex_graph's (built if needed; same node numbering) and is left
+ * unchanged there; the result is plan-owned until the next pass or simplification:
+ *   d_alive[n_nodes] (1 = survives), d_nodeptr[n_nodes+1] / d_adj[n_adj] / d_mult[n_adj] (CSR, every
+ *   arc in both rows, neighbours increasing), counts[4] (points left by index), d_log (3 uint32 per
+ *   cancellation in order: upper node, lower node, round).  Host-synchronised once per round.
+ *   MSC_ERR_OVERFLOW if a multiplicity exceeds 2^64 - 1; MSC_ERR_ITER_LIMIT after max_iterations
+ *   rounds. */
+typedef struct msc_simplified {
+    int64_t n_nodes, n_rounds, n_cancelled, n_adj;
+    int64_t counts[4];
+    const uint8_t* d_alive;
+    const int64_t* d_nodeptr;
+    const uint32_t* d_adj;
+    const uint64_t* d_mult;
+    const uint32_t* d_log;
+} msc_simplified;
+msc_status msc_simplify(msc_plan_t plan, msc_stream_t stream, const float* d_field, double threshold,
+                        msc_simplified* out);
+
 /* ---- outputs into host memory --------------------------------------------------------
  * Sec. 3.5 "Data structure": the complex is assembled on the host from the arrays the GPU
  * stages produce.  This copies one of those arrays into caller-owned host memory, computing the stage if

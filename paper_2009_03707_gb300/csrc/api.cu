@@ -701,13 +701,8 @@ msc_status msc_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_arc
     return MSC_OK;
 }
 
-msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
-                             int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult) {
-    if (!plan || !n_nodes || !n_adj) return MSC_ERR_ARG;
-    Plan* p = plan;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+static msc_status ensure_graph(Plan* p, cudaStream_t s) {
     msc_status st;
-    if ((st = msc::bind_device(p))) return st;
     if ((st = ensure_extremum(p, s))) return st;
     if ((st = ensure_dstar(p, s))) return st;
     if (!p->have_dstar_csc) {
@@ -720,6 +715,54 @@ msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_no
         if ((st = msc::finish_stage(p, s))) return st;
         p->have_graph = true;
     }
+    return MSC_OK;
+}
+
+msc_status msc_simplify(msc_plan_t plan, msc_stream_t stream, const float* d_field, double threshold,
+                        msc_simplified* out) {
+    if (!plan || !d_field || !out || !(threshold >= 0.0)) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    if ((st = ensure_graph(p, s))) return st;
+    if ((st = msc::run_simplify(p, d_field, threshold, s))) return st;
+    const int64_t n = p->graph_nodes;
+    const int c = p->simp_cur;
+    out->n_nodes = n;
+    out->n_rounds = p->simp_rounds;
+    out->n_cancelled = p->simp_cancelled;
+    out->n_adj = p->simp_nnz;
+    int64_t base[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k) {
+        base[k + 1] = base[k] + p->counts[k];
+        out->counts[k] = 0;
+    }
+    const uint8_t* alive = static_cast<const uint8_t*>(p->simp_alive.ptr) + size_t(c) * size_t(n ? n : 1);
+    if (n) {
+        std::vector<uint8_t> h(static_cast<size_t>(n));
+        if ((st = msc::check_cuda(p, cudaMemcpyAsync(h.data(), alive, size_t(n), cudaMemcpyDeviceToHost, s), "copy out")) ||
+            (st = msc::check_cuda(p, cudaStreamSynchronize(s), "stream sync")))
+            return st;
+        for (int k = 0; k < 4; ++k)
+            for (int64_t u = base[k]; u < base[k + 1]; ++u) out->counts[k] += h[size_t(u)];
+    }
+    out->d_alive = alive;
+    out->d_nodeptr = static_cast<const int64_t*>(p->simp_ptr[c].ptr);
+    out->d_adj = static_cast<const uint32_t*>(p->simp_nbr[c].ptr);
+    out->d_mult = static_cast<const uint64_t*>(p->simp_mult[c].ptr);
+    out->d_log = static_cast<const uint32_t*>(p->simp_log.ptr);
+    return MSC_OK;
+}
+
+msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_nodes, int64_t* n_adj,
+                             int64_t* h_nodeptr, uint32_t* h_adj, uint64_t* h_mult) {
+    if (!plan || !n_nodes || !n_adj) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    if ((st = ensure_graph(p, s))) return st;
     const int64_t room = *n_adj;
     *n_nodes = p->graph_nodes;
     *n_adj = p->graph_nadj;

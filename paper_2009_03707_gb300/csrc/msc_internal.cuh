@@ -96,6 +96,10 @@ struct Plan {
     DeviceBuffer csc_colptr, csc_row, csc_count, csc_work;  // D* by 2-saddle (transpose.cu)
     DeviceBuffer graph_nodeptr, graph_adj, graph_mult, graph_work, graph_none;  // the 1-skeleton (graph.cu)
     DeviceBuffer geo_len, geo_off, geo_scan, geo_cells;  // cells along the saddle-extremum arcs (geometry.cu)
+    // simplification (simplify.cu): node cells, values, alive (two copies), keys, per-node scratch,
+    // row lengths, log positions, scan scratch, two CSRs, the log, the per-round host read-out
+    DeviceBuffer simp_cell, simp_value, simp_alive, simp_keys, simp_node, simp_len, simp_pos, simp_scan;
+    DeviceBuffer simp_ptr[2], simp_nbr[2], simp_mult[2], simp_log, simp_round;
     DeviceBuffer dp_pend, dp_in_cnt, dp_in_ptr, dp_in_idx, dp_j_off, dp_j_len, dp_pool_col, dp_pool_cnt, dp_long, dp_chunks;
 
     template <class F>
@@ -110,7 +114,10 @@ struct Plan {
                                &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
                                &dp_j_len, &dp_pool_col, &dp_pool_cnt, &dp_long, &dp_chunks, &csc_colptr, &csc_row, &csc_count, &csc_work,
                                &graph_nodeptr, &graph_adj, &graph_mult, &graph_work, &graph_none,
-                               &geo_len, &geo_off, &geo_scan, &geo_cells};
+                               &geo_len, &geo_off, &geo_scan, &geo_cells, &simp_cell, &simp_value,
+                               &simp_alive, &simp_keys, &simp_node, &simp_len, &simp_pos, &simp_scan,
+                               &simp_ptr[0], &simp_ptr[1], &simp_nbr[0], &simp_nbr[1], &simp_mult[0],
+                               &simp_mult[1], &simp_log, &simp_round};
         for (DeviceBuffer* b : all) f(*b);
     }
 
@@ -159,6 +166,9 @@ struct Plan {
          have_dstar_csc = false, have_graph = false, have_geometry = false;
     int64_t graph_nodes = 0, graph_nadj = 0;
     int64_t geo_cells_n = 0;  // cells along all arcs (geometry.cu)
+    // the last simplification (simplify.cu): which CSR copy holds it, its size, rounds, cancellations
+    int simp_cur = 0;
+    int64_t simp_nnz = 0, simp_rounds = 0, simp_cancelled = 0;
     cudaEvent_t kev0 = nullptr, kev1 = nullptr;  // around the tier-0 path-count kernel
     cudaEvent_t tev0 = nullptr, tev1 = nullptr;  // around the trace kernel
     cudaEvent_t gev0 = nullptr, gev1 = nullptr;  // around the lower-star kernel
@@ -230,6 +240,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s);
 msc_status build_dstar_csc(Plan* p, cudaStream_t s);  // D* by 2-saddle (on request; syncs)
 msc_status build_complex_graph(Plan* p, cudaStream_t s);  // the 1-skeleton adjacency (on request; syncs)
 msc_status build_arc_geometry(Plan* p, cudaStream_t s);   // cells along the saddle-extremum arcs (on request; syncs)
+msc_status run_simplify(Plan* p, const float* d_field, double threshold, cudaStream_t s);  // (on request; syncs)
 msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t out_cap);
 int grid_cap(const Plan* p, int64_t threads, int block, int per_sm = 8);  // grid for a count-bounded loop
 

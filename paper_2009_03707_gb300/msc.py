@@ -44,6 +44,7 @@ SIGNATURES = {
     "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_complex_graph": ([_P, _P, _PI64, _PI64, _P, _P, _P], _I32),
     "msc_arc_geometry": ([_P, _P, _PI64, _PI64, _PP, _PP], _I32),
+    "msc_simplify": ([_P, _P, _P, ctypes.c_double, _P], _I32),
     "msc_compute_async": ([_P, _P, _P], _I32),
     "msc_copy_to_host": ([_P, _P, _I32, _P, _PI64], _I32),
     "msc_compute_wait": ([_P], _I32),
@@ -132,7 +133,7 @@ def _view(ptr, shape, typestr):
     for s in shape:
         n *= int(s)
     if n == 0 or not ptr:
-        dt = {"<u4": torch.uint32, "<u8": torch.uint64, "<i8": torch.int64}[typestr]
+        dt = {"<u4": torch.uint32, "<u8": torch.uint64, "<i8": torch.int64, "|u1": torch.uint8}[typestr]
         return torch.empty(tuple(int(s) for s in shape), dtype=dt, device="cuda")
     return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
 
@@ -259,6 +260,31 @@ def msc_arc_geometry(plan: Plan):
     _check(lib.msc_arc_geometry(plan.handle, _stream(), ctypes.byref(n_arcs), ctypes.byref(n_cells), ctypes.byref(off),
                                 ctypes.byref(cells)), plan.handle)
     return _view(off.value, (n_arcs.value + 1,), "<i8"), _view(cells.value, (n_cells.value,), "<u4")
+
+
+class MscSimplified(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_rounds", ctypes.c_int64), ("n_cancelled", ctypes.c_int64),
+                ("n_adj", ctypes.c_int64), ("counts", ctypes.c_int64 * 4), ("d_alive", ctypes.c_void_p),
+                ("d_nodeptr", ctypes.c_void_p), ("d_adj", ctypes.c_void_p), ("d_mult", ctypes.c_void_p),
+                ("d_log", ctypes.c_void_p)]
+
+
+def msc_simplify(plan: Plan, field: torch.Tensor, threshold: float) -> dict:
+    """Cancels critical-point pairs up to `threshold` (absolute persistence) on the GPU, in rounds of
+    independent cancellations; `field` is the plan's last pass's field.  Returns the counts left, the
+    rounds, and zero-copy views of the result (alive flags, CSR adjacency, cancellation log)."""
+    if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    if tuple(field.shape) != plan.shape_zyx:
+        raise ValueError(f"field shape {tuple(field.shape)} does not match the plan {plan.shape_zyx}")
+    o = MscSimplified()
+    _check(lib.msc_simplify(plan.handle, _stream(), ctypes.c_void_p(field.data_ptr()), float(threshold),
+                            ctypes.byref(o)), plan.handle)
+    n, nadj, k = o.n_nodes, o.n_adj, o.n_cancelled
+    return dict(counts=[int(c) for c in o.counts], n_rounds=int(o.n_rounds), n_cancelled=int(k),
+                alive=_view(o.d_alive, (n,), "|u1"), nodeptr=_view(o.d_nodeptr, (n + 1,), "<i8"),
+                adj=_view(o.d_adj, (nadj,), "<u4"), mult=_view(o.d_mult, (nadj,), "<u8"),
+                log=_view(o.d_log, (k, 3), "<u4"))
 
 
 def msc_complex_graph(plan: Plan):
