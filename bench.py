@@ -479,11 +479,14 @@ def run_gpu(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f)
     if world == 1 and args.workload == "grf256" and not args.no_legs:
-        # the other workloads of the metric, in the same run: the largest single volume, batched
-        # against one volume at a time, served against one request at a time
+        # the other workloads of the metric, in the same run: simplification of this pass's complex,
+        # the largest single volume, batched against one volume at a time, served against one
+        # request at a time
+        simp = leg_simplify(msc, torch, plan, d_field, f, uuid)
         del lanes, plan, d_field
         torch.cuda.empty_cache()
         line["legs"] = {
+            "simplify": simp,
             "blobs512": leg_single(msc, torch, "blobs512", steps=5, warmup=3, uuid=uuid),
             "batch64": leg_batch(msc, torch, steps=3, workers=args.workers, uuid=uuid),
             "serve": leg_serve(msc, torch, args.requests, args.workers, args.serve_budget, uuid),
@@ -508,6 +511,27 @@ def _events_ms(torch, fn, reps):
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
     return statistics.median(out)
+
+
+def leg_simplify(msc, torch, plan, d_field, f, uuid, frac=0.05, reps=3):
+    """Simplification of the pass's 1-skeleton at a persistence threshold of `frac` of the field's
+    range (the paper's 5 %), on the GPU in rounds of independent cancellations; timed by CUDA events
+    around msc_simplify (which synchronises once per round), median of reps."""
+    counts, _ = msc.msc_critical(plan)
+    threshold = frac * float(f.max() - f.min())
+    msc.msc_simplify(plan, d_field, threshold)  # builds the host-side graph once; warm
+    res = {}
+
+    def run():
+        res.update(msc.msc_simplify(plan, d_field, threshold))
+
+    with ClockSampler(uuid) as clk:
+        ms = _events_ms(torch, run, reps)
+    return {"threshold": threshold, "threshold_fraction_of_range": frac, "ms": ms, "rounds": res["n_rounds"],
+            "cancelled_pairs": res["n_cancelled"], "critical_before": counts, "critical_after": res["counts"],
+            "arcs_after": int(res["adj"].numel() // 2),
+            "how": "msc_simplify on the 256^3 pass's complex (rounds of independent least-key cancellations)",
+            "clocks": clk.summary()}
 
 
 def leg_single(msc, torch, name, steps, warmup, uuid):
