@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
     if (saw_nan) atomicOr(status, ST_NAN);
     __syncthreads();
 
-    // size every star (cheap mask arithmetic) and counting-sort the non-minimal ones (a ballot-based
-    // warp histogram instead of the per-vertex atomics measured slower)
+    // size every star (cheap mask arithmetic) and counting-sort the non-minimal ones by size, one shared
+    // atomic per vertex (a ballot-based warp histogram measured slower)
     for (int i = t; i < NOWN; i += THREADS) {
         const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
         uint32_t inL = 0;
