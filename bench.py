@@ -482,15 +482,20 @@ def run_gpu(args):
         # the other workloads of the metric, in the same run: simplification of this pass's complex,
         # the largest single volume, batched against one volume at a time, served against one
         # request at a time
-        simp = leg_simplify(msc, torch, plan, d_field, f, uuid)
+        legs = {}
+        want = set(args.legs.split(","))
+        if "simplify" in want:
+            legs["simplify"] = leg_simplify(msc, torch, plan, d_field, f, uuid)
         del lanes, plan, d_field
         torch.cuda.empty_cache()
-        line["legs"] = {
-            "simplify": simp,
-            "blobs512": leg_single(msc, torch, "blobs512", steps=5, warmup=3, uuid=uuid),
-            "batch64": leg_batch(msc, torch, steps=3, workers=args.workers, uuid=uuid),
-            "serve": leg_serve(msc, torch, args.requests, args.workers, args.serve_budget, uuid),
-        }
+        if "blobs512" in want:
+            legs["blobs512"] = leg_single(msc, torch, "blobs512", steps=5, warmup=3, uuid=uuid)
+        if "batch64" in want:
+            legs["batch64"] = leg_batch(msc, torch, steps=3, workers=args.workers, uuid=uuid,
+                                        with_cpu=not args.no_cpu_baseline)
+        if "serve" in want:
+            legs["serve"] = leg_serve(msc, torch, args.requests, args.workers, args.serve_budget, uuid)
+        line["legs"] = legs
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -755,7 +760,9 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serving: the first R requests of the 500-request trace")
     ap.add_argument("--serve-budget", type=int, default=24 << 30, help="serving: HBM admission budget in bytes")
     ap.add_argument("--no-legs", action="store_true",
-                    help="grf256: skip the blobs512, batch64 and serving legs that the default run adds")
+                    help="grf256: skip the legs that the default run adds")
+    ap.add_argument("--legs", default="simplify,blobs512,batch64,serve",
+                    help="grf256: the legs to add (comma-separated subset of the default)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run every pass synchronised between stages instead of replaying its CUDA graph "
                          "(same kernels; profilers list each launch)")

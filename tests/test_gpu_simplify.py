@@ -67,6 +67,21 @@ def test_simplification_matches_oracle_rounds(name, f):
         assert np.array_equal(serial["alive"], want["alive"])
 
 
+@pytest.mark.slow
+def test_anisotropic_batch_volume():
+    """The smallest volume of the uneven batch (seed 126, 91 x 48 x 61): rounds against the oracle at the
+    median persistence, and the serial order's survivors."""
+    f = fields.batch_volume(126)
+    sk = oracle.skeleton(f)
+    th = float(np.median(np.abs(sk["value"][sk["arc_u"]] - sk["value"][sk["arc_v"]])))
+    (g,) = _gpu(f, [th])
+    want = oracle.simplify(sk, th, rounds=True)
+    assert g["n_rounds"] == want["n_rounds"] and np.array_equal(g["alive"], want["alive"])
+    assert np.array_equal(g["log"][:, 0], want["upper"]) and np.array_equal(g["log"][:, 1], want["lower"])
+    assert g["arcs"] == sorted(zip(want["arc_u"].tolist(), want["arc_v"].tolist(), want["arc_mult"].tolist()))
+    assert np.array_equal(oracle.simplify(sk, th)["alive"], want["alive"])
+
+
 def test_closed_forms():
     (g,) = _gpu(_two_wells(), [39.0])
     assert g["counts"] == [1, 0, 0, 0] and g["n_cancelled"] == 1
