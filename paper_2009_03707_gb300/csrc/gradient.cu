@@ -10,11 +10,11 @@
 //    stars.  The field tile plus a one-vertex halo is staged in shared memory as order-preserving
 //    uint32 keys.
 //  * A cell's 3-bit code lives in the word of its lowest corner vertex (its owner) but is decided
-//    by its highest vertex.  Codes whose owner is in the tile are OR-ed into shared words; codes
-//    whose owner is in the neighbouring tile on the - side go straight to global memory with
-//    atomicOr.  So the tile's words on its + faces are finished with atomicOr too, into words a
-//    small kernel zeroes beforehand (about a quarter of all words, mostly whole rows and planes),
-//    and every other word is a plain coalesced store.
+//    by its highest vertex, so a tile's stars write the words of the tile and of a one-vertex
+//    layer on its - sides.  All of them are OR-ed into shared words; at the end the layer's words
+//    go to global memory with atomicOr, as do the tile's words on its + faces (which receive the
+//    next tiles' layers), into words a small kernel zeroes beforehand (about a quarter of all
+//    words, mostly whole rows and planes).  Every other word is a plain coalesced store.
 //  * A lower star is handled as 27-bit masks over the offsets d in {-1,0,1}^3 (lower_star.cuh),
 //    with the per-position masks tabulated in shared memory and the vertex keys read straight
 //    from the staged tile.  Large stars rank their vertices once with a sorting network and keep
@@ -55,16 +55,17 @@ template <int TY, int TZ, int THREADS>
 struct Shared {
     static constexpr int FX = TX + 2, FY = TY + 2, FZ = TZ + 2;  // field keys staged (x0-1 .. x0+TX)
     static constexpr int NOWN = TX * TY * TZ;
+    static constexpr int WX = TX + 1, WY = TY + 1, WZ = TZ + 1;  // words kept (x0-1 .. x0+TX-1)
     uint32_t fkey[FZ][FY][FX];   // order keys of the field tile (OUTSIDE_KEY off-grid)
-    uint32_t words[TZ][TY][TX];  // packed codes of the owned tile
+    uint32_t words[WZ][WY][WX];  // packed codes of the owned tile and its - layer
     uint32_t inl[NOWN];          // lower-star mask of every owned vertex (0: off-grid)
     uint16_t order[NOWN];        // non-minimal vertices, largest stars first
     uint32_t ckey[27][THREADS];  // per-thread cell keys of the star in hand (ranked path)
     int bin[28];                 // counting-sort bins by star size
     int next;                    // next unclaimed entry of `order`
     star::Tables tab;            // per-position masks; key offsets within fkey
-    // per position p: slot of the cell (bits 0-2), whether its owner is one step back along
-    // x, y, z (bits 3-5), and the owner's distance back in `words` (bits 8+)
+    // per position p: the bit offset of the cell's slot in its owner's word (bits 0-4) and the
+    // owner's distance back in `words` (bits 8+)
     uint32_t emit_info[27];
 };
 
@@ -74,19 +75,20 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
                                                            uint32_t* __restrict__ status) {
     using S = Shared<TY, TZ, THREADS>;
     constexpr int FX = S::FX, FY = S::FY, FZ = S::FZ, NOWN = S::NOWN;
+    constexpr int WX = S::WX, WY = S::WY, WZ = S::WZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S& sh = *reinterpret_cast<S*>(smem_raw);
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
 
-    for (int i = t; i < NOWN; i += THREADS) (&sh.words[0][0][0])[i] = 0;
+    for (int i = t; i < WX * WY * WZ; i += THREADS) (&sh.words[0][0][0])[i] = 0;
     if (t < 28) sh.bin[t] = 0;
     if (t == 0) sh.next = 0;
     if (t < 27) {
         star::fill_tables(sh.tab, t, FX, FX * FY);
         const uint32_t xn = (star::XN >> t) & 1, yn = (star::YN >> t) & 1, zn = (star::ZN >> t) & 1;
         const uint32_t slot = (pdx(t) != 0) | ((pdy(t) != 0) << 1) | ((pdz(t) != 0) << 2);
-        sh.emit_info[t] = slot | (xn << 3) | (yn << 4) | (zn << 5) | ((xn + yn * TX + zn * TX * TY) << 8);
+        sh.emit_info[t] = (3 * slot) | ((xn + yn * WX + zn * WX * WY) << 8);
     }
     // stage the field tile with its one-vertex halo as order keys
     bool saw_nan = false;
@@ -141,7 +143,6 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
     // warps claim 32 consecutive stars at a time, largest first, so the CTA's stars are
     // spread over its warps by longest-processing-time order
     bool ok = true;
-    uint32_t* const wtile = &sh.words[0][0][0];
     for (;;) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&sh.next, 32);
@@ -152,18 +153,11 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
         const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
         const uint32_t inL = sh.inl[i];
         const star::Star st{&sh.fkey[lz + 1][ly + 1][lx + 1], &sh.tab};
-        const uint32_t low_face = (lx == 0) | ((ly == 0) << 1) | ((lz == 0) << 2);
-        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+        uint32_t* const wx = &sh.words[lz + 1][ly + 1][lx + 1];
         // a cell is owned by its lowest corner vertex: OR its code into that vertex's word
         auto emit = [&](int p, uint32_t code) {
             const uint32_t e = sh.emit_info[p];
-            const uint32_t bits = code << (3 * (e & 7u));
-            if (((e >> 3) & low_face) == 0) {
-                atomicOr(wtile + (i - int(e >> 8)), bits);
-            } else {
-                const int xn = (e >> 3) & 1, yn = (e >> 4) & 1, zn = (e >> 5) & 1;
-                atomicOr(words_out + g.vid(gx - xn, gy - yn, gz - zn), bits);
-            }
+            atomicOr(wx - int(e >> 8), code << (e & 31u));
         };
         // the scratch word of position p of this thread, in its own bank column
         auto ckey = [&](int p) -> uint32_t& { return sh.ckey[p][t]; };
@@ -173,20 +167,32 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
     if (!ok) atomicOr(status, ST_INTERNAL);
     __syncthreads();
 
-    // epilogue: far-boundary codes, then plain stores -- or atomicOr on the tile's + faces,
-    // whose words also receive codes from the neighbouring tiles
-    // (code 7 in the slots with a = 1, b = 1 or c = 1 of a vertex on the last x, y or z layer)
+    // epilogue, a warp per row of kept words: the tile's words get their far-boundary codes and a
+    // plain store -- or atomicOr on the tile's + faces, whose words also receive codes from the
+    // neighbouring tiles; the - layer's words (the previous tiles' + faces) get atomicOr where
+    // they received a code (code 7 in the slots with a = 1, b = 1 or c = 1 of a vertex on the last
+    // x, y or z layer)
     constexpr uint32_t OUT_X = 0xE38E38u, OUT_Y = 0xFC0FC0u, OUT_Z = 0xFFF000u;
     const int gx = x0 + lane;
-    for (int r = warp; r < TY * TZ; r += THREADS / 32) {
-        const int ly = r % TY, lz = r / TY;
-        const int gy = y0 + ly, gz = z0 + lz;
-        if (gy >= g.ny || gz >= g.nz || gx >= g.nx) continue;
-        const uint32_t w = sh.words[lz][ly][lane] | (gx == g.nx - 1 ? OUT_X : 0u) | (gy == g.ny - 1 ? OUT_Y : 0u) |
-                           (gz == g.nz - 1 ? OUT_Z : 0u);
+    for (int r = warp; r < WY * WZ; r += THREADS / 32) {
+        const int ey = r % WY, ez = r / WY;
+        const int gy = y0 - 1 + ey, gz = z0 - 1 + ez;
+        if (gy < 0 || gz < 0 || gy >= g.ny || gz >= g.nz) continue;  // warp-uniform
+        if (lane == 0 && x0 > 0) {
+            const uint32_t w = sh.words[ez][ey][0];
+            if (w) atomicOr(words_out + g.vid(x0 - 1, gy, gz), w);
+        }
+        if (gx >= g.nx) continue;
         uint32_t* dst = words_out + g.vid(gx, gy, gz);
-        if (lane == TX - 1 || ly == TY - 1 || lz == TZ - 1) atomicOr(dst, w);
-        else *dst = w;
+        const uint32_t w = sh.words[ez][ey][lane + 1];
+        if (ey == 0 || ez == 0) {  // the - layer
+            if (w) atomicOr(dst, w);
+            continue;
+        }
+        const uint32_t wf = w | (gx == g.nx - 1 ? OUT_X : 0u) | (gy == g.ny - 1 ? OUT_Y : 0u) |
+                            (gz == g.nz - 1 ? OUT_Z : 0u);
+        if (lane == TX - 1 || ey == TY || ez == TZ) atomicOr(dst, wf);
+        else *dst = wf;
     }
 }
 

@@ -75,12 +75,16 @@ __host__ __device__ constexpr uint32_t cofacet_mask(int p) {
            (pdz(p) ? 0u : (1u << (p - 9)) | (1u << (p + 9)));
 }
 
-// 3-bit direction code of the partner at position q seen from the cell at position p:
-// q - p = -1, +1, -3, +3, -9, +9 gives 1..6 (axis x, y, z; - side first).
-__host__ __device__ inline uint32_t dir_code(int p, int q) {
+// Emits the pair (p, q) of neighbouring positions: each cell gets the 3-bit direction code of
+// the other, 1..6 for the partner at -1, +1, -3, +3, -9, +9 positions away (axis x, y, z; - side
+// first) -- the same axis for both, opposite signs.
+template <class Emit>
+__host__ __device__ __forceinline__ void emit_pair(int p, int q, Emit& emit) {
     const int d = q - p;
     const int ad = d < 0 ? -d : d;
-    return 1u + 2u * (uint32_t(ad > 1) + uint32_t(ad > 3)) + uint32_t(d > 0);
+    const uint32_t base = 1u + 2u * (uint32_t(ad > 1) + uint32_t(ad > 3));
+    emit(p, base + uint32_t(d > 0));
+    emit(q, base + uint32_t(d < 0));
 }
 
 // Cells of the star in L(x): AND of the "lower" mask over every projection of the offset.
@@ -220,31 +224,33 @@ struct FacetCount {
 // least(S) returns the least cell of a non-empty set S; emit(p, code) is called for every
 // non-critical cell with its direction code.  Returns false if a cell was left unclassified (an
 // internal error).
+//
+// One step either pairs or declares a cell critical; both take the least cell of one set (the
+// cells with one unclassified facet if there are any, else those with none), so a step runs the
+// same instructions whichever it does -- threads of a warp that differ there do not serialise.
 template <class Least, class Emit>
 __host__ __device__ __forceinline__ bool classify_star(const uint32_t inL, const int delta, const Tables* T,
                                                        Least&& least, Emit&& emit) {
-    emit(CENTER, dir_code(CENTER, delta));
-    emit(delta, dir_code(delta, CENTER));
+    emit_pair(CENTER, delta, emit);
     uint32_t U = inL & ~((1u << CENTER) | (1u << delta));
     FacetCount n{inL & DIM3, inL & (DIM2 | DIM3)};
     n.dec(T->cofacet[delta] & U);
     for (int guard = 0; guard < 27 && U; ++guard) {
         const uint32_t one = n.one(U);
-        if (one) {
-            const int a = least(one);
-            const int f = MSC_FFS(T->facet[a] & U) - 1;  // the only unclassified facet
-            emit(f, dir_code(f, a));
-            emit(a, dir_code(a, f));
-            U &= ~((1u << a) | (1u << f));
+        const uint32_t S = one ? one : n.zero(U);
+        if (!S) return false;
+        const int a = least(S);
+        // pairing: a's only unclassified facet; otherwise a is critical and its code stays 0
+        const uint32_t fb = one ? (T->facet[a] & U) : 0u;
+        U &= ~((1u << a) | fb);
+        uint32_t cof = T->cofacet[a];
+        if (fb) {
+            const int f = MSC_FFS(fb) - 1;
+            emit_pair(f, a, emit);
             // a cell with both a and f as facets would have two dimensions: the sets are disjoint
-            n.dec((T->cofacet[a] | T->cofacet[f]) & U);
-        } else {
-            const uint32_t zero = n.zero(U);
-            if (!zero) return false;
-            const int c = least(zero);  // critical: its code stays 0
-            U &= ~(1u << c);
-            n.dec(T->cofacet[c] & U);
+            cof |= T->cofacet[f];
         }
+        n.dec(cof & U);
     }
     return U == 0;
 }
