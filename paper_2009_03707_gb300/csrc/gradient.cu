@@ -81,6 +81,19 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
 
+    // stage the field tile with its one-vertex halo as order keys: every load of the thread is
+    // issued first (their latencies overlap, and the shared initialisation runs under them), then
+    // the values are converted and stored
+    constexpr int NST = FX * FY * FZ, ST_IT = (NST + THREADS - 1) / THREADS;
+    float v[ST_IT];
+#pragma unroll
+    for (int k = 0; k < ST_IT; ++k) {
+        const int i = t + k * THREADS;
+        const int fx = i % FX, fy = (i / FX) % FY, fz = i / (FX * FY);
+        const int gx = x0 - 1 + fx, gy = y0 - 1 + fy, gz = z0 - 1 + fz;
+        const bool in = i < NST && gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz;
+        v[k] = in ? __ldg(field + g.vid(gx, gy, gz)) : __uint_as_float(0x7FFFFFFFu);
+    }
     for (int i = t; i < WX * WY * WZ; i += THREADS) (&sh.words[0][0][0])[i] = 0;
     if (t < 28) sh.bin[t] = 0;
     if (t == 0) sh.next = 0;
@@ -90,19 +103,17 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
         const uint32_t slot = (pdx(t) != 0) | ((pdy(t) != 0) << 1) | ((pdz(t) != 0) << 2);
         sh.emit_info[t] = (3 * slot) | ((xn + yn * WX + zn * WX * WY) << 8);
     }
-    // stage the field tile with its one-vertex halo as order keys
     bool saw_nan = false;
     const int lane = t & 31, warp = t >> 5;
-    for (int i = t; i < FX * FY * FZ; i += THREADS) {
+#pragma unroll
+    for (int k = 0; k < ST_IT; ++k) {
+        const int i = t + k * THREADS;
+        if (i >= NST) break;
         const int fx = i % FX, fy = (i / FX) % FY, fz = i / (FX * FY);
         const int gx = x0 - 1 + fx, gy = y0 - 1 + fy, gz = z0 - 1 + fz;
-        uint32_t key = OUTSIDE_KEY;
-        if (gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz) {
-            const float v = __ldg(field + g.vid(gx, gy, gz));
-            saw_nan |= isnan(v);
-            key = order_key(v);
-        }
-        sh.fkey[fz][fy][fx] = key;
+        const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz;
+        saw_nan |= in && isnan(v[k]);
+        (&sh.fkey[0][0][0])[i] = in ? order_key(v[k]) : OUTSIDE_KEY;
     }
     if (saw_nan) atomicOr(status, ST_NAN);
     __syncthreads();
