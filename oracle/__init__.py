@@ -79,6 +79,8 @@ _SIGNATURES = {
     "ora_lazy_dstar_rows": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_void_p),
     "ora_arc_cells": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                        ctypes.c_void_p], ctypes.c_void_p),
+    "ora_ss_arc_cells": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_void_p),
     "ora_arc_status": ([ctypes.c_void_p], ctypes.c_int),
     "ora_arc_count": ([ctypes.c_void_p], ctypes.c_int64),
     "ora_arc_cells_size": ([ctypes.c_void_p], ctypes.c_int64),
@@ -221,6 +223,33 @@ def arc_cells(dims, pair, s1, s2):
         st = lib.ora_arc_status(h)
         if st:
             raise OracleError(st, "arc_cells")
+        offsets = np.empty(lib.ora_arc_count(h) + 1, dtype=np.int64)
+        cells = np.empty(lib.ora_arc_cells_size(h), dtype=np.uint32)
+        lib.ora_arc_copy(h, _p(offsets), _p(cells))
+    finally:
+        lib.ora_arc_free(h)
+    return offsets, cells
+
+
+def ss_arc_cells(dims, pair, s1, s2, dstar):
+    """The cells along every saddle-saddle arc of multiplicity 1 (Sec. 3.3): for each D* entry
+    (dstar = (rows, cols, counts), sorted by row then column) the V-path from its 1-saddle to its
+    2-saddle -- s, then (quad, 1-cell) per step, then t -- or nothing when the count is not 1.
+    Returns (offsets int64[nnz + 1], cells uint32)."""
+    d = _dims(dims)
+    s1 = np.ascontiguousarray(s1, dtype=np.uint32)
+    s2 = np.ascontiguousarray(s2, dtype=np.uint32)
+    rows, cols, cnt = dstar
+    rows = np.asarray(rows, dtype=np.int64)
+    rowptr = np.ascontiguousarray(np.searchsorted(rows, np.arange(len(s1) + 1)), dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.uint32)
+    cnt = np.ascontiguousarray(cnt, dtype=np.uint64)
+    lib = _load()
+    h = lib.ora_ss_arc_cells(_p(d), _p(pair), len(s1), _p(s1), len(s2), _p(s2), _p(rowptr), _p(cols), _p(cnt))
+    try:
+        st = lib.ora_arc_status(h)
+        if st:
+            raise OracleError(st, "ss_arc_cells")
         offsets = np.empty(lib.ora_arc_count(h) + 1, dtype=np.int64)
         cells = np.empty(lib.ora_arc_cells_size(h), dtype=np.uint32)
         lib.ora_arc_copy(h, _p(offsets), _p(cells))

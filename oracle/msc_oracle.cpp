@@ -19,6 +19,8 @@
 //     (matrices A, B, B*, D), and the saddle-saddle path counts D*, here computed by the
 //     plain definition -- per 1-saddle, a topological-order count of paths in the DAG --
 //     rather than by the paper's iterated sparse products.
+//   * Sec. 3.4 and Sec. 3.5 "Data structure": the cells along each saddle-extremum arc and
+//     along each saddle-saddle arc of multiplicity 1 (its single V-path), as plain walks.
 //
 // Readings where the paper is silent (each one is also listed in the design notes):
 //   R1 vertex order: v < w iff (f(v), index(v)) < (f(w), index(w)); IEEE compare, so
@@ -709,6 +711,91 @@ void* ora_arc_cells(const int64_t* dims, const uint32_t* pair_of, int64_t n1, co
                     if (!g.inside(ax, ay, az)) break;  // R4: the path leaves the domain here
                     c = g.cell(ax, ay, az);
                     res->cells.push_back(uint32_t(c));
+                }
+            }
+            res->offsets.push_back(int64_t(res->cells.size()));
+        }
+    }
+    return res;
+}
+
+// Cells along the saddle-saddle arcs of multiplicity 1 (Sec. 3.3 and Sec. 3.5 "Data structure").
+// A D* entry (s, t) with count 1 is a single V-path from the 2-saddle t down to the 1-saddle s, so
+// it has one cell sequence; an entry with a larger count stands for several paths and gets none.
+// The path is walked from s along the DAG (Sec. 3.2), at each node taking the one successor from
+// which t can still be reached; the cells are s, then for each step to a 1-cell e' the quad paired
+// with e' followed by e', and finally t.  The paths from a node to t are counted by a memoised
+// depth-first search over the DAG (saturating at 2: only "none", "one" and "several" matter).
+// Entries come as the D* CSR (rowptr over 1-saddle ranks, 2-saddle rank columns, counts) and the
+// offsets follow its entry order.
+void* ora_ss_arc_cells(const int64_t* dims, const uint32_t* pair_of, int64_t n1, const uint32_t* s1, int64_t n2,
+                       const uint32_t* s2, const int64_t* rowptr, const uint32_t* col, const uint64_t* cnt) {
+    ArcCells* res = new ArcCells();
+    if (!check_dims(dims) || !pair_of || n1 < 0 || n2 < 0 || (n1 > 0 && (!s1 || !rowptr)) || (n2 > 0 && !s2)) {
+        res->status = ERR_ARG;
+        return res;
+    }
+    Grid g(dims, nullptr);
+    const int64_t limit = g.ncells();
+    res->offsets.push_back(0);
+    for (int64_t i = 0; i < n1; ++i) {
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (cnt[k] == 1) {
+                if (int64_t(col[k]) >= n2) { res->status = ERR_ARG; return res; }
+                const int64_t s = int64_t(s1[i]), t = int64_t(s2[col[k]]);
+                std::map<int64_t, uint64_t> memo;  // node -> paths to t, capped at 2
+                bool bad = false;
+                // the count of a node that needs no search: t itself, another 2-saddle, or memoised
+                auto known = [&](int64_t y, uint64_t& v) {
+                    if (y == t) { v = 1; return true; }
+                    if (g.dim(y) != 1) { v = 0; return true; }
+                    auto it = memo.find(y);
+                    if (it == memo.end()) return false;
+                    v = it->second;
+                    return true;
+                };
+                auto paths_to_t = [&](int64_t start) -> uint64_t {
+                    uint64_t v;
+                    if (known(start, v)) return v;
+                    struct Frame { int64_t x; std::vector<int64_t> out; size_t next; uint64_t n; };
+                    std::vector<Frame> st;
+                    st.push_back(Frame{start, dag_out(g, pair_of, start), 0, 0});
+                    for (int64_t steps = 0; !st.empty(); ++steps) {
+                        if (steps > 8 * limit) { bad = true; return 0; }  // a cycle: cannot happen
+                        if (st.back().next < st.back().out.size()) {
+                            const int64_t y = st.back().out[st.back().next];
+                            if (known(y, v)) {
+                                st.back().n = std::min<uint64_t>(2, st.back().n + v);
+                                ++st.back().next;
+                            } else {
+                                st.push_back(Frame{y, dag_out(g, pair_of, y), 0, 0});
+                            }
+                        } else {
+                            const uint64_t done = st.back().n;
+                            memo[st.back().x] = done;
+                            st.pop_back();
+                            if (!st.empty()) {
+                                st.back().n = std::min<uint64_t>(2, st.back().n + done);
+                                ++st.back().next;
+                            }
+                        }
+                    }
+                    return memo[start];
+                };
+                if (paths_to_t(s) != 1 || bad) { res->status = ERR_INTERNAL; return res; }
+                res->cells.push_back(uint32_t(s));
+                int64_t e = s;
+                for (int64_t steps = 0;; ++steps) {
+                    if (steps > limit) { res->status = ERR_INTERNAL; return res; }
+                    int64_t next = -1;
+                    int found = 0;
+                    for (int64_t y : dag_out(g, pair_of, e))
+                        if (paths_to_t(y) > 0) { next = y; ++found; }
+                    if (found != 1 || bad) { res->status = ERR_INTERNAL; return res; }
+                    if (next == t) { res->cells.push_back(uint32_t(t)); break; }
+                    res->cells.push_back(pair_of[next]);  // the quad between e and next
+                    res->cells.push_back(uint32_t(next));
+                    e = next;
                 }
             }
             res->offsets.push_back(int64_t(res->cells.size()));

@@ -43,6 +43,8 @@ MUTANTS = [
      "const Key k = *std::prev(queue.end());\n        queue.erase(std::prev(queue.end()));"),
     ("rounds_select_one_link_minima", "for (const auto& kv : adj[size_t(u)]) m2[size_t(u)] = std::min(m2[size_t(u)], m1[size_t(kv.first)]);",
      "for (const auto& kv : adj[size_t(u)]) m2[size_t(u)] = std::min(m2[size_t(u)], m0[size_t(kv.first)]);"),
+    ("ss_arc_quad_of_the_wrong_cell", "res->cells.push_back(pair_of[next]);  // the quad between e and next",
+     "res->cells.push_back(pair_of[e]);  // the quad between e and next"),
     ("packed_codes_x_sides_swapped", "    if (bx == ax - 1) return 1;\n    if (bx == ax + 1) return 2;",
      "    if (bx == ax - 1) return 2;\n    if (bx == ax + 1) return 1;"),
 ]
@@ -61,6 +63,7 @@ def _run_pins():
     checks.append(pins.test_cosine_lattice_counts)
     checks += [lambda s=s: pins.test_packed_words_decode_to_the_gradient_pairs(s) for s in range(2)]
     checks += [lambda s=s: pins.test_arc_cells_are_the_v_paths_of_the_arcs(s) for s in range(2)]
+    checks += [lambda s=s: pins.test_ss_arc_cells_are_the_single_v_paths(s) for s in (0, 4)]
     checks += [lambda s=s: pins.test_simplification_matches_brute_force_replay(s) for s in range(2)]
     checks += [pins.test_simplification_two_wells_closed_form, pins.test_simplification_cosine_lattice_closed_form]
     checks += [lambda s=s: pins.test_simplification_rounds_match_brute_force_and_the_serial_order(s) for s in range(2)]

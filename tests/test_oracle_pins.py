@@ -14,6 +14,8 @@
   2-saddle (independent of the oracle's upward DAG walk), and against the paper's own
   iterated-product formulation (Sec. 3.3) in exact Python integers.
 * Destination minima against steepest descent on the raw field.
+* Cells of the saddle-saddle arcs of multiplicity 1 against the same downward V-path
+  enumeration: exactly one path, cell for cell.
 """
 from __future__ import annotations
 
@@ -532,6 +534,63 @@ def test_arc_cells_are_the_v_paths_of_the_arcs(seed):
                     even = [i for i in range(3) if lc[i] % 2 == 0][0]
                     inside = [0 <= lc[even] + s < ext[even] for s in (-1, 1)]
                     assert sum(inside) == 1 and int(amax[b]) == NONE
+
+
+def vpath_cell_lists(C, pair, crit1, crit2):
+    """{(1-saddle cell, 2-saddle cell): [cell sequence of each V-path]}, enumerated downward from
+    every 2-saddle as in vpath_counts, each sequence read from the 1-saddle up: s, then the quad
+    and the 1-cell of each step (the quad the 1-cell is paired with), then t."""
+    pd = pairs_dict(pair)
+    crit1 = set(int(c) for c in crit1)
+    out = defaultdict(list)
+    for t in crit2:
+        t = int(t)
+        stack = [(t, None, [t])]
+        while stack:
+            q, excluded, down = stack.pop()
+            for e in C.facets(q):
+                if e == excluded:
+                    continue
+                if e in crit1:
+                    out[(e, t)].append([e] + down[::-1])
+                    continue
+                p = pd[e]
+                if C.dim(p) == 2:
+                    stack.append((p, e, down + [e, p]))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ss_arc_cells_are_the_single_v_paths(seed):
+    """Every D* entry of count 1 gets the cells of its one V-path (enumerated downward from the
+    2-saddle, independently of the oracle's upward walk), every other entry none; the enumeration
+    also reproduces every count."""
+    if seed < 4:
+        f = random_field([(6, 6, 6), (5, 7, 8), (8, 6, 5), (4, 9, 7)][seed], 700 + seed,
+                         "normal" if seed % 2 == 0 else "ties")
+    else:
+        f = fields.gaussian_blobs(n=14, n_blobs=5, sigma_range=(2, 4), seed=60 + seed)
+    d = _dims(f)
+    C = Complex(d)
+    r = oracle.compute_all(f)
+    s1, s2 = r["lists"][1], r["lists"][2]
+    rows, cols, cnt = r["dstar"]
+    off, cells = oracle.ss_arc_cells(d, r["pair"], s1, s2, r["dstar"])
+    assert len(off) == len(cnt) + 1 and off[-1] == len(cells)
+    paths = vpath_cell_lists(C, r["pair"], s1, s2)
+    assert sum(len(v) for v in paths.values()) == int(np.sum(cnt))
+    n_one = n_long = 0
+    for k, (a, b, c) in enumerate(zip(rows, cols, cnt)):
+        key = (int(s1[a]), int(s2[b]))
+        got = [int(x) for x in cells[off[k]:off[k + 1]]]
+        assert len(paths[key]) == int(c)
+        if int(c) == 1:
+            assert got == paths[key][0]
+            n_one += 1
+            n_long += len(got) > 2
+        else:
+            assert got == []
+    assert n_one > 0 and n_long > 0
 
 
 def test_packed_at_matches_full_pack():
