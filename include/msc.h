@@ -250,6 +250,22 @@ msc_status msc_complex_graph(msc_plan_t plan, msc_stream_t stream, int64_t* n_no
 msc_status msc_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_arcs, int64_t* n_cells,
                             const int64_t** d_offsets, const uint32_t** d_cells);
 
+/* ---- the cells along the saddle-saddle arcs of multiplicity 1 (on request) -----------------
+ * Sec. 3.3 and Sec. 3.5 "Data structure": a saddle-saddle arc (s, t) of D* with count 1 is a single
+ * V-path (Sec. 2.2) from the 2-saddle t down to the 1-saddle s, so it has one geometry; an entry with
+ * a larger count stands for several paths and gets none.  Entry k of the D* CSR (msc_saddle_arcs
+ * order: by 1-saddle rank, columns increasing) has the cells d_cells[d_offsets[k] .. d_offsets[k+1]),
+ * read from s against the gradient: s, then for each step the quad and the 1-cell paired with it,
+ * then t.  Empty for a count other than 1.  *n_entries = nnz of D*; d_offsets has nnz+1 int64
+ * entries; *n_cells = d_offsets[nnz].  Built on the first call after a pass (host-synchronised): the
+ * path is chosen at each junction by the junction-to-2-saddle path counts J of the junction waves
+ * (which run once more for this, giving the same D*, when the pass counted paths row by row; the
+ * pass's statistics are kept), then walked through the gradient words.  MSC_ERR_INTERNAL if the
+ * minor and the gradient disagree (cannot happen).  Plan-owned until the next pass; any output pointer
+ * may be null. */
+msc_status msc_saddle_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_entries, int64_t* n_cells,
+                                   const int64_t** d_offsets, const uint32_t** d_cells);
+
 /* ---- simplification of the 1-skeleton (on request) --------------------------------------
  * Sec. 4 "Parallel Simplification": critical-point pairs of consecutive index joined by exactly one
  * arc are cancelled in order of persistence; a cancellation reroutes the upper point's descending
@@ -292,6 +308,7 @@ msc_status msc_simplify(msc_plan_t plan, msc_stream_t stream, const float* d_fie
  *   MSC_OUT_DSTAR_ROWPTR   D* row pointers (int64, counts[1]+1) MSC_OUT_DSTAR_COL columns (uint32, nnz)
  *   MSC_OUT_DSTAR_COUNT    path counts (uint64, nnz)
  *   MSC_OUT_ARC_OFFSETS    arc geometry offsets (int64, n_arcs+1)  MSC_OUT_ARC_CELLS  cells along the arcs (uint32)
+ *   MSC_OUT_SS_ARC_OFFSETS saddle-saddle arc offsets (int64, nnz+1) MSC_OUT_SS_ARC_CELLS their cells (uint32)
  * Size query: *bytes on entry is the room in h_out; on return it is the output's size in bytes.
  * With h_out null nothing is copied.  Otherwise the copy is made and the stream synchronised;
  * MSC_ERR_CAPACITY (nothing copied) if the room is smaller.  MSC_ERR_ARG for an unknown `what`. */
@@ -308,7 +325,9 @@ enum {
     MSC_OUT_DSTAR_COL = 9,
     MSC_OUT_DSTAR_COUNT = 10,
     MSC_OUT_ARC_OFFSETS = 11,
-    MSC_OUT_ARC_CELLS = 12
+    MSC_OUT_ARC_CELLS = 12,
+    MSC_OUT_SS_ARC_OFFSETS = 13,
+    MSC_OUT_SS_ARC_CELLS = 14
 };
 msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void* h_out, int64_t* bytes);
 

@@ -199,7 +199,7 @@ msc_status bind_device(Plan* p) {
 void invalidate(Plan* p) {
     p->have_gradient = p->have_critical = p->have_extremum = p->have_reach = false;
     p->have_junctions = p->have_trace = p->have_minor = p->have_dstar = p->have_dstar_csc = p->have_graph = false;
-    p->have_geometry = false;
+    p->have_geometry = p->have_ss_geometry = p->have_j = false;
 }
 
 // Host mirrors and statistics from the summary last copied to p->hsum.
@@ -701,6 +701,59 @@ msc_status msc_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_arc
     return MSC_OK;
 }
 
+// The cells of the saddle-saddle arcs of multiplicity 1 need the rows of J.  A pass that counted
+// paths row by row has none, so the junction waves run once more for them (they give the same D*);
+// the pass's summary, statistics and kernel timings are put back afterwards.
+static msc_status ensure_ss_geometry(Plan* p, cudaStream_t s) {
+    msc_status st;
+    if ((st = ensure_dstar(p, s))) return st;
+    if (p->have_ss_geometry) return MSC_OK;
+    if (!p->have_j && p->pc_method_used != 2) {
+        if ((st = msc::read_summary(p, s))) return st;
+        const msc::Summary saved = *p->hsum;
+        const msc_stats stats = p->stats;
+        const int32_t forced = p->opts.path_count_method;
+        const int used = p->pc_method_used;
+        cudaEvent_t k0 = p->kev0, k1 = p->kev1;
+        p->kev0 = p->kev1 = nullptr;
+        p->opts.path_count_method = 2;
+        st = msc::run_path_count(p, s);
+        if (st == MSC_OK) st = msc::finish_stage(p, s);
+        p->opts.path_count_method = forced;
+        p->pc_method_used = used;
+        p->kev0 = k0;
+        p->kev1 = k1;
+        if (st == MSC_OK) {
+            *p->hsum = saved;
+            st = msc::check_cuda(p, cudaMemcpyAsync(p->dsum(), p->hsum, sizeof(msc::Summary), cudaMemcpyHostToDevice, s),
+                                 "summary restore");
+            if (st == MSC_OK) st = msc::check_cuda(p, cudaStreamSynchronize(s), "stream sync");
+        }
+        p->stats = stats;
+        if (st) return st;
+    }
+    p->have_j = true;
+    if ((st = msc::build_ss_geometry(p, s))) return st;
+    if ((st = msc::finish_stage(p, s))) return st;
+    p->have_ss_geometry = true;
+    return MSC_OK;
+}
+
+msc_status msc_saddle_arc_geometry(msc_plan_t plan, msc_stream_t stream, int64_t* n_entries, int64_t* n_cells,
+                                   const int64_t** d_offsets, const uint32_t** d_cells) {
+    if (!plan) return MSC_ERR_ARG;
+    Plan* p = plan;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    msc_status st;
+    if ((st = msc::bind_device(p))) return st;
+    if ((st = ensure_ss_geometry(p, s))) return st;
+    if (n_entries) *n_entries = p->dstar_nnz;
+    if (n_cells) *n_cells = p->ss_cells_n;
+    if (d_offsets) *d_offsets = static_cast<const int64_t*>(p->ss_off.ptr);
+    if (d_cells) *d_cells = static_cast<const uint32_t*>(p->ss_cells.ptr);
+    return MSC_OK;
+}
+
 static msc_status ensure_graph(Plan* p, cudaStream_t s) {
     msc_status st;
     if ((st = ensure_extremum(p, s))) return st;
@@ -842,7 +895,7 @@ msc_status msc_compute(msc_plan_t plan, const float* d_field, msc_stream_t strea
 }
 
 msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void* h_out, int64_t* bytes) {
-    if (!plan || !bytes || what < MSC_OUT_CELLS0 || what > MSC_OUT_ARC_CELLS) return MSC_ERR_ARG;
+    if (!plan || !bytes || what < MSC_OUT_CELLS0 || what > MSC_OUT_SS_ARC_CELLS) return MSC_ERR_ARG;
     Plan* p = plan;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     msc_status st;
@@ -860,6 +913,11 @@ msc_status msc_copy_to_host(msc_plan_t plan, msc_stream_t stream, int what, void
         const int64_t len[4] = {2 * p->counts[1], 2 * p->counts[2], nv, nv};
         src = b[what - MSC_OUT_MIN_ARCS]->ptr;
         n = int64_t(sizeof(uint32_t)) * len[what - MSC_OUT_MIN_ARCS];
+    } else if (what >= MSC_OUT_SS_ARC_OFFSETS) {
+        if ((st = ensure_ss_geometry(p, s))) return st;
+        src = what == MSC_OUT_SS_ARC_OFFSETS ? p->ss_off.ptr : p->ss_cells.ptr;
+        n = what == MSC_OUT_SS_ARC_OFFSETS ? int64_t(sizeof(int64_t)) * (p->dstar_nnz + 1)
+                                           : int64_t(sizeof(uint32_t)) * p->ss_cells_n;
     } else if (what >= MSC_OUT_ARC_OFFSETS) {
         if ((st = ensure_geometry(p, s))) return st;
         const int64_t n_arcs = 2 * (p->counts[1] + p->counts[2]);

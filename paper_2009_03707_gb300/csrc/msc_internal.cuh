@@ -96,6 +96,7 @@ struct Plan {
     DeviceBuffer csc_colptr, csc_row, csc_count, csc_work;  // D* by 2-saddle (transpose.cu)
     DeviceBuffer graph_nodeptr, graph_adj, graph_mult, graph_work, graph_none;  // the 1-skeleton (graph.cu)
     DeviceBuffer geo_len, geo_off, geo_scan, geo_cells;  // cells along the saddle-extremum arcs (geometry.cu)
+    DeviceBuffer ss_len, ss_off, ss_scan, ss_cells;      // cells along the saddle-saddle arcs of count 1 (geometry.cu)
     // simplification (simplify.cu): node cells, values, alive (two copies), keys, per-node scratch,
     // row lengths, log positions, scan scratch, two CSRs, the log, the per-round host read-out
     DeviceBuffer simp_cell, simp_value, simp_alive, simp_keys, simp_node, simp_len, simp_pos, simp_scan;
@@ -114,7 +115,8 @@ struct Plan {
                                &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
                                &dp_j_len, &dp_pool_col, &dp_pool_cnt, &dp_long, &dp_chunks, &csc_colptr, &csc_row, &csc_count, &csc_work,
                                &graph_nodeptr, &graph_adj, &graph_mult, &graph_work, &graph_none,
-                               &geo_len, &geo_off, &geo_scan, &geo_cells, &simp_cell, &simp_value,
+                               &geo_len, &geo_off, &geo_scan, &geo_cells, &ss_len, &ss_off, &ss_scan, &ss_cells,
+                               &simp_cell, &simp_value,
                                &simp_alive, &simp_keys, &simp_node, &simp_len, &simp_pos, &simp_scan,
                                &simp_ptr[0], &simp_ptr[1], &simp_nbr[0], &simp_nbr[1], &simp_mult[0],
                                &simp_mult[1], &simp_log, &simp_round};
@@ -163,7 +165,9 @@ struct Plan {
     // which stages are valid for the current field
     bool have_gradient = false, have_critical = false, have_extremum = false, have_reach = false,
          have_junctions = false, have_trace = false, have_minor = false, have_dstar = false,
-         have_dstar_csc = false, have_graph = false, have_geometry = false;
+         have_dstar_csc = false, have_graph = false, have_geometry = false, have_ss_geometry = false,
+         have_j = false;  // the junction-DP rows J of the current field (junction_dp.cu), whichever method ran
+    int64_t ss_cells_n = 0;  // cells along all saddle-saddle arcs of count 1 (geometry.cu)
     int64_t graph_nodes = 0, graph_nadj = 0;
     int64_t geo_cells_n = 0;  // cells along all arcs (geometry.cu)
     // the last simplification (simplify.cu): which CSR copy holds it, its size, rounds, cancellations
@@ -191,6 +195,7 @@ __host__ __device__ __forceinline__ uint32_t trace_kind(uint32_t kinds, int k) {
 // Records a timing event on s; inside a capture it must be an external event-record node (a plain
 // record there only orders captured work and is never recorded when the graph runs).
 inline void record_event(const Plan* p, cudaEvent_t ev, cudaStream_t s) {
+    if (!ev) return;  // a timing deliberately not taken
     if (p->capturing) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
     else cudaEventRecord(ev, s);
 }
@@ -240,6 +245,7 @@ msc_status run_path_count(Plan* p, cudaStream_t s);
 msc_status build_dstar_csc(Plan* p, cudaStream_t s);  // D* by 2-saddle (on request; syncs)
 msc_status build_complex_graph(Plan* p, cudaStream_t s);  // the 1-skeleton adjacency (on request; syncs)
 msc_status build_arc_geometry(Plan* p, cudaStream_t s);   // cells along the saddle-extremum arcs (on request; syncs)
+msc_status build_ss_geometry(Plan* p, cudaStream_t s);    // cells along the saddle-saddle arcs of count 1 (needs J; syncs)
 msc_status run_simplify(Plan* p, const float* d_field, double threshold, cudaStream_t s);  // (on request; syncs)
 msc_status run_junction_dp(Plan* p, cudaStream_t s, uint64_t pool_cap, uint64_t out_cap);
 int grid_cap(const Plan* p, int64_t threads, int block, int per_sm = 8);  // grid for a count-bounded loop

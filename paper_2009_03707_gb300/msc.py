@@ -44,6 +44,7 @@ SIGNATURES = {
     "msc_saddle_arcs_csc": ([_P, _P, _PI64, _PP, _PP, _PP], _I32),
     "msc_complex_graph": ([_P, _P, _PI64, _PI64, _P, _P, _P], _I32),
     "msc_arc_geometry": ([_P, _P, _PI64, _PI64, _PP, _PP], _I32),
+    "msc_saddle_arc_geometry": ([_P, _P, _PI64, _PI64, _PP, _PP], _I32),
     "msc_simplify": ([_P, _P, _P, ctypes.c_double, _P], _I32),
     "msc_compute_async": ([_P, _P, _P], _I32),
     "msc_copy_to_host": ([_P, _P, _I32, _P, _PI64], _I32),
@@ -262,6 +263,16 @@ def msc_arc_geometry(plan: Plan):
     return _view(off.value, (n_arcs.value + 1,), "<i8"), _view(cells.value, (n_cells.value,), "<u4")
 
 
+def msc_saddle_arc_geometry(plan: Plan):
+    """The cells along every saddle-saddle arc of multiplicity 1: (offsets [nnz+1] int64, cells
+    [n_cells] uint32), one range per D* entry in msc_saddle_arcs order (empty when its count is not 1)."""
+    nnz, n_cells = ctypes.c_int64(), ctypes.c_int64()
+    off, cells = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.msc_saddle_arc_geometry(plan.handle, _stream(), ctypes.byref(nnz), ctypes.byref(n_cells),
+                                       ctypes.byref(off), ctypes.byref(cells)), plan.handle)
+    return _view(off.value, (nnz.value + 1,), "<i8"), _view(cells.value, (n_cells.value,), "<u4")
+
+
 class MscSimplified(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_rounds", ctypes.c_int64), ("n_cancelled", ctypes.c_int64),
                 ("n_adj", ctypes.c_int64), ("counts", ctypes.c_int64 * 4), ("d_alive", ctypes.c_void_p),
@@ -313,7 +324,8 @@ def msc_compute(plan: Plan, field: torch.Tensor) -> None:
 MSC_OUT = {"cells0": (0, np.uint32), "cells1": (1, np.uint32), "cells2": (2, np.uint32), "cells3": (3, np.uint32),
            "min_arcs": (4, np.uint32), "max_arcs": (5, np.uint32), "vertex_min": (6, np.uint32),
            "cube_max": (7, np.uint32), "dstar_rowptr": (8, np.int64), "dstar_col": (9, np.uint32),
-           "dstar_count": (10, np.uint64), "arc_offsets": (11, np.int64), "arc_cells": (12, np.uint32)}
+           "dstar_count": (10, np.uint64), "arc_offsets": (11, np.int64), "arc_cells": (12, np.uint32),
+           "ss_arc_offsets": (13, np.int64), "ss_arc_cells": (14, np.uint32)}
 
 
 def msc_copy_to_host(plan: Plan, what: str) -> np.ndarray:

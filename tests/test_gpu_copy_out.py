@@ -58,5 +58,5 @@ def test_size_query_capacity_and_arguments():
     assert lib.msc_copy_to_host(plan.handle, None, 6, buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(small)) == 12
     assert small.value == n.value and not buf.any()
     bad = ctypes.c_int64(0)
-    assert lib.msc_copy_to_host(plan.handle, None, 13, None, ctypes.byref(bad)) == 1  # past the last selector
+    assert lib.msc_copy_to_host(plan.handle, None, 15, None, ctypes.byref(bad)) == 1  # past the last selector
     assert lib.msc_copy_to_host(plan.handle, None, -1, None, ctypes.byref(bad)) == 1
