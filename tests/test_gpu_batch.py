@@ -134,3 +134,33 @@ def test_group_volume_outgrowing_its_branch_is_rerun():
         for f, plan in zip([smooth[0], rough, smooth[2]], plans):
             _same(_outputs(m, plan), _alone(m, f))
     batch.close()
+
+
+def test_on_request_outputs_of_batch_plans_equal_alone():
+    """The on-request outputs -- both arc geometries, the host 1-skeleton and a simplification -- of
+    the plans a batch submission returns equal those of the same volumes computed alone, after the
+    first submission and after the group graph's replay."""
+    m = msc()
+    vols = _volumes()[:4] + [fields.gaussian_blobs(n=28, n_blobs=5, sigma_range=(3, 7), seed=71)]
+    batch = m.Batch(n_workers=3)
+    dev = [gpu_field(f) for f in vols]
+    ticket, plans = batch.msc_batch_submit(dev)
+    assert batch.msc_batch_wait(ticket) == 0
+    for rep in range(2):
+        if rep:
+            ticket, _ = batch.msc_batch_submit(dev, plans)
+            assert batch.msc_batch_wait(ticket) == 0
+        for f, d, plan in zip(vols, dev, plans):
+            alone = m.Plan(dims_of(f))
+            m.msc_compute(alone, d)
+            for fn in (m.msc_arc_geometry, m.msc_saddle_arc_geometry):
+                for x, y in zip(fn(plan), fn(alone)):
+                    assert np.array_equal(to_np(x), to_np(y)), fn.__name__
+            for x, y in zip(m.msc_complex_graph(plan), m.msc_complex_graph(alone)):
+                assert np.array_equal(x, y)
+            thr = 0.1 * float(f.max() - f.min())
+            a, b = m.msc_simplify(plan, d, thr), m.msc_simplify(alone, d, thr)
+            assert a["counts"] == b["counts"] and a["n_rounds"] == b["n_rounds"]
+            for key in ("alive", "nodeptr", "adj", "mult", "log"):
+                assert np.array_equal(to_np(a[key]), to_np(b[key])), key
+    batch.close()

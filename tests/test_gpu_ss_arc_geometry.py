@@ -21,6 +21,8 @@ def _cases():
     out = [("cos32", fields.cosine_lattice()), ("grf40", fields.grf((40, 36, 44), 3.0, seed=12)),
            ("blobs36", fields.gaussian_blobs(n=36, n_blobs=10, sigma_range=(2, 6), seed=5)),
            ("blobs30", fields.gaussian_blobs(n=30, n_blobs=4, sigma_range=(3, 8), seed=17))]
+    z, y, x = np.meshgrid(np.arange(9), np.arange(10), np.arange(11), indexing="ij")
+    out.append(("ramp", (x + 2.0 * y + 3.0 * z).astype(np.float32)))  # no saddles: D* is empty
     for i, shp in enumerate([(2, 2, 2), (3, 5, 7), (9, 8, 33), (17, 16, 65)]):
         out.append((f"normal{shp}", random_field(shp, 1900 + i, "normal")))
         out.append((f"ties{shp}", random_field(shp, 1950 + i, "ties")))
