@@ -60,3 +60,28 @@ def test_size_query_capacity_and_arguments():
     bad = ctypes.c_int64(0)
     assert lib.msc_copy_to_host(plan.handle, None, 15, None, ctypes.byref(bad)) == 1  # past the last selector
     assert lib.msc_copy_to_host(plan.handle, None, -1, None, ctypes.byref(bad)) == 1
+
+
+def test_every_query_before_a_pass_is_a_state_error():
+    """On a plan that has seen no field, every stage query, on-request output and host copy returns
+    MSC_ERR_STATE (nothing runs), and the plan then computes normally."""
+    m = msc()
+    f = fields.grf((14, 15, 16), 3.0, seed=85)
+    plan = m.Plan(dims_of(f))
+    d = gpu_field(f)
+    calls = [lambda: m.msc_critical(plan), lambda: m.msc_extremum_arcs(plan), lambda: m.msc_saddle_arcs(plan),
+             lambda: m.msc_saddle_arcs_csc(plan), lambda: m.msc_arc_geometry(plan),
+             lambda: m.msc_saddle_arc_geometry(plan), lambda: m.msc_complex_graph(plan),
+             lambda: m.msc_simplify(plan, d, 0.1)]
+    calls += [lambda w=w: m.msc_copy_to_host(plan, w) for w in m.MSC_OUT]
+    for call in calls:
+        with pytest.raises(m.MscError) as err:
+            call()
+        assert err.value.status == 11  # MSC_ERR_STATE
+    m.msc_compute(plan, d)
+    e = oracle.compute_all(f)
+    counts, _ = m.msc_critical(plan)
+    assert list(counts) == [len(c) for c in e["lists"]]
+    off, cells = m.msc_saddle_arc_geometry(plan)
+    want_off, want_cells = oracle.ss_arc_cells(dims_of(f), e["pair"], e["lists"][1], e["lists"][2], e["dstar"])
+    assert np.array_equal(to_np(off), want_off) and np.array_equal(to_np(cells), want_cells)
