@@ -54,7 +54,8 @@ struct SimpArgs {
     Key* m2;
     uint32_t* sel;      // upper node -> selected lower node, or NO_NODE
     uint32_t* owner;    // touched node -> upper node of the cancellation that touches it, or NO_NODE
-    uint8_t* role;      // 1: descending neighbour of the upper node, 2: ascending neighbour of the lower
+    uint8_t* role;      // 1: descending neighbour of the upper node, 2: ascending neighbour of the lower,
+                        // 3: another neighbour of either (loses its arc only), 0: untouched
     unsigned long long* factor;  // multiplicity of the touched node's arc to the cancelled node
     uint32_t* flags;    // 1 per selected upper node (for the log positions)
     uint32_t* status;
@@ -138,7 +139,9 @@ __global__ void __launch_bounds__(THREADS) simp_select(SimpArgs a) {
 }
 
 // Footprints of the selected arcs: each descending neighbour of p (other than q) and each ascending
-// neighbour of q (other than p) learns its cancellation; p and q die; the log gets (p, q, round).
+// neighbour of q (other than p) learns its cancellation (role 1, 2); the other neighbours of p and q
+// only lose their arc (role 3); p and q die; the log gets (p, q, round).  Every other live node keeps
+// its row as it is (role 0).
 __global__ void __launch_bounds__(THREADS) simp_mark(SimpArgs a, const int64_t* __restrict__ log_pos, uint32_t* log,
                                                      uint32_t round) {
     for (int64_t p = int64_t(blockIdx.x) * THREADS + threadIdx.x; p < a.n; p += int64_t(gridDim.x) * THREADS) {
@@ -147,14 +150,22 @@ __global__ void __launch_bounds__(THREADS) simp_mark(SimpArgs a, const int64_t* 
         const int iq = node_index(a, q);
         for (int64_t e = a.ptr[p]; e < a.ptr[p + 1]; ++e) {
             const uint32_t x = a.nbr[e];
-            if (x == q || node_index(a, x) != iq) continue;
+            if (x == q) continue;
+            if (node_index(a, x) != iq) {
+                a.role[x] = 3;
+                continue;
+            }
             a.owner[x] = uint32_t(p);
             a.role[x] = 1;
             a.factor[x] = a.mult[e];
         }
         for (int64_t e = a.ptr[q]; e < a.ptr[q + 1]; ++e) {
             const uint32_t x = a.nbr[e];
-            if (x == uint32_t(p) || node_index(a, x) != iq + 1) continue;
+            if (x == uint32_t(p)) continue;
+            if (node_index(a, x) != iq + 1) {
+                a.role[x] = 3;
+                continue;
+            }
             a.owner[x] = uint32_t(p);
             a.role[x] = 2;
             a.factor[x] = a.mult[e];
@@ -177,7 +188,7 @@ struct Extra {
 
 __device__ __forceinline__ Extra extra_of(const SimpArgs& a, int64_t u) {
     Extra x{0, 0, NO_NODE, -1};
-    if (a.role[u] == 0) return x;
+    if (a.role[u] != 1 && a.role[u] != 2) return x;
     const uint32_t p = a.owner[u], q = a.sel[p];
     if (a.role[u] == 1) {  // u is a descending neighbour of p: gains q's ascending neighbours
         x.from = a.ptr[q];
@@ -197,9 +208,19 @@ __device__ __forceinline__ Extra extra_of(const SimpArgs& a, int64_t u) {
 // counts.  Multiplicities: old + factor * (the extra row's multiplicity), overflow -> ST_OVERFLOW.
 __device__ int64_t merge_row(const SimpArgs& a, int64_t u, uint32_t* out_nbr, unsigned long long* out_mult) {
     if (!a.alive_next[u]) return 0;
+    const uint8_t role = a.role[u];
+    if (role == 0) {  // no neighbour dies and none is added: the row as it is
+        const int64_t b = a.ptr[u], len = a.ptr[u + 1] - b;
+        if (out_nbr)
+            for (int64_t k = 0; k < len; ++k) {
+                out_nbr[k] = a.nbr[b + k];
+                out_mult[k] = a.mult[b + k];
+            }
+        return len;
+    }
     const Extra x = extra_of(a, u);
     int64_t i = a.ptr[u], ie = a.ptr[u + 1], j = x.from, n = 0;
-    const unsigned long long fu = a.role[u] ? a.factor[u] : 0ull;
+    const unsigned long long fu = (role == 1 || role == 2) ? a.factor[u] : 0ull;
     while (true) {
         while (i < ie && !a.alive_next[a.nbr[i]]) ++i;
         while (j < x.to && (a.nbr[j] == x.skip || node_index(a, a.nbr[j]) != x.keep_index)) ++j;
