@@ -93,12 +93,17 @@ __global__ void __launch_bounds__(THREADS) simp_values(Geom g, const float* __re
     }
 }
 
-// Least key of the valid arcs at each node; resets the per-round marks.
-__global__ void __launch_bounds__(THREADS) simp_min0(SimpArgs a) {
+// Least key of the valid arcs at each node; resets the per-round marks.  A live node the previous
+// round left untouched (role 0: same row, no neighbour died) keeps its key from that round.
+__global__ void __launch_bounds__(THREADS) simp_min0(SimpArgs a, int first) {
     for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < a.n; u += int64_t(gridDim.x) * THREADS) {
         Key k = no_key();
-        if (a.alive[u])
-            for (int64_t e = a.ptr[u]; e < a.ptr[u + 1]; ++e) k = key_min(k, arc_key(a, u, a.nbr[e], a.mult[e]));
+        if (a.alive[u]) {
+            if (!first && a.role[u] == 0)
+                k = a.m0[u];
+            else
+                for (int64_t e = a.ptr[u]; e < a.ptr[u + 1]; ++e) k = key_min(k, arc_key(a, u, a.nbr[e], a.mult[e]));
+        }
         a.m0[u] = k;
         a.owner[u] = NO_NODE;
         a.role[u] = 0;
@@ -372,7 +377,7 @@ msc_status run_simplify(Plan* p, const float* d_field, double threshold, cudaStr
         a.any_valid = &rout->any_valid;
         if ((st = check_cuda(p, cudaMemsetAsync(rout, 0, sizeof(RoundOut), s), "simplify round"))) return st;
         const int grid = grid_cap(p, n, THREADS);
-        simp_min0<<<grid, THREADS, 0, s>>>(a);
+        simp_min0<<<grid, THREADS, 0, s>>>(a, rounds == 0 ? 1 : 0);
         simp_spread<<<grid, THREADS, 0, s>>>(a, a.m0, a.m1);
         simp_spread<<<grid, THREADS, 0, s>>>(a, a.m1, a.m2);
         simp_select<<<grid, THREADS, 0, s>>>(a);
