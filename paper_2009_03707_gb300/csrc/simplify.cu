@@ -124,21 +124,27 @@ __global__ void __launch_bounds__(THREADS) simp_spread(SimpArgs a, const Key* __
 }
 
 // Selection by the upper node: its valid arc whose key is the least within two links of both ends
-// (at most one per node: two valid arcs at one node are within each other's neighbourhood).
+// (at most one per node: two valid arcs at one node are within each other's neighbourhood).  Such an
+// arc's key k satisfies m0[p] <= k = min(m2[p], m2[q]) <= m2[p] <= m0[p], so it is p's own least key
+// and p's least key is the least within two links; only such nodes look at their rows, for that arc.
 __global__ void __launch_bounds__(THREADS) simp_select(SimpArgs a) {
     for (int64_t p = int64_t(blockIdx.x) * THREADS + threadIdx.x; p < a.n; p += int64_t(gridDim.x) * THREADS) {
-        if (!a.alive[p] || a.m0[p].hi == ~0ull) continue;
+        const Key k0 = a.m0[p];
+        if (!a.alive[p] || k0.hi == ~0ull) continue;
+        const Key k2 = a.m2[p];
+        if (k2.hi != k0.hi || k2.lo != k0.lo) continue;
         const int ip = node_index(a, p);
         for (int64_t e = a.ptr[p]; e < a.ptr[p + 1]; ++e) {
             const uint32_t q = a.nbr[e];
             if (node_index(a, q) != ip - 1) continue;
             const Key k = arc_key(a, p, q, a.mult[e]);
-            if (k.hi == ~0ull) continue;
-            const Key z = key_min(a.m2[p], a.m2[q]);
+            if (k.hi != k0.hi || k.lo != k0.lo) continue;
+            const Key z = a.m2[q];
             if (k.hi == z.hi && k.lo == z.lo) {
                 a.sel[p] = q;
                 a.flags[p] = 1;
             }
+            break;  // keys are distinct: no other arc of p has this one
         }
     }
 }
@@ -256,11 +262,27 @@ __global__ void __launch_bounds__(THREADS) simp_count(SimpArgs a, uint32_t* __re
         len[u] = uint32_t(merge_row(a, u, nullptr, nullptr));
 }
 
+// A thread per row -- except that when none of a warp's 32 consecutive nodes changes (each either
+// untouched or already without arcs), their rows are one contiguous block in both CSRs and the warp
+// copies it lane by lane.
 __global__ void __launch_bounds__(THREADS) simp_fill(SimpArgs a, const int64_t* __restrict__ ptr_next,
                                                      uint32_t* __restrict__ nbr_next,
                                                      unsigned long long* __restrict__ mult_next) {
-    for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < a.n; u += int64_t(gridDim.x) * THREADS)
-        merge_row(a, u, nbr_next + ptr_next[u], mult_next + ptr_next[u]);
+    const int lane = threadIdx.x & 31;
+    const int64_t step = int64_t(gridDim.x) * THREADS;
+    for (int64_t base = int64_t(blockIdx.x) * THREADS + (threadIdx.x & ~31); base < a.n; base += step) {
+        const int64_t u = base + lane;
+        const bool same = u >= a.n || (a.alive_next[u] ? a.role[u] == 0 : a.ptr[u + 1] == a.ptr[u]);
+        if (__all_sync(0xFFFFFFFFu, same) && base + 32 <= a.n) {
+            const int64_t b = a.ptr[base], len = a.ptr[base + 32] - b, o = ptr_next[base];
+            for (int64_t k = lane; k < len; k += 32) {
+                nbr_next[o + k] = a.nbr[b + k];
+                mult_next[o + k] = a.mult[b + k];
+            }
+        } else if (u < a.n) {
+            merge_row(a, u, nbr_next + ptr_next[u], mult_next + ptr_next[u]);
+        }
+    }
 }
 
 __global__ void simp_copy_alive(int64_t n, const uint8_t* __restrict__ from, uint8_t* __restrict__ to) {
