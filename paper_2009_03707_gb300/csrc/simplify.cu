@@ -98,17 +98,24 @@ __global__ void __launch_bounds__(THREADS) simp_values(Geom g, const float* __re
 __global__ void __launch_bounds__(THREADS) simp_min0(SimpArgs a, int first) {
     for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < a.n; u += int64_t(gridDim.x) * THREADS) {
         Key k = no_key();
-        if (a.alive[u]) {
-            if (!first && a.role[u] == 0)
-                k = a.m0[u];
-            else
+        const uint8_t role = first ? 1 : a.role[u];
+        const bool keep = a.alive[u] && role == 0;
+        if (keep) {
+            k = a.m0[u];
+        } else {
+            if (a.alive[u])
                 for (int64_t e = a.ptr[u]; e < a.ptr[u + 1]; ++e) k = key_min(k, arc_key(a, u, a.nbr[e], a.mult[e]));
+            a.m0[u] = k;
         }
-        a.m0[u] = k;
-        a.owner[u] = NO_NODE;
-        a.role[u] = 0;
-        a.sel[u] = NO_NODE;
-        a.flags[u] = 0;
+        // the marks of the previous round (everything in the first): only what was set is cleared
+        if (role != 0) {
+            a.owner[u] = NO_NODE;
+            a.role[u] = 0;
+        }
+        if (first || a.sel[u] != NO_NODE) {
+            a.sel[u] = NO_NODE;
+            a.flags[u] = 0;
+        }
         a.alive_next[u] = a.alive[u];
         if (k.hi != ~0ull) atomicOr(a.any_valid, 1u);
     }
