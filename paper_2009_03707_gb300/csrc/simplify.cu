@@ -121,9 +121,12 @@ __global__ void __launch_bounds__(THREADS) simp_min0(SimpArgs a, int first) {
     }
 }
 
-// Least over the closed neighbourhood: out[u] = min(in[u], in[v] for v in row(u)).
-__global__ void __launch_bounds__(THREADS) simp_spread(SimpArgs a, const Key* __restrict__ in, Key* __restrict__ out) {
+// Least over the closed neighbourhood: out[u] = min(in[u], in[v] for v in row(u)).  With only_valid,
+// just at the nodes that have a valid arc (selection reads the second spread only there).
+__global__ void __launch_bounds__(THREADS) simp_spread(SimpArgs a, const Key* __restrict__ in, Key* __restrict__ out,
+                                                       int only_valid) {
     for (int64_t u = int64_t(blockIdx.x) * THREADS + threadIdx.x; u < a.n; u += int64_t(gridDim.x) * THREADS) {
+        if (only_valid && a.m0[u].hi == ~0ull) continue;
         Key k = in[u];
         for (int64_t e = a.ptr[u]; e < a.ptr[u + 1]; ++e) k = key_min(k, in[a.nbr[e]]);
         out[u] = k;
@@ -407,8 +410,8 @@ msc_status run_simplify(Plan* p, const float* d_field, double threshold, cudaStr
         if ((st = check_cuda(p, cudaMemsetAsync(rout, 0, sizeof(RoundOut), s), "simplify round"))) return st;
         const int grid = grid_cap(p, n, THREADS);
         simp_min0<<<grid, THREADS, 0, s>>>(a, rounds == 0 ? 1 : 0);
-        simp_spread<<<grid, THREADS, 0, s>>>(a, a.m0, a.m1);
-        simp_spread<<<grid, THREADS, 0, s>>>(a, a.m1, a.m2);
+        simp_spread<<<grid, THREADS, 0, s>>>(a, a.m0, a.m1, 0);
+        simp_spread<<<grid, THREADS, 0, s>>>(a, a.m1, a.m2, 1);
         simp_select<<<grid, THREADS, 0, s>>>(a);
         launched(p, 4);
         // log positions of the selected upper nodes (node order), then the footprints
