@@ -60,11 +60,12 @@ def test_geometry_of_replayed_passes_follows_the_field():
 
 
 @pytest.mark.slow
-def test_grf256_sampled_arcs_are_v_paths():
-    """The bench workload after three passes (the replayed graph): sampled arcs checked cell by cell
+@pytest.mark.parametrize("name", ["grf256", "blobs512"])
+def test_full_size_sampled_arcs_are_v_paths(name):
+    """The bench workloads after three passes (the replayed graph): sampled arcs checked cell by cell
     against the oracle's lazily computed pairs, ending at the pass's arc end points."""
     m = msc()
-    f = fields.config_field("grf256")
+    f = fields.config_field(name)
     plan = m.Plan(dims_of(f))
     d = gpu_field(f)
     for _ in range(3):

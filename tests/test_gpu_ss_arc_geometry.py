@@ -72,11 +72,14 @@ def test_ss_geometry_of_replayed_passes_follows_the_field():
 
 
 @pytest.mark.slow
-def test_grf256_sampled_ss_arcs_are_single_v_paths():
-    """The bench workload after three passes (the replayed graph, row-wise products): sampled arcs
-    of count 1 checked step by step against the oracle's lazily computed pairs."""
+@pytest.mark.parametrize("name", ["grf256", "blobs512"])
+def test_full_size_sampled_ss_arcs_are_single_v_paths(name):
+    """The bench workloads after three passes (the replayed graph: row-wise products on the GRF, whose
+    J comes from a second run of the junction waves; the junction waves on the blob field, with paths
+    hundreds of cells long): sampled arcs of count 1 checked step by step against the oracle's lazily
+    computed pairs."""
     m = msc()
-    f = fields.config_field("grf256")
+    f = fields.config_field(name)
     d = dims_of(f)
     plan = m.Plan(d)
     dev = gpu_field(f)
