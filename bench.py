@@ -12,7 +12,9 @@ the steps in turn so that copies overlap compute.  That pass is timed three time
 is reported (the host copies share the machine's host memory with other jobs).
 
 The default run adds the metric's other workloads to the same JSON line ("legs"), each with
-the clocks sampled while it ran: the 512^3 blob field (the largest single volume); the
+the clocks sampled while it ran: the 256^3 pass's on-request outputs (D* by 2-saddle, the host
+1-skeleton, the cells along both kinds of arcs) and its simplification at 5 % of the field's
+range; the 512^3 blob field (the largest single volume); the
 64-volume uneven batch as one submission against the same volumes one msc_compute at a time;
 and the serving trace (the first 200 requests of the Poisson stream) through the
 continuous-batching runtime against the same trace served one request at a time.
@@ -496,6 +498,8 @@ def run_gpu(args):
         # request at a time
         legs = {}
         want = set(args.legs.split(","))
+        if "outputs" in want:
+            legs["outputs"] = leg_outputs(msc, torch, plan, d_field, uuid)
         if "simplify" in want:
             legs["simplify"] = leg_simplify(msc, torch, plan, d_field, f, uuid)
         del lanes, plan, d_field
@@ -549,6 +553,45 @@ def leg_simplify(msc, torch, plan, d_field, f, uuid, frac=0.05, reps=3):
             "arcs_after": int(res["adj"].numel() // 2),
             "how": "msc_simplify on the 256^3 pass's complex (rounds of independent least-key cancellations)",
             "clocks": clk.summary()}
+
+
+def leg_outputs(msc, torch, plan, d_field, uuid, reps=3):
+    """The on-request outputs of the 256^3 pass, each built on its first call after a pass and timed by
+    CUDA events around that call (every call synchronises): D* by 2-saddle (CSC), the 1-skeleton's
+    adjacency (built on the device; the size query, so no host copy), the cells along the
+    saddle-extremum arcs, and the cells along the
+    saddle-saddle arcs of count 1 (after a row-wise pass this runs the junction waves once more for
+    the rows of J).  A fresh pass (untimed) before each rep; median of reps."""
+    calls = {"dstar_csc": lambda: msc.msc_saddle_arcs_csc(plan),
+             "complex_graph": lambda: msc.msc_complex_graph_size(plan),
+             "arc_geometry": lambda: msc.msc_arc_geometry(plan),
+             "saddle_arc_geometry": lambda: msc.msc_saddle_arc_geometry(plan)}
+    times = {k: [] for k in calls}
+    got = {}
+    with ClockSampler(uuid) as clk:
+        for _ in range(reps):
+            msc.msc_compute(plan, d_field)
+            torch.cuda.synchronize()
+            stream = torch.cuda.current_stream()
+            for k, fn in calls.items():
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                got[k] = fn()
+                e1.record(stream)
+                e1.synchronize()
+                times[k].append(e0.elapsed_time(e1))
+    cnt = got["saddle_arc_geometry"]
+    _, dstar_col, dstar_cnt = msc.msc_saddle_arcs(plan)
+    sizes = {"dstar_csc": {"nnz": int(got["dstar_csc"][1].numel())},
+             "complex_graph": {"nodes": got["complex_graph"][0], "adjacency": got["complex_graph"][1]},
+             "arc_geometry": {"arcs": int(got["arc_geometry"][0].numel() - 1), "cells": int(got["arc_geometry"][1].numel())},
+             "saddle_arc_geometry": {"entries": int(cnt[0].numel() - 1), "count_one": int((dstar_cnt == 1).sum()),
+                                     "cells": int(cnt[1].numel())}}
+    out = {k: dict(ms=statistics.median(v), **sizes[k]) for k, v in times.items()}
+    out["how"] = ("each call's first build after a fresh 256^3 pass, CUDA events around the call, median of "
+                  f"{reps}; the 1-skeleton as msc_complex_graph's size query (built on the device, not copied)")
+    out["clocks"] = clk.summary()
+    return out
 
 
 def leg_single(msc, torch, name, steps, warmup, uuid):
@@ -773,7 +816,7 @@ def main():
     ap.add_argument("--serve-budget", type=int, default=24 << 30, help="serving: HBM admission budget in bytes")
     ap.add_argument("--no-legs", action="store_true",
                     help="grf256: skip the legs that the default run adds")
-    ap.add_argument("--legs", default="simplify,blobs512,batch64,serve",
+    ap.add_argument("--legs", default="outputs,simplify,blobs512,batch64,serve",
                     help="grf256: the legs to add (comma-separated subset of the default)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run every pass synchronised between stages instead of replaying its CUDA graph "

@@ -304,13 +304,21 @@ def msc_complex_graph(plan: Plan):
     n_nodes, n_adj = ctypes.c_int64(), ctypes.c_int64(0)
     _check(lib.msc_complex_graph(plan.handle, _stream(), ctypes.byref(n_nodes), ctypes.byref(n_adj), None, None, None),
            plan.handle)
-    nodeptr = np.zeros(n_nodes.value + 1, dtype=np.int64)
-    adj = np.zeros(max(n_adj.value, 1), dtype=np.uint32)
-    mult = np.zeros(max(n_adj.value, 1), dtype=np.uint64)
+    nodeptr = np.empty(n_nodes.value + 1, dtype=np.int64)  # every entry is written by the copy
+    adj = np.empty(max(n_adj.value, 1), dtype=np.uint32)
+    mult = np.empty(max(n_adj.value, 1), dtype=np.uint64)
     _check(lib.msc_complex_graph(plan.handle, _stream(), ctypes.byref(n_nodes), ctypes.byref(n_adj),
                                  nodeptr.ctypes.data_as(ctypes.c_void_p), adj.ctypes.data_as(ctypes.c_void_p),
                                  mult.ctypes.data_as(ctypes.c_void_p)), plan.handle)
     return nodeptr, adj[:n_adj.value], mult[:n_adj.value]
+
+
+def msc_complex_graph_size(plan: Plan):
+    """Builds the 1-skeleton on the device if needed and returns (n_nodes, n_adj), copying nothing."""
+    n_nodes, n_adj = ctypes.c_int64(), ctypes.c_int64(0)
+    _check(lib.msc_complex_graph(plan.handle, _stream(), ctypes.byref(n_nodes), ctypes.byref(n_adj), None, None, None),
+           plan.handle)
+    return int(n_nodes.value), int(n_adj.value)
 
 
 def msc_compute(plan: Plan, field: torch.Tensor) -> None:
