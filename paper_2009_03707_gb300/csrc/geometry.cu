@@ -139,6 +139,7 @@ struct SsArgs {
     const uint32_t* j_len;
     const uint32_t* j_col;  // pool columns (2-saddle ranks), ascending within a row
     const int64_t* rowptr;  // D* CSR over 1-saddle ranks
+    const uint32_t* erow;   // the row of every D* entry
     const uint32_t* col;
     const unsigned long long* cnt;
     int64_t n1, nnz;
@@ -248,21 +249,17 @@ __device__ bool walk_ss(const SsArgs& a, int64_t row, uint32_t t, Emit& emit) {
     }
 }
 
-// The D* row of entry k (rowptr is ascending).
-__device__ __forceinline__ int64_t row_of_entry(const SsArgs& a, int64_t k) {
-    int64_t lo = 0, hi = a.n1;  // the last row whose start is <= k
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a.rowptr[mid] <= k) lo = mid;
-        else hi = mid;
-    }
-    return lo;
+// The row of every D* entry, a thread per row.
+__global__ void __launch_bounds__(THREADS) ss_entry_rows(const int64_t* __restrict__ rowptr, int64_t n1,
+                                                         uint32_t* __restrict__ erow) {
+    for (int64_t r = int64_t(blockIdx.x) * THREADS + threadIdx.x; r < n1; r += int64_t(gridDim.x) * THREADS)
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) erow[k] = uint32_t(r);
 }
 
 __global__ void __launch_bounds__(THREADS) ss_lengths(SsArgs a, uint32_t* __restrict__ len) {
     for (int64_t k = int64_t(blockIdx.x) * THREADS + threadIdx.x; k < a.nnz; k += int64_t(gridDim.x) * THREADS) {
         Emit e{nullptr, 0};
-        if (a.cnt[k] == 1 && !walk_ss(a, row_of_entry(a, k), a.col[k], e)) atomicOr(a.status, ST_INTERNAL);
+        if (a.cnt[k] == 1 && !walk_ss(a, a.erow[k], a.col[k], e)) atomicOr(a.status, ST_INTERNAL);
         len[k] = a.cnt[k] == 1 ? e.n : 0u;
     }
 }
@@ -272,7 +269,7 @@ __global__ void __launch_bounds__(THREADS) ss_cells(SsArgs a, const int64_t* __r
     for (int64_t k = int64_t(blockIdx.x) * THREADS + threadIdx.x; k < a.nnz; k += int64_t(gridDim.x) * THREADS) {
         if (a.cnt[k] != 1) continue;
         Emit e{cells + off[k], 0};
-        if (!walk_ss(a, row_of_entry(a, k), a.col[k], e)) atomicOr(a.status, ST_INTERNAL);
+        if (!walk_ss(a, a.erow[k], a.col[k], e)) atomicOr(a.status, ST_INTERNAL);
     }
 }
 
@@ -324,6 +321,7 @@ msc_status build_ss_geometry(Plan* p, cudaStream_t s) {
     if ((st = ensure(p, p->ss_len, sizeof(uint32_t) * size_t(nnz + 1)))) return st;
     if ((st = ensure(p, p->ss_off, sizeof(int64_t) * size_t(nnz + 1)))) return st;
     if ((st = ensure(p, p->ss_scan, row_scan_scratch_bytes(nnz)))) return st;
+    if ((st = ensure(p, p->ss_row, sizeof(uint32_t) * size_t(nnz + 1)))) return st;
     SsArgs a{};
     a.g = p->g;
     a.words = static_cast<const uint32_t*>(p->words.ptr);
@@ -336,6 +334,7 @@ msc_status build_ss_geometry(Plan* p, cudaStream_t s) {
     a.j_len = static_cast<const uint32_t*>(p->dp_j_len.ptr);
     a.j_col = static_cast<const uint32_t*>(p->dp_pool_col.ptr);
     a.rowptr = static_cast<const int64_t*>(p->dstar_rowptr.ptr);
+    a.erow = static_cast<const uint32_t*>(p->ss_row.ptr);
     a.col = static_cast<const uint32_t*>(p->dstar_col.ptr);
     a.cnt = static_cast<const unsigned long long*>(p->dstar_count.ptr);
     a.n1 = p->counts[1];
@@ -344,8 +343,9 @@ msc_status build_ss_geometry(Plan* p, cudaStream_t s) {
     auto* len = static_cast<uint32_t*>(p->ss_len.ptr);
     auto* off = static_cast<int64_t*>(p->ss_off.ptr);
     if (nnz) {
+        ss_entry_rows<<<grid_cap(p, a.n1, THREADS), THREADS, 0, s>>>(a.rowptr, a.n1, static_cast<uint32_t*>(p->ss_row.ptr));
         ss_lengths<<<grid_cap(p, nnz, THREADS), THREADS, 0, s>>>(a, len);
-        launched(p);
+        launched(p, 2);
     }
     if ((st = check_cuda(p, row_scan(p, len, nullptr, nnz, off, static_cast<unsigned long long*>(p->ss_scan.ptr), s),
                          "saddle-saddle geometry scan")))

@@ -96,7 +96,7 @@ struct Plan {
     DeviceBuffer csc_colptr, csc_row, csc_count, csc_work;  // D* by 2-saddle (transpose.cu)
     DeviceBuffer graph_nodeptr, graph_adj, graph_mult, graph_work, graph_none;  // the 1-skeleton (graph.cu)
     DeviceBuffer geo_len, geo_off, geo_scan, geo_cells;  // cells along the saddle-extremum arcs (geometry.cu)
-    DeviceBuffer ss_len, ss_off, ss_scan, ss_cells;      // cells along the saddle-saddle arcs of count 1 (geometry.cu)
+    DeviceBuffer ss_len, ss_off, ss_scan, ss_cells, ss_row;  // cells along the saddle-saddle arcs of count 1 (geometry.cu)
     // simplification (simplify.cu): node cells, values, alive (two copies), keys, per-node scratch,
     // row lengths, log positions, scan scratch, two CSRs, the log, the per-round host read-out
     DeviceBuffer simp_cell, simp_value, simp_alive, simp_keys, simp_node, simp_len, simp_pos, simp_scan;
@@ -115,7 +115,7 @@ struct Plan {
                                &dstar_count, &dp_pend, &dp_in_cnt, &dp_in_ptr, &dp_in_idx, &dp_j_off,
                                &dp_j_len, &dp_pool_col, &dp_pool_cnt, &dp_long, &dp_chunks, &csc_colptr, &csc_row, &csc_count, &csc_work,
                                &graph_nodeptr, &graph_adj, &graph_mult, &graph_work, &graph_none,
-                               &geo_len, &geo_off, &geo_scan, &geo_cells, &ss_len, &ss_off, &ss_scan, &ss_cells,
+                               &geo_len, &geo_off, &geo_scan, &geo_cells, &ss_len, &ss_off, &ss_scan, &ss_cells, &ss_row,
                                &simp_cell, &simp_value,
                                &simp_alive, &simp_keys, &simp_node, &simp_len, &simp_pos, &simp_scan,
                                &simp_ptr[0], &simp_ptr[1], &simp_nbr[0], &simp_nbr[1], &simp_mult[0],
