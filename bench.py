@@ -8,7 +8,7 @@ flushed (a 256 MB write) before every timed step.  A second pass times the same 
 end to end from pinned host memory: the field goes up every step, and every output of the
 pass (critical lists, both arc arrays, both label arrays, D* CSR) comes back through
 msc_copy_to_host into caller-owned pinned buffers, with three plans on three streams taking
-the steps in turn so that copies overlap compute.  That pass is timed three times and the median
+the steps in turn so that copies overlap compute.  That pass is timed five times and the median
 is reported (the host copies share the machine's host memory with other jobs).
 
 The default run adds the metric's other workloads to the same JSON line ("legs"), each with
@@ -65,7 +65,7 @@ def _peaks():
 
 
 E2E_LANES = 3  # plans in flight in the end-to-end leg
-E2E_REPEATS = 3  # timed runs of the end-to-end leg (the median is reported)
+E2E_REPEATS = 5  # timed runs of the end-to-end leg (the median is reported)
 # every output of a pass, copied to the host by the end-to-end leg (msc_copy_to_host selectors)
 E2E_OUTPUTS = ("cells0", "cells1", "cells2", "cells3", "min_arcs", "max_arcs", "vertex_min", "cube_max",
                "dstar_rowptr", "dstar_col", "dstar_count")
