@@ -54,9 +54,10 @@ __device__ __forceinline__ uint32_t order_key(float f) {
 template <int TY, int TZ, int THREADS>
 struct Shared {
     static constexpr int FX = TX + 2, FY = TY + 2, FZ = TZ + 2;  // field keys staged (x0-1 .. x0+TX)
+    static constexpr int FXP = TX + 4;                            // their row pitch: 16-byte rows
     static constexpr int NOWN = TX * TY * TZ;
     static constexpr int WX = TX + 1, WY = TY + 1, WZ = TZ + 1;  // words kept (x0-1 .. x0+TX-1)
-    uint32_t fkey[FZ][FY][FX];   // order keys of the field tile (OUTSIDE_KEY off-grid)
+    uint32_t fkey[FZ][FY][FXP];  // order keys of the field tile (OUTSIDE_KEY off-grid); columns >= FX unused
     uint32_t words[WZ][WY][WX];  // packed codes of the owned tile and its - layer
     uint32_t inl[NOWN];          // lower-star mask of every owned vertex (0: off-grid)
     uint16_t order[NOWN];        // non-minimal vertices, largest stars first
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
                                                            uint32_t* __restrict__ words_out,
                                                            uint32_t* __restrict__ status) {
     using S = Shared<TY, TZ, THREADS>;
-    constexpr int FX = S::FX, FY = S::FY, FZ = S::FZ, NOWN = S::NOWN;
+    constexpr int FX = S::FX, FXP = S::FXP, FY = S::FY, FZ = S::FZ, NOWN = S::NOWN;
     constexpr int WX = S::WX, WY = S::WY, WZ = S::WZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S& sh = *reinterpret_cast<S*>(smem_raw);
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
     if (t < 28) sh.bin[t] = 0;
     if (t == 0) sh.next = 0;
     if (t < 27) {
-        star::fill_tables(sh.tab, t, FX, FX * FY);
+        star::fill_tables(sh.tab, t, FXP, FXP * FY);
         const uint32_t xn = (star::XN >> t) & 1, yn = (star::YN >> t) & 1, zn = (star::ZN >> t) & 1;
         const uint32_t slot = (pdx(t) != 0) | ((pdy(t) != 0) << 1) | ((pdz(t) != 0) << 2);
         sh.emit_info[t] = (3 * slot) | ((xn + yn * WX + zn * WX * WY) << 8);
@@ -113,25 +114,59 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
         const int gx = x0 - 1 + fx, gy = y0 - 1 + fy, gz = z0 - 1 + fz;
         const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz;
         saw_nan |= in && isnan(v[k]);
-        (&sh.fkey[0][0][0])[i] = in ? order_key(v[k]) : OUTSIDE_KEY;
+        sh.fkey[fz][fy][fx] = in ? order_key(v[k]) : OUTSIDE_KEY;
     }
     if (saw_nan) atomicOr(status, ST_NAN);
     __syncthreads();
 
     // size every star (cheap mask arithmetic) and counting-sort the non-minimal ones by size, one shared
-    // atomic per vertex (a ballot-based warp histogram measured slower)
-    for (int i = t; i < NOWN; i += THREADS) {
-        const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-        uint32_t inL = 0;
-        if (x0 + lx < g.nx && y0 + ly < g.ny && z0 + lz < g.nz) {
-            uint32_t k[27];
-#pragma unroll
-            for (int p = 0; p < 27; ++p) k[p] = sh.fkey[lz + 1 + pdz(p)][ly + 1 + pdy(p)][lx + 1 + pdx(p)];
-            inL = star::lower_star_mask(star::lower_mask(k));
-            const int m = __popc(inL) - 1;
-            if (m > 0) atomicAdd(&sh.bin[m], 1);
+    // atomic per vertex (a ballot-based warp histogram measured slower).  A thread takes four
+    // consecutive vertices of a row: the six keys of each of their nine neighbour rows come in one
+    // 16-byte and one 8-byte shared load.
+    for (int i4 = t; i4 < NOWN / 4; i4 += THREADS) {
+        const int lx0 = (i4 % (TX / 4)) * 4, ly = (i4 / (TX / 4)) % TY, lz = i4 / ((TX / 4) * TY);
+        uint32_t lower[4], kc[4];
+        {
+            const uint32_t* c = &sh.fkey[lz + 1][ly + 1][lx0];
+            const uint4 a = *reinterpret_cast<const uint4*>(c);
+            const uint2 b = *reinterpret_cast<const uint2*>(c + 4);
+            kc[0] = a.y;
+            kc[1] = a.z;
+            kc[2] = a.w;
+            kc[3] = b.x;
         }
-        sh.inl[i] = inL;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) lower[v] = 1u << star::CENTER;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const uint32_t* row = &sh.fkey[lz + 1 + dz][ly + 1 + dy][lx0];
+                const uint4 a = *reinterpret_cast<const uint4*>(row);
+                const uint2 b = *reinterpret_cast<const uint2*>(row + 4);
+                const uint32_t r[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int p = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
+                        if (p == star::CENTER) continue;
+                        const uint32_t kp = r[v + 1 + dx];  // lower: smaller key, or equal and earlier
+                        const bool lo = p < star::CENTER ? kp <= kc[v] : kp < kc[v];
+                        lower[v] |= uint32_t(lo) << p;
+                    }
+            }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int lx = lx0 + v, i = lx + TX * (ly + TY * lz);
+            uint32_t inL = 0;
+            if (x0 + lx < g.nx && y0 + ly < g.ny && z0 + lz < g.nz) {
+                inL = star::lower_star_mask(lower[v]);
+                const int m = __popc(inL) - 1;
+                if (m > 0) atomicAdd(&sh.bin[m], 1);
+            }
+            sh.inl[i] = inL;
+        }
     }
     __syncthreads();
     if (t == 0) {
@@ -172,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) gradient_kern
         };
         // the scratch word of position p of this thread, in its own bank column
         auto ckey = [&](int p) -> uint32_t& { return sh.ckey[p][t]; };
-        ok &= star::pair_lower_star<FX, FX * FY>(inL, st, ckey, emit);
+        ok &= star::pair_lower_star<FXP, FXP * FY>(inL, st, ckey, emit);
         }
     }
     if (!ok) atomicOr(status, ST_INTERNAL);
